@@ -1,0 +1,96 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the benchmark.
+
+This module holds none of the method's arithmetic: it only lays out structured simplex
+meshes, draws per-element material fields, source positions and random states from a
+seed. Both the CUDA library (through ``bench.py`` and the tests) and the CPU oracle
+receive the same arrays from here.
+
+Mesh recipes (the shapes of the paper's workloads, Sec. 2.1 meshes of simplices):
+  * unit square, N x N squares, each cut by the (i, j) -> (i+1, j+1) diagonal: 2 N^2
+    triangles;
+  * unit cube, N^3 cubes, each cut into the 6 Kuhn tetrahedra that share the cube's main
+    diagonal (conforming across cubes): 6 N^3 tetrahedra.
+"""
+import itertools
+
+import numpy as np
+
+DEFAULT_SEED = 1807
+
+
+def unit_square_tri(N):
+    """Returns (vert[(N+1)^2, 2], elem[2 N^2, 3]); vertex id = i + (N+1) j."""
+    g = np.linspace(0.0, 1.0, N + 1)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    vert = np.stack([X.ravel(), Y.ravel()], axis=1)
+    vid = lambda i, j: i + (N + 1) * j
+    elem = []
+    for j in range(N):
+        for i in range(N):
+            v00, v10, v01, v11 = vid(i, j), vid(i + 1, j), vid(i, j + 1), vid(i + 1, j + 1)
+            elem.append((v00, v10, v11))
+            elem.append((v00, v11, v01))
+    return vert, np.array(elem, dtype=np.int32)
+
+
+def unit_cube_tet(N):
+    """Returns (vert[(N+1)^3, 3], elem[6 N^3, 4]); vertex id = i + (N+1)(j + (N+1) l)."""
+    g = np.linspace(0.0, 1.0, N + 1)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    vert = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    n1 = N + 1
+    I, J, L = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    base = np.stack([I.ravel(), J.ravel(), L.ravel()], axis=1)   # cube corner (i, j, l)
+    # order cubes by l, then j, then i (i fastest)
+    order = np.lexsort((base[:, 0], base[:, 1], base[:, 2]))
+    base = base[order]
+    elems = []
+    for perm in itertools.permutations(range(3)):
+        c = base.copy()
+        path = [c.copy()]
+        for ax in perm:
+            c = c.copy()
+            c[:, ax] += 1
+            path.append(c)
+        ids = [p[:, 0] + n1 * (p[:, 1] + n1 * p[:, 2]) for p in path]
+        elems.append(np.stack(ids, axis=1))
+    elem = np.stack(elems, axis=1).reshape(-1, 4)   # 6 consecutive tets per cube
+    return vert, elem.astype(np.int32)
+
+
+def loguniform(n, lo, hi, seed=DEFAULT_SEED):
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n))
+
+
+def lognormal(n, median, sigma, seed=DEFAULT_SEED):
+    rng = np.random.default_rng(seed)
+    return median * np.exp(sigma * rng.standard_normal(n))
+
+
+def uniform_points(n, dim, lo=0.1, hi=0.9, seed=DEFAULT_SEED):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(n, dim))
+
+
+def random_state(n_elem, n_local, seed=DEFAULT_SEED):
+    """Seeded random element coefficients [n_elem, n_local] (for parity tests)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n_elem, n_local))
+
+
+def random_traces(n_faces, n_face_dofs, seed=DEFAULT_SEED):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n_faces, n_face_dofs))
+
+
+def acoustic_3d_workload(N=32, k=3, seed=DEFAULT_SEED):
+    """3D acoustic wave workload: unit cube, 6 N^3 tets, c ~ logU[1, 3] per element, rho = 1,
+    one Ricker point source at the cube centre shifted by 0.3 h (1, 1, 1) (no vertex/face tie)."""
+    vert, elem = unit_cube_tet(N)
+    ne = elem.shape[0]
+    c = loguniform(ne, 1.0, 3.0, seed)
+    rho = np.ones(ne)
+    h = 1.0 / N
+    src = np.array([[0.5 + 0.3 * h, 0.5 + 0.3 * h, 0.5 + 0.3 * h]])
+    return dict(vert=vert, elem=elem, k=k, rho=rho, c=c, tau=1.0, sources=src, f0=10.0, t0=1.2 / 10.0)
