@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark: HDG DOF-steps/s of the implicit acoustic wave solver on GB300.
+
+Workload (one step = one implicit BDF2 step through the whole hot path: element
+right-hand sides, condensed right-hand side, Krylov trace solve with the matrix-free
+S_K apply, local recovery): 3D acoustic wave on the unit cube, structured mesh of
+32^3 cubes x 6 = 196,608 tetrahedra, degree k = 3 (80 field DOFs per element), tau = 1,
+c ~ logU[1, 3] per element (seeded), rho = 1, BDF2 dt = 2e-3, Ricker point source
+f0 = 10. Inputs are seeded and synthetic; the per-element operators (S_K: 2.5 GB FP64)
+are far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle on a bounded sample of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (the path does not shard
+across GPUs; no collective on the data path); value = units of all ranks / max time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "HDG DOF-steps/s on 1 GB300, mixed vs FP64 at <=1e-9 rel err; serve p50/p99 ms"
+UNIT = "DOF-steps/s"
+DT = 2e-3
+SAMPLE_N = 4          # oracle sample: 4^3 x 6 = 384 tetrahedra, same k, same recipe
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi during the timed region (SM clock, max clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------- oracle legs
+def oracle_sample(steps=None, budget_s=None, warmup=0):
+    """Times the CPU oracle on the bounded sample: BDF2 steps of the 384-tet workload."""
+    from oracle import acoustic as ac
+    from paper_1807_00086_gb300 import inputs
+    w = inputs.acoustic_3d_workload(N=SAMPLE_N)
+    prob = ac.build_problem(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"])
+    ac.add_point_source(prob, w["sources"][0], w["f0"], w["t0"])
+    ne = w["elem"].shape[0]
+    nloc = 4 * prob.Np
+    u = np.zeros((ne, nloc))
+    cond = ac.condense(prob, 1.5 / DT)
+    hist = [u, u]
+    t = 0.0
+    times = []
+
+    def one_step():
+        nonlocal hist, t
+        t += DT
+        h = (4.0 / 3.0) * hist[1] - (1.0 / 3.0) * hist[0]
+        un, lam = ac.solve_stage(prob, cond, h, t)
+        hist = [hist[1], un]
+
+    for _ in range(warmup):
+        one_step()
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        one_step()
+        times.append(time.perf_counter() - t0)
+        if steps is not None and len(times) >= steps:
+            break
+        if budget_s is not None and time.perf_counter() - t_start >= budget_s:
+            break
+    total = sum(times)
+    dofs = ne * nloc
+    return {"value": dofs * len(times) / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d BDF2 steps of the same workload on a %d^3x6 = %d-tet mesh (k=3, %d field DOFs); "
+                      "oracle = numpy/scipy FP64, per-element LU + sparse direct trace solve" % (len(times), SAMPLE_N,
+                                                                                                ne, dofs),
+            "ms_per_step": 1e3 * total / len(times), "steps": len(times)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    r = oracle_sample(steps=args.steps, warmup=args.warmup)
+    out = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "acoustic3d_k3_32cube_bdf2 (bounded sample: %d^3x6 tets)" % SAMPLE_N},
+           "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+           "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import torch
+    from paper_1807_00086_gb300 import hdg, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = inputs.acoustic_3d_workload(N=args.N, k=args.k)
+    ne = w["elem"].shape[0]
+    s = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=args.prec, rtol=args.rtol)
+    s.hdg_set_sources(w["sources"], [1.0], w["f0"], w["t0"])
+    s.hdg_set_dirichlet(None)
+    s.hdg_set_state(s.empty_fields(), 0.0)
+    dofs = ne * s.n
+    stream = s.stream
+    # warm-up (includes the condensation for alpha = 3/(2 dt))
+    for _ in range(args.warmup):
+        s.hdg_step(DT, "bdf2", 1)
+    torch.cuda.synchronize()
+    s.hdg_enable_stats(True)
+    s.hdg_get_stats(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters = 0
+    for _ in range(args.steps):
+        info = s.hdg_step(DT, "bdf2", 1)
+        iters += info["iterations"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    st = s.hdg_get_stats(reset=True)
+    s.hdg_enable_stats(False)
+    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = world * dofs * args.steps / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers: the state (u^n, u^{n-1}) goes
+    # host -> device, one step, and u^{n+1}, u^n come back device -> host, every step.
+    u_h = torch.empty((ne, s.n), dtype=torch.float64).pin_memory()
+    up_h = torch.empty((ne, s.n), dtype=torch.float64).pin_memory()
+    l_h = torch.empty((s.n_faces, s.Nf), dtype=torch.float64).pin_memory()
+    u_d, up_d, l_d = s.empty_fields(), s.empty_fields(), s.empty_traces()
+    _, _, _, t_now = s.hdg_get_state(u=u_d, uprev=up_d, lam=l_d, want_prev=True)
+    u_h.copy_(u_d)
+    up_h.copy_(up_d)
+    l_h.copy_(l_d)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_steps = max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            u_d.copy_(u_h, non_blocking=True)
+            up_d.copy_(up_h, non_blocking=True)
+            l_d.copy_(l_h, non_blocking=True)
+        s.hdg_set_state(u_d, t_now, uprev=up_d, lam=l_d)
+        s.hdg_step(DT, "bdf2", 1)
+        _, _, _, t_now = s.hdg_get_state(u=u_d, uprev=up_d, lam=l_d, want_prev=True)
+        with torch.cuda.stream(stream):
+            u_h.copy_(u_d, non_blocking=True)
+            up_h.copy_(up_d, non_blocking=True)
+            l_h.copy_(l_d, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t_e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+    e2e_value = world * dofs * e2e_steps / float(t_e.item())
+    field_bytes = ne * s.n * 8
+    trace_bytes = s.n_faces * s.Nf * 8
+
+    # roofline of the dominant kernel (matrix-free trace apply)
+    peaks, src = load_peaks()
+    m = s.m
+    apply_avg_ms = st["apply_ms"] / max(1, st["apply_launches"])
+    if args.prec == "fp64":
+        bytes_el = m * m * 8 + 2 * m * 8
+        flops_el = 2 * m * m
+        ach = flops_el * ne / (apply_avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                "traffic": None, "kernel": "apply_kernel<3,3> (FP64 S_K x lambda_K)",
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (probe measured 1.20)",
+                "hbm_view": {"achieved_gbs": bytes_el * ne / (apply_avg_ms / 1e3) / 1e9,
+                             "peak_gbs": peaks["hbm_gbs"], "peak_source": src},
+                "launch_ms": apply_avg_ms, "launches": st["apply_launches"]}
+    else:
+        bytes_el = m * m * 4 + 2 * m * 4
+        ach = bytes_el * ne / (apply_avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "apply kernel (FP32 S_K)",
+                "peak_source": src, "launch_ms": apply_avg_ms, "launches": st["apply_launches"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(budget_s=args.cpu_budget)
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32+f64",
+               "data": "synthetic",
+               "config": {"workload": "acoustic3d_k3_32cube_bdf2", "n_elem": ne, "k": args.k, "dofs": dofs,
+                          "trace_dofs": int(s.n_faces - s.n_bnd) * s.Nf, "dt": DT, "scheme": "BDF2",
+                          "precision": args.prec, "rtol": args.rtol, "parallelism": "replicas",
+                          "l2": "inputs larger than L2 (S_K %.2f GB)" % (ne * m * m * 8 / 1e9),
+                          "krylov_iters_per_step": iters / args.steps},
+               "roofline": roof, "cpu_baseline": cpu,
+               "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * field_bytes + trace_bytes,
+                       "d2h_bytes_per_step": 2 * field_bytes + trace_bytes, "steps": e2e_steps},
+               "gpu_launches": st["kernel_launches"], "clocks": clk}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--rtol", type=float, default=1e-12)
+    ap.add_argument("--N", type=int, default=32)
+    ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

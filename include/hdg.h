@@ -1,0 +1,187 @@
+/* hdg.h - C ABI of the GB300 HDG static-condensation library (libhdg.so).
+ *
+ * The library implements the data-parallel hot path of the hybridized DG method of
+ * Fernandez, Christophe, Terrana, Nguyen and Peraire, "Hybridized discontinuous Galerkin
+ * methods for wave propagation" (arXiv 1807.00086), for first-order acoustics
+ * (1/(rho c^2)) p_t + div v = s, rho v_t + grad p = 0 on affine triangles (d = 2) and
+ * tetrahedra (d = 3):
+ *
+ *   Sec. 2.2 (Eqs. e:spaces1, e:spaces2)  discontinuous P_k fields, P_k face traces (HDG);
+ *   Sec. 2.3 (Eqs. ch5appendx1:eq8-eq10)  the semi-discrete DAE, BDF steps and DIRK stages;
+ *   Sec. 2.4 (Eq. LS)                      static condensation K = D - C A^{-1} B,
+ *                                          r = g - C A^{-1} h, element-local recovery.
+ *
+ * Conventions (fixed here; every array below follows them):
+ *   - element vertices are used in ascending global id; local face j is opposite local
+ *     vertex j; a face is parametrised from its vertices in ascending global id;
+ *   - faces are numbered 0..n_faces-1 in lexicographic order of their sorted vertex ids;
+ *   - element fields: [n_elem][d+1][Np] FP64, components (p, v_1, .., v_d), coefficients
+ *     in the orthonormal Dubiner basis of the unit reference simplex (mass = |det J| I);
+ *   - face traces: [n_faces][Nf] FP64 in the orthonormal basis of the reference face
+ *     (face mass = J_F I, J_F = edge length (d = 2) or twice the face area (d = 3));
+ *   - Np = C(k+d, d), Nf = C(k+d-1, d-1), n = (d+1) Np, m = (d+1) Nf;
+ *   - boundary faces carry Dirichlet data for p_hat; only interior faces are unknowns.
+ *
+ * Memory: pointers named *_dev are device pointers owned by the caller, used on the
+ * context's stream and borrowed for the duration of the call (the call returns after
+ * the work is enqueued or, where stated, completed). Pointers named *_host are host
+ * memory, borrowed for the call. The context owns every other buffer.
+ *
+ * Errors: every call returns an hdg_status; on failure hdg_last_error(ctx) gives a
+ * message owned by ctx (valid until the next call on ctx). Nothing is printed, nothing
+ * exits, and no kernel traps: device-side failures surface as status codes.
+ */
+#ifndef HDG_H
+#define HDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdg_ctx hdg_ctx;
+
+typedef enum {
+  HDG_OK = 0,
+  HDG_EINVAL = -1,   /* bad argument or mesh                                   */
+  HDG_ENOMEM = -2,   /* device allocation failed                               */
+  HDG_ECUDA = -3,    /* a CUDA runtime call failed                             */
+  HDG_ENOCONV = -4,  /* Krylov solve hit maxit before rtol                     */
+  HDG_ETIMEOUT = -5, /* a device wait gave up (reserved)                       */
+  HDG_ESTATE = -6    /* call out of order (e.g. solve before condense)         */
+} hdg_status;
+
+typedef enum { HDG_BE = 1, HDG_BDF2 = 2, HDG_DIRK3 = 3 } hdg_scheme;
+typedef enum { HDG_FP64 = 0, HDG_MIXED = 1 } hdg_precision;
+
+typedef struct {
+  int32_t dim;              /* 2 or 3                                                */
+  int64_t n_vert, n_elem;
+  const double* vert;       /* _host [n_vert][dim]                                   */
+  const int32_t* elem_vert; /* _host [n_elem][dim+1], any vertex order               */
+} hdg_mesh;
+
+typedef struct {
+  const double* rho;        /* _host [n_elem] density, > 0                           */
+  const double* c;          /* _host [n_elem] sound speed, > 0                       */
+} hdg_material;
+
+typedef struct {
+  hdg_precision prec;       /* HDG_FP64: everything FP64. HDG_MIXED: FP32 S_K and     */
+                            /* FP32 Krylov apply inside FP64 iterative refinement     */
+  double rtol;              /* relative residual target of the trace solve (FP64)     */
+  int32_t maxit;            /* Krylov iteration cap per solve                         */
+  int32_t check_every;      /* host polls the device convergence flag this often      */
+} hdg_options;
+
+typedef struct {
+  int32_t dim, k, Np, Nf, n_local, n_trace_local;  /* n_local = n, n_trace_local = m */
+  int64_t n_elem, n_faces, n_bnd_faces;
+  int32_t nq_vol, nq_face;  /* projection quadrature points per element / face       */
+  int64_t device_bytes;     /* device memory held by the context                     */
+} hdg_sizes;
+
+typedef struct {
+  int32_t iterations;       /* Krylov iterations of the last solve (sum over sweeps)  */
+  int32_t sweeps;           /* refinement sweeps (mixed precision), else 1            */
+  double rel_residual;      /* final ||r|| / ||b|| of the trace system (FP64)         */
+} hdg_solve_info;
+
+/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16. */
+void hdg_default_options(hdg_options* opt);
+
+/* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face
+ * table and affine geometry on the host, uploads them and the reference tables of
+ * degree k (1 <= k <= 4), and binds the context to `cuda_stream` (a cudaStream_t, may
+ * be NULL for the legacy stream). tau > 0 is the stabilisation of the numerical flux
+ * v_hat.n = v.n + tau (p - p_hat). Returns HDG_EINVAL for a degenerate element, a face
+ * shared by more than two elements, or sizes out of range. */
+hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_material* mat,
+                     const hdg_options* opt, void* cuda_stream, hdg_ctx** out);
+void hdg_destroy(hdg_ctx* ctx);
+const char* hdg_last_error(const hdg_ctx* ctx);
+hdg_status hdg_get_sizes(const hdg_ctx* ctx, hdg_sizes* out);
+
+/* Sec. 2.4, Eq. LS: forms, for the mass shift alpha > 0 (A_K = alpha M_K + df/du), the
+ * factor of each A_K and the Schur block S_K = D_K - C_K A_K^{-1} B_K of every element,
+ * and the Jacobi preconditioner of the trace system. Enqueued on the context stream. */
+hdg_status hdg_condense(hdg_ctx* ctx, double alpha);
+
+/* Copies S_K of the last hdg_condense into S_dev [n_elem][m][m] (row-major). */
+hdg_status hdg_get_schur(hdg_ctx* ctx, double* S_dev);
+
+/* Matrix-free trace apply (Sec. 2.4): y = K x = sum_K P_K^T S_K P_K x on interior faces.
+ * x_dev, y_dev: [n_faces][Nf]; boundary entries of x are ignored (treated as zero) and
+ * boundary entries of y are set to zero. */
+hdg_status hdg_trace_apply(hdg_ctx* ctx, const double* x_dev, double* y_dev);
+
+/* Condensed right-hand side (Eq. LS): r = -sum_K P_K^T C_K A_K^{-1} (F_K - B_K lamD_K)
+ * on interior faces (zero on boundary faces). F_dev: element right-hand sides
+ * [n_elem][n] of A_K u_K + B_K lam_K = F_K; lamD_dev: [n_faces][Nf] whose boundary
+ * entries hold the Dirichlet trace (may be NULL for zero data); r_dev: [n_faces][Nf]. */
+hdg_status hdg_condensed_rhs(hdg_ctx* ctx, const double* F_dev, const double* lamD_dev, double* r_dev);
+
+/* Krylov solve of K lam = r on interior faces (preconditioned CG on -K, which is SPD).
+ * r_dev, lam_dev: [n_faces][Nf]; lam_dev on entry is the initial guess (interior
+ * entries), on exit the solution; its boundary entries are left unchanged. Completes
+ * before returning; fills info (may be NULL). HDG_ENOCONV if maxit was reached. */
+hdg_status hdg_trace_solve(hdg_ctx* ctx, const double* r_dev, double* lam_dev, hdg_solve_info* info);
+
+/* Local recovery: u_K = A_K^{-1} (F_K - B_K lam_K) for every element, lam_dev over all
+ * faces (boundary entries = Dirichlet trace). F_dev, u_dev: [n_elem][n]. */
+hdg_status hdg_recover(hdg_ctx* ctx, const double* F_dev, const double* lam_dev, double* u_dev);
+
+/* Data of the time-dependent problem. Point sources (pressure equation, Ricker wavelet
+ * r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), amplitude amp_host[i]) at
+ * positions pos_host [nsrc][dim]; each is attached to the lowest-id element containing
+ * it. nsrc = 0 removes all sources. */
+hdg_status hdg_set_sources(hdg_ctx* ctx, int32_t nsrc, const double* pos_host, const double* amp_host,
+                           double f0, double t0);
+
+/* Physical coordinates of the projection quadrature points: which = 0 volume
+ * ([n_elem][nq_vol][dim]), which = 1 boundary faces in face order ([n_bnd][nq_face][dim]). */
+hdg_status hdg_quadrature_points(hdg_ctx* ctx, int32_t which, double* xyz_host);
+
+/* Element-wise L2 projection of point values vals_host [n_elem][nq_vol][d+1] (p, v) at
+ * the volume quadrature points into u_dev [n_elem][n]. */
+hdg_status hdg_project_volume(hdg_ctx* ctx, const double* vals_host, double* u_dev);
+
+/* Dirichlet trace p_hat = g(x) cos(omega t + phase) on all boundary faces; vals_host
+ * [n_bnd][nq_face] holds g at the boundary quadrature points (NULL: zero data). */
+hdg_status hdg_set_dirichlet(hdg_ctx* ctx, const double* vals_host, double omega, double phase);
+
+/* Time state (checkpoint/resume). hdg_set_state sets the fields u at time t (u_dev
+ * [n_elem][n]), the previous level used by BDF2 (uprev_dev, same layout; NULL: equal
+ * to u, i.e. a start from rest or a steady state) and the traces (lam_dev
+ * [n_faces][Nf]; NULL: zero), which the next trace solve takes as its initial guess.
+ * hdg_get_state copies the current
+ * fields, the previous level and the traces (lam_dev [n_faces][Nf], boundary entries =
+ * Dirichlet values); any output pointer may be NULL. Both complete before returning. */
+hdg_status hdg_set_state(hdg_ctx* ctx, const double* u_dev, const double* uprev_dev, const double* lam_dev,
+                         double t);
+hdg_status hdg_get_state(hdg_ctx* ctx, double* u_dev, double* uprev_dev, double* lam_dev, double* t);
+
+/* Advances nsteps implicit steps of size dt with BE or BDF2 (Eq. ch5appendx1:eq9b) or
+ * Alexander's DIRK(3,3) in the stage form of Eq. ch5appendx1:eq10_1 with the update of
+ * Eq. 10_2. Each step (stage) forms the element right-hand sides, the condensed
+ * right-hand side, solves the trace system and recovers the fields; the operators are
+ * re-condensed when alpha = a_s/(b_s dt) or 1/(gamma dt) changes. Completes before
+ * returning; info (may be NULL) accumulates over the steps. */
+hdg_status hdg_step(hdg_ctx* ctx, double dt, hdg_scheme scheme, int32_t nsteps, hdg_solve_info* info);
+
+/* Instrumentation (not part of the method). When enabled, the context counts its kernel
+ * launches and times every launch of the matrix-free trace apply with CUDA events on the
+ * context stream; hdg_get_stats returns the totals since the last reset. */
+typedef struct {
+  int64_t kernel_launches;  /* all kernels launched by the context                     */
+  int64_t apply_launches;   /* launches of the trace-apply kernel                      */
+  double apply_ms;          /* summed device time of those launches (CUDA events)      */
+} hdg_stats;
+hdg_status hdg_enable_stats(hdg_ctx* ctx, int32_t enable);
+hdg_status hdg_get_stats(hdg_ctx* ctx, hdg_stats* out, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDG_H */

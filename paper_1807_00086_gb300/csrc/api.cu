@@ -1,0 +1,728 @@
+// C ABI of the HDG library: context, memory, dispatch and the time-step driver.
+// The steps follow Sec. 2.3 (BDF, Eq. ch5appendx1:eq9b; DIRK, Eqs. ch5appendx1:eq10_1-2)
+// and Sec. 2.4 (static condensation, Eq. LS) of arXiv 1807.00086.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/hdg.h"
+#include "kernels.cuh"
+#include "mesh.h"
+#include "reftab.h"
+
+using namespace hdg;
+
+struct hdg_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  hdg_options opt{};
+  int dim = 0, k = 0, Np = 0, Nf = 0, n = 0, m = 0, nfc = 0;
+  int sms = 148;
+  double tau = 1.0;
+  Skeleton sk;
+  RefTables T;
+  std::vector<double> h_vert_elem;   // [ne][d+1][d] element vertex coordinates (sorted order)
+  // device: mesh and tables
+  double *d_geo = nullptr, *d_rho = nullptr, *d_c = nullptr, *d_tab = nullptr;
+  int32_t *d_elem_face = nullptr, *d_face_slot = nullptr, *d_face_bnd = nullptr;
+  int64_t* d_bnd_faces = nullptr;
+  Tabs tabs{};
+  double *d_qv_w = nullptr, *d_qv_phi = nullptr;
+  // condensed operators
+  double *d_S = nullptr, *d_Hinv = nullptr, *d_dinv = nullptr;
+  double alpha = 0.0;
+  bool condensed = false;
+  int* d_err = nullptr;
+  // Krylov workspace
+  double *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_b = nullptr, *d_slot = nullptr;
+  double* d_part = nullptr;
+  CgScal* d_sc = nullptr;
+  CgScal* h_sc = nullptr;   // pinned
+  int nb_red = 0;
+  // time state
+  double *d_u = nullptr, *d_uprev = nullptr, *d_lam = nullptr, *d_h = nullptr, *d_unew = nullptr;
+  double* d_stage[3] = {nullptr, nullptr, nullptr};
+  double t = 0.0;
+  bool have_state = false;
+  // data
+  int nsrc = 0;
+  int32_t* d_src_ptr = nullptr;
+  double* d_src_phi = nullptr;
+  double f0 = 0.0, t0 = 0.0;
+  double* d_bnd_coef = nullptr;
+  double omega = 0.0, phase = 0.0;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+  // instrumentation
+  bool stats_on = false;
+  int64_t n_launch = 0, n_apply = 0;
+  double apply_ms = 0.0;
+  std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
+  size_t ev_used = 0;
+};
+
+namespace {
+
+hdg_status fail(hdg_ctx* c, hdg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                       \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(ctx, HDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+hdg_status dalloc(hdg_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, HDG_ENOMEM, std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) + "): " + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  c->bytes += (int64_t)(count * sizeof(T));
+  return HDG_OK;
+}
+
+void dfree(hdg_ctx* c, void* p) {
+  if (!p) return;
+  cudaFree(p);
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+}
+
+int grid_for(const hdg_ctx* c, int64_t n, int block = 256) {
+  int64_t g = (n + block - 1) / block;
+  int64_t cap = (int64_t)c->sms * 8;
+  return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+DevMesh devmesh(const hdg_ctx* c) {
+  DevMesh m;
+  m.ne = c->sk.ne; m.nf = c->sk.nf;
+  m.geo = c->d_geo; m.rho = c->d_rho; m.c = c->d_c;
+  m.elem_face = c->d_elem_face; m.face_slot = c->d_face_slot; m.face_bnd = c->d_face_bnd;
+  return m;
+}
+
+// Event pair around one apply launch (instrumentation); returns the stop event or null.
+cudaEvent_t apply_begin(hdg_ctx* c) {
+  if (!c->stats_on) return nullptr;
+  if (c->ev_used + 2 > c->ev_pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      c->ev_pool.push_back(e);
+    }
+  }
+  cudaEvent_t a = c->ev_pool[c->ev_used];
+  cudaEventRecord(a, c->stream);
+  return c->ev_pool[c->ev_used + 1];
+}
+void apply_end(hdg_ctx* c, cudaEvent_t stop) {
+  if (!stop) return;
+  cudaEventRecord(stop, c->stream);
+  c->ev_used += 2;
+}
+// Harvests the recorded pairs (call after a stream synchronisation).
+void harvest(hdg_ctx* c) {
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
+      c->apply_ms += ms;
+      c->n_apply += 1;
+    }
+  }
+  c->ev_used = 0;
+}
+
+// ---- dispatch on (dim, k)
+#define HDG_DISPATCH(c, FN, ...)                     \
+  switch ((c)->dim * 10 + (c)->k) {                  \
+    case 21: FN<2, 1>(__VA_ARGS__); break;           \
+    case 22: FN<2, 2>(__VA_ARGS__); break;           \
+    case 23: FN<2, 3>(__VA_ARGS__); break;           \
+    case 24: FN<2, 4>(__VA_ARGS__); break;           \
+    case 31: FN<3, 1>(__VA_ARGS__); break;           \
+    case 32: FN<3, 2>(__VA_ARGS__); break;           \
+    case 33: FN<3, 3>(__VA_ARGS__); break;           \
+    case 34: FN<3, 4>(__VA_ARGS__); break;           \
+    default: break;                                  \
+  }
+
+template <int DIM, int K>
+void launch_condense(hdg_ctx* c) {
+  constexpr int NT = 128;
+  c->n_launch += 2;
+  condense_kernel<DIM, K, NT><<<(unsigned)c->sk.ne, NT, 0, c->stream>>>(devmesh(c), c->tabs, c->alpha, c->tau, c->d_S,
+                                                                       c->d_Hinv, c->d_err);
+  diag_kernel<DIM, K><<<grid_for(c, c->sk.nf * c->Nf), 256, 0, c->stream>>>(devmesh(c), c->d_S, c->d_dinv);
+}
+
+template <int DIM, int K>
+void launch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double src_rt, const double* lam, double* out) {
+  constexpr int NT = 64;
+  const int32_t* sp = c->nsrc > 0 ? c->d_src_ptr : nullptr;
+  c->n_launch += 1;
+  if (mode == 0)
+    local_kernel<DIM, K, 0, NT><<<(unsigned)c->sk.ne, NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F,
+                                                                         hist, sp, c->d_src_phi, src_rt, lam, out);
+  else
+    local_kernel<DIM, K, 1, NT><<<(unsigned)c->sk.ne, NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F,
+                                                                         hist, sp, c->d_src_phi, src_rt, lam, out);
+}
+
+template <int DIM, int K>
+void launch_apply(hdg_ctx* c, const double* x, double* zslot, const int* done) {
+  using C = ApplyCfg<DIM, K>;
+  const unsigned grid = (unsigned)((c->sk.ne + C::EPB - 1) / C::EPB);
+  c->n_launch += 1;
+  cudaEvent_t stop = apply_begin(c);
+  apply_kernel<DIM, K><<<grid, C::NT, 0, c->stream>>>(devmesh(c), c->d_S, x, zslot, done);
+  apply_end(c, stop);
+}
+
+hdg_status check_launch(hdg_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, HDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return HDG_OK;
+}
+
+hdg_status do_condense(hdg_ctx* c, double alpha) {
+  if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(c, HDG_EINVAL, "alpha must be positive and finite");
+  c->alpha = alpha;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+  HDG_DISPATCH(c, launch_condense, c);
+  hdg_status s = check_launch(c, "condense");
+  if (s) return s;
+  int herr = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (herr) { c->condensed = false; return fail(c, HDG_EINVAL, "local pressure block not positive definite"); }
+  c->condensed = true;
+  return HDG_OK;
+}
+
+// b (face array) = sum of gslot over each interior face's two slots
+hdg_status faces_from_slots(hdg_ctx* c, double scale, double* out) {
+  c->n_launch += 1;
+  face_gather_kernel<<<grid_for(c, c->sk.nf * c->Nf), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd,
+                                                                           c->d_slot, scale, out);
+  return check_launch(c, "face_gather");
+}
+
+// PCG on (-K) x = bvec over interior faces; x holds the initial guess (interior entries).
+hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int64_t nfe = c->sk.nf * c->Nf;
+  const int nb = c->nb_red;
+  HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
+  c->n_launch += 2;
+  cg_init_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec, c->d_dinv, c->d_r,
+                                            c->d_z, c->d_p, c->d_part);
+  cg_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->opt.rtol, c->d_sc);
+  hdg_status s = check_launch(c, "cg_init");
+  if (s) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->h_sc->bb == 0.0) {
+    c->n_launch += 1;
+    zero_interior_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_bnd, x);
+    if (info) { info->rel_residual = 0.0; info->sweeps = 1; }
+    return check_launch(c, "zero_interior");
+  }
+  int it = 0;
+  const int maxit = c->opt.maxit;
+  const int chk = std::max(1, c->opt.check_every);
+  while (!c->h_sc->done && it < maxit) {
+    const int upto = std::min(maxit, it + chk);
+    for (; it < upto; ++it) {
+      const int par = it & 1;
+      HDG_DISPATCH(c, launch_apply, c, c->d_p, c->d_slot, &c->d_sc->done);
+      c->n_launch += 3;
+      cg_face_q_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd, c->d_slot, c->d_p, c->d_q,
+                                                  c->d_part, c->d_sc);
+      cg_update_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, c->d_part, c->d_p, c->d_q, c->d_dinv, x, c->d_r, c->d_z,
+                                                  c->d_part + nb, c->d_sc);
+      cg_direction_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, it, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit);
+    }
+    s = check_launch(c, "cg_iter");
+    if (s) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    harvest(c);
+  }
+  const CgScal& h = *c->h_sc;
+  if (info) {
+    info->iterations += h.iters;
+    info->sweeps = 1;
+    info->rel_residual = std::sqrt(std::max(0.0, h.rr) / h.bb);
+  }
+  if (h.done != 1)
+    return fail(c, HDG_ENOCONV, "trace solve reached maxit=" + std::to_string(maxit) + " with relative residual " +
+                                    std::to_string(std::sqrt(std::max(0.0, h.rr) / h.bb)));
+  return HDG_OK;
+}
+
+double ricker(double t, double f0, double t0) {
+  const double pi = 3.14159265358979323846;
+  const double a = (pi * f0 * (t - t0)) * (pi * f0 * (t - t0));
+  return (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+// one implicit solve at mass shift alpha: alpha Mw u + f(u, lam, t) = alpha Mw hist
+hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info) {
+  const double fac = std::cos(c->omega * tt + c->phase);
+  c->n_launch += 1;
+  dirichlet_kernel<<<grid_for(c, c->sk.nb * c->Nf), 256, 0, c->stream>>>(c->sk.nb, c->Nf, c->d_bnd_faces, c->d_bnd_coef, fac,
+                                                                         c->d_lam);
+  const double rt = c->nsrc > 0 ? ricker(tt, c->f0, c->t0) : 0.0;
+  HDG_DISPATCH(c, launch_local, c, 0, (const double*)nullptr, hist, rt, c->d_lam, c->d_slot);
+  hdg_status s = check_launch(c, "rhs");
+  if (s) return s;
+  if ((s = faces_from_slots(c, 1.0, c->d_b))) return s;
+  if ((s = cg_solve(c, c->d_b, c->d_lam, info))) return s;
+  HDG_DISPATCH(c, launch_local, c, 1, (const double*)nullptr, hist, rt, c->d_lam, uout);
+  return check_launch(c, "recover");
+}
+
+hdg_status ensure_alpha(hdg_ctx* c, double alpha) {
+  if (c->condensed && std::fabs(alpha - c->alpha) <= 1e-14 * alpha) return HDG_OK;
+  return do_condense(c, alpha);
+}
+
+void combine(hdg_ctx* c, double* out, double c0, const double* i0, double c1 = 0, const double* i1 = nullptr,
+             double c2 = 0, const double* i2 = nullptr, double c3 = 0, const double* i3 = nullptr) {
+  const int64_t n = c->sk.ne * c->n;
+  c->n_launch += 1;
+  combine_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c0, i0, c1, i1, c2, i2, c3, i3, out);
+}
+
+// Alexander's L-stable DIRK(3,3): gamma is the root in (1/3, 1/2) of
+// gamma^3 - 3 gamma^2 + 3/2 gamma - 1/6 = 0.
+void dirk3(double a[3][3], double b[3], double cc[3]) {
+  double g = 0.4358;
+  for (int i = 0; i < 60; ++i) {
+    const double f = ((g - 3.0) * g + 1.5) * g - 1.0 / 6.0, df = (3.0 * g - 6.0) * g + 1.5;
+    g -= f / df;
+  }
+  const double b1 = -(6 * g * g - 16 * g + 1) / 4, b2 = (6 * g * g - 20 * g + 5) / 4;
+  double A[3][3] = {{g, 0, 0}, {(1 - g) / 2, g, 0}, {b1, b2, g}};
+  std::memcpy(a, A, sizeof(A));
+  b[0] = b1; b[1] = b2; b[2] = g;
+  cc[0] = g; cc[1] = (1 + g) / 2; cc[2] = 1.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hdg_default_options(hdg_options* o) {
+  if (!o) return;
+  o->prec = HDG_FP64;
+  o->rtol = 1e-13;
+  o->maxit = 2000;
+  o->check_every = 16;
+}
+
+const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void hdg_destroy(hdg_ctx* c) {
+  if (!c) return;
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_sc) cudaFreeHost(c->h_sc);
+  delete c;
+}
+
+hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_material* mat, const hdg_options* opt,
+                     void* cuda_stream, hdg_ctx** out) {
+  if (!out) return HDG_EINVAL;
+  *out = nullptr;
+  hdg_ctx* c = new (std::nothrow) hdg_ctx();
+  if (!c) return HDG_ENOMEM;
+  *out = c;
+  if (!mesh || !mat || !mesh->vert || !mesh->elem_vert || !mat->rho || !mat->c)
+    return fail(c, HDG_EINVAL, "null mesh or material pointer");
+  if (k < 1 || k > 4) return fail(c, HDG_EINVAL, "degree k must be in 1..4");
+  if (!(tau > 0.0)) return fail(c, HDG_EINVAL, "tau must be positive");
+  if (opt) c->opt = *opt; else hdg_default_options(&c->opt);
+  if (c->opt.prec != HDG_FP64 && c->opt.prec != HDG_MIXED) return fail(c, HDG_EINVAL, "unknown precision mode");
+  if (!(c->opt.rtol > 0.0) || c->opt.maxit < 1) return fail(c, HDG_EINVAL, "rtol must be > 0 and maxit >= 1");
+  std::string err;
+  if (!build_skeleton(mesh->dim, mesh->n_vert, mesh->n_elem, mesh->vert, mesh->elem_vert, c->sk, err))
+    return fail(c, HDG_EINVAL, err);
+  for (int64_t e = 0; e < mesh->n_elem; ++e)
+    if (!(mat->rho[e] > 0.0) || !(mat->c[e] > 0.0)) return fail(c, HDG_EINVAL, "rho and c must be positive");
+  c->dim = mesh->dim; c->k = k; c->tau = tau;
+  try {
+    c->T = build_tables(c->dim, k);
+  } catch (const std::exception& ex) {
+    return fail(c, HDG_EINVAL, ex.what());
+  }
+  c->Np = c->T.Np; c->Nf = c->T.Nf; c->nfc = c->dim + 1;
+  c->n = c->nfc * c->Np; c->m = c->nfc * c->Nf;
+  c->stream = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  CUDA_TRY(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+  c->nb_red = std::max(1, std::min(2 * c->sms, (int)((c->sk.nf * c->Nf + 255) / 256)));
+  const int64_t ne = c->sk.ne, nf = c->sk.nf, nb = c->sk.nb, nc = c->nfc;
+  // element vertex coordinates in sorted order (host, for quadrature points and point location)
+  c->h_vert_elem.resize((size_t)ne * nc * c->dim);
+  for (int64_t e = 0; e < ne; ++e)
+    for (int a = 0; a < nc; ++a)
+      for (int r = 0; r < c->dim; ++r)
+        c->h_vert_elem[((size_t)e * nc + a) * c->dim + r] = mesh->vert[(int64_t)c->sk.elem[e * nc + a] * c->dim + r];
+  hdg_status s;
+  if ((s = dalloc(c, &c->d_geo, (size_t)ne * GEO_STRIDE))) return s;
+  if ((s = dalloc(c, &c->d_rho, (size_t)ne))) return s;
+  if ((s = dalloc(c, &c->d_c, (size_t)ne))) return s;
+  if ((s = dalloc(c, &c->d_elem_face, (size_t)ne * nc))) return s;
+  if ((s = dalloc(c, &c->d_face_slot, (size_t)nf * 2))) return s;
+  if ((s = dalloc(c, &c->d_face_bnd, (size_t)nf))) return s;
+  if ((s = dalloc(c, &c->d_bnd_faces, (size_t)nb))) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_geo, c->sk.geo.data(), c->sk.geo.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_rho, mat->rho, ne * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_c, mat->c, ne * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_elem_face, c->sk.elem_face.data(), c->sk.elem_face.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_face_slot, c->sk.face_slot.data(), c->sk.face_slot.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_face_bnd, c->sk.face_bnd.data(), c->sk.face_bnd.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  if (nb) CUDA_TRY(c, cudaMemcpyAsync(c->d_bnd_faces, c->sk.bnd_faces.data(), nb * 8, cudaMemcpyHostToDevice, c->stream));
+  // reference tables packed in one buffer
+  std::vector<double> tab;
+  size_t off[6];
+  const std::vector<double>* parts[6] = {&c->T.Dr, &c->T.Ff, &c->T.Ef, &c->T.Trs, &c->T.DFrf, &c->T.Pfg};
+  for (int i = 0; i < 6; ++i) { off[i] = tab.size(); tab.insert(tab.end(), parts[i]->begin(), parts[i]->end()); }
+  if ((s = dalloc(c, &c->d_tab, tab.size()))) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  c->tabs.Dr = c->d_tab + off[0]; c->tabs.Ff = c->d_tab + off[1]; c->tabs.Ef = c->d_tab + off[2];
+  c->tabs.Trs = c->d_tab + off[3]; c->tabs.DFrf = c->d_tab + off[4]; c->tabs.Pfg = c->d_tab + off[5];
+  if ((s = dalloc(c, &c->d_qv_w, c->T.qv_w.size()))) return s;
+  if ((s = dalloc(c, &c->d_qv_phi, c->T.qv_phi.size()))) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_qv_w, c->T.qv_w.data(), c->T.qv_w.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_qv_phi, c->T.qv_phi.data(), c->T.qv_phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  // condensed operators and workspaces
+  const size_t nfe = (size_t)nf * c->Nf;
+  if ((s = dalloc(c, &c->d_S, (size_t)ne * c->m * c->m))) return s;
+  if ((s = dalloc(c, &c->d_Hinv, (size_t)ne * c->Np * c->Np))) return s;
+  if ((s = dalloc(c, &c->d_dinv, nfe))) return s;
+  if ((s = dalloc(c, &c->d_err, 1))) return s;
+  for (double** p : {&c->d_r, &c->d_z, &c->d_p, &c->d_q, &c->d_b, &c->d_lam})
+    if ((s = dalloc(c, p, nfe))) return s;
+  if ((s = dalloc(c, &c->d_slot, (size_t)ne * std::max(c->m, 1)))) return s;
+  if ((s = dalloc(c, &c->d_part, (size_t)c->nb_red * 3))) return s;
+  if ((s = dalloc(c, &c->d_sc, 1))) return s;
+  CUDA_TRY(c, cudaMallocHost((void**)&c->h_sc, sizeof(CgScal)));
+  std::memset(c->h_sc, 0, sizeof(CgScal));
+  for (double** p : {&c->d_u, &c->d_uprev, &c->d_h, &c->d_unew, &c->d_stage[0], &c->d_stage[1], &c->d_stage[2]})
+    if ((s = dalloc(c, p, (size_t)ne * c->n))) return s;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, nfe * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_u, 0, (size_t)ne * c->n * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_uprev, 0, (size_t)ne * c->n * 8, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->have_state = true;
+  return HDG_OK;
+}
+
+hdg_status hdg_get_sizes(const hdg_ctx* c, hdg_sizes* o) {
+  if (!c || !o) return HDG_EINVAL;
+  o->dim = c->dim; o->k = c->k; o->Np = c->Np; o->Nf = c->Nf; o->n_local = c->n; o->n_trace_local = c->m;
+  o->n_elem = c->sk.ne; o->n_faces = c->sk.nf; o->n_bnd_faces = c->sk.nb;
+  o->nq_vol = c->T.nqv; o->nq_face = c->T.nqf;
+  o->device_bytes = c->bytes;
+  return HDG_OK;
+}
+
+hdg_status hdg_condense(hdg_ctx* c, double alpha) {
+  if (!c) return HDG_EINVAL;
+  return do_condense(c, alpha);
+}
+
+hdg_status hdg_get_schur(hdg_ctx* c, double* S_dev) {
+  if (!c || !S_dev) return fail(c, HDG_EINVAL, "null argument");
+  if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  CUDA_TRY(c, cudaMemcpyAsync(S_dev, c->d_S, (size_t)c->sk.ne * c->m * c->m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  return HDG_OK;
+}
+
+hdg_status hdg_trace_apply(hdg_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return fail(c, HDG_EINVAL, "null argument");
+  if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
+  hdg_status s = check_launch(c, "apply");
+  if (s) return s;
+  return faces_from_slots(c, 1.0, y);
+}
+
+hdg_status hdg_condensed_rhs(hdg_ctx* c, const double* F, const double* lamD, double* r) {
+  if (!c || !F || !r) return fail(c, HDG_EINVAL, "null argument");
+  if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  HDG_DISPATCH(c, launch_local, c, 0, F, (const double*)nullptr, 0.0, lamD, c->d_slot);
+  hdg_status s = check_launch(c, "condensed_rhs");
+  if (s) return s;
+  return faces_from_slots(c, -1.0, r);
+}
+
+hdg_status hdg_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_info* info) {
+  if (!c || !r || !lam) return fail(c, HDG_EINVAL, "null argument");
+  if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  if (info) { info->iterations = 0; info->sweeps = 0; info->rel_residual = 0; }
+  // K lam = r  <=>  (-K) lam = -r
+  const int64_t nfe = c->sk.nf * c->Nf;
+  combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, -1.0, r, 0, nullptr, 0, nullptr, 0, nullptr, c->d_b);
+  hdg_status s = check_launch(c, "negate");
+  if (s) return s;
+  return cg_solve(c, c->d_b, lam, info);
+}
+
+hdg_status hdg_recover(hdg_ctx* c, const double* F, const double* lam, double* u) {
+  if (!c || !F || !lam || !u) return fail(c, HDG_EINVAL, "null argument");
+  if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  HDG_DISPATCH(c, launch_local, c, 1, F, (const double*)nullptr, 0.0, lam, u);
+  return check_launch(c, "recover");
+}
+
+hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const double* amp, double f0, double t0) {
+  if (!c || nsrc < 0 || (nsrc > 0 && (!pos || !amp))) return fail(c, HDG_EINVAL, "bad source arguments");
+  dfree(c, c->d_src_ptr); dfree(c, c->d_src_phi);
+  c->d_src_ptr = nullptr; c->d_src_phi = nullptr; c->nsrc = 0;
+  if (nsrc == 0) return HDG_OK;
+  const int d = c->dim, nc = c->nfc, Np = c->Np;
+  const int64_t ne = c->sk.ne;
+  std::vector<std::pair<int64_t, int>> owner;   // (element, source)
+  std::vector<double> xi_all((size_t)nsrc * d);
+  for (int s = 0; s < nsrc; ++s) {
+    int64_t found = -1;
+    for (int64_t e = 0; e < ne && found < 0; ++e) {
+      const double* g = &c->sk.geo[e * GEO_STRIDE];
+      const double* X0 = &c->h_vert_elem[(size_t)e * nc * d];
+      double xi[3], sum = 0.0, mn = 1e300;
+      for (int r = 0; r < d; ++r) {
+        double v = 0.0;
+        for (int j = 0; j < d; ++j) v += g[1 + r * d + j] * (pos[s * d + j] - X0[j]);
+        xi[r] = v; sum += v; mn = std::min(mn, v);
+      }
+      if (mn >= -1e-12 && sum <= 1.0 + 1e-12) {
+        found = e;
+        for (int r = 0; r < d; ++r) xi_all[(size_t)s * d + r] = xi[r];
+      }
+    }
+    if (found < 0) return fail(c, HDG_EINVAL, "source " + std::to_string(s) + " lies outside the mesh");
+    owner.push_back({found, s});
+  }
+  std::stable_sort(owner.begin(), owner.end());
+  std::vector<int32_t> ptr(ne + 1, 0);
+  std::vector<double> phi((size_t)nsrc * Np);
+  for (size_t i = 0; i < owner.size(); ++i) {
+    ptr[owner[i].first + 1]++;
+    const int s = owner[i].second;
+    dubiner(d, c->k, &xi_all[(size_t)s * d], 1, &phi[i * Np], nullptr);
+    for (int q = 0; q < Np; ++q) phi[i * Np + q] *= amp[s];
+  }
+  for (int64_t e = 0; e < ne; ++e) ptr[e + 1] += ptr[e];
+  hdg_status st;
+  if ((st = dalloc(c, &c->d_src_ptr, (size_t)ne + 1))) return st;
+  if ((st = dalloc(c, &c->d_src_phi, phi.size()))) return st;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_src_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_src_phi, phi.data(), phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->nsrc = nsrc; c->f0 = f0; c->t0 = t0;
+  return HDG_OK;
+}
+
+hdg_status hdg_quadrature_points(hdg_ctx* c, int32_t which, double* xyz) {
+  if (!c || !xyz || (which != 0 && which != 1)) return fail(c, HDG_EINVAL, "bad arguments");
+  const int d = c->dim, nc = c->nfc;
+  if (which == 0) {
+    const int nq = c->T.nqv;
+    for (int64_t e = 0; e < c->sk.ne; ++e) {
+      const double* X = &c->h_vert_elem[(size_t)e * nc * d];
+      for (int q = 0; q < nq; ++q)
+        for (int j = 0; j < d; ++j) {
+          double v = X[j];
+          for (int r = 0; r < d; ++r) v += c->T.qv_pts[(size_t)q * d + r] * (X[(r + 1) * d + j] - X[j]);
+          xyz[((size_t)e * nq + q) * d + j] = v;
+        }
+    }
+  } else {
+    const int nq = c->T.nqf;
+    for (int64_t b = 0; b < c->sk.nb; ++b) {
+      const int64_t f = c->sk.bnd_faces[b];
+      const int64_t slot = c->sk.face_slot[2 * f];
+      const int64_t e = slot / nc;
+      const int j = (int)(slot % nc);
+      const double* X = &c->h_vert_elem[(size_t)e * nc * d];
+      int fv[3], cnt = 0;
+      for (int a = 0; a < nc; ++a) if (a != j) fv[cnt++] = a;
+      for (int q = 0; q < nq; ++q)
+        for (int jj = 0; jj < d; ++jj) {
+          double v = X[fv[0] * d + jj];
+          for (int r = 1; r < d; ++r) v += c->T.qf_pts[(size_t)q * (d - 1) + r - 1] * (X[fv[r] * d + jj] - X[fv[0] * d + jj]);
+          xyz[((size_t)b * nq + q) * d + jj] = v;
+        }
+    }
+  }
+  return HDG_OK;
+}
+
+hdg_status hdg_project_volume(hdg_ctx* c, const double* vals, double* u) {
+  if (!c || !vals || !u) return fail(c, HDG_EINVAL, "null argument");
+  const size_t cnt = (size_t)c->sk.ne * c->T.nqv * c->nfc;
+  double* dv = nullptr;
+  hdg_status s;
+  if ((s = dalloc(c, &dv, cnt))) return s;
+  cudaError_t e1 = cudaMemcpyAsync(dv, vals, cnt * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e1 == cudaSuccess) {
+    const int64_t n = c->sk.ne * c->n;
+    project_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->nfc, c->d_qv_w, c->d_qv_phi, dv, u);
+    e1 = cudaGetLastError();
+  }
+  if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(c->stream);
+  dfree(c, dv);
+  c->bytes -= (int64_t)(cnt * 8);
+  if (e1 != cudaSuccess) return fail(c, HDG_ECUDA, std::string("project_volume: ") + cudaGetErrorString(e1));
+  return HDG_OK;
+}
+
+hdg_status hdg_set_dirichlet(hdg_ctx* c, const double* vals, double omega, double phase) {
+  if (!c) return HDG_EINVAL;
+  dfree(c, c->d_bnd_coef);
+  c->d_bnd_coef = nullptr;
+  c->omega = omega; c->phase = phase;
+  if (!vals || c->sk.nb == 0) return HDG_OK;
+  // lam_f[m] = sum_q w_q g(x_q) mu_m(eta_q)   (face mass J_F I cancels J_F)
+  const int nq = c->T.nqf, Nf = c->Nf;
+  std::vector<double> coef((size_t)c->sk.nb * Nf, 0.0);
+  for (int64_t b = 0; b < c->sk.nb; ++b)
+    for (int mm = 0; mm < Nf; ++mm) {
+      double s = 0.0;
+      for (int q = 0; q < nq; ++q) s += c->T.qf_w[q] * vals[(size_t)b * nq + q] * c->T.qf_mu[(size_t)q * Nf + mm];
+      coef[(size_t)b * Nf + mm] = s;
+    }
+  hdg_status s;
+  if ((s = dalloc(c, &c->d_bnd_coef, coef.size()))) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_bnd_coef, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return HDG_OK;
+}
+
+hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const double* lam, double t) {
+  if (!c || !u) return fail(c, HDG_EINVAL, "null argument");
+  const size_t bytes = (size_t)c->sk.ne * c->n * 8;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_u, u, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_uprev, uprev ? uprev : u, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (lam)
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_lam, lam, (size_t)c->sk.nf * c->Nf * 8, cudaMemcpyDeviceToDevice, c->stream));
+  else
+    CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, (size_t)c->sk.nf * c->Nf * 8, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->t = t;
+  c->have_state = true;
+  return HDG_OK;
+}
+
+hdg_status hdg_get_state(hdg_ctx* c, double* u, double* uprev, double* lam, double* t) {
+  if (!c) return HDG_EINVAL;
+  const size_t bytes = (size_t)c->sk.ne * c->n * 8;
+  if (u) CUDA_TRY(c, cudaMemcpyAsync(u, c->d_u, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (uprev) CUDA_TRY(c, cudaMemcpyAsync(uprev, c->d_uprev, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  if (lam) CUDA_TRY(c, cudaMemcpyAsync(lam, c->d_lam, (size_t)c->sk.nf * c->Nf * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (t) *t = c->t;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return HDG_OK;
+}
+
+hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hdg_solve_info* info) {
+  if (!c) return HDG_EINVAL;
+  if (!(dt > 0.0) || nsteps < 0) return fail(c, HDG_EINVAL, "dt must be positive and nsteps >= 0");
+  if (scheme != HDG_BE && scheme != HDG_BDF2 && scheme != HDG_DIRK3) return fail(c, HDG_EINVAL, "unknown scheme");
+  if (info) { info->iterations = 0; info->sweeps = 0; info->rel_residual = 0; }
+  hdg_solve_info si{};
+  hdg_status s;
+  for (int32_t step = 0; step < nsteps; ++step) {
+    const double tn = c->t;
+    if (scheme == HDG_BE || scheme == HDG_BDF2) {
+      // Eq. ch5appendx1:eq9b with b_s = 1: alpha = a_s/dt, hist = -(sum_{i<s} a_i u^{n+i}) / a_s
+      double alpha;
+      if (scheme == HDG_BE) {
+        alpha = 1.0 / dt;
+        combine(c, c->d_h, 1.0, c->d_u);
+      } else {
+        alpha = 1.5 / dt;
+        combine(c, c->d_h, 4.0 / 3.0, c->d_u, -1.0 / 3.0, c->d_uprev);
+      }
+      if ((s = ensure_alpha(c, alpha))) return s;
+      if ((s = stage_solve(c, c->d_h, tn + dt, c->d_unew, &si))) return s;
+      std::swap(c->d_uprev, c->d_u);   // u^{n-1} <- u^n
+      std::swap(c->d_u, c->d_unew);    // u^n <- u^{n+1}
+    } else {
+      double a[3][3], b[3], cc[3];
+      dirk3(a, b, cc);
+      // d = a^{-1} (lower triangular)
+      double d[3][3] = {};
+      for (int i = 0; i < 3; ++i) {
+        d[i][i] = 1.0 / a[i][i];
+        for (int j = 0; j < i; ++j) {
+          double sum = 0.0;
+          for (int q = j; q < i; ++q) sum += a[i][q] * d[q][j];
+          d[i][j] = -sum / a[i][i];
+        }
+      }
+      const double alpha = d[0][0] / dt;
+      if ((s = ensure_alpha(c, alpha))) return s;
+      for (int i = 0; i < 3; ++i) {
+        // Eq. 10_1, stage i: d_ii Mw U_i + dt f(U_i) = Mw [ (sum_{j<=i} d_ij) u^n - sum_{j<i} d_ij U_j ]
+        double cu = 0.0;
+        for (int j = 0; j <= i; ++j) cu += d[i][j];
+        const double* in[3] = {nullptr, nullptr, nullptr};
+        double co[3] = {0, 0, 0};
+        for (int j = 0; j < i; ++j) { in[j] = c->d_stage[j]; co[j] = -d[i][j] / d[i][i]; }
+        combine(c, c->d_h, cu / d[i][i], c->d_u, co[0], in[0], co[1], in[1], co[2], in[2]);
+        if ((s = stage_solve(c, c->d_h, tn + cc[i] * dt, c->d_stage[i], &si))) return s;
+      }
+      // Eq. 10_2: u^{n+1} = (1 - sum_i b_i sum_j d_ij) u^n + sum_j e_j U_j, e_j = sum_i b_i d_ij
+      double e[3] = {0, 0, 0}, w0 = 1.0;
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) e[j] += b[i] * d[i][j];
+      for (int j = 0; j < 3; ++j) w0 -= e[j];
+      combine(c, c->d_unew, w0, c->d_u, e[0], c->d_stage[0], e[1], c->d_stage[1], e[2], c->d_stage[2]);
+      std::swap(c->d_uprev, c->d_u);
+      std::swap(c->d_u, c->d_unew);
+    }
+    c->t = tn + dt;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (info) { info->iterations = si.iterations; info->sweeps = 1; info->rel_residual = si.rel_residual; }
+  return HDG_OK;
+}
+
+hdg_status hdg_enable_stats(hdg_ctx* c, int32_t enable) {
+  if (!c) return HDG_EINVAL;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  harvest(c);
+  c->stats_on = enable != 0;
+  return HDG_OK;
+}
+
+hdg_status hdg_get_stats(hdg_ctx* c, hdg_stats* o, int32_t reset) {
+  if (!c || !o) return HDG_EINVAL;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  harvest(c);
+  o->kernel_launches = c->n_launch;
+  o->apply_launches = c->n_apply;
+  o->apply_ms = c->apply_ms;
+  if (reset) { c->n_launch = 0; c->n_apply = 0; c->apply_ms = 0.0; }
+  return HDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,33 @@
+// Reference-element tables of the library (host side). Written independently of the
+// CPU oracle; both follow the basis and quadrature conventions stated in include/hdg.h.
+#pragma once
+#include <vector>
+
+namespace hdg {
+
+int n_modes(int dim, int k);  // C(k+dim, dim)
+
+// Gauss-Jacobi rule for weight (1-x)^a (1+x)^b on [-1, 1], n points.
+void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);
+// Collapsed product rule with n points per direction on the unit simplex of dimension dim
+// (dim = 1: [0,1]); pts is [nq][dim], weights sum to the simplex measure.
+void simplex_rule(int dim, int n, std::vector<double>& pts, std::vector<double>& w);
+// Orthonormal Dubiner basis of degree k at points pts [np][dim] of the unit simplex:
+// val [np][Nb], grad [np][Nb][dim] (grad may be null).
+void dubiner(int dim, int k, const double* pts, int np, double* val, double* grad);
+
+struct RefTables {
+  int dim = 0, k = 0, Np = 0, Nf = 0, nqv = 0, nqf = 0;
+  std::vector<double> Dr;    // [dim][Np][Np]     Dr[r][i][l] = int d_r phi_l phi_i
+  std::vector<double> Ff;    // [dim+1][Np][Nf]   int_face phi_i(xi_f(eta)) mu_m(eta) d eta
+  std::vector<double> Ef;    // [dim+1][Np][Np]   Ff Ff^T
+  std::vector<double> Trs;   // [dim][dim][Np][Np] Dr Ds^T
+  std::vector<double> DFrf;  // [dim][dim+1][Np][Nf] Dr Ff
+  std::vector<double> Pfg;   // [dim+1][dim+1][Nf][Nf] Ff^T Fg
+  std::vector<double> qv_pts, qv_w, qv_phi;  // volume rule: [nqv][dim], [nqv], [nqv][Np]
+  std::vector<double> qf_pts, qf_w, qf_mu;   // face rule:   [nqf][dim-1], [nqf], [nqf][Nf]
+};
+
+RefTables build_tables(int dim, int k);
+
+}  // namespace hdg

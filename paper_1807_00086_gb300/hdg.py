@@ -1,0 +1,267 @@
+"""Python binding of libhdg.so (ctypes). Argument marshalling only: every step of the
+hot path runs in the library's CUDA kernels. Torch tensors are used as device buffers
+(contiguous float64 on the context's device); the context is bound to the torch stream
+that is current when it is created.
+
+Names follow include/hdg.h: hdg_setup, hdg_condense, hdg_trace_apply, hdg_condensed_rhs,
+hdg_trace_solve, hdg_recover, hdg_step, ...
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhdg.so")
+
+c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+P_double, P_int32 = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+
+HDG_BE, HDG_BDF2, HDG_DIRK3 = 1, 2, 3
+HDG_FP64, HDG_MIXED = 0, 1
+SCHEMES = {"be": HDG_BE, "bdf2": HDG_BDF2, "dirk3": HDG_DIRK3}
+STATUS = {0: "HDG_OK", -1: "HDG_EINVAL", -2: "HDG_ENOMEM", -3: "HDG_ECUDA", -4: "HDG_ENOCONV",
+          -5: "HDG_ETIMEOUT", -6: "HDG_ESTATE"}
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", c_int32), ("n_vert", c_int64), ("n_elem", c_int64), ("vert", P_double),
+                ("elem_vert", P_int32)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("rho", P_double), ("c", P_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32)]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("dim", c_int32), ("k", c_int32), ("Np", c_int32), ("Nf", c_int32), ("n_local", c_int32),
+                ("n_trace_local", c_int32), ("n_elem", c_int64), ("n_faces", c_int64), ("n_bnd_faces", c_int64),
+                ("nq_vol", c_int32), ("nq_face", c_int32), ("device_bytes", c_int64)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("sweeps", c_int32), ("rel_residual", c_double)]
+
+    def as_dict(self):
+        return {"iterations": self.iterations, "sweeps": self.sweeps, "rel_residual": self.rel_residual}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", c_int64), ("apply_launches", c_int64), ("apply_ms", c_double)]
+
+
+# exported entry points: name -> (restype, argtypes)
+SIGNATURES = {
+    "hdg_default_options": (None, [ctypes.POINTER(Options)]),
+    "hdg_setup": (c_int32, [ctypes.POINTER(Mesh), c_int32, c_double, ctypes.POINTER(Material),
+                            ctypes.POINTER(Options), c_void_p, ctypes.POINTER(c_void_p)]),
+    "hdg_destroy": (None, [c_void_p]),
+    "hdg_last_error": (ctypes.c_char_p, [c_void_p]),
+    "hdg_get_sizes": (c_int32, [c_void_p, ctypes.POINTER(Sizes)]),
+    "hdg_condense": (c_int32, [c_void_p, c_double]),
+    "hdg_get_schur": (c_int32, [c_void_p, c_void_p]),
+    "hdg_trace_apply": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "hdg_condensed_rhs": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hdg_trace_solve": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(SolveInfo)]),
+    "hdg_recover": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hdg_set_sources": (c_int32, [c_void_p, c_int32, P_double, P_double, c_double, c_double]),
+    "hdg_quadrature_points": (c_int32, [c_void_p, c_int32, P_double]),
+    "hdg_project_volume": (c_int32, [c_void_p, P_double, c_void_p]),
+    "hdg_set_dirichlet": (c_int32, [c_void_p, P_double, c_double, c_double]),
+    "hdg_set_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_double]),
+    "hdg_get_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
+    "hdg_step": (c_int32, [c_void_p, c_double, c_int32, c_int32, ctypes.POINTER(SolveInfo)]),
+    "hdg_enable_stats": (c_int32, [c_void_p, c_int32]),
+    "hdg_get_stats": (c_int32, [c_void_p, ctypes.POINTER(Stats), c_int32]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libhdg.so (raises if it has not been built: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhdg.so is not built (run __graft_entry__.build()); no CPU fallback exists")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class HDGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _np_ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+class Solver:
+    """One HDG problem resident on the current CUDA device (wraps an hdg_ctx)."""
+
+    def __init__(self, vert, elem, k, tau, rho, c, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
+                 stream=None):
+        import torch
+        self.lib = load()
+        self.torch = torch
+        vert = np.ascontiguousarray(vert, dtype=np.float64)
+        elem = np.ascontiguousarray(elem, dtype=np.int32)
+        ne = elem.shape[0]
+        self._rho = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), (ne,)))
+        self._c = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), (ne,)))
+        mesh = Mesh(vert.shape[1], vert.shape[0], ne, _np_ptr(vert, c_double), _np_ptr(elem, c_int32))
+        mat = Material(_np_ptr(self._rho, c_double), _np_ptr(self._c, c_double))
+        opt = Options()
+        self.lib.hdg_default_options(ctypes.byref(opt))
+        opt.prec = {"fp64": HDG_FP64, "mixed": HDG_MIXED}[prec]
+        opt.rtol, opt.maxit, opt.check_every = rtol, maxit, check_every
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        ctx = ctypes.c_void_p()
+        st = self.lib.hdg_setup(ctypes.byref(mesh), k, tau, ctypes.byref(mat), ctypes.byref(opt),
+                                ctypes.c_void_p(stream.cuda_stream), ctypes.byref(ctx))
+        self.ctx = ctx
+        self._check(st)
+        sz = Sizes()
+        self._check(self.lib.hdg_get_sizes(self.ctx, ctypes.byref(sz)))
+        self.sizes = sz
+        self.dim, self.k, self.Np, self.Nf = sz.dim, sz.k, sz.Np, sz.Nf
+        self.n, self.m = sz.n_local, sz.n_trace_local
+        self.n_elem, self.n_faces, self.n_bnd = sz.n_elem, sz.n_faces, sz.n_bnd_faces
+
+    def _check(self, st):
+        if st != 0:
+            msg = self.lib.hdg_last_error(self.ctx)
+            raise HDGError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "ctx", None) and self.ctx.value:
+            self.lib.hdg_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # buffers -------------------------------------------------------------------------------
+    def empty_fields(self):
+        return self.torch.zeros((self.n_elem, self.n), dtype=self.torch.float64, device=self.device)
+
+    def empty_traces(self):
+        return self.torch.zeros((self.n_faces, self.Nf), dtype=self.torch.float64, device=self.device)
+
+    def _dev(self, t, shape):
+        assert t.dtype == self.torch.float64 and t.is_cuda and t.is_contiguous(), "float64 contiguous CUDA tensor"
+        assert t.numel() == int(np.prod(shape)), (tuple(t.shape), shape)
+        return _ptr(t)
+
+    # entry points --------------------------------------------------------------------------
+    def hdg_condense(self, alpha):
+        self._check(self.lib.hdg_condense(self.ctx, alpha))
+
+    def hdg_get_schur(self):
+        S = self.torch.empty((self.n_elem, self.m, self.m), dtype=self.torch.float64, device=self.device)
+        self._check(self.lib.hdg_get_schur(self.ctx, _ptr(S)))
+        return S
+
+    def hdg_trace_apply(self, x, y=None):
+        y = self.empty_traces() if y is None else y
+        self._check(self.lib.hdg_trace_apply(self.ctx, self._dev(x, (self.n_faces, self.Nf)),
+                                             self._dev(y, (self.n_faces, self.Nf))))
+        return y
+
+    def hdg_condensed_rhs(self, F, lamD=None, r=None):
+        r = self.empty_traces() if r is None else r
+        self._check(self.lib.hdg_condensed_rhs(self.ctx, self._dev(F, (self.n_elem, self.n)),
+                                               None if lamD is None else self._dev(lamD, (self.n_faces, self.Nf)),
+                                               self._dev(r, (self.n_faces, self.Nf))))
+        return r
+
+    def hdg_trace_solve(self, r, lam):
+        info = SolveInfo()
+        self._check(self.lib.hdg_trace_solve(self.ctx, self._dev(r, (self.n_faces, self.Nf)),
+                                             self._dev(lam, (self.n_faces, self.Nf)), ctypes.byref(info)))
+        return info.as_dict()
+
+    def hdg_recover(self, F, lam, u=None):
+        u = self.empty_fields() if u is None else u
+        self._check(self.lib.hdg_recover(self.ctx, self._dev(F, (self.n_elem, self.n)),
+                                         self._dev(lam, (self.n_faces, self.Nf)), self._dev(u, (self.n_elem, self.n))))
+        return u
+
+    def hdg_set_sources(self, pos, amp, f0, t0):
+        pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, self.dim))
+        amp = np.ascontiguousarray(np.broadcast_to(np.asarray(amp, dtype=np.float64), (pos.shape[0],)))
+        self._check(self.lib.hdg_set_sources(self.ctx, pos.shape[0], _np_ptr(pos, c_double), _np_ptr(amp, c_double),
+                                             f0, t0))
+
+    def hdg_quadrature_points(self, which):
+        nq = self.sizes.nq_vol if which == 0 else self.sizes.nq_face
+        cnt = self.n_elem if which == 0 else self.n_bnd
+        out = np.zeros((cnt, nq, self.dim))
+        self._check(self.lib.hdg_quadrature_points(self.ctx, which, _np_ptr(out, c_double)))
+        return out
+
+    def hdg_project_volume(self, vals, u=None):
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        assert vals.shape == (self.n_elem, self.sizes.nq_vol, self.dim + 1)
+        u = self.empty_fields() if u is None else u
+        self._check(self.lib.hdg_project_volume(self.ctx, _np_ptr(vals, c_double), self._dev(u, (self.n_elem, self.n))))
+        return u
+
+    def hdg_set_dirichlet(self, vals=None, omega=0.0, phase=0.0):
+        if vals is None:
+            self._check(self.lib.hdg_set_dirichlet(self.ctx, None, omega, phase))
+            return
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        assert vals.shape == (self.n_bnd, self.sizes.nq_face)
+        self._check(self.lib.hdg_set_dirichlet(self.ctx, _np_ptr(vals, c_double), omega, phase))
+
+    def hdg_set_state(self, u, t=0.0, uprev=None, lam=None):
+        shp = (self.n_elem, self.n)
+        self._check(self.lib.hdg_set_state(self.ctx, self._dev(u, shp), None if uprev is None else self._dev(uprev, shp),
+                                           None if lam is None else self._dev(lam, (self.n_faces, self.Nf)), t))
+
+    def hdg_get_state(self, u=None, uprev=None, lam=None, want_prev=False):
+        """Returns (u, lam, t) or, with want_prev, (u, uprev, lam, t); buffers may be passed in."""
+        u = self.empty_fields() if u is None else u
+        lam = self.empty_traces() if lam is None else lam
+        if want_prev and uprev is None:
+            uprev = self.empty_fields()
+        t = ctypes.c_double()
+        self._check(self.lib.hdg_get_state(self.ctx, _ptr(u), _ptr(uprev) if uprev is not None else None, _ptr(lam),
+                                           ctypes.byref(t)))
+        return (u, uprev, lam, t.value) if want_prev else (u, lam, t.value)
+
+    def hdg_enable_stats(self, enable=True):
+        self._check(self.lib.hdg_enable_stats(self.ctx, 1 if enable else 0))
+
+    def hdg_get_stats(self, reset=False):
+        st = Stats()
+        self._check(self.lib.hdg_get_stats(self.ctx, ctypes.byref(st), 1 if reset else 0))
+        return {"kernel_launches": st.kernel_launches, "apply_launches": st.apply_launches, "apply_ms": st.apply_ms}
+
+    def hdg_step(self, dt, scheme, nsteps=1):
+        info = SolveInfo()
+        self._check(self.lib.hdg_step(self.ctx, dt, SCHEMES[scheme] if isinstance(scheme, str) else scheme, nsteps,
+                                      ctypes.byref(info)))
+        return info.as_dict()
