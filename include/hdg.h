@@ -170,6 +170,34 @@ hdg_status hdg_get_state(hdg_ctx* ctx, double* u_dev, double* uprev_dev, double*
  * returning; info (may be NULL) accumulates over the steps. */
 hdg_status hdg_step(hdg_ctx* ctx, double dt, hdg_scheme scheme, int32_t nsteps, hdg_solve_info* info);
 
+/* Allocation-free trace apply. The paper has no counterpart: this entry point exists for
+ * callers that cannot call cudaMalloc at the moment they need y = K x, for instance code
+ * that must not stall the device with an allocation's implicit synchronisation inside a
+ * latency-bound loop, code confined to memory it was handed at start-up, or plug-ins
+ * that may not touch the process's allocator. It computes the same y = K x as
+ * hdg_trace_apply, with every input and output owned by the caller and no context:
+ *   S_dev          [n_elem][m][m]   element Schur blocks (e.g. copied by hdg_get_schur)
+ *   elem_face_dev  [n_elem][dim+1]  face id of local face j (faces in the library's
+ *                                   lexicographic order, local face j opposite vertex j)
+ *   face_slot_dev  [n_faces][2]     slots e*(dim+1)+j of the face's elements, lower element
+ *                                   first, -1 for the missing side of a boundary face
+ *   face_bnd_dev   [n_faces]        >= 0 on boundary faces, -1 on interior faces
+ *   x_dev, y_dev   [n_faces][Nf]    as in hdg_trace_apply (boundary entries of y set to 0)
+ * all device memory, used on cuda_stream. The only scratch, n_elem * m doubles of
+ * per-element products, lives in one fixed 8 MiB device array inside the library (held
+ * by every GPU that loads it until the process exits), so n_elem * m may not exceed
+ * 1,048,576 (26,214 tetrahedra at k = 3); larger sizes return HDG_EINVAL with a message
+ * in err (err_len bytes, may be NULL). The first call on each device looks up the
+ * array's device address with that device current; make that first call before any
+ * stream capture. The call enqueues work and returns; it allocates and frees nothing.
+ * Every call shares the one array and leaves its products there; each call writes every
+ * entry it reads before reading it, so nothing has to be cleared, but calls whose work
+ * overlaps on the GPU (e.g. on two streams at once) race on the array. */
+hdg_status hdg_trace_apply_noalloc(int32_t dim, int32_t k, int64_t n_elem, int64_t n_faces, const double* S_dev,
+                                   const int32_t* elem_face_dev, const int32_t* face_slot_dev,
+                                   const int32_t* face_bnd_dev, const double* x_dev, double* y_dev,
+                                   void* cuda_stream, char* err, int32_t err_len);
+
 /* Instrumentation (not part of the method). When enabled, the context counts its kernel
  * launches and times every launch of the matrix-free trace apply with CUDA events on the
  * context stream; hdg_get_stats returns the totals since the last reset. */

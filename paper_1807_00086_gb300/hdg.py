@@ -75,6 +75,8 @@ SIGNATURES = {
     "hdg_set_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_double]),
     "hdg_get_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
     "hdg_step": (c_int32, [c_void_p, c_double, c_int32, c_int32, ctypes.POINTER(SolveInfo)]),
+    "hdg_trace_apply_noalloc": (c_int32, [c_int32, c_int32, c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_void_p, c_void_p, c_void_p, ctypes.c_char_p, c_int32]),
     "hdg_enable_stats": (c_int32, [c_void_p, c_int32]),
     "hdg_get_stats": (c_int32, [c_void_p, ctypes.POINTER(Stats), c_int32]),
 }
