@@ -292,6 +292,20 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_apply_only(args):
+    """Profiling driver: condense the workload at size N and run `steps` trace applies."""
+    import torch
+    from paper_1807_00086_gb300 import hdg, inputs
+    w = inputs.acoustic_3d_workload(N=args.N, k=args.k)
+    s = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=args.prec)
+    s.hdg_condense(1.5 / DT)
+    x = torch.tensor(inputs.random_traces(s.n_faces, s.Nf, 1), device="cuda")
+    for _ in range(args.steps):
+        y = s.hdg_trace_apply(x)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "apply", "n_elem": s.n_elem, "applies": args.steps, "max_abs": float(y.abs().max())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,8 +318,12 @@ def main():
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "apply"],
+                    help="apply: profiling driver that only condenses and applies K (no JSON bench line)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "apply":
+        run_apply_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
