@@ -177,7 +177,8 @@ def run_ours(args):
 
     w = inputs.acoustic_3d_workload(N=args.N, k=args.k)
     ne = w["elem"].shape[0]
-    s = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=args.prec, rtol=args.rtol)
+    s = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=args.prec, rtol=args.rtol,
+                   inner_rtol=args.inner_rtol)
     s.hdg_set_sources(w["sources"], [1.0], w["f0"], w["t0"])
     s.hdg_set_dirichlet(None)
     s.hdg_set_state(s.empty_fields(), 0.0)
@@ -197,9 +198,11 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     iters = 0
+    sweeps = 0
     for _ in range(args.steps):
         info = s.hdg_step(DT, "bdf2", 1)
         iters += info["iterations"]
+        sweeps += info["sweeps"]
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -252,22 +255,56 @@ def run_ours(args):
     peaks, src = load_peaks()
     m = s.m
     apply_avg_ms = st["apply_ms"] / max(1, st["apply_launches"])
+    fp64_view = {"kernel": "apply_kernel<3,3> (FP64 S_K x lambda_K)", "launches": st["apply_launches"],
+                 "launch_ms": apply_avg_ms,
+                 "achieved_tflops": 2 * m * m * ne / (apply_avg_ms / 1e3) / 1e12 if st["apply_launches"] else None,
+                 "achieved_gbs": (m * m * 8 + 2 * m * 8) * ne / (apply_avg_ms / 1e3) / 1e9 if st["apply_launches"] else None}
     if args.prec == "fp64":
-        bytes_el = m * m * 8 + 2 * m * 8
-        flops_el = 2 * m * m
-        ach = flops_el * ne / (apply_avg_ms / 1e3) / 1e12
+        ach = fp64_view["achieved_tflops"]
         roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
-                "traffic": None, "kernel": "apply_kernel<3,3> (FP64 S_K x lambda_K)",
+                "traffic": None, "kernel": fp64_view["kernel"],
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (probe measured 1.20)",
-                "hbm_view": {"achieved_gbs": bytes_el * ne / (apply_avg_ms / 1e3) / 1e9,
-                             "peak_gbs": peaks["hbm_gbs"], "peak_source": src},
-                "launch_ms": apply_avg_ms, "launches": st["apply_launches"]}
+                "bytes_per_elem": m * m * 8 + 2 * m * 8, "flops_per_elem": 2 * m * m,
+                "launch_ms": apply_avg_ms, "launches": st["apply_launches"],
+                "hbm_view": {"achieved_gbs": fp64_view["achieved_gbs"], "peak_gbs": peaks["hbm_gbs"]}}
     else:
-        bytes_el = m * m * 4 + 2 * m * 4
-        ach = bytes_el * ne / (apply_avg_ms / 1e3) / 1e9
+        a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
+        p4 = (m * (m + 1) // 2 + 3) // 4
+        bytes_el = p4 * 16 + 2 * m * 4
+        ach = bytes_el * ne / (a32 / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None, "kernel": "apply kernel (FP32 S_K)",
-                "peak_source": src, "launch_ms": apply_avg_ms, "launches": st["apply_launches"]}
+                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "apply32_kernel<3,3> (FP32 packed-symmetric S_K x lambda_K)",
+                "peak_source": src + " (hbm_gbs: copy)", "bytes_per_elem": bytes_el,
+                "launch_ms": a32, "launches": st["apply32_launches"], "fp64_refinement_apply": fp64_view}
+
+    # the plain FP64 GPU path on the same workload and steps, for the mixed-vs-FP64 comparison
+    fp64 = None
+    if args.prec == "mixed" and not args.no_fp64_compare:
+        u_mixed = s.hdg_get_state()[0]
+        s.close()
+        torch.cuda.empty_cache()
+        s64 = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec="fp64", rtol=args.rtol)
+        s64.hdg_set_sources(w["sources"], [1.0], w["f0"], w["t0"])
+        s64.hdg_set_state(s64.empty_fields(), 0.0)
+        for _ in range(args.warmup):
+            s64.hdg_step(DT, "bdf2", 1)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            s64.hdg_step(DT, "bdf2", 1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = ev0.elapsed_time(ev1)
+        # same steps from the same start; the e2e leg advanced the mixed run by e2e_steps more
+        for _ in range(e2e_steps):
+            s64.hdg_step(DT, "bdf2", 1)
+        u64 = s64.hdg_get_state()[0]
+        rel = float((u_mixed - u64).abs().max() / u64.abs().max().clamp_min(1e-300))
+        fp64 = {"value": dofs * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
+                "speedup_mixed_over_fp64": (dofs * args.steps / (ms_max / 1e3)) / (dofs * args.steps / (ms64 / 1e3)),
+                "max_rel_diff_fields_after_%d_steps" % (args.warmup + args.steps + e2e_steps): rel}
+        s64.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -282,8 +319,10 @@ def run_ours(args):
                           "trace_dofs": int(s.n_faces - s.n_bnd) * s.Nf, "dt": DT, "scheme": "BDF2",
                           "precision": args.prec, "rtol": args.rtol, "parallelism": "replicas",
                           "l2": "inputs larger than L2 (S_K %.2f GB)" % (ne * m * m * 8 / 1e9),
-                          "krylov_iters_per_step": iters / args.steps},
-               "roofline": roof, "cpu_baseline": cpu,
+                          "krylov_iters_per_step": iters / args.steps,
+                          "refinement_sweeps_per_step": sweeps / args.steps if args.prec == "mixed" else None,
+                          "inner_rtol": args.inner_rtol if args.prec == "mixed" else None},
+               "roofline": roof, "cpu_baseline": cpu, "fp64_gpu": fp64,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * field_bytes + trace_bytes,
                        "d2h_bytes_per_step": 2 * field_bytes + trace_bytes, "steps": e2e_steps},
                "gpu_launches": st["kernel_launches"], "clocks": clk}
@@ -312,8 +351,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the plain FP64 comparison run that follows a mixed-precision measurement")
     ap.add_argument("--rtol", type=float, default=1e-12)
+    ap.add_argument("--inner-rtol", type=float, default=1e-5)
     ap.add_argument("--N", type=int, default=32)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

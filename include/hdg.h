@@ -68,11 +68,14 @@ typedef struct {
 } hdg_material;
 
 typedef struct {
-  hdg_precision prec;       /* HDG_FP64: everything FP64. HDG_MIXED: FP32 S_K and     */
-                            /* FP32 Krylov apply inside FP64 iterative refinement     */
+  hdg_precision prec;       /* HDG_FP64: everything FP64. HDG_MIXED: the Krylov       */
+                            /* iterations apply an FP32 copy of S_K inside FP64        */
+                            /* iterative refinement of the trace system                */
   double rtol;              /* relative residual target of the trace solve (FP64)     */
-  int32_t maxit;            /* Krylov iteration cap per solve                         */
+  int32_t maxit;            /* Krylov iteration cap per solve (per sweep if MIXED)    */
   int32_t check_every;      /* host polls the device convergence flag this often      */
+  double inner_rtol;        /* MIXED: relative residual target of each FP32 solve     */
+  int32_t max_sweeps;       /* MIXED: refinement sweep cap                            */
 } hdg_options;
 
 typedef struct {
@@ -88,7 +91,7 @@ typedef struct {
   double rel_residual;      /* final ||r|| / ||b|| of the trace system (FP64)         */
 } hdg_solve_info;
 
-/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16. */
+/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-5, max_sweeps 20. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face
@@ -203,8 +206,10 @@ hdg_status hdg_trace_apply_noalloc(int32_t dim, int32_t k, int64_t n_elem, int64
  * context stream; hdg_get_stats returns the totals since the last reset. */
 typedef struct {
   int64_t kernel_launches;  /* all kernels launched by the context                     */
-  int64_t apply_launches;   /* launches of the trace-apply kernel                      */
+  int64_t apply_launches;   /* launches of the FP64 trace-apply kernel                 */
   double apply_ms;          /* summed device time of those launches (CUDA events)      */
+  int64_t apply32_launches; /* launches of the FP32 (mixed precision) trace apply      */
+  double apply32_ms;        /* summed device time of those launches                    */
 } hdg_stats;
 hdg_status hdg_enable_stats(hdg_ctx* ctx, int32_t enable);
 hdg_status hdg_get_stats(hdg_ctx* ctx, hdg_stats* out, int32_t reset);

@@ -45,6 +45,16 @@ struct hdg_ctx {
   CgScal* d_sc = nullptr;
   CgScal* h_sc = nullptr;   // pinned
   int nb_red = 0;
+  // mixed precision
+  float *d_S32 = nullptr, *d_dinv32 = nullptr, *d_slot32 = nullptr;
+  float *d_r32 = nullptr, *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_x32 = nullptr, *d_b32 = nullptr;
+  double* d_res = nullptr;   // FP64 refinement residual
+  int64_t nfe4 = 0;          // FP32 face vectors padded to a multiple of 4 entries
+  int last_it32 = 16, last_it64 = 16;   // iteration counts of the previous solves (poll schedule)
+  double *d_lam_prev = nullptr, *d_lam_x = nullptr;  // trace history for the extrapolated guess
+  bool have_lam_prev = false;
+  RefScal* d_rs = nullptr;
+  RefScal* h_rs = nullptr;   // pinned
   // time state
   double *d_u = nullptr, *d_uprev = nullptr, *d_lam = nullptr, *d_h = nullptr, *d_unew = nullptr;
   double* d_stage[3] = {nullptr, nullptr, nullptr};
@@ -61,9 +71,11 @@ struct hdg_ctx {
   std::vector<void*> allocs;
   // instrumentation
   bool stats_on = false;
-  int64_t n_launch = 0, n_apply = 0;
-  double apply_ms = 0.0;
+  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0;
+  double apply_ms = 0.0, apply32_ms = 0.0;
   std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
+  std::vector<char> ev_kind;          // per pair: 0 FP64 apply, 1 FP32 apply
+  std::vector<int> ev_iter;           // per pair: Krylov iteration index (-1: always live)
   size_t ev_used = 0;
 };
 
@@ -116,7 +128,7 @@ DevMesh devmesh(const hdg_ctx* c) {
 }
 
 // Event pair around one apply launch (instrumentation); returns the stop event or null.
-cudaEvent_t apply_begin(hdg_ctx* c) {
+cudaEvent_t apply_begin(hdg_ctx* c, int kind = 0, int iter = -1) {
   if (!c->stats_on) return nullptr;
   if (c->ev_used + 2 > c->ev_pool.size()) {
     for (int i = 0; i < 64; ++i) {
@@ -124,8 +136,12 @@ cudaEvent_t apply_begin(hdg_ctx* c) {
       if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
       c->ev_pool.push_back(e);
     }
+    c->ev_kind.resize(c->ev_pool.size() / 2 + 1);
+    c->ev_iter.resize(c->ev_pool.size() / 2 + 1);
   }
   cudaEvent_t a = c->ev_pool[c->ev_used];
+  c->ev_kind[c->ev_used / 2] = (char)kind;
+  c->ev_iter[c->ev_used / 2] = iter;
   cudaEventRecord(a, c->stream);
   return c->ev_pool[c->ev_used + 1];
 }
@@ -134,13 +150,16 @@ void apply_end(hdg_ctx* c, cudaEvent_t stop) {
   cudaEventRecord(stop, c->stream);
   c->ev_used += 2;
 }
-// Harvests the recorded pairs (call after a stream synchronisation).
-void harvest(hdg_ctx* c) {
+// Harvests the recorded pairs (call after a stream synchronisation). Launches of Krylov
+// iterations at or beyond live_iters returned early (the solve had converged) and are
+// dropped, so the statistics time only launches that did the work.
+void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
   for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
     float ms = 0.f;
+    if (c->ev_iter[i / 2] >= live_iters) continue;
     if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
-      c->apply_ms += ms;
-      c->n_apply += 1;
+      if (c->ev_kind[i / 2]) { c->apply32_ms += ms; c->n_apply32 += 1; }
+      else { c->apply_ms += ms; c->n_apply += 1; }
     }
   }
   c->ev_used = 0;
@@ -171,23 +190,24 @@ void launch_condense(hdg_ctx* c) {
 
 template <int DIM, int K>
 void launch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double src_rt, const double* lam, double* out) {
-  constexpr int NT = 64;
+  using L = LocalCfg<DIM, K>;
+  const unsigned grid = (unsigned)((c->sk.ne + L::EPB - 1) / L::EPB);
   const int32_t* sp = c->nsrc > 0 ? c->d_src_ptr : nullptr;
   c->n_launch += 1;
   if (mode == 0)
-    local_kernel<DIM, K, 0, NT><<<(unsigned)c->sk.ne, NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F,
-                                                                         hist, sp, c->d_src_phi, src_rt, lam, out);
+    local_kernel<DIM, K, 0><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F, hist, sp,
+                                                            c->d_src_phi, src_rt, lam, out);
   else
-    local_kernel<DIM, K, 1, NT><<<(unsigned)c->sk.ne, NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F,
-                                                                         hist, sp, c->d_src_phi, src_rt, lam, out);
+    local_kernel<DIM, K, 1><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F, hist, sp,
+                                                            c->d_src_phi, src_rt, lam, out);
 }
 
 template <int DIM, int K>
-void launch_apply(hdg_ctx* c, const double* x, double* zslot, const int* done) {
+void launch_apply(hdg_ctx* c, const double* x, double* zslot, const int* done, int iter = -1) {
   using C = ApplyCfg<DIM, K>;
   const unsigned grid = (unsigned)((c->sk.ne + C::EPB - 1) / C::EPB);
   c->n_launch += 1;
-  cudaEvent_t stop = apply_begin(c);
+  cudaEvent_t stop = apply_begin(c, 0, iter);
   apply_kernel<DIM, K><<<grid, C::NT, 0, c->stream>>>(devmesh(c), c->d_S, x, zslot, done);
   apply_end(c, stop);
 }
@@ -198,6 +218,36 @@ hdg_status check_launch(hdg_ctx* c, const char* what) {
   return HDG_OK;
 }
 
+template <int DIM, int K>
+void launch_pack32(hdg_ctx* c) {
+  using PK = Packed<DIM, K>;
+  const int64_t n = ((c->sk.ne + 31) / 32) * PK::P4 * 128;
+  c->n_launch += 1;
+  pack32_kernel<DIM, K><<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->d_S, c->d_S32);
+}
+
+template <int DIM, int K>
+void launch_face_q64(hdg_ctx* c) {
+  cg_face_q_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->d_face_slot, c->d_face_bnd, c->d_slot, c->d_p,
+                                                             c->d_q, c->d_part, c->d_sc);
+}
+
+template <int DIM, int K>
+void launch_face_q32(hdg_ctx* c) {
+  cg32_face_q_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->d_face_slot, c->d_face_bnd, c->d_slot32,
+                                                               c->d_p32, c->d_q32, c->d_part, c->d_sc);
+}
+
+template <int DIM, int K>
+void launch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, int iter) {
+  const int64_t ngroups = (c->sk.ne + 31) / 32;
+  c->n_launch += 1;
+  cudaEvent_t stop = apply_begin(c, 1, iter);
+  apply32_kernel<DIM, K><<<(unsigned)((ngroups + 3) / 4), 128, 0, c->stream>>>(c->sk.ne, c->d_elem_face, c->d_face_bnd,
+                                                                              c->d_S32, x, slot, done);
+  apply_end(c, stop);
+}
+
 hdg_status do_condense(hdg_ctx* c, double alpha) {
   if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(c, HDG_EINVAL, "alpha must be positive and finite");
   c->alpha = alpha;
@@ -205,6 +255,13 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
   HDG_DISPATCH(c, launch_condense, c);
   hdg_status s = check_launch(c, "condense");
   if (s) return s;
+  if (c->opt.prec == HDG_MIXED) {
+    HDG_DISPATCH(c, launch_pack32, c);
+    const int64_t nfe = c->sk.nf * c->Nf;
+    c->n_launch += 1;
+    to32_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_dinv, c->d_dinv32);
+    if ((s = check_launch(c, "pack32"))) return s;
+  }
   int herr = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -221,8 +278,94 @@ hdg_status faces_from_slots(hdg_ctx* c, double scale, double* out) {
   return check_launch(c, "face_gather");
 }
 
+// FP32 PCG on (-K32) x32 = b32 from x32 = 0 (inner solve of the mixed path).
+hdg_status cg32_inner(hdg_ctx* c, int* iters) {
+  const int64_t nfe = c->sk.nf * c->Nf;
+  const int nb = c->nb_red;
+  const int64_t n4 = c->nfe4 / 4;
+  c->n_launch += 2;
+  cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32, (float4*)c->d_x32,
+                                              (float4*)c->d_r32, (float4*)c->d_z32, (float4*)c->d_p32, c->d_part);
+  cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->opt.inner_rtol, c->d_sc);
+  hdg_status s = check_launch(c, "cg32_init");
+  if (s) return s;
+  int it = 0;
+  const int maxit = c->opt.maxit;
+  const int chk = std::max(1, c->opt.check_every);
+  c->h_sc->done = 0;
+  const int first = std::max(2, std::min(chk, c->last_it32 - 1));   // first poll near the last solve's count
+  while (!c->h_sc->done && it < maxit) {
+    const int upto = std::min(maxit, it + (it == 0 ? first : std::min(chk, 3)));
+    for (; it < upto; ++it) {
+      const int par = it & 1;
+      HDG_DISPATCH(c, launch_apply32, c, c->d_p32, c->d_slot32, &c->d_sc->done, it);
+      c->n_launch += 3;
+      HDG_DISPATCH(c, launch_face_q32, c);
+      cg32_update_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, c->d_part, (const float4*)c->d_p32, (const float4*)c->d_q32,
+                                                    (const float4*)c->d_dinv32, (float4*)c->d_x32, (float4*)c->d_r32,
+                                                    (float4*)c->d_z32, c->d_part + nb, c->d_sc);
+      cg32_direction_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, it, c->d_part + nb, (const float4*)c->d_z32,
+                                                       (float4*)c->d_p32, c->d_sc, maxit);
+    }
+    if ((s = check_launch(c, "cg32_iter"))) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    harvest(c, c->h_sc->done ? c->h_sc->iters : (1 << 30));
+  }
+  *iters = c->h_sc->iters;
+  c->last_it32 = std::max(1, c->h_sc->iters);
+  return HDG_OK;
+}
+
+// Mixed precision: FP64 iterative refinement of (-K) x = bvec. Each sweep forms the FP64
+// residual with the FP64 S_K, solves for the correction with FP32 S_K (inner PCG with FP64
+// inner products) and adds it to x in FP64.
+hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int64_t nfe = c->sk.nf * c->Nf;
+  const int nb = c->nb_red;
+  int total_it = 0;
+  hdg_status s;
+  double rel = 0.0;
+  for (int sweep = 0;; ++sweep) {
+    HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
+    c->n_launch += 2;
+    refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec,
+                                                      c->d_res, c->d_part);
+    refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
+    if ((s = check_launch(c, "refine_residual"))) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_rs, c->d_rs, sizeof(RefScal), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    harvest(c);
+    const RefScal r = *c->h_rs;
+    if (r.bb == 0.0) {
+      c->n_launch += 1;
+      zero_interior_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_bnd, x);
+      if (info) { info->rel_residual = 0.0; info->sweeps += sweep; }
+      return check_launch(c, "zero_interior");
+    }
+    rel = std::sqrt(r.rr / r.bb);
+    if (rel <= c->opt.rtol) {
+      if (info) { info->iterations += total_it; info->sweeps += sweep; info->rel_residual = rel; }
+      return HDG_OK;
+    }
+    if (sweep >= c->opt.max_sweeps) break;
+    c->n_launch += 1;
+    to32_scaled_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_res, c->d_rs, c->d_b32);
+    int it = 0;
+    if ((s = cg32_inner(c, &it))) return s;
+    total_it += it;
+    c->n_launch += 1;
+    refine_update_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_bnd, c->d_x32, c->d_rs, x);
+    if ((s = check_launch(c, "refine_update"))) return s;
+  }
+  if (info) { info->iterations += total_it; info->sweeps += c->opt.max_sweeps; info->rel_residual = rel; }
+  return fail(c, HDG_ENOCONV, "mixed-precision refinement reached max_sweeps=" + std::to_string(c->opt.max_sweeps) +
+                                  " with relative residual " + std::to_string(rel));
+}
+
 // PCG on (-K) x = bvec over interior faces; x holds the initial guess (interior entries).
 hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  if (c->opt.prec == HDG_MIXED) return solve_mixed(c, bvec, x, info);
   const int64_t nfe = c->sk.nf * c->Nf;
   const int nb = c->nb_red;
   HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
@@ -237,20 +380,20 @@ hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* i
   if (c->h_sc->bb == 0.0) {
     c->n_launch += 1;
     zero_interior_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_bnd, x);
-    if (info) { info->rel_residual = 0.0; info->sweeps = 1; }
+    if (info) { info->rel_residual = 0.0; info->sweeps += 1; }
     return check_launch(c, "zero_interior");
   }
   int it = 0;
   const int maxit = c->opt.maxit;
   const int chk = std::max(1, c->opt.check_every);
+  int first = std::max(2, std::min(chk, c->last_it64 - 1));   // first poll near the last solve's count
   while (!c->h_sc->done && it < maxit) {
-    const int upto = std::min(maxit, it + chk);
+    const int upto = std::min(maxit, it + (it == 0 ? first : std::min(chk, 4)));
     for (; it < upto; ++it) {
       const int par = it & 1;
-      HDG_DISPATCH(c, launch_apply, c, c->d_p, c->d_slot, &c->d_sc->done);
+      HDG_DISPATCH(c, launch_apply, c, c->d_p, c->d_slot, &c->d_sc->done, it);
       c->n_launch += 3;
-      cg_face_q_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd, c->d_slot, c->d_p, c->d_q,
-                                                  c->d_part, c->d_sc);
+      HDG_DISPATCH(c, launch_face_q64, c);
       cg_update_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, c->d_part, c->d_p, c->d_q, c->d_dinv, x, c->d_r, c->d_z,
                                                   c->d_part + nb, c->d_sc);
       cg_direction_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, it, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit);
@@ -259,12 +402,13 @@ hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* i
     if (s) return s;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    harvest(c);
+    harvest(c, c->h_sc->done ? c->h_sc->iters : (1 << 30));
   }
   const CgScal& h = *c->h_sc;
+  c->last_it64 = std::max(1, h.iters);
   if (info) {
     info->iterations += h.iters;
-    info->sweeps = 1;
+    info->sweeps += 1;
     info->rel_residual = std::sqrt(std::max(0.0, h.rr) / h.bb);
   }
   if (h.done != 1)
@@ -332,6 +476,8 @@ void hdg_default_options(hdg_options* o) {
   o->rtol = 1e-13;
   o->maxit = 2000;
   o->check_every = 16;
+  o->inner_rtol = 1e-5;
+  o->max_sweeps = 20;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -341,6 +487,7 @@ void hdg_destroy(hdg_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
+  if (c->h_rs) cudaFreeHost(c->h_rs);
   delete c;
 }
 
@@ -358,6 +505,8 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if (opt) c->opt = *opt; else hdg_default_options(&c->opt);
   if (c->opt.prec != HDG_FP64 && c->opt.prec != HDG_MIXED) return fail(c, HDG_EINVAL, "unknown precision mode");
   if (!(c->opt.rtol > 0.0) || c->opt.maxit < 1) return fail(c, HDG_EINVAL, "rtol must be > 0 and maxit >= 1");
+  if (c->opt.prec == HDG_MIXED && (!(c->opt.inner_rtol > 0.0) || !(c->opt.inner_rtol < 1.0) || c->opt.max_sweeps < 1))
+    return fail(c, HDG_EINVAL, "mixed precision needs 0 < inner_rtol < 1 and max_sweeps >= 1");
   std::string err;
   if (!build_skeleton(mesh->dim, mesh->n_vert, mesh->n_elem, mesh->vert, mesh->elem_vert, c->sk, err))
     return fail(c, HDG_EINVAL, err);
@@ -375,7 +524,13 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   int dev = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
   CUDA_TRY(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
-  c->nb_red = std::max(1, std::min(2 * c->sms, (int)((c->sk.nf * c->Nf + 255) / 256)));
+  {
+    // reduction grid = one resident wave of the heaviest vector kernel (no partial second wave)
+    int per_sm = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg32_update_kernel, 256, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 4;
+    c->nb_red = std::max(1, std::min(per_sm * c->sms, (int)((c->sk.nf * c->Nf + 255) / 256)));
+  }
   const int64_t ne = c->sk.ne, nf = c->sk.nf, nb = c->sk.nb, nc = c->nfc;
   // element vertex coordinates in sorted order (host, for quadrature points and point location)
   c->h_vert_elem.resize((size_t)ne * nc * c->dim);
@@ -417,7 +572,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if ((s = dalloc(c, &c->d_Hinv, (size_t)ne * c->Np * c->Np))) return s;
   if ((s = dalloc(c, &c->d_dinv, nfe))) return s;
   if ((s = dalloc(c, &c->d_err, 1))) return s;
-  for (double** p : {&c->d_r, &c->d_z, &c->d_p, &c->d_q, &c->d_b, &c->d_lam})
+  for (double** p : {&c->d_r, &c->d_z, &c->d_p, &c->d_q, &c->d_b, &c->d_lam, &c->d_lam_prev, &c->d_lam_x})
     if ((s = dalloc(c, p, nfe))) return s;
   if ((s = dalloc(c, &c->d_slot, (size_t)ne * std::max(c->m, 1)))) return s;
   if ((s = dalloc(c, &c->d_part, (size_t)c->nb_red * 3))) return s;
@@ -426,6 +581,20 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   std::memset(c->h_sc, 0, sizeof(CgScal));
   for (double** p : {&c->d_u, &c->d_uprev, &c->d_h, &c->d_unew, &c->d_stage[0], &c->d_stage[1], &c->d_stage[2]})
     if ((s = dalloc(c, p, (size_t)ne * c->n))) return s;
+  if (c->opt.prec == HDG_MIXED) {
+    const int64_t ngroups = (ne + 31) / 32;
+    const int P4 = (c->m * (c->m + 1) / 2 + 3) / 4;
+    if ((s = dalloc(c, &c->d_S32, (size_t)ngroups * P4 * 128))) return s;
+    if ((s = dalloc(c, &c->d_slot32, (size_t)ngroups * c->m * 32))) return s;
+    c->nfe4 = (int64_t)((nfe + 3) / 4) * 4;
+    for (float** p : {&c->d_dinv32, &c->d_r32, &c->d_z32, &c->d_p32, &c->d_q32, &c->d_x32, &c->d_b32}) {
+      if ((s = dalloc(c, p, (size_t)c->nfe4))) return s;
+      CUDA_TRY(c, cudaMemsetAsync(*p, 0, (size_t)c->nfe4 * 4, c->stream));
+    }
+    if ((s = dalloc(c, &c->d_res, nfe))) return s;
+    if ((s = dalloc(c, &c->d_rs, 1))) return s;
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_rs, sizeof(RefScal)));
+  }
   CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, nfe * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_u, 0, (size_t)ne * c->n * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_uprev, 0, (size_t)ne * c->n * 8, c->stream));
@@ -628,6 +797,7 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->t = t;
   c->have_state = true;
+  c->have_lam_prev = false;
   return HDG_OK;
 }
 
@@ -662,10 +832,23 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
         combine(c, c->d_h, 4.0 / 3.0, c->d_u, -1.0 / 3.0, c->d_uprev);
       }
       if ((s = ensure_alpha(c, alpha))) return s;
+      // initial guess of the trace solve: 2 lam^n - lam^{n-1} (lam^n alone on the first step)
+      const int64_t nfe = c->sk.nf * c->Nf;
+      if (c->have_lam_prev) {
+        c->n_launch += 1;
+        combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, 2.0, c->d_lam, -1.0, c->d_lam_prev, 0, nullptr, 0,
+                                                                nullptr, c->d_lam_x);
+        std::swap(c->d_lam_prev, c->d_lam);
+        std::swap(c->d_lam, c->d_lam_x);
+      } else {
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_lam_prev, c->d_lam, nfe * 8, cudaMemcpyDeviceToDevice, c->stream));
+        c->have_lam_prev = true;
+      }
       if ((s = stage_solve(c, c->d_h, tn + dt, c->d_unew, &si))) return s;
       std::swap(c->d_uprev, c->d_u);   // u^{n-1} <- u^n
       std::swap(c->d_u, c->d_unew);    // u^n <- u^{n+1}
     } else {
+      c->have_lam_prev = false;
       double a[3][3], b[3], cc[3];
       dirk3(a, b, cc);
       // d = a^{-1} (lower triangular)
@@ -702,7 +885,7 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
     c->t = tn + dt;
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  if (info) { info->iterations = si.iterations; info->sweeps = 1; info->rel_residual = si.rel_residual; }
+  if (info) { info->iterations = si.iterations; info->sweeps = si.sweeps; info->rel_residual = si.rel_residual; }
   return HDG_OK;
 }
 
@@ -721,7 +904,9 @@ hdg_status hdg_get_stats(hdg_ctx* c, hdg_stats* o, int32_t reset) {
   o->kernel_launches = c->n_launch;
   o->apply_launches = c->n_apply;
   o->apply_ms = c->apply_ms;
-  if (reset) { c->n_launch = 0; c->n_apply = 0; c->apply_ms = 0.0; }
+  o->apply32_launches = c->n_apply32;
+  o->apply32_ms = c->apply32_ms;
+  if (reset) { c->n_launch = 0; c->n_apply = 0; c->apply_ms = 0.0; c->n_apply32 = 0; c->apply32_ms = 0.0; }
   return HDG_OK;
 }
 

@@ -187,114 +187,177 @@ __global__ void diag_kernel(DevMesh mesh, const double* __restrict__ S, double* 
 // MODE 0 (condensed rhs): out = gslot [ne][M] = C_K A_K^{-1} (F_K - B_K lamD_K)
 // MODE 1 (recovery):      out = u     [ne][N] = A_K^{-1} (F_K - B_K lam_K)
 // F_K is F[e] when hist == nullptr, else alpha Mw_K hist[e] + r(t) sum_src phi(x_s).
-template <int DIM, int K, int MODE, int NT>
-__global__ void __launch_bounds__(NT) local_kernel(DevMesh mesh, Tabs T, const double* __restrict__ Hinv,
-                                                   double alpha, double tau, const double* __restrict__ F,
-                                                   const double* __restrict__ hist, const int32_t* __restrict__ src_ptr,
-                                                   const double* __restrict__ src_phi, double src_rt,
-                                                   const double* __restrict__ lam, double* __restrict__ out) {
+// EPB elements per CTA, one thread per (element, row i < NP); only three block-wide
+// barriers, the rest of each element's work is row-local.
+template <int DIM, int K>
+struct LocalCfg {
+  static constexpr int NP = Dims<DIM, K>::NP;
+  static constexpr int EPB = NP <= 10 ? 16 : (NP <= 20 ? 8 : 4);
+  static constexpr int NT = EPB * NP;
+};
+
+template <int DIM, int K, int MODE>
+__global__ void __launch_bounds__(LocalCfg<DIM, K>::NT) local_kernel(DevMesh mesh, Tabs T, const double* __restrict__ Hinv,
+                                                                    double alpha, double tau, const double* __restrict__ F,
+                                                                    const double* __restrict__ hist,
+                                                                    const int32_t* __restrict__ src_ptr,
+                                                                    const double* __restrict__ src_phi, double src_rt,
+                                                                    const double* __restrict__ lam, double* __restrict__ out) {
   using D = Dims<DIM, K>;
-  constexpr int NP = D::NP, NF = D::NF, M = D::M, NFC = D::NFC, N = D::N;
-  __shared__ double g[GEO_STRIDE];
-  __shared__ double ll[M];
-  __shared__ double Fl[NFC * NP];
-  __shared__ double Fu[N];          // p block then v blocks
-  __shared__ double Tr[DIM * NP];
-  __shared__ double rp[NP], pp[NP];
-  __shared__ double qd[DIM * NP];
-  __shared__ double vv[DIM * NP];
-  const int64_t e = blockIdx.x;
+  using L = LocalCfg<DIM, K>;
+  constexpr int NP = D::NP, NF = D::NF, M = D::M, NFC = D::NFC, N = D::N, EPB = L::EPB, NT = L::NT;
+  __shared__ double g[EPB][GEO_STRIDE];
+  __shared__ double ll[EPB][M];
+  __shared__ double Tr[EPB][DIM * NP];   // reused for the face weights w_f in MODE 0
+  __shared__ double rp[EPB][NP];
+  __shared__ double pp[EPB][NP];
+  __shared__ double co[EPB][2];          // b = alpha rho, a' = alpha dJ / (rho c^2) (hist mode)
+  __shared__ int fuse[EPB][NFC];         // face contributes a trace (nonzero lam) to this element
   const int tid = threadIdx.x;
-  if (tid < GEO_STRIDE) g[tid] = mesh.geo[e * GEO_STRIDE + tid];
-  for (int t = tid; t < M; t += NT) {
-    const int f = mesh.elem_face[e * NFC + t / NF];
-    const bool use = (MODE == 1) || (mesh.face_bnd[f] >= 0);
-    ll[t] = (use && lam) ? lam[(int64_t)f * NF + t % NF] : 0.0;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  for (int t = tid; t < EPB * GEO_STRIDE; t += NT) {
+    const int64_t e = e0 + t / GEO_STRIDE;
+    g[t / GEO_STRIDE][t % GEO_STRIDE] = e < mesh.ne ? mesh.geo[e * GEO_STRIDE + t % GEO_STRIDE] : (t % GEO_STRIDE == 0 ? 1.0 : 0.0);
   }
-  __syncthreads();
-  const double dJ = g[0];
-  const double rho = mesh.rho[e], cc = mesh.c[e];
-  const double b = alpha * rho;
-  for (int t = tid; t < NFC * NP; t += NT) {
-    const int f = t / NP, i = t % NP;
-    double s = 0.0;
-    for (int mm = 0; mm < NF; ++mm) s += T.Ff[(f * NP + i) * NF + mm] * ll[f * NF + mm];
-    Fl[t] = s;
-  }
-  __syncthreads();
-  for (int t = tid; t < N; t += NT) {
-    const int comp = t / NP, i = t % NP;
-    double v;
-    if (hist) {
-      v = (comp == 0 ? alpha * dJ / (rho * cc * cc) : alpha * rho * dJ) * hist[e * N + t];
-      if (comp == 0 && src_ptr)
-        for (int s = src_ptr[e]; s < src_ptr[e + 1]; ++s) v += src_rt * src_phi[(int64_t)s * NP + i];
-    } else {
-      v = F[e * N + t];
+  for (int t = tid; t < EPB * NFC; t += NT) {
+    const int64_t e = e0 + t / NFC;
+    int use = 0;
+    if (e < mesh.ne && lam) {
+      const int f = mesh.elem_face[e * NFC + t % NFC];
+      use = (MODE == 1) || (mesh.face_bnd[f] >= 0);
     }
-    double bl = 0.0;
-    if (comp == 0) {
-      for (int f = 0; f < NFC; ++f) bl += g[D::OJF + f] * Fl[f * NP + i];
-      v += tau * bl;
-    } else {
-      for (int f = 0; f < NFC; ++f) bl += g[D::ON + f * DIM + comp - 1] * g[D::OJF + f] * Fl[f * NP + i];
-      v -= bl;
+    fuse[t / NFC][t % NFC] = use;
+  }
+  for (int t = tid; t < EPB * M; t += NT) {
+    const int64_t e = e0 + t / M;
+    const int r = t % M;
+    double v = 0.0;
+    if (e < mesh.ne && lam) {
+      const int f = mesh.elem_face[e * NFC + r / NF];
+      if ((MODE == 1) || (mesh.face_bnd[f] >= 0)) v = lam[(int64_t)f * NF + r % NF];
     }
-    Fu[t] = v;
+    ll[t / M][r] = v;
+  }
+  if (tid < EPB) {
+    const int64_t e = e0 + tid;
+    const double rho = e < mesh.ne ? mesh.rho[e] : 1.0, cc = e < mesh.ne ? mesh.c[e] : 1.0;
+    co[tid][0] = alpha * rho;
+    co[tid][1] = alpha / (rho * cc * cc);
   }
   __syncthreads();
-  for (int t = tid; t < DIM * NP; t += NT) {
-    const int r = t / NP, l = t % NP;
-    double s = 0.0;
-    for (int j = 0; j < DIM; ++j) s += g[1 + r * DIM + j] * Fu[(j + 1) * NP + l];
-    Tr[t] = s;
-  }
-  __syncthreads();
-  for (int i = tid; i < NP; i += NT) {
-    double s = 0.0;
-    for (int r = 0; r < DIM; ++r)
-      for (int l = 0; l < NP; ++l) s += T.Dr[(r * NP + i) * NP + l] * Tr[r * NP + l];
-    rp[i] = Fu[i] - s / b;
-  }
-  __syncthreads();
-  const double* He = Hinv + e * (int64_t)(NP * NP);
-  for (int i = tid; i < NP; i += NT) {
-    double s = 0.0;
-    for (int l = 0; l < NP; ++l) s += He[i * NP + l] * rp[l];
-    pp[i] = s;
-  }
-  __syncthreads();
-  for (int t = tid; t < DIM * NP; t += NT) {
-    const int r = t / NP, i = t % NP;
-    double s = 0.0;
-    for (int l = 0; l < NP; ++l) s += T.Dr[(r * NP + l) * NP + i] * pp[l];
-    qd[t] = s;
-  }
-  __syncthreads();
-  for (int t = tid; t < DIM * NP; t += NT) {
-    const int j = t / NP, i = t % NP;
-    double s = 0.0;
-    for (int r = 0; r < DIM; ++r) s += g[1 + r * DIM + j] * qd[r * NP + i];
-    vv[t] = Fu[(j + 1) * NP + i] / (b * dJ) + s / b;
-  }
-  __syncthreads();
-  if (MODE == 1) {
-    for (int t = tid; t < N; t += NT) out[e * N + t] = (t < NP) ? pp[t] : vv[t - NP];
-  } else {
-    // reuse Fl as w_f = tau p + sum_j n_fj v_j per face
-    for (int t = tid; t < NFC * NP; t += NT) {
-      const int f = t / NP, i = t % NP;
-      double s = tau * pp[i];
-      for (int j = 0; j < DIM; ++j) s += g[D::ON + f * DIM + j] * vv[j * NP + i];
-      Fl[t] = s;
-    }
-    __syncthreads();
-    for (int t = tid; t < M; t += NT) {
-      const int f = t / NF, mm = t % NF;
+  const int el = tid / NP, i = tid % NP;
+  const int64_t e = e0 + el;
+  const bool live = e < mesh.ne;
+  const double* ge = g[el];
+  const double dJ = ge[0];
+  const double b = co[el][0];
+  // row i of F~ for all components (+ the F^ lam face products it needs)
+  double Fu[DIM + 1];
+  {
+    double Fl[NFC];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
       double s = 0.0;
-      for (int i = 0; i < NP; ++i) s += T.Ff[(f * NP + i) * NF + mm] * Fl[f * NP + i];
-      out[e * M + t] = g[D::OJF + f] * s;
+      if (fuse[el][f])
+        for (int mm = 0; mm < NF; ++mm) s += T.Ff[(f * NP + i) * NF + mm] * ll[el][f * NF + mm];
+      Fl[f] = s;
     }
+#pragma unroll
+    for (int comp = 0; comp <= DIM; ++comp) {
+      double v = 0.0;
+      if (live) {
+        if (hist) {
+          const double sc = comp == 0 ? co[el][1] * dJ : b * dJ;
+          v = sc * hist[e * N + comp * NP + i];
+          if (comp == 0 && src_ptr)
+            for (int q = src_ptr[e]; q < src_ptr[e + 1]; ++q) v += src_rt * src_phi[(int64_t)q * NP + i];
+        } else {
+          v = F[e * N + comp * NP + i];
+        }
+      }
+      double bl = 0.0;
+      if (comp == 0) {
+#pragma unroll
+        for (int f = 0; f < NFC; ++f) bl += ge[D::OJF + f] * Fl[f];
+        v += tau * bl;
+      } else {
+#pragma unroll
+        for (int f = 0; f < NFC; ++f) bl += ge[D::ON + f * DIM + comp - 1] * ge[D::OJF + f] * Fl[f];
+        v -= bl;
+      }
+      Fu[comp] = v;
+    }
+  }
+  // Tr[r][i] = sum_j Jinv[r][j] F~v_j[i]
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) s += ge[1 + r * DIM + j] * Fu[j + 1];
+    Tr[el][r * NP + i] = s;
+  }
+  __syncthreads();
+  {
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+      for (int l = 0; l < NP; ++l) s += T.Dr[(r * NP + i) * NP + l] * Tr[el][r * NP + l];
+    rp[el][i] = Fu[0] - s / b;
+  }
+  __syncthreads();
+  {
+    // p = H^{-1} rp; H^{-1} is symmetric, so row i is read as column i (coalesced)
+    const double* He = Hinv + (live ? e : 0) * (int64_t)(NP * NP);
+    double s = 0.0;
+    for (int l = 0; l < NP; ++l) s += He[l * NP + i] * rp[el][l];
+    pp[el][i] = s;
+  }
+  __syncthreads();
+  double vv[DIM];
+  {
+    double qd[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      double s = 0.0;
+      for (int l = 0; l < NP; ++l) s += T.Dr[(r * NP + l) * NP + i] * pp[el][l];
+      qd[r] = s;
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) s += ge[1 + r * DIM + j] * qd[r];
+      vv[j] = Fu[j + 1] / (b * dJ) + s / b;
+    }
+  }
+  if (MODE == 1) {
+    if (live) {
+      out[e * N + i] = pp[el][i];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) out[e * N + (j + 1) * NP + i] = vv[j];
+    }
+    return;
+  }
+  // MODE 0: w_f[i] = tau p[i] + sum_j n_fj v_j[i]  (Tr reused: NFC*NP <= DIM*NP + NP)
+  double* w = &Tr[el][0];
+  __syncthreads();   // every thread is done reading Tr
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    double s = tau * pp[el][i];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) s += ge[D::ON + f * DIM + j] * vv[j];
+    if (f < DIM) w[f * NP + i] = s;
+    else rp[el][i] = s;                   // last face's weights live in rp (no longer needed)
+  }
+  __syncthreads();
+  for (int t = tid; t < EPB * M; t += NT) {
+    const int el2 = t / M, r = t % M, f = r / NF, mm = r % NF;
+    const int64_t e2 = e0 + el2;
+    if (e2 >= mesh.ne) continue;
+    const double* wf = f < DIM ? &Tr[el2][f * NP] : &rp[el2][0];
+    double s = 0.0;
+    for (int q = 0; q < NP; ++q) s += T.Ff[(f * NP + q) * NF + mm] * wf[q];
+    out[e2 * M + r] = g[el2][D::OJF + f] * s;
   }
 }
 
@@ -358,6 +421,27 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
     for (int i = 0; i < 8; ++i) s += red[i];
   return s;
 }
+
+// Inner products of FP32 vectors, accurate to FP64 level but evaluated on the FP32 pipe
+// (GB300's FP64 rate is 1/58 of FP32): each product is split exactly into p + e with an
+// FMA, and the terms are accumulated in a compensated (s, c) float pair (TwoSum). Only
+// the per-thread result is widened to FP64 for the block/grid reduction.
+struct Acc2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bb = t - s;
+    c += (s - (t - bb)) + (x - bb);
+    s = t;
+  }
+  __device__ __forceinline__ void dot(float a, float b) {
+    const float p = a * b;
+    c += fmaf(a, b, -p);
+    add(p);
+  }
+  __device__ __forceinline__ void dot4(float4 a, float4 b) { dot(a.x, b.x); dot(a.y, b.y); dot(a.z, b.z); dot(a.w, b.w); }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 
 // Deterministic sum of a partials array (same order in every block); result in all threads.
 __device__ __forceinline__ double reduce_partials(const double* __restrict__ part, int n, int stride, double* red) {
@@ -430,22 +514,33 @@ __global__ void cg_init_scalars(int nb, const double* __restrict__ part, double 
   }
 }
 
-// q = (-K) p on faces; partial p.q
-__global__ void cg_face_q_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_slot,
-                                 const int32_t* __restrict__ face_bnd, const double* __restrict__ zslot,
-                                 const double* __restrict__ p, double* __restrict__ q, double* __restrict__ part,
-                                 const CgScal* __restrict__ sc) {
+// q = (-K) p on faces; partial p.q (NF compile-time)
+template <int DIM, int K>
+__global__ void __launch_bounds__(256) cg_face_q_kernel(int nf, const int32_t* __restrict__ face_slot,
+                                                        const int32_t* __restrict__ face_bnd,
+                                                        const double* __restrict__ zslot, const double* __restrict__ p,
+                                                        double* __restrict__ q, double* __restrict__ part,
+                                                        const CgScal* __restrict__ sc) {
+  constexpr int NF = Dims<DIM, K>::NF;
   if (sc->done) return;
   __shared__ double red[8];
-  const int64_t n = nf * NF;
   double pq = 0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t f = t / NF;
-    const int mm = (int)(t % NF);
-    double qv = 0;
-    if (face_bnd[f] < 0) qv = -face_sum(face_slot, zslot, f, mm, NF);
-    q[t] = qv;
-    pq += p[t] * qv;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    double qv[NF];
+    if (face_bnd[f] < 0) {
+      const double* s0 = zslot + (int64_t)face_slot[2 * f] * NF;
+      const double* s1 = zslot + (int64_t)face_slot[2 * f + 1] * NF;
+#pragma unroll
+      for (int mm = 0; mm < NF; ++mm) qv[mm] = -(s0[mm] + s1[mm]);
+    } else {
+#pragma unroll
+      for (int mm = 0; mm < NF; ++mm) qv[mm] = 0.0;
+    }
+#pragma unroll
+    for (int mm = 0; mm < NF; ++mm) {
+      q[(int64_t)f * NF + mm] = qv[mm];
+      pq += p[(int64_t)f * NF + mm] * qv[mm];
+    }
   }
   const double s = block_sum256(pq, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -461,7 +556,25 @@ __global__ void cg_update_kernel(int64_t n, int nb, int parity, const double* __
   const double pq = reduce_partials(part_pq, nb, 1, red);
   const double al = sc->rho[parity] / pq;
   double rz = 0, rr = 0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; t + 3 * stride < n; t += 4 * stride) {
+    double pv[4], qv[4], xv[4], rv[4], dv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pv[u] = p[t + u * stride]; qv[u] = q[t + u * stride]; xv[u] = x[t + u * stride];
+      rv[u] = r[t + u * stride]; dv[u] = dinv[t + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[t + u * stride] = xv[u] + al * pv[u];
+      const double rn = rv[u] - al * qv[u];
+      const double zn = dv[u] * rn;
+      r[t + u * stride] = rn; z[t + u * stride] = zn;
+      rz += rn * zn; rr += rn * rn;
+    }
+  }
+  for (; t < n; t += stride) {
     const double pv = p[t];
     x[t] += al * pv;
     const double rv = r[t] - al * q[t];
@@ -485,8 +598,16 @@ __global__ void cg_direction_kernel(int64_t n, int nb, int parity, int iter, con
   const int it = iter + 1;  // iteration index from the host: no block reads what block 0 writes
   if (!conv && it < maxit) {
     const double be = rz / sc->rho[parity];
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-      p[t] = z[t] + be * p[t];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; t + 3 * stride < n; t += 4 * stride) {
+      double pv[4], zv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { pv[u] = p[t + u * stride]; zv[u] = z[t + u * stride]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) p[t + u * stride] = zv[u] + be * pv[u];
+    }
+    for (; t < n; t += stride) p[t] = z[t] + be * p[t];
   }
   // every block has read sc->rho[parity] above; block 0 alone writes the other slot
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -539,6 +660,297 @@ __global__ void project_volume_kernel(int64_t ne, int NP, int nq, int ncomp, con
     for (int q = 0; q < nq; ++q) s += w[q] * vals[(e * nq + q) * ncomp + c] * phi[q * NP + i];
     u[t] = s;
   }
+}
+
+}  // namespace hdg
+
+namespace hdg {
+
+// ================================================================ mixed precision (FP32 inner solve)
+// S32: the upper triangle (row-major, c >= r) of every S_K rounded to FP32, stored for groups
+// of 32 elements as [group][P4][32][4] floats, P4 = ceil(M(M+1)/2 / 4): one warp handles a
+// group, lane = element, each lane reads float4s and the warp's loads are contiguous.
+template <int DIM, int K>
+struct Packed {
+  static constexpr int M = Dims<DIM, K>::M;
+  static constexpr int P = M * (M + 1) / 2;
+  static constexpr int P4 = (P + 3) / 4;
+};
+
+__host__ __device__ constexpr int packed_index(int M, int r, int c) { return r * M - r * (r - 1) / 2 + (c - r); }
+
+template <int DIM, int K>
+__global__ void pack32_kernel(int64_t ne, const double* __restrict__ S, float* __restrict__ S32) {
+  using PK = Packed<DIM, K>;
+  constexpr int M = PK::M, P4 = PK::P4;
+  const int64_t ngroups = (ne + 31) / 32;
+  const int64_t n = ngroups * P4 * 32 * 4;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t & 3);
+    const int lane = (int)((t >> 2) & 31);
+    const int64_t q = (t >> 7) % P4;
+    const int64_t g = (t >> 7) / P4;
+    const int64_t e = g * 32 + lane;
+    const int p = (int)(q * 4 + j);
+    float v = 0.f;
+    if (e < ne && p < PK::P) {
+      // invert the packed index: row r holds entries [packed_index(r, r), packed_index(r, M-1)]
+      int r = 0;
+      while (packed_index(M, r, M - 1) < p) ++r;
+      const int c = r + (p - packed_index(M, r, r));
+      v = (float)S[e * (int64_t)(M * M) + r * M + c];
+    }
+    S32[t] = v;
+  }
+}
+
+// slot32 layout: [e][M] floats (element-major, like the FP64 slots); the warp transposes
+// its 32 x M products through shared memory so that the stores are contiguous float4s.
+template <int DIM, int K>
+__global__ void __launch_bounds__(128) apply32_kernel(int64_t ne, const int32_t* __restrict__ elem_face,
+                                                      const int32_t* __restrict__ face_bnd,
+                                                      const float* __restrict__ S32, const float* __restrict__ x,
+                                                      float* __restrict__ slot, const int* __restrict__ done) {
+  using D = Dims<DIM, K>;
+  using PK = Packed<DIM, K>;
+  constexpr int NF = D::NF, M = D::M, NFC = D::NFC, P4 = PK::P4;
+  constexpr int MP = M + 1;   // padded row: conflict-free transposed writes
+  __shared__ float tr[4][32 * MP];
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t g = (int64_t)blockIdx.x * 4 + wid;
+  const int64_t e = g * 32 + lane;
+  if (g * 32 >= ne) return;
+  float xl[M], y[M];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    int fid = -1;
+    if (e < ne) fid = elem_face[e * NFC + f];
+    const bool use = fid >= 0 && face_bnd[fid] < 0;
+#pragma unroll
+    for (int mm = 0; mm < NF; ++mm) xl[f * NF + mm] = use ? x[(int64_t)fid * NF + mm] : 0.f;
+  }
+#pragma unroll
+  for (int r = 0; r < M; ++r) y[r] = 0.f;
+  const float4* Sg = reinterpret_cast<const float4*>(S32) + g * (int64_t)P4 * 32 + lane;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+#pragma unroll
+    for (int c = r; c < M; ++c) {
+      const int p = packed_index(M, r, c);
+      if ((p & 3) == 0) v = __ldcs(Sg + (p >> 2) * 32);
+      const float s = (p & 3) == 0 ? v.x : (p & 3) == 1 ? v.y : (p & 3) == 2 ? v.z : v.w;
+      y[r] = fmaf(s, xl[c], y[r]);
+      if (c != r) y[c] = fmaf(s, xl[r], y[c]);
+    }
+  }
+  float* t = tr[wid];
+#pragma unroll
+  for (int r = 0; r < M; ++r) t[lane * MP + r] = y[r];
+  __syncwarp();
+  const int64_t nvalid = (ne - g * 32) < 32 ? (ne - g * 32) : 32;
+  float* dst = slot + g * 32 * (int64_t)M;
+  for (int idx = lane; idx < nvalid * M; idx += 32) dst[idx] = t[(idx / M) * MP + idx % M];
+}
+
+// q = (-K32) p on faces; partial p.q in FP64. NF is compile-time (no integer division).
+template <int DIM, int K>
+__global__ void __launch_bounds__(256) cg32_face_q_kernel(int nf, const int32_t* __restrict__ face_slot,
+                                                          const int32_t* __restrict__ face_bnd,
+                                                          const float* __restrict__ slot, const float* __restrict__ p,
+                                                          float* __restrict__ q, double* __restrict__ part,
+                                                          const CgScal* __restrict__ sc) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  if (sc->done) return;
+  __shared__ double red[8];
+  Acc2 pq;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+    float qv[NF];
+    if (face_bnd[f] < 0) {
+      const float* s0 = slot + (int64_t)face_slot[2 * f] * NF;
+      const float* s1 = slot + (int64_t)face_slot[2 * f + 1] * NF;
+#pragma unroll
+      for (int mm = 0; mm < NF; ++mm) qv[mm] = -(s0[mm] + s1[mm]);
+    } else {
+#pragma unroll
+      for (int mm = 0; mm < NF; ++mm) qv[mm] = 0.f;
+    }
+#pragma unroll
+    for (int mm = 0; mm < NF; ++mm) {
+      q[(int64_t)f * NF + mm] = qv[mm];
+      pq.dot(p[(int64_t)f * NF + mm], qv[mm]);
+    }
+  }
+  const double s = block_sum256(pq.value(), red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// FP32 vectors are padded to a multiple of 4 entries (padding: zero, dinv = 0) and
+// processed as float4.
+__device__ __forceinline__ float4 f4fma(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 f4mul(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
+
+
+// inner solve start from x = 0: r = b, z = Dinv r, p = z; partials (rz, rr)
+__global__ void cg32_init_kernel(int64_t n4, const float4* __restrict__ b, const float4* __restrict__ dinv,
+                                 float4* __restrict__ x, float4* __restrict__ r, float4* __restrict__ z,
+                                 float4* __restrict__ p, double* __restrict__ part) {
+  __shared__ double red[8];
+  Acc2 rz, rr;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+    const float4 rv = b[t];
+    const float4 zv = f4mul(dinv[t], rv);
+    x[t] = make_float4(0.f, 0.f, 0.f, 0.f); r[t] = rv; z[t] = zv; p[t] = zv;
+    rz.dot4(rv, zv); rr.dot4(rv, rv);
+  }
+  double s;
+  s = block_sum256(rz.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 0] = s;
+  s = block_sum256(rr.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
+}
+
+__global__ void cg32_init_scalars(int nb, const double* __restrict__ part, double rtol, CgScal* sc) {
+  __shared__ double red[8];
+  const double rz = reduce_partials(part + 0, nb, 2, red);
+  const double rr = reduce_partials(part + 1, nb, 2, red);
+  if (threadIdx.x == 0) {
+    sc->rho[0] = rz; sc->rho[1] = 0; sc->bb = rr; sc->rr = rr;
+    sc->tol2 = rtol * rtol * rr;
+    sc->iters = 0;
+    sc->done = (rr == 0.0) ? 1 : 0;
+  }
+}
+
+__global__ void cg32_update_kernel(int64_t n4, int nb, int parity, const double* __restrict__ part_pq,
+                                   const float4* __restrict__ p, const float4* __restrict__ q,
+                                   const float4* __restrict__ dinv, float4* __restrict__ x, float4* __restrict__ r,
+                                   float4* __restrict__ z, double* __restrict__ part, const CgScal* __restrict__ sc) {
+  if (sc->done) return;
+  __shared__ double red[8];
+  const double pq = reduce_partials(part_pq, nb, 1, red);
+  const float al = (float)(sc->rho[parity] / pq);
+  Acc2 rz, rr;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; t + 3 * stride < n4; t += 4 * stride) {
+    float4 pv[4], qv[4], xv[4], rv[4], dv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pv[u] = p[t + u * stride]; qv[u] = q[t + u * stride]; xv[u] = x[t + u * stride];
+      rv[u] = r[t + u * stride]; dv[u] = dinv[t + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[t + u * stride] = f4fma(al, pv[u], xv[u]);
+      const float4 rn = f4fma(-al, qv[u], rv[u]);
+      const float4 zn = f4mul(dv[u], rn);
+      r[t + u * stride] = rn; z[t + u * stride] = zn;
+      rz.dot4(rn, zn); rr.dot4(rn, rn);
+    }
+  }
+  for (; t < n4; t += stride) {
+    x[t] = f4fma(al, p[t], x[t]);
+    const float4 rv1 = f4fma(-al, q[t], r[t]);
+    const float4 zv1 = f4mul(dinv[t], rv1);
+    r[t] = rv1; z[t] = zv1;
+    rz.dot4(rv1, zv1); rr.dot4(rv1, rv1);
+  }
+  double s;
+  s = block_sum256(rz.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 0] = s;
+  s = block_sum256(rr.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
+}
+
+__global__ void cg32_direction_kernel(int64_t n4, int nb, int parity, int iter, const double* __restrict__ part,
+                                      const float4* __restrict__ z, float4* __restrict__ p, CgScal* sc, int maxit) {
+  if (sc->done) return;
+  __shared__ double red[8];
+  const double rz = reduce_partials(part + 0, nb, 2, red);
+  const double rr = reduce_partials(part + 1, nb, 2, red);
+  const bool conv = rr <= sc->tol2;
+  const int it = iter + 1;
+  if (!conv && it < maxit) {
+    const float be = (float)(rz / sc->rho[parity]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; t + 3 * stride < n4; t += 4 * stride) {
+      float4 pv[4], zv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { pv[u] = p[t + u * stride]; zv[u] = z[t + u * stride]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) p[t + u * stride] = f4fma(be, pv[u], zv[u]);
+    }
+    for (; t < n4; t += stride) p[t] = f4fma(be, p[t], z[t]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->rho[parity ^ 1] = rz;
+    sc->rr = rr;
+    sc->iters = it;
+    if (conv || it >= maxit) sc->done = conv ? 1 : 2;
+  }
+}
+
+// FP64 refinement residual rho = b - (-K) lam = b + sum slots64 (interior), partial |rho|^2 and |b|^2
+__global__ void refine_residual_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_slot,
+                                       const int32_t* __restrict__ face_bnd, const double* __restrict__ zslot,
+                                       const double* __restrict__ b, double* __restrict__ rho,
+                                       double* __restrict__ part) {
+  __shared__ double red[8];
+  const int64_t n = nf * NF;
+  double rr = 0, bb = 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = t / NF;
+    const int mm = (int)(t % NF);
+    double v = 0.0;
+    if (face_bnd[f] < 0) {
+      const double bv = b[t];
+      v = bv + face_sum(face_slot, zslot, f, mm, NF);
+      bb += bv * bv;
+    }
+    rho[t] = v;
+    rr += v * v;
+  }
+  double s;
+  s = block_sum256(rr, red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 0] = s;
+  s = block_sum256(bb, red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
+}
+
+struct RefScal {
+  double rr, bb, scale;
+};
+
+__global__ void refine_scalars(int nb, const double* __restrict__ part, RefScal* rs) {
+  __shared__ double red[8];
+  const double rr = reduce_partials(part + 0, nb, 2, red);
+  const double bb = reduce_partials(part + 1, nb, 2, red);
+  if (threadIdx.x == 0) {
+    rs->rr = rr; rs->bb = bb;
+    rs->scale = rr > 0.0 ? 1.0 / sqrt(rr) : 1.0;
+  }
+}
+
+// b32 = rho * scale (inner right-hand side of unit norm)
+__global__ void to32_scaled_kernel(int64_t n, const double* __restrict__ rho, const RefScal* __restrict__ rs,
+                                   float* __restrict__ b32) {
+  const double s = rs->scale;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    b32[t] = (float)(rho[t] * s);
+}
+
+// lam += delta / scale on interior faces (delta is zero on boundary faces)
+__global__ void refine_update_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_bnd,
+                                     const float* __restrict__ delta, const RefScal* __restrict__ rs,
+                                     double* __restrict__ lam) {
+  const double inv = 1.0 / rs->scale;
+  const int64_t n = nf * NF;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    if (face_bnd[t / NF] < 0) lam[t] += (double)delta[t] * inv;
+}
+
+__global__ void to32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    b[t] = (float)a[t];
 }
 
 }  // namespace hdg

@@ -34,7 +34,8 @@ class Material(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32)]
+    _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32),
+                ("inner_rtol", c_double), ("max_sweeps", c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -51,7 +52,8 @@ class SolveInfo(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("kernel_launches", c_int64), ("apply_launches", c_int64), ("apply_ms", c_double)]
+    _fields_ = [("kernel_launches", c_int64), ("apply_launches", c_int64), ("apply_ms", c_double),
+                ("apply32_launches", c_int64), ("apply32_ms", c_double)]
 
 
 # exported entry points: name -> (restype, argtypes)
@@ -117,7 +119,7 @@ class Solver:
     """One HDG problem resident on the current CUDA device (wraps an hdg_ctx)."""
 
     def __init__(self, vert, elem, k, tau, rho, c, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
-                 stream=None):
+                 inner_rtol=None, max_sweeps=None, stream=None):
         import torch
         self.lib = load()
         self.torch = torch
@@ -132,6 +134,10 @@ class Solver:
         self.lib.hdg_default_options(ctypes.byref(opt))
         opt.prec = {"fp64": HDG_FP64, "mixed": HDG_MIXED}[prec]
         opt.rtol, opt.maxit, opt.check_every = rtol, maxit, check_every
+        if inner_rtol is not None:
+            opt.inner_rtol = inner_rtol
+        if max_sweeps is not None:
+            opt.max_sweeps = max_sweeps
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -260,7 +266,8 @@ class Solver:
     def hdg_get_stats(self, reset=False):
         st = Stats()
         self._check(self.lib.hdg_get_stats(self.ctx, ctypes.byref(st), 1 if reset else 0))
-        return {"kernel_launches": st.kernel_launches, "apply_launches": st.apply_launches, "apply_ms": st.apply_ms}
+        return {"kernel_launches": st.kernel_launches, "apply_launches": st.apply_launches, "apply_ms": st.apply_ms,
+                "apply32_launches": st.apply32_launches, "apply32_ms": st.apply32_ms}
 
     def hdg_step(self, dt, scheme, nsteps=1):
         info = SolveInfo()
