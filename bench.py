@@ -355,7 +355,7 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain FP64 comparison run that follows a mixed-precision measurement")
     ap.add_argument("--rtol", type=float, default=1e-12)
-    ap.add_argument("--inner-rtol", type=float, default=1e-5)
+    ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--N", type=int, default=32)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -91,7 +91,7 @@ typedef struct {
   double rel_residual;      /* final ||r|| / ||b|| of the trace system (FP64)         */
 } hdg_solve_info;
 
-/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-5, max_sweeps 20. */
+/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face

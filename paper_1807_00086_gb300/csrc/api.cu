@@ -476,7 +476,7 @@ void hdg_default_options(hdg_options* o) {
   o->rtol = 1e-13;
   o->maxit = 2000;
   o->check_every = 16;
-  o->inner_rtol = 1e-5;
+  o->inner_rtol = 1e-4;
   o->max_sweeps = 20;
 }
 
