@@ -175,14 +175,23 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    w = inputs.acoustic_3d_workload(N=args.N, k=args.k)
+    R = args.nrhs
+    if R > 1:
+        w = inputs.acoustic_3d_multisource_workload(N=args.N, k=args.k, nsrc=R)
+    else:
+        w = inputs.acoustic_3d_workload(N=args.N, k=args.k)
     ne = w["elem"].shape[0]
-    s = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=args.prec, rtol=args.rtol,
-                   inner_rtol=args.inner_rtol)
-    s.hdg_set_sources(w["sources"], [1.0], w["f0"], w["t0"])
-    s.hdg_set_dirichlet(None)
-    s.hdg_set_state(s.empty_fields(), 0.0)
-    dofs = ne * s.n
+
+    def make_solver(prec):
+        sv = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=prec, rtol=args.rtol,
+                        inner_rtol=args.inner_rtol, nrhs=R)
+        sv.hdg_set_sources(w["sources"], np.ones(len(w["sources"])), w["f0"], w["t0"], col=w.get("source_cols"))
+        sv.hdg_set_dirichlet(None)
+        sv.hdg_set_state(sv.empty_fields(), 0.0)
+        return sv
+
+    s = make_solver(args.prec)
+    dofs = ne * s.n * R
     stream = s.stream
     # warm-up (includes the condensation for alpha = 3/(2 dt))
     for _ in range(args.warmup):
@@ -218,9 +227,9 @@ def run_ours(args):
 
     # end to end through the public API with host buffers: the state (u^n, u^{n-1}) goes
     # host -> device, one step, and u^{n+1}, u^n come back device -> host, every step.
-    u_h = torch.empty((ne, s.n), dtype=torch.float64).pin_memory()
-    up_h = torch.empty((ne, s.n), dtype=torch.float64).pin_memory()
-    l_h = torch.empty((s.n_faces, s.Nf), dtype=torch.float64).pin_memory()
+    u_h = torch.empty(s._fshape, dtype=torch.float64).pin_memory()
+    up_h = torch.empty(s._fshape, dtype=torch.float64).pin_memory()
+    l_h = torch.empty(s._tshape, dtype=torch.float64).pin_memory()
     u_d, up_d, l_d = s.empty_fields(), s.empty_fields(), s.empty_traces()
     _, _, _, t_now = s.hdg_get_state(u=u_d, uprev=up_d, lam=l_d, want_prev=True)
     u_h.copy_(u_d)
@@ -228,7 +237,7 @@ def run_ours(args):
     l_h.copy_(l_d)
     torch.cuda.synchronize()
     barrier()
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = max(1, min(args.steps, 10 if R == 1 else 3))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with torch.cuda.stream(stream):
@@ -248,13 +257,28 @@ def run_ours(args):
     if dist is not None:
         dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
     e2e_value = world * dofs * e2e_steps / float(t_e.item())
-    field_bytes = ne * s.n * 8
-    trace_bytes = s.n_faces * s.Nf * 8
+    field_bytes = ne * s.n * R * 8
+    trace_bytes = s.n_faces * s.Nf * R * 8
 
     # roofline of the dominant kernel (matrix-free trace apply)
     peaks, src = load_peaks()
     m = s.m
     apply_avg_ms = st["apply_ms"] / max(1, st["apply_launches"])
+    if R > 1:
+        # multi-column apply: S_K read once per element, the R-column trace blocks gathered twice
+        # (once per neighbour) and the slot products written once
+        a32 = (st["apply32_ms"] / max(1, st["apply32_launches"])) if args.prec == "mixed" else apply_avg_ms
+        ebytes = 4 if args.prec == "mixed" else 8
+        sbytes = ((m * (m + 1) // 2 + 3) // 4) * 16 if args.prec == "mixed" else m * m * 8
+        bytes_el = sbytes + 2 * m * R * ebytes
+        ach = bytes_el * ne / (a32 / 1e3) / 1e9
+        peaks, src = load_peaks()
+        roof_multi = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                      "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                      "kernel": "apply_multi_kernel<3,3,%s> (%d columns)" % ("float" if args.prec == "mixed" else "double", R),
+                      "bytes_per_elem": bytes_el, "launch_ms": a32,
+                      "launches": st["apply32_launches"] if args.prec == "mixed" else st["apply_launches"],
+                      "flops_per_elem": 2 * m * m * R}
     fp64_view = {"kernel": "apply_kernel<3,3> (FP64 S_K x lambda_K)", "launches": st["apply_launches"],
                  "launch_ms": apply_avg_ms,
                  "achieved_tflops": 2 * m * m * ne / (apply_avg_ms / 1e3) / 1e12 if st["apply_launches"] else None,
@@ -284,9 +308,7 @@ def run_ours(args):
         u_mixed = s.hdg_get_state()[0]
         s.close()
         torch.cuda.empty_cache()
-        s64 = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec="fp64", rtol=args.rtol)
-        s64.hdg_set_sources(w["sources"], [1.0], w["f0"], w["t0"])
-        s64.hdg_set_state(s64.empty_fields(), 0.0)
+        s64 = make_solver("fp64")
         for _ in range(args.warmup):
             s64.hdg_step(DT, "bdf2", 1)
         torch.cuda.synchronize()
@@ -306,6 +328,9 @@ def run_ours(args):
                 "max_rel_diff_fields_after_%d_steps" % (args.warmup + args.steps + e2e_steps): rel}
         s64.close()
 
+    if R > 1:
+        roof = roof_multi
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = oracle_sample(budget_s=args.cpu_budget)
@@ -315,8 +340,9 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32+f64",
                "data": "synthetic",
-               "config": {"workload": "acoustic3d_k3_32cube_bdf2", "n_elem": ne, "k": args.k, "dofs": dofs,
-                          "trace_dofs": int(s.n_faces - s.n_bnd) * s.Nf, "dt": DT, "scheme": "BDF2",
+               "config": {"workload": "acoustic3d_k3_32cube_bdf2" + ("_%dsrc" % R if R > 1 else ""), "n_elem": ne,
+                          "k": args.k, "dofs": dofs, "nrhs": R,
+                          "trace_dofs": int(s.n_faces - s.n_bnd) * s.Nf * R, "dt": DT, "scheme": "BDF2",
                           "precision": args.prec, "rtol": args.rtol, "parallelism": "replicas",
                           "l2": "inputs larger than L2 (S_K %.2f GB)" % (ne * m * m * 8 / 1e9),
                           "krylov_iters_per_step": iters / args.steps,
@@ -358,6 +384,8 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--N", type=int, default=32)
     ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--nrhs", type=int, default=1,
+                    help="right-hand-side columns solved together (64: the multi-source workload)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="step", choices=["step", "apply"],

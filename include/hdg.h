@@ -76,6 +76,10 @@ typedef struct {
   int32_t check_every;      /* host polls the device convergence flag this often      */
   double inner_rtol;        /* MIXED: relative residual target of each FP32 solve     */
   int32_t max_sweeps;       /* MIXED: refinement sweep cap                            */
+  int32_t nrhs;             /* R independent right-hand sides (power of two, 1..256)  */
+                            /* solved together: every field and trace array below     */
+                            /* gains an innermost column index [..][R]; one read of    */
+                            /* each S_K serves all R columns                           */
 } hdg_options;
 
 typedef struct {
@@ -91,7 +95,7 @@ typedef struct {
   double rel_residual;      /* final ||r|| / ||b|| of the trace system (FP64)         */
 } hdg_solve_info;
 
-/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20. */
+/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face
@@ -138,9 +142,10 @@ hdg_status hdg_recover(hdg_ctx* ctx, const double* F_dev, const double* lam_dev,
 /* Data of the time-dependent problem. Point sources (pressure equation, Ricker wavelet
  * r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), amplitude amp_host[i]) at
  * positions pos_host [nsrc][dim]; each is attached to the lowest-id element containing
- * it. nsrc = 0 removes all sources. */
+ * it and acts on right-hand-side column col_host[i] (NULL: column 0). nsrc = 0 removes
+ * all sources. */
 hdg_status hdg_set_sources(hdg_ctx* ctx, int32_t nsrc, const double* pos_host, const double* amp_host,
-                           double f0, double t0);
+                           const int32_t* col_host, double f0, double t0);
 
 /* Physical coordinates of the projection quadrature points: which = 0 volume
  * ([n_elem][nq_vol][dim]), which = 1 boundary faces in face order ([n_bnd][nq_face][dim]). */

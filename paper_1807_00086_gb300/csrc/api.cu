@@ -13,6 +13,7 @@
 
 #include "../../include/hdg.h"
 #include "kernels.cuh"
+#include "multi.cuh"
 #include "mesh.h"
 #include "reftab.h"
 
@@ -53,6 +54,15 @@ struct hdg_ctx {
   int last_it32 = 16, last_it64 = 16;   // iteration counts of the previous solves (poll schedule)
   double *d_lam_prev = nullptr, *d_lam_x = nullptr;  // trace history for the extrapolated guess
   bool have_lam_prev = false;
+  // multiple right-hand sides (R columns, innermost index)
+  int R = 1;
+  double *d_mslot = nullptr;            // FP64 slots [ne][m][R]
+  float *d_mslot32 = nullptr;           // FP32 slots [ne][m][R]
+  double *d_mrho0 = nullptr, *d_mrho1 = nullptr, *d_malpha = nullptr, *d_mbeta = nullptr, *d_mrr = nullptr,
+         *d_mbb = nullptr, *d_mtol2 = nullptr, *d_mscale = nullptr, *d_mrr2 = nullptr, *d_mbb2 = nullptr;
+  int *d_mconv = nullptr, *d_mdone = nullptr, *d_mnconv = nullptr, *d_miters = nullptr;
+  int* h_mint = nullptr;                // pinned: [0] done flag, [1] nconv, [2] iterations
+  int32_t* d_src_col = nullptr;
   RefScal* d_rs = nullptr;
   RefScal* h_rs = nullptr;   // pinned
   // time state
@@ -239,6 +249,14 @@ void launch_face_q32(hdg_ctx* c) {
 }
 
 template <int DIM, int K>
+void launch_pack32m(hdg_ctx* c) {
+  using PK = Packed<DIM, K>;
+  const int64_t n = c->sk.ne * PK::P4 * 4;
+  c->n_launch += 1;
+  pack32m_kernel<DIM, K><<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->d_S, c->d_S32);
+}
+
+template <int DIM, int K>
 void launch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, int iter) {
   const int64_t ngroups = (c->sk.ne + 31) / 32;
   c->n_launch += 1;
@@ -256,7 +274,11 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
   hdg_status s = check_launch(c, "condense");
   if (s) return s;
   if (c->opt.prec == HDG_MIXED) {
-    HDG_DISPATCH(c, launch_pack32, c);
+    if (c->R > 1) {
+      HDG_DISPATCH(c, launch_pack32m, c);
+    } else {
+      HDG_DISPATCH(c, launch_pack32, c);
+    }
     const int64_t nfe = c->sk.nf * c->Nf;
     c->n_launch += 1;
     to32_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_dinv, c->d_dinv32);
@@ -417,6 +439,199 @@ hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* i
   return HDG_OK;
 }
 
+
+// ======================================================================= multiple right-hand sides
+MScal mscal(hdg_ctx* c) {
+  MScal m;
+  m.rho0 = c->d_mrho0; m.rho1 = c->d_mrho1; m.alpha = c->d_malpha; m.rr = c->d_mrr; m.bb = c->d_mbb;
+  m.tol2 = c->d_mtol2; m.conv = c->d_mconv; m.done = c->d_mdone; m.iters = c->d_miters;
+  return m;
+}
+
+template <int DIM, int K>
+void mlaunch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double src_rt, const double* lam, double* out) {
+  using L = LocalMultiCfg<DIM, K>;
+  dim3 grid((unsigned)c->sk.ne, (unsigned)((c->R + L::CW - 1) / L::CW));
+  const int32_t* sp = c->nsrc > 0 ? c->d_src_ptr : nullptr;
+  c->n_launch += 1;
+  if (mode == 0)
+    local_multi_kernel<DIM, K, 0><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, c->R, F,
+                                                                  hist, sp, c->d_src_phi, c->d_src_col, src_rt, lam, out);
+  else
+    local_multi_kernel<DIM, K, 1><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, c->R, F,
+                                                                  hist, sp, c->d_src_phi, c->d_src_col, src_rt, lam, out);
+}
+
+template <int DIM, int K, typename TV>
+void mlaunch_apply(hdg_ctx* c, const TV* x, TV* slot, const int* done, int iter) {
+  dim3 grid((unsigned)((c->sk.ne + 3) / 4), (unsigned)((c->R + 31) / 32));
+  c->n_launch += 1;
+  cudaEvent_t stop = apply_begin(c, sizeof(TV) == 4 ? 1 : 0, iter);
+  apply_multi_kernel<DIM, K, TV><<<grid, 128, 0, c->stream>>>(c->sk.ne, c->R, c->d_elem_face, c->d_face_bnd, c->d_S32,
+                                                              c->d_S, x, slot, done);
+  apply_end(c, stop);
+}
+template <int DIM, int K>
+void mlaunch_apply64(hdg_ctx* c, const double* x, double* slot, const int* done, int iter) {
+  mlaunch_apply<DIM, K, double>(c, x, slot, done, iter);
+}
+template <int DIM, int K>
+void mlaunch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, int iter) {
+  using AC = Apply32mCfg<DIM, K>;
+  const unsigned grid = (unsigned)((c->sk.ne + AC::EPB - 1) / AC::EPB);
+  c->n_launch += 1;
+  cudaEvent_t stop = apply_begin(c, 1, iter);
+  apply32m_kernel<DIM, K><<<grid, 256, 0, c->stream>>>(c->sk.ne, c->R, c->d_elem_face, c->d_face_bnd,
+                                                         (const float4*)c->d_S32, x, slot, done);
+  apply_end(c, stop);
+}
+
+template <int DIM, int K, typename TV>
+void mlaunch_face_q(hdg_ctx* c, const TV* slot, const TV* p, TV* q) {
+  mface_q_kernel<DIM, K, TV><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->R, c->d_face_slot, c->d_face_bnd, slot, p, q,
+                                                                c->d_part, c->d_mdone);
+}
+template <int DIM, int K>
+void mlaunch_face_q64(hdg_ctx* c, const double* slot, const double* p, double* q) { mlaunch_face_q<DIM, K, double>(c, slot, p, q); }
+template <int DIM, int K>
+void mlaunch_face_q32(hdg_ctx* c, const float* slot, const float* p, float* q) { mlaunch_face_q<DIM, K, float>(c, slot, p, q); }
+
+template <int DIM, int K, typename TV>
+void mlaunch_init(hdg_ctx* c, const TV* slot, const TV* b, const TV* dinv, TV* r, TV* z, TV* p) {
+  minit_kernel<DIM, K, TV><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->R, c->d_face_slot, c->d_face_bnd, slot, b, dinv,
+                                                              r, z, p, c->d_part);
+}
+template <int DIM, int K>
+void mlaunch_init64(hdg_ctx* c, const double* slot, const double* b, const double* dinv, double* r, double* z, double* p) {
+  mlaunch_init<DIM, K, double>(c, slot, b, dinv, r, z, p);
+}
+template <int DIM, int K>
+void mlaunch_init32(hdg_ctx* c, const float* slot, const float* b, const float* dinv, float* r, float* z, float* p) {
+  mlaunch_init<DIM, K, float>(c, slot, b, dinv, r, z, p);
+}
+
+template <int DIM, int K>
+void mlaunch_gather(hdg_ctx* c, const double* slot, double scale, double* out) {
+  const int64_t n = c->sk.nf * c->Nf * (int64_t)c->R;
+  c->n_launch += 1;
+  mface_gather_kernel<DIM, K><<<grid_for(c, n), 256, 0, c->stream>>>((int)c->sk.nf, c->R, c->d_face_slot, c->d_face_bnd, slot,
+                                                                     scale, out);
+}
+
+template <int DIM, int K>
+void mlaunch_refres(hdg_ctx* c, const double* b) {
+  c->n_launch += 2;
+  mrefine_residual_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->R, c->d_face_slot, c->d_face_bnd,
+                                                                     c->d_mslot, b, c->d_res, c->d_part);
+  mrefine_scalars<<<1, 256, 0, c->stream>>>(c->nb_red, c->R, c->opt.rtol, c->d_part, c->d_mrr2, c->d_mbb2, c->d_mscale,
+                                            c->d_mnconv);
+}
+
+// Per-column PCG on (-K) x = b. FP64 (outer, x holds the initial guess) or FP32 (inner, x0 = 0).
+template <typename TV>
+hdg_status mcg(hdg_ctx* c, const TV* b, TV* x, TV* r, TV* z, TV* p, TV* q, TV* slot, const TV* dinv, double rtol,
+               bool x0_zero, int* iters_out) {
+  const int64_t n = c->sk.nf * c->Nf * (int64_t)c->R;
+  const int nb = c->nb_red;
+  hdg_status s;
+  if (x0_zero) {
+    CUDA_TRY(c, cudaMemsetAsync(x, 0, (size_t)n * sizeof(TV), c->stream));
+  } else {
+    if (sizeof(TV) == 8) {
+      HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)x, (double*)slot, (const int*)nullptr, -1);
+    }
+  }
+  c->n_launch += 2;
+  if (sizeof(TV) == 8) {
+    HDG_DISPATCH(c, mlaunch_init64, c, x0_zero ? nullptr : (const double*)slot, (const double*)b, (const double*)dinv,
+                 (double*)r, (double*)z, (double*)p);
+  } else {
+    HDG_DISPATCH(c, mlaunch_init32, c, nullptr, (const float*)b, (const float*)dinv, (float*)r, (float*)z, (float*)p);
+  }
+  mcols_init<<<1, 256, 0, c->stream>>>(nb, c->R, rtol, x0_zero ? 1 : 0, c->d_part, mscal(c));
+  if ((s = check_launch(c, "mcg_init"))) return s;
+  const int maxit = c->opt.maxit;
+  const int chk = std::max(1, c->opt.check_every);
+  int& last = sizeof(TV) == 4 ? c->last_it32 : c->last_it64;
+  const int first = std::max(2, std::min(chk, last - 1));
+  int it = 0;
+  c->h_mint[0] = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_mint, c->d_mdone, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  while (!c->h_mint[0] && it < maxit) {
+    const int upto = std::min(maxit, it + (it == 0 ? first : std::min(chk, 3)));
+    for (; it < upto; ++it) {
+      const int par = it & 1;
+      c->n_launch += 5;
+      if (sizeof(TV) == 8) {
+        HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)p, (double*)slot, c->d_mdone, it);
+        HDG_DISPATCH(c, mlaunch_face_q64, c, (const double*)slot, (const double*)p, (double*)q);
+      } else {
+        HDG_DISPATCH(c, mlaunch_apply32, c, (const float*)p, (float*)slot, c->d_mdone, it);
+        HDG_DISPATCH(c, mlaunch_face_q32, c, (const float*)slot, (const float*)p, (float*)q);
+      }
+      mcols_alpha<<<1, 256, 0, c->stream>>>(nb, c->R, par, c->d_part, mscal(c));
+      mupdate_kernel<TV><<<nb, 256, 0, c->stream>>>(n, c->R, p, q, dinv, x, r, z, c->d_part, mscal(c));
+      mcols_beta<<<1, 256, 0, c->stream>>>(nb, c->R, par, it, maxit, c->d_part, mscal(c), c->d_mbeta);
+      mdirection_kernel<TV><<<nb, 256, 0, c->stream>>>(n, c->R, z, p, c->d_mbeta, c->d_mdone);
+    }
+    if ((s = check_launch(c, "mcg_iter"))) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_mint, c->d_mdone, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_mint + 2, c->d_miters, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    harvest(c, c->h_mint[0] ? c->h_mint[2] : (1 << 30));
+  }
+  *iters_out = c->h_mint[2];
+  last = std::max(1, c->h_mint[2]);
+  if (c->h_mint[0] == 0 || c->h_mint[0] == 2) return fail(c, HDG_ENOCONV, "multi-column Krylov solve reached maxit");
+  return HDG_OK;
+}
+
+hdg_status msolve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) {
+  const int64_t n = c->sk.nf * c->Nf * (int64_t)c->R;
+  hdg_status s;
+  if (c->opt.prec == HDG_FP64) {
+    int it = 0;
+    if ((s = mcg<double>(c, b, x, c->d_r, c->d_z, c->d_p, c->d_q, c->d_mslot, c->d_dinv, c->opt.rtol, false, &it))) return s;
+    std::vector<double> rr(c->R), bb(c->R);
+    CUDA_TRY(c, cudaMemcpy(rr.data(), c->d_mrr, c->R * 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(bb.data(), c->d_mbb, c->R * 8, cudaMemcpyDeviceToHost));
+    double worst = 0.0;
+    for (int j = 0; j < c->R; ++j) worst = std::max(worst, bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0);
+    if (info) { info->iterations += it; info->sweeps += 1; info->rel_residual = std::max(info->rel_residual, worst); }
+    return HDG_OK;
+  }
+  int total = 0;
+  for (int sweep = 0;; ++sweep) {
+    HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)x, c->d_mslot, (const int*)nullptr, -1);
+    HDG_DISPATCH(c, mlaunch_refres, c, b);
+    if ((s = check_launch(c, "mrefine_residual"))) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_mint + 1, c->d_mnconv, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    harvest(c);
+    if (c->h_mint[1] == 0 || sweep >= c->opt.max_sweeps) {
+      std::vector<double> rr(c->R), bb(c->R);
+      CUDA_TRY(c, cudaMemcpy(rr.data(), c->d_mrr2, c->R * 8, cudaMemcpyDeviceToHost));
+      CUDA_TRY(c, cudaMemcpy(bb.data(), c->d_mbb2, c->R * 8, cudaMemcpyDeviceToHost));
+      double worst = 0.0;
+      for (int j = 0; j < c->R; ++j) worst = std::max(worst, bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0);
+      if (info) { info->iterations += total; info->sweeps += sweep; info->rel_residual = std::max(info->rel_residual, worst); }
+      if (c->h_mint[1] != 0) return fail(c, HDG_ENOCONV, "multi-column refinement reached max_sweeps");
+      return HDG_OK;
+    }
+    c->n_launch += 1;
+    mto32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->R, c->d_res, c->d_mscale, c->d_b32);
+    int it = 0;
+    if ((s = mcg<float>(c, c->d_b32, c->d_x32, c->d_r32, c->d_z32, c->d_p32, c->d_q32, c->d_mslot32, c->d_dinv32,
+                        c->opt.inner_rtol, true, &it)))
+      if (s != HDG_ENOCONV) return s;
+    total += it;
+    c->n_launch += 1;
+    mrefine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->R, c->Nf, c->d_face_bnd, c->d_x32, c->d_mscale, x);
+    if ((s = check_launch(c, "mrefine_update"))) return s;
+  }
+}
+
 double ricker(double t, double f0, double t0) {
   const double pi = 3.14159265358979323846;
   const double a = (pi * f0 * (t - t0)) * (pi * f0 * (t - t0));
@@ -426,6 +641,20 @@ double ricker(double t, double f0, double t0) {
 // one implicit solve at mass shift alpha: alpha Mw u + f(u, lam, t) = alpha Mw hist
 hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info) {
   const double fac = std::cos(c->omega * tt + c->phase);
+  if (c->R > 1) {
+    const int64_t nbe = c->sk.nb * c->Nf * (int64_t)c->R;
+    c->n_launch += 1;
+    mdirichlet_kernel<<<grid_for(c, nbe), 256, 0, c->stream>>>(c->sk.nb, c->Nf, c->R, c->d_bnd_faces, c->d_bnd_coef, fac,
+                                                              c->d_lam);
+    const double rt = c->nsrc > 0 ? ricker(tt, c->f0, c->t0) : 0.0;
+    HDG_DISPATCH(c, mlaunch_local, c, 0, (const double*)nullptr, hist, rt, c->d_lam, c->d_mslot);
+    HDG_DISPATCH(c, mlaunch_gather, c, (const double*)c->d_mslot, 1.0, c->d_b);
+    hdg_status s = check_launch(c, "rhs_multi");
+    if (s) return s;
+    if ((s = msolve(c, c->d_b, c->d_lam, info))) return s;
+    HDG_DISPATCH(c, mlaunch_local, c, 1, (const double*)nullptr, hist, rt, c->d_lam, uout);
+    return check_launch(c, "recover_multi");
+  }
   c->n_launch += 1;
   dirichlet_kernel<<<grid_for(c, c->sk.nb * c->Nf), 256, 0, c->stream>>>(c->sk.nb, c->Nf, c->d_bnd_faces, c->d_bnd_coef, fac,
                                                                          c->d_lam);
@@ -446,7 +675,7 @@ hdg_status ensure_alpha(hdg_ctx* c, double alpha) {
 
 void combine(hdg_ctx* c, double* out, double c0, const double* i0, double c1 = 0, const double* i1 = nullptr,
              double c2 = 0, const double* i2 = nullptr, double c3 = 0, const double* i3 = nullptr) {
-  const int64_t n = c->sk.ne * c->n;
+  const int64_t n = c->sk.ne * c->n * (int64_t)c->R;
   c->n_launch += 1;
   combine_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c0, i0, c1, i1, c2, i2, c3, i3, out);
 }
@@ -478,6 +707,7 @@ void hdg_default_options(hdg_options* o) {
   o->check_every = 16;
   o->inner_rtol = 1e-4;
   o->max_sweeps = 20;
+  o->nrhs = 1;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -488,6 +718,7 @@ void hdg_destroy(hdg_ctx* c) {
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
   if (c->h_rs) cudaFreeHost(c->h_rs);
+  if (c->h_mint) cudaFreeHost(c->h_mint);
   delete c;
 }
 
@@ -507,6 +738,9 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if (!(c->opt.rtol > 0.0) || c->opt.maxit < 1) return fail(c, HDG_EINVAL, "rtol must be > 0 and maxit >= 1");
   if (c->opt.prec == HDG_MIXED && (!(c->opt.inner_rtol > 0.0) || !(c->opt.inner_rtol < 1.0) || c->opt.max_sweeps < 1))
     return fail(c, HDG_EINVAL, "mixed precision needs 0 < inner_rtol < 1 and max_sweeps >= 1");
+  if (c->opt.nrhs < 1 || c->opt.nrhs > 256 || (c->opt.nrhs & (c->opt.nrhs - 1)))
+    return fail(c, HDG_EINVAL, "nrhs must be a power of two in 1..256");
+  c->R = c->opt.nrhs;
   std::string err;
   if (!build_skeleton(mesh->dim, mesh->n_vert, mesh->n_elem, mesh->vert, mesh->elem_vert, c->sk, err))
     return fail(c, HDG_EINVAL, err);
@@ -568,36 +802,52 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   CUDA_TRY(c, cudaMemcpyAsync(c->d_qv_phi, c->T.qv_phi.data(), c->T.qv_phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
   // condensed operators and workspaces
   const size_t nfe = (size_t)nf * c->Nf;
+  const size_t R = (size_t)c->R;
   if ((s = dalloc(c, &c->d_S, (size_t)ne * c->m * c->m))) return s;
   if ((s = dalloc(c, &c->d_Hinv, (size_t)ne * c->Np * c->Np))) return s;
   if ((s = dalloc(c, &c->d_dinv, nfe))) return s;
   if ((s = dalloc(c, &c->d_err, 1))) return s;
   for (double** p : {&c->d_r, &c->d_z, &c->d_p, &c->d_q, &c->d_b, &c->d_lam, &c->d_lam_prev, &c->d_lam_x})
-    if ((s = dalloc(c, p, nfe))) return s;
+    if ((s = dalloc(c, p, nfe * R))) return s;
   if ((s = dalloc(c, &c->d_slot, (size_t)ne * std::max(c->m, 1)))) return s;
-  if ((s = dalloc(c, &c->d_part, (size_t)c->nb_red * 3))) return s;
+  if ((s = dalloc(c, &c->d_part, (size_t)c->nb_red * 3 * R))) return s;
+  if (c->R > 1) {
+    if ((s = dalloc(c, &c->d_mslot, (size_t)ne * c->m * R))) return s;
+    for (double** p : {&c->d_mrho0, &c->d_mrho1, &c->d_malpha, &c->d_mbeta, &c->d_mrr, &c->d_mbb, &c->d_mtol2, &c->d_mscale,
+                       &c->d_mrr2, &c->d_mbb2})
+      if ((s = dalloc(c, p, R))) return s;
+    if ((s = dalloc(c, &c->d_mconv, R))) return s;
+    if ((s = dalloc(c, &c->d_mdone, 1))) return s;
+    if ((s = dalloc(c, &c->d_mnconv, 1))) return s;
+    if ((s = dalloc(c, &c->d_miters, 1))) return s;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_mdone, 0, sizeof(int), c->stream));
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_mint, 4 * sizeof(int)));
+  }
   if ((s = dalloc(c, &c->d_sc, 1))) return s;
   CUDA_TRY(c, cudaMallocHost((void**)&c->h_sc, sizeof(CgScal)));
   std::memset(c->h_sc, 0, sizeof(CgScal));
   for (double** p : {&c->d_u, &c->d_uprev, &c->d_h, &c->d_unew, &c->d_stage[0], &c->d_stage[1], &c->d_stage[2]})
-    if ((s = dalloc(c, p, (size_t)ne * c->n))) return s;
+    if ((s = dalloc(c, p, (size_t)ne * c->n * R))) return s;
   if (c->opt.prec == HDG_MIXED) {
     const int64_t ngroups = (ne + 31) / 32;
     const int P4 = (c->m * (c->m + 1) / 2 + 3) / 4;
     if ((s = dalloc(c, &c->d_S32, (size_t)ngroups * P4 * 128))) return s;
     if ((s = dalloc(c, &c->d_slot32, (size_t)ngroups * c->m * 32))) return s;
     c->nfe4 = (int64_t)((nfe + 3) / 4) * 4;
+    const size_t n32 = c->R > 1 ? nfe * R : (size_t)c->nfe4;
     for (float** p : {&c->d_dinv32, &c->d_r32, &c->d_z32, &c->d_p32, &c->d_q32, &c->d_x32, &c->d_b32}) {
-      if ((s = dalloc(c, p, (size_t)c->nfe4))) return s;
-      CUDA_TRY(c, cudaMemsetAsync(*p, 0, (size_t)c->nfe4 * 4, c->stream));
+      const size_t cnt = p == &c->d_dinv32 ? (size_t)c->nfe4 : n32;
+      if ((s = dalloc(c, p, cnt))) return s;
+      CUDA_TRY(c, cudaMemsetAsync(*p, 0, cnt * 4, c->stream));
     }
-    if ((s = dalloc(c, &c->d_res, nfe))) return s;
+    if (c->R > 1 && (s = dalloc(c, &c->d_mslot32, (size_t)ne * c->m * R))) return s;
+    if ((s = dalloc(c, &c->d_res, nfe * R))) return s;
     if ((s = dalloc(c, &c->d_rs, 1))) return s;
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_rs, sizeof(RefScal)));
   }
-  CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, nfe * 8, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(c->d_u, 0, (size_t)ne * c->n * 8, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(c->d_uprev, 0, (size_t)ne * c->n * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, nfe * R * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_u, 0, (size_t)ne * c->n * R * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_uprev, 0, (size_t)ne * c->n * R * 8, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->have_state = true;
   return HDG_OK;
@@ -627,6 +877,11 @@ hdg_status hdg_get_schur(hdg_ctx* c, double* S_dev) {
 hdg_status hdg_trace_apply(hdg_ctx* c, const double* x, double* y) {
   if (!c || !x || !y) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  if (c->R > 1) {
+    HDG_DISPATCH(c, mlaunch_apply64, c, x, c->d_mslot, (const int*)nullptr, -1);
+    HDG_DISPATCH(c, mlaunch_gather, c, (const double*)c->d_mslot, 1.0, y);
+    return check_launch(c, "apply_multi");
+  }
   HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
   hdg_status s = check_launch(c, "apply");
   if (s) return s;
@@ -636,6 +891,11 @@ hdg_status hdg_trace_apply(hdg_ctx* c, const double* x, double* y) {
 hdg_status hdg_condensed_rhs(hdg_ctx* c, const double* F, const double* lamD, double* r) {
   if (!c || !F || !r) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  if (c->R > 1) {
+    HDG_DISPATCH(c, mlaunch_local, c, 0, F, (const double*)nullptr, 0.0, lamD, c->d_mslot);
+    HDG_DISPATCH(c, mlaunch_gather, c, (const double*)c->d_mslot, -1.0, r);
+    return check_launch(c, "condensed_rhs_multi");
+  }
   HDG_DISPATCH(c, launch_local, c, 0, F, (const double*)nullptr, 0.0, lamD, c->d_slot);
   hdg_status s = check_launch(c, "condensed_rhs");
   if (s) return s;
@@ -647,24 +907,36 @@ hdg_status hdg_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_i
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
   if (info) { info->iterations = 0; info->sweeps = 0; info->rel_residual = 0; }
   // K lam = r  <=>  (-K) lam = -r
-  const int64_t nfe = c->sk.nf * c->Nf;
+  const int64_t nfe = c->sk.nf * c->Nf * (int64_t)c->R;
   combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, -1.0, r, 0, nullptr, 0, nullptr, 0, nullptr, c->d_b);
   hdg_status s = check_launch(c, "negate");
   if (s) return s;
+  if (c->R > 1) {
+    if ((s = msolve(c, c->d_b, lam, info))) return s;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return HDG_OK;
+  }
   return cg_solve(c, c->d_b, lam, info);
 }
 
 hdg_status hdg_recover(hdg_ctx* c, const double* F, const double* lam, double* u) {
   if (!c || !F || !lam || !u) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  if (c->R > 1) {
+    HDG_DISPATCH(c, mlaunch_local, c, 1, F, (const double*)nullptr, 0.0, lam, u);
+    return check_launch(c, "recover_multi");
+  }
   HDG_DISPATCH(c, launch_local, c, 1, F, (const double*)nullptr, 0.0, lam, u);
   return check_launch(c, "recover");
 }
 
-hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const double* amp, double f0, double t0) {
+hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const double* amp, const int32_t* col,
+                           double f0, double t0) {
   if (!c || nsrc < 0 || (nsrc > 0 && (!pos || !amp))) return fail(c, HDG_EINVAL, "bad source arguments");
-  dfree(c, c->d_src_ptr); dfree(c, c->d_src_phi);
-  c->d_src_ptr = nullptr; c->d_src_phi = nullptr; c->nsrc = 0;
+  for (int s2 = 0; col && s2 < nsrc; ++s2)
+    if (col[s2] < 0 || col[s2] >= c->R) return fail(c, HDG_EINVAL, "source column out of range");
+  dfree(c, c->d_src_ptr); dfree(c, c->d_src_phi); dfree(c, c->d_src_col);
+  c->d_src_ptr = nullptr; c->d_src_phi = nullptr; c->d_src_col = nullptr; c->nsrc = 0;
   if (nsrc == 0) return HDG_OK;
   const int d = c->dim, nc = c->nfc, Np = c->Np;
   const int64_t ne = c->sk.ne;
@@ -692,9 +964,11 @@ hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const do
   std::stable_sort(owner.begin(), owner.end());
   std::vector<int32_t> ptr(ne + 1, 0);
   std::vector<double> phi((size_t)nsrc * Np);
+  std::vector<int32_t> cols(nsrc, 0);
   for (size_t i = 0; i < owner.size(); ++i) {
     ptr[owner[i].first + 1]++;
     const int s = owner[i].second;
+    cols[i] = col ? col[s] : 0;
     dubiner(d, c->k, &xi_all[(size_t)s * d], 1, &phi[i * Np], nullptr);
     for (int q = 0; q < Np; ++q) phi[i * Np + q] *= amp[s];
   }
@@ -702,6 +976,8 @@ hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const do
   hdg_status st;
   if ((st = dalloc(c, &c->d_src_ptr, (size_t)ne + 1))) return st;
   if ((st = dalloc(c, &c->d_src_phi, phi.size()))) return st;
+  if ((st = dalloc(c, &c->d_src_col, cols.size()))) return st;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_src_col, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_src_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_src_phi, phi.data(), phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -752,8 +1028,13 @@ hdg_status hdg_project_volume(hdg_ctx* c, const double* vals, double* u) {
   if ((s = dalloc(c, &dv, cnt))) return s;
   cudaError_t e1 = cudaMemcpyAsync(dv, vals, cnt * 8, cudaMemcpyHostToDevice, c->stream);
   if (e1 == cudaSuccess) {
-    const int64_t n = c->sk.ne * c->n;
-    project_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->nfc, c->d_qv_w, c->d_qv_phi, dv, u);
+    const int64_t n = c->sk.ne * c->n * (int64_t)c->R;
+    if (c->R > 1)
+      mproject_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->nfc, c->R, c->d_qv_w,
+                                                                   c->d_qv_phi, dv, u);
+    else
+      project_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->nfc, c->d_qv_w, c->d_qv_phi,
+                                                                  dv, u);
     e1 = cudaGetLastError();
   }
   if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(c->stream);
@@ -787,13 +1068,14 @@ hdg_status hdg_set_dirichlet(hdg_ctx* c, const double* vals, double omega, doubl
 
 hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const double* lam, double t) {
   if (!c || !u) return fail(c, HDG_EINVAL, "null argument");
-  const size_t bytes = (size_t)c->sk.ne * c->n * 8;
+  const size_t bytes = (size_t)c->sk.ne * c->n * c->R * 8;
+  const size_t tbytes = (size_t)c->sk.nf * c->Nf * c->R * 8;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_u, u, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_uprev, uprev ? uprev : u, bytes, cudaMemcpyDeviceToDevice, c->stream));
   if (lam)
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_lam, lam, (size_t)c->sk.nf * c->Nf * 8, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_lam, lam, tbytes, cudaMemcpyDeviceToDevice, c->stream));
   else
-    CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, (size_t)c->sk.nf * c->Nf * 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, tbytes, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->t = t;
   c->have_state = true;
@@ -803,10 +1085,10 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
 
 hdg_status hdg_get_state(hdg_ctx* c, double* u, double* uprev, double* lam, double* t) {
   if (!c) return HDG_EINVAL;
-  const size_t bytes = (size_t)c->sk.ne * c->n * 8;
+  const size_t bytes = (size_t)c->sk.ne * c->n * c->R * 8;
   if (u) CUDA_TRY(c, cudaMemcpyAsync(u, c->d_u, bytes, cudaMemcpyDeviceToDevice, c->stream));
   if (uprev) CUDA_TRY(c, cudaMemcpyAsync(uprev, c->d_uprev, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  if (lam) CUDA_TRY(c, cudaMemcpyAsync(lam, c->d_lam, (size_t)c->sk.nf * c->Nf * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (lam) CUDA_TRY(c, cudaMemcpyAsync(lam, c->d_lam, (size_t)c->sk.nf * c->Nf * c->R * 8, cudaMemcpyDeviceToDevice, c->stream));
   if (t) *t = c->t;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return HDG_OK;
@@ -833,7 +1115,7 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
       }
       if ((s = ensure_alpha(c, alpha))) return s;
       // initial guess of the trace solve: 2 lam^n - lam^{n-1} (lam^n alone on the first step)
-      const int64_t nfe = c->sk.nf * c->Nf;
+      const int64_t nfe = c->sk.nf * c->Nf * (int64_t)c->R;
       if (c->have_lam_prev) {
         c->n_launch += 1;
         combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, 2.0, c->d_lam, -1.0, c->d_lam_prev, 0, nullptr, 0,

@@ -1,0 +1,620 @@
+// Multi-right-hand-side kernels: R columns (R a power of two, 2..256) share every S_K,
+// H^{-1} and table read. Layouts put the column index innermost:
+//   fields [n_elem][n][R], traces and Krylov vectors [n_faces][Nf][R], slots [n_elem][m][R].
+// Each column is an independent problem (its own sources and Krylov recurrence); the
+// operators are the same as in the single-column kernels of kernels.cuh.
+#pragma once
+#include "kernels.cuh"
+
+namespace hdg {
+
+// ------------------------------------------------------------------ element-local solves, R columns
+// CTA = one element x CW columns x NP rows; warp = one row over 32 columns, so table,
+// geometry and H^{-1} reads are warp-uniform and field reads are coalesced along columns.
+template <int DIM, int K>
+struct LocalMultiCfg {
+  static constexpr int NP = Dims<DIM, K>::NP;
+  static constexpr int CW = NP <= 32 ? 32 : 16;
+  static constexpr int NT = NP * CW;
+};
+
+template <int DIM, int K, int MODE>
+__global__ void __launch_bounds__(LocalMultiCfg<DIM, K>::NT)
+    local_multi_kernel(DevMesh mesh, Tabs T, const double* __restrict__ Hinv, double alpha, double tau, int R,
+                       const double* __restrict__ F, const double* __restrict__ hist, const int32_t* __restrict__ src_ptr,
+                       const double* __restrict__ src_phi, const int32_t* __restrict__ src_col, double src_rt,
+                       const double* __restrict__ lam, double* __restrict__ out) {
+  using D = Dims<DIM, K>;
+  using L = LocalMultiCfg<DIM, K>;
+  constexpr int NP = D::NP, NF = D::NF, M = D::M, NFC = D::NFC, N = D::N, CW = L::CW;
+  __shared__ double g[GEO_STRIDE];
+  __shared__ double Tr[DIM * NP][CW];
+  __shared__ double rp[NP][CW];
+  __shared__ double pp[NP][CW];
+  __shared__ double ll[M][CW];
+  __shared__ int fuse[NFC];
+  const int64_t e = blockIdx.x;
+  const int jl = threadIdx.x % CW, i = threadIdx.x / CW;
+  const int j = blockIdx.y * CW + jl;
+  const bool col = j < R;
+  if (threadIdx.x < GEO_STRIDE) g[threadIdx.x] = mesh.geo[e * GEO_STRIDE + threadIdx.x];
+  if (threadIdx.x < NFC) {
+    int use = 0;
+    if (lam) {
+      const int f = mesh.elem_face[e * NFC + threadIdx.x];
+      use = (MODE == 1) || (mesh.face_bnd[f] >= 0);
+    }
+    fuse[threadIdx.x] = use;
+  }
+  for (int t = threadIdx.x; t < M * CW; t += L::NT) {
+    const int r = t / CW, jj = blockIdx.y * CW + t % CW;
+    double v = 0.0;
+    if (lam && jj < R) {
+      const int f = mesh.elem_face[e * NFC + r / NF];
+      if ((MODE == 1) || (mesh.face_bnd[f] >= 0)) v = lam[((int64_t)f * NF + r % NF) * R + jj];
+    }
+    ll[r][t % CW] = v;
+  }
+  __syncthreads();
+  const double dJ = g[0];
+  const double rho = mesh.rho[e], cc = mesh.c[e];
+  const double b = alpha * rho;
+  double Fu[DIM + 1];
+  {
+    double Fl[NFC];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      double s = 0.0;
+      if (fuse[f])
+        for (int mm = 0; mm < NF; ++mm) s += T.Ff[(f * NP + i) * NF + mm] * ll[f * NF + mm][jl];
+      Fl[f] = s;
+    }
+#pragma unroll
+    for (int comp = 0; comp <= DIM; ++comp) {
+      double v = 0.0;
+      if (col) {
+        const int64_t idx = (e * N + comp * NP + i) * R + j;
+        if (hist) {
+          v = (comp == 0 ? alpha * dJ / (rho * cc * cc) : b * dJ) * hist[idx];
+          if (comp == 0 && src_ptr)
+            for (int q = src_ptr[e]; q < src_ptr[e + 1]; ++q)
+              if (src_col[q] == j) v += src_rt * src_phi[(int64_t)q * NP + i];
+        } else {
+          v = F[idx];
+        }
+      }
+      double bl = 0.0;
+      if (comp == 0) {
+#pragma unroll
+        for (int f = 0; f < NFC; ++f) bl += g[D::OJF + f] * Fl[f];
+        v += tau * bl;
+      } else {
+#pragma unroll
+        for (int f = 0; f < NFC; ++f) bl += g[D::ON + f * DIM + comp - 1] * g[D::OJF + f] * Fl[f];
+        v -= bl;
+      }
+      Fu[comp] = v;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) {
+    double s = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < DIM; ++jj) s += g[1 + r * DIM + jj] * Fu[jj + 1];
+    Tr[r * NP + i][jl] = s;
+  }
+  __syncthreads();
+  {
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+      for (int l = 0; l < NP; ++l) s += T.Dr[(r * NP + i) * NP + l] * Tr[r * NP + l][jl];
+    rp[i][jl] = Fu[0] - s / b;
+  }
+  __syncthreads();
+  {
+    const double* He = Hinv + e * (int64_t)(NP * NP);
+    double s = 0.0;
+    for (int l = 0; l < NP; ++l) s += He[i * NP + l] * rp[l][jl];
+    pp[i][jl] = s;
+  }
+  __syncthreads();
+  double vv[DIM];
+  {
+    double qd[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      double s = 0.0;
+      for (int l = 0; l < NP; ++l) s += T.Dr[(r * NP + l) * NP + i] * pp[l][jl];
+      qd[r] = s;
+    }
+#pragma unroll
+    for (int jj = 0; jj < DIM; ++jj) {
+      double s = 0.0;
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) s += g[1 + r * DIM + jj] * qd[r];
+      vv[jj] = Fu[jj + 1] / (b * dJ) + s / b;
+    }
+  }
+  if (MODE == 1) {
+    if (col) {
+      out[(e * N + i) * R + j] = pp[i][jl];
+#pragma unroll
+      for (int jj = 0; jj < DIM; ++jj) out[(e * N + (jj + 1) * NP + i) * R + j] = vv[jj];
+    }
+    return;
+  }
+  __syncthreads();   // all reads of Tr done: reuse it (and rp) for the face weights
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    double s = tau * pp[i][jl];
+#pragma unroll
+    for (int jj = 0; jj < DIM; ++jj) s += g[D::ON + f * DIM + jj] * vv[jj];
+    if (f < DIM) Tr[f * NP + i][jl] = s;
+    else rp[i][jl] = s;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < M * CW; t += L::NT) {
+    const int r = t / CW, jj2 = t % CW, f = r / NF, mm = r % NF;
+    const int jc = blockIdx.y * CW + jj2;
+    if (jc >= R) continue;
+    double s = 0.0;
+    for (int q = 0; q < NP; ++q) s += T.Ff[(f * NP + q) * NF + mm] * (f < DIM ? Tr[f * NP + q][jj2] : rp[q][jj2]);
+    out[(e * M + r) * R + jc] = g[D::OJF + f] * s;
+  }
+}
+
+// ------------------------------------------------------------------ trace apply, R columns
+// warp = (element, 32-column group); lane = column. S_K entries are warp-uniform loads.
+// FP32: S from the packed group layout of pack32_kernel. FP64: S from [e][M][M].
+template <int DIM, int K, typename TV>
+__global__ void __launch_bounds__(128) apply_multi_kernel(int64_t ne, int R, const int32_t* __restrict__ elem_face,
+                                                          const int32_t* __restrict__ face_bnd,
+                                                          const float* __restrict__ S32, const double* __restrict__ S64,
+                                                          const TV* __restrict__ x, TV* __restrict__ slot,
+                                                          const int* __restrict__ done) {
+  using Dm = Dims<DIM, K>;
+  using PK = Packed<DIM, K>;
+  constexpr int NF = Dm::NF, M = Dm::M, NFC = Dm::NFC, P4 = PK::P4;
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int j = blockIdx.y * 32 + lane;
+  if (e >= ne) return;
+  const bool col = j < R;
+  TV xl[M], y[M];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    const int fid = elem_face[e * NFC + f];
+    const bool use = face_bnd[fid] < 0 && col;
+#pragma unroll
+    for (int mm = 0; mm < NF; ++mm) xl[f * NF + mm] = use ? x[((int64_t)fid * NF + mm) * R + j] : TV(0);
+  }
+#pragma unroll
+  for (int r = 0; r < M; ++r) y[r] = TV(0);
+  if constexpr (sizeof(TV) == 4) {
+    const float4* Sg = reinterpret_cast<const float4*>(S32) + (e >> 5) * (int64_t)P4 * 32 + (e & 31);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+#pragma unroll
+      for (int c = r; c < M; ++c) {
+        const int p = packed_index(M, r, c);
+        if ((p & 3) == 0) v = Sg[(p >> 2) * 32];
+        const float s = (p & 3) == 0 ? v.x : (p & 3) == 1 ? v.y : (p & 3) == 2 ? v.z : v.w;
+        y[r] = fmaf(s, xl[c], y[r]);
+        if (c != r) y[c] = fmaf(s, xl[r], y[c]);
+      }
+    }
+  } else {
+    const double* Se = S64 + e * (int64_t)(M * M);
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+#pragma unroll
+      for (int c = r; c < M; ++c) {
+        const double s = Se[r * M + c];
+        y[r] += s * xl[c];
+        if (c != r) y[c] += s * xl[r];
+      }
+    }
+  }
+  if (col) {
+#pragma unroll
+    for (int r = 0; r < M; ++r) slot[(e * M + r) * R + j] = y[r];
+  }
+}
+
+// FP32 S for the multi-column path: element-major packed upper triangles [e][P4] float4, so a
+// CTA streams its elements' blocks contiguously into shared memory.
+template <int DIM, int K>
+__global__ void pack32m_kernel(int64_t ne, const double* __restrict__ S, float* __restrict__ S32m) {
+  using PK = Packed<DIM, K>;
+  constexpr int M = PK::M, P4 = PK::P4;
+  const int64_t n = ne * P4 * 4;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / (P4 * 4);
+    const int p = (int)(t % (P4 * 4));
+    float v = 0.f;
+    if (p < PK::P) {
+      int r = 0;
+      while (packed_index(M, r, M - 1) < p) ++r;
+      const int c = r + (p - packed_index(M, r, r));
+      v = (float)S[e * (int64_t)(M * M) + r * M + c];
+    }
+    S32m[t] = v;
+  }
+}
+
+// CTA = EPB elements x all column groups (CG = R/32 warps per element); the elements' packed
+// S_K are staged once in shared memory and read by every warp as broadcasts.
+template <int DIM, int K>
+struct Apply32mCfg {
+  static constexpr int P4 = Packed<DIM, K>::P4;
+  static constexpr int EPB = 4;
+};
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(256) apply32m_kernel(int64_t ne, int R, const int32_t* __restrict__ elem_face,
+                                                       const int32_t* __restrict__ face_bnd, const float4* __restrict__ S32m,
+                                                       const float* __restrict__ x, float* __restrict__ slot,
+                                                       const int* __restrict__ done) {
+  using Dm = Dims<DIM, K>;
+  using PK = Packed<DIM, K>;
+  constexpr int NF = Dm::NF, M = Dm::M, NFC = Dm::NFC, P4 = PK::P4, EPB = Apply32mCfg<DIM, K>::EPB;
+  __shared__ float4 Ss[EPB * P4];
+  if (done && *done) return;
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  const int nel = (int)((ne - e0) < EPB ? (ne - e0) : EPB);
+  for (int t = threadIdx.x; t < nel * P4; t += blockDim.x) Ss[t] = __ldcs(S32m + e0 * P4 + t);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cgs = (R + 31) / 32;                 // column groups
+  for (int task = w; task < nel * cgs; task += blockDim.x >> 5) {
+    const int el = task / cgs, cg = task % cgs;
+    const int64_t e = e0 + el;
+    const int j = cg * 32 + lane;
+    const bool col = j < R;
+    float xl[M], y[M];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      const int fid = elem_face[e * NFC + f];
+      const bool use = face_bnd[fid] < 0 && col;
+#pragma unroll
+      for (int mm = 0; mm < NF; ++mm) xl[f * NF + mm] = use ? x[((int64_t)fid * NF + mm) * R + j] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < M; ++r) y[r] = 0.f;
+    const float4* Se = Ss + el * P4;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+#pragma unroll
+      for (int c = r; c < M; ++c) {
+        const int p = packed_index(M, r, c);
+        if ((p & 3) == 0) v = Se[p >> 2];
+        const float s = (p & 3) == 0 ? v.x : (p & 3) == 1 ? v.y : (p & 3) == 2 ? v.z : v.w;
+        y[r] = fmaf(s, xl[c], y[r]);
+        if (c != r) y[c] = fmaf(s, xl[r], y[c]);
+      }
+    }
+    if (col) {
+#pragma unroll
+      for (int r = 0; r < M; ++r) slot[(e * M + r) * R + j] = y[r];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ per-column Krylov kernels
+// Vector entries t = entry * R + column; with a grid stride that is a multiple of R (256
+// threads per block, R | 256) every thread keeps one column, so per-thread accumulators
+// are per column. Block partials: part[blk][R]; column scalars are reduced in fixed order.
+template <typename TV>
+struct MAcc;
+template <>
+struct MAcc<float> {
+  Acc2 a;
+  __device__ __forceinline__ void dot(float x, float y) { a.dot(x, y); }
+  __device__ __forceinline__ double value() const { return a.value(); }
+};
+template <>
+struct MAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void dot(double x, double y) { s += x * y; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// per-column block sum of one value per thread (thread t holds column t % R); result in red[0..R)
+__device__ __forceinline__ void block_cols(double v, int R, double* red /*[256]*/) {
+  __syncthreads();
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w >= R; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+}
+
+struct MScal {              // per-column Krylov scalars, arrays of R entries
+  double *rho0, *rho1, *alpha, *rr, *bb, *tol2;
+  int* conv;                // per column: converged
+  int* done;                // all columns converged (or maxit)
+  int* iters;               // iterations executed
+};
+
+// q = (-K) p; partial p.q per column
+template <int DIM, int K, typename TV>
+__global__ void __launch_bounds__(256) mface_q_kernel(int nf, int R, const int32_t* __restrict__ face_slot,
+                                                      const int32_t* __restrict__ face_bnd, const TV* __restrict__ slot,
+                                                      const TV* __restrict__ p, TV* __restrict__ q,
+                                                      double* __restrict__ part, const int* __restrict__ done) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  if (*done) return;
+  __shared__ double red[256];
+  MAcc<TV> acc;
+  const int lg = __ffs(R) - 1;   // R is a power of two
+  const int64_t n = (int64_t)nf * NF * R;
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256) {
+    const int j = (int)(t & (R - 1));
+    const uint32_t fe = (uint32_t)(t >> lg);
+    const uint32_t f = fe / NF;
+    const int mm = (int)(fe - f * NF);
+    TV qv = TV(0);
+    if (face_bnd[f] < 0)
+      qv = -(slot[((int64_t)face_slot[2 * f] * NF + mm) * R + j] + slot[((int64_t)face_slot[2 * f + 1] * NF + mm) * R + j]);
+    q[t] = qv;
+    acc.dot(p[t], qv);
+  }
+  block_cols(acc.value(), R, red);
+  if (threadIdx.x < R) part[(int64_t)blockIdx.x * R + threadIdx.x] = red[threadIdx.x];
+}
+
+// alpha_j = rho_j / pq_j (0 for converged columns)
+__global__ void mcols_alpha(int nb, int R, int parity, const double* __restrict__ part, MScal sc) {
+  for (int j = threadIdx.x; j < R; j += blockDim.x) {
+    if (*sc.done) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * R + j];
+    const double rho = parity ? sc.rho1[j] : sc.rho0[j];
+    sc.alpha[j] = (sc.conv[j] || s == 0.0) ? 0.0 : rho / s;
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(256) mupdate_kernel(int64_t n, int R, const TV* __restrict__ p, const TV* __restrict__ q,
+                                                      const TV* __restrict__ dinv, TV* __restrict__ x, TV* __restrict__ r,
+                                                      TV* __restrict__ z, double* __restrict__ part, MScal sc) {
+  if (*sc.done) return;
+  __shared__ double red[256];
+  MAcc<TV> rz, rr;
+  const int j = threadIdx.x % R;
+  const int lg = __ffs(R) - 1;
+  const TV al = (TV)sc.alpha[j];
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256) {
+    x[t] += al * p[t];
+    const TV rv = r[t] - al * q[t];
+    const TV zv = dinv[t >> lg] * rv;
+    r[t] = rv; z[t] = zv;
+    rz.dot(rv, zv); rr.dot(rv, rv);
+  }
+  block_cols(rz.value(), R, red);
+  if (threadIdx.x < R) part[(int64_t)blockIdx.x * R + threadIdx.x] = red[threadIdx.x];
+  block_cols(rr.value(), R, red);
+  if (threadIdx.x < R) part[(int64_t)(gridDim.x + blockIdx.x) * R + threadIdx.x] = red[threadIdx.x];
+}
+
+// rho_new, rr per column; convergence; beta (written to alpha slot of the other parity use)
+__global__ void mcols_beta(int nb, int R, int parity, int iter, int maxit, const double* __restrict__ part,
+                           MScal sc, double* __restrict__ beta) {
+  __shared__ int notconv;
+  if (threadIdx.x == 0) notconv = 0;
+  __syncthreads();
+  if (*sc.done) return;
+  for (int j = threadIdx.x; j < R; j += blockDim.x) {
+    double rz = 0.0, rr = 0.0;
+    for (int b = 0; b < nb; ++b) { rz += part[(int64_t)b * R + j]; rr += part[(int64_t)(nb + b) * R + j]; }
+    const double rho = parity ? sc.rho1[j] : sc.rho0[j];
+    const int c = sc.conv[j] || rr <= sc.tol2[j];
+    beta[j] = c ? 0.0 : rz / rho;
+    if (parity) sc.rho0[j] = rz; else sc.rho1[j] = rz;
+    sc.rr[j] = rr;
+    sc.conv[j] = c;
+    if (!c) atomicAdd(&notconv, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *sc.iters = iter + 1;
+    if (notconv == 0 || iter + 1 >= maxit) *sc.done = notconv == 0 ? 1 : 2;
+  }
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(256) mdirection_kernel(int64_t n, int R, const TV* __restrict__ z, TV* __restrict__ p,
+                                                         const double* __restrict__ beta, const int* __restrict__ done) {
+  if (*done) return;
+  const TV be = (TV)beta[threadIdx.x % R];
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256) p[t] = z[t] + be * p[t];
+}
+
+// PCG start: r = b - (-K) x0 (x0 given; slot holds S x0 or zero), z = Dinv r, p = z; partials rz, rr, bb
+template <int DIM, int K, typename TV>
+__global__ void __launch_bounds__(256) minit_kernel(int nf, int R, const int32_t* __restrict__ face_slot,
+                                                    const int32_t* __restrict__ face_bnd, const TV* __restrict__ slot,
+                                                    const TV* __restrict__ bvec, const TV* __restrict__ dinv,
+                                                    TV* __restrict__ r, TV* __restrict__ z, TV* __restrict__ p,
+                                                    double* __restrict__ part) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  __shared__ double red[256];
+  MAcc<TV> rz, rr, bb;
+  const int lg = __ffs(R) - 1;
+  const int64_t n = (int64_t)nf * NF * R;
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256) {
+    const int j = (int)(t & (R - 1));
+    const uint32_t fe = (uint32_t)(t >> lg);
+    const uint32_t f = fe / NF;
+    const int mm = (int)(fe - f * NF);
+    TV rv = TV(0), zv = TV(0);
+    if (face_bnd[f] < 0) {
+      TV q = TV(0);
+      if (slot)
+        q = -(slot[((int64_t)face_slot[2 * f] * NF + mm) * R + j] + slot[((int64_t)face_slot[2 * f + 1] * NF + mm) * R + j]);
+      const TV bv = bvec[t];
+      rv = bv - q;
+      zv = dinv[fe] * rv;
+      bb.dot(bv, bv);
+    }
+    r[t] = rv; z[t] = zv; p[t] = zv;
+    rz.dot(rv, zv); rr.dot(rv, rv);
+  }
+  block_cols(rz.value(), R, red);
+  if (threadIdx.x < R) part[(int64_t)blockIdx.x * R + threadIdx.x] = red[threadIdx.x];
+  block_cols(rr.value(), R, red);
+  if (threadIdx.x < R) part[(int64_t)(gridDim.x + blockIdx.x) * R + threadIdx.x] = red[threadIdx.x];
+  block_cols(bb.value(), R, red);
+  if (threadIdx.x < R) part[(int64_t)(2 * gridDim.x + blockIdx.x) * R + threadIdx.x] = red[threadIdx.x];
+}
+
+// column scalars after minit: rho0 = rz, rr, bb, tol2 = rtol^2 * (bb or rr when bb_from_rr)
+__global__ void mcols_init(int nb, int R, double rtol, int tol_from_rr, const double* __restrict__ part, MScal sc) {
+  __shared__ int notconv;
+  if (threadIdx.x == 0) notconv = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < R; j += blockDim.x) {
+    double rz = 0.0, rr = 0.0, bb = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      rz += part[(int64_t)b * R + j];
+      rr += part[(int64_t)(nb + b) * R + j];
+      bb += part[(int64_t)(2 * nb + b) * R + j];
+    }
+    sc.rho0[j] = rz; sc.rho1[j] = 0.0; sc.rr[j] = rr; sc.bb[j] = bb;
+    sc.tol2[j] = rtol * rtol * (tol_from_rr ? rr : bb);
+    const int c = rr <= sc.tol2[j];
+    sc.conv[j] = c;
+    if (!c) atomicAdd(&notconv, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *sc.done = notconv == 0 ? 1 : 0;
+    *sc.iters = 0;
+  }
+}
+
+// FP64 refinement (per column): rho = b + sum slots64; partial |rho|^2, |b|^2 per column
+template <int DIM, int K>
+__global__ void __launch_bounds__(256) mrefine_residual_kernel(int nf, int R, const int32_t* __restrict__ face_slot,
+                                                               const int32_t* __restrict__ face_bnd,
+                                                               const double* __restrict__ slot, const double* __restrict__ b,
+                                                               double* __restrict__ res, double* __restrict__ part) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  __shared__ double red[256];
+  double rr = 0.0, bb = 0.0;
+  const int lg = __ffs(R) - 1;
+  const int64_t n = (int64_t)nf * NF * R;
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256) {
+    const int j = (int)(t & (R - 1));
+    const uint32_t fe = (uint32_t)(t >> lg);
+    const uint32_t f = fe / NF;
+    const int mm = (int)(fe - f * NF);
+    double v = 0.0;
+    if (face_bnd[f] < 0) {
+      const double bv = b[t];
+      v = bv + slot[((int64_t)face_slot[2 * f] * NF + mm) * R + j] + slot[((int64_t)face_slot[2 * f + 1] * NF + mm) * R + j];
+      bb += bv * bv;
+    }
+    res[t] = v;
+    rr += v * v;
+  }
+  block_cols(rr, R, red);
+  if (threadIdx.x < R) part[(int64_t)blockIdx.x * R + threadIdx.x] = red[threadIdx.x];
+  block_cols(bb, R, red);
+  if (threadIdx.x < R) part[(int64_t)(gridDim.x + blockIdx.x) * R + threadIdx.x] = red[threadIdx.x];
+}
+
+// per column: rr, bb, scale = 1/|rho| (0 -> column converged: its inner right-hand side is zero)
+__global__ void mrefine_scalars(int nb, int R, double rtol, const double* __restrict__ part, double* __restrict__ rr,
+                                double* __restrict__ bb, double* __restrict__ scale, int* __restrict__ nconv) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < R; j += blockDim.x) {
+    double a = 0.0, c = 0.0;
+    for (int b = 0; b < nb; ++b) { a += part[(int64_t)b * R + j]; c += part[(int64_t)(nb + b) * R + j]; }
+    rr[j] = a; bb[j] = c;
+    const bool ok = a <= rtol * rtol * c;
+    scale[j] = (ok || a == 0.0) ? 0.0 : 1.0 / sqrt(a);
+    if (!ok) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *nconv = cnt;
+}
+
+__global__ void mto32_scaled_kernel(int64_t n, int R, const double* __restrict__ res, const double* __restrict__ scale,
+                                    float* __restrict__ b32) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    b32[t] = (float)(res[t] * scale[t & (R - 1)]);
+}
+
+__global__ void mrefine_update_kernel(int64_t n, int R, int NF, const int32_t* __restrict__ face_bnd,
+                                      const float* __restrict__ delta, const double* __restrict__ scale,
+                                      double* __restrict__ lam) {
+  const int lg = __ffs(R) - 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double s = scale[t & (R - 1)];
+    if (s != 0.0 && face_bnd[(uint32_t)(t >> lg) / (uint32_t)NF] < 0) lam[t] += (double)delta[t] / s;
+  }
+}
+
+// boundary entries of lam (all columns) <- coef[b] * fac
+__global__ void mdirichlet_kernel(int64_t nb, int NF, int R, const int64_t* __restrict__ bnd_faces,
+                                  const double* __restrict__ coef, double fac, double* __restrict__ lam) {
+  const int64_t n = nb * NF * R;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t bf = t / R;
+    const int64_t b = bf / NF;
+    lam[(bnd_faces[b] * NF + bf % NF) * R + t % R] = coef ? coef[bf] * fac : 0.0;
+  }
+}
+
+// faces from slots (all columns): out = scale * (slot0 + slot1) on interior faces, 0 on boundary
+template <int DIM, int K>
+__global__ void mface_gather_kernel(int nf, int R, const int32_t* __restrict__ face_slot,
+                                    const int32_t* __restrict__ face_bnd, const double* __restrict__ slot, double scale,
+                                    double* __restrict__ out) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  const int lg = __ffs(R) - 1;
+  const int64_t n = (int64_t)nf * NF * R;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t & (R - 1));
+    const uint32_t fe = (uint32_t)(t >> lg);
+    const uint32_t f = fe / NF;
+    const int mm = (int)(fe - f * NF);
+    double v = 0.0;
+    if (face_bnd[f] < 0)
+      v = scale * (slot[((int64_t)face_slot[2 * f] * NF + mm) * R + j] + slot[((int64_t)face_slot[2 * f + 1] * NF + mm) * R + j]);
+    out[t] = v;
+  }
+}
+
+// interior entries (all columns) <- 0
+__global__ void mzero_interior_kernel(int64_t n, int R, int NF, const int32_t* __restrict__ face_bnd,
+                                      double* __restrict__ x) {
+  const int lg = __ffs(R) - 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    if (face_bnd[(uint32_t)(t >> lg) / (uint32_t)NF] < 0) x[t] = 0.0;
+}
+
+// volume projection replicated over R columns: u[e][c*NP+i][j] = sum_q w_q vals[e][q][c] phi_i(xi_q)
+__global__ void mproject_volume_kernel(int64_t ne, int NP, int nq, int ncomp, int R, const double* __restrict__ w,
+                                       const double* __restrict__ phi, const double* __restrict__ vals,
+                                       double* __restrict__ u) {
+  const int64_t n = ne * ncomp * NP * R;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = t / R;
+    const int64_t e = row / (ncomp * NP);
+    const int c = (int)((row / NP) % ncomp), i = (int)(row % NP);
+    double s = 0.0;
+    for (int q = 0; q < nq; ++q) s += w[q] * vals[(e * nq + q) * ncomp + c] * phi[q * NP + i];
+    u[t] = s;
+  }
+}
+
+}  // namespace hdg

@@ -35,7 +35,7 @@ class Material(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32),
-                ("inner_rtol", c_double), ("max_sweeps", c_int32)]
+                ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -70,7 +70,7 @@ SIGNATURES = {
     "hdg_condensed_rhs": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hdg_trace_solve": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(SolveInfo)]),
     "hdg_recover": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
-    "hdg_set_sources": (c_int32, [c_void_p, c_int32, P_double, P_double, c_double, c_double]),
+    "hdg_set_sources": (c_int32, [c_void_p, c_int32, P_double, P_double, P_int32, c_double, c_double]),
     "hdg_quadrature_points": (c_int32, [c_void_p, c_int32, P_double]),
     "hdg_project_volume": (c_int32, [c_void_p, P_double, c_void_p]),
     "hdg_set_dirichlet": (c_int32, [c_void_p, P_double, c_double, c_double]),
@@ -119,7 +119,7 @@ class Solver:
     """One HDG problem resident on the current CUDA device (wraps an hdg_ctx)."""
 
     def __init__(self, vert, elem, k, tau, rho, c, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
-                 inner_rtol=None, max_sweeps=None, stream=None):
+                 inner_rtol=None, max_sweeps=None, nrhs=1, stream=None):
         import torch
         self.lib = load()
         self.torch = torch
@@ -138,6 +138,7 @@ class Solver:
             opt.inner_rtol = inner_rtol
         if max_sweeps is not None:
             opt.max_sweeps = max_sweeps
+        opt.nrhs = nrhs
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -153,6 +154,9 @@ class Solver:
         self.dim, self.k, self.Np, self.Nf = sz.dim, sz.k, sz.Np, sz.Nf
         self.n, self.m = sz.n_local, sz.n_trace_local
         self.n_elem, self.n_faces, self.n_bnd = sz.n_elem, sz.n_faces, sz.n_bnd_faces
+        self.R = nrhs
+        self._fshape = (self.n_elem, self.n) if nrhs == 1 else (self.n_elem, self.n, nrhs)
+        self._tshape = (self.n_faces, self.Nf) if nrhs == 1 else (self.n_faces, self.Nf, nrhs)
 
     def _check(self, st):
         if st != 0:
@@ -172,10 +176,10 @@ class Solver:
 
     # buffers -------------------------------------------------------------------------------
     def empty_fields(self):
-        return self.torch.zeros((self.n_elem, self.n), dtype=self.torch.float64, device=self.device)
+        return self.torch.zeros(self._fshape, dtype=self.torch.float64, device=self.device)
 
     def empty_traces(self):
-        return self.torch.zeros((self.n_faces, self.Nf), dtype=self.torch.float64, device=self.device)
+        return self.torch.zeros(self._tshape, dtype=self.torch.float64, device=self.device)
 
     def _dev(self, t, shape):
         assert t.dtype == self.torch.float64 and t.is_cuda and t.is_contiguous(), "float64 contiguous CUDA tensor"
@@ -193,34 +197,38 @@ class Solver:
 
     def hdg_trace_apply(self, x, y=None):
         y = self.empty_traces() if y is None else y
-        self._check(self.lib.hdg_trace_apply(self.ctx, self._dev(x, (self.n_faces, self.Nf)),
-                                             self._dev(y, (self.n_faces, self.Nf))))
+        self._check(self.lib.hdg_trace_apply(self.ctx, self._dev(x, self._tshape),
+                                             self._dev(y, self._tshape)))
         return y
 
     def hdg_condensed_rhs(self, F, lamD=None, r=None):
         r = self.empty_traces() if r is None else r
-        self._check(self.lib.hdg_condensed_rhs(self.ctx, self._dev(F, (self.n_elem, self.n)),
-                                               None if lamD is None else self._dev(lamD, (self.n_faces, self.Nf)),
-                                               self._dev(r, (self.n_faces, self.Nf))))
+        self._check(self.lib.hdg_condensed_rhs(self.ctx, self._dev(F, self._fshape),
+                                               None if lamD is None else self._dev(lamD, self._tshape),
+                                               self._dev(r, self._tshape)))
         return r
 
     def hdg_trace_solve(self, r, lam):
         info = SolveInfo()
-        self._check(self.lib.hdg_trace_solve(self.ctx, self._dev(r, (self.n_faces, self.Nf)),
-                                             self._dev(lam, (self.n_faces, self.Nf)), ctypes.byref(info)))
+        self._check(self.lib.hdg_trace_solve(self.ctx, self._dev(r, self._tshape),
+                                             self._dev(lam, self._tshape), ctypes.byref(info)))
         return info.as_dict()
 
     def hdg_recover(self, F, lam, u=None):
         u = self.empty_fields() if u is None else u
-        self._check(self.lib.hdg_recover(self.ctx, self._dev(F, (self.n_elem, self.n)),
-                                         self._dev(lam, (self.n_faces, self.Nf)), self._dev(u, (self.n_elem, self.n))))
+        self._check(self.lib.hdg_recover(self.ctx, self._dev(F, self._fshape),
+                                         self._dev(lam, self._tshape), self._dev(u, self._fshape)))
         return u
 
-    def hdg_set_sources(self, pos, amp, f0, t0):
+    def hdg_set_sources(self, pos, amp, f0, t0, col=None):
         pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, self.dim))
         amp = np.ascontiguousarray(np.broadcast_to(np.asarray(amp, dtype=np.float64), (pos.shape[0],)))
+        colp = None
+        if col is not None:
+            col = np.ascontiguousarray(np.asarray(col, dtype=np.int32).reshape(-1))
+            colp = _np_ptr(col, c_int32)
         self._check(self.lib.hdg_set_sources(self.ctx, pos.shape[0], _np_ptr(pos, c_double), _np_ptr(amp, c_double),
-                                             f0, t0))
+                                             colp, f0, t0))
 
     def hdg_quadrature_points(self, which):
         nq = self.sizes.nq_vol if which == 0 else self.sizes.nq_face
@@ -233,7 +241,7 @@ class Solver:
         vals = np.ascontiguousarray(vals, dtype=np.float64)
         assert vals.shape == (self.n_elem, self.sizes.nq_vol, self.dim + 1)
         u = self.empty_fields() if u is None else u
-        self._check(self.lib.hdg_project_volume(self.ctx, _np_ptr(vals, c_double), self._dev(u, (self.n_elem, self.n))))
+        self._check(self.lib.hdg_project_volume(self.ctx, _np_ptr(vals, c_double), self._dev(u, self._fshape)))
         return u
 
     def hdg_set_dirichlet(self, vals=None, omega=0.0, phase=0.0):
@@ -245,9 +253,9 @@ class Solver:
         self._check(self.lib.hdg_set_dirichlet(self.ctx, _np_ptr(vals, c_double), omega, phase))
 
     def hdg_set_state(self, u, t=0.0, uprev=None, lam=None):
-        shp = (self.n_elem, self.n)
+        shp = self._fshape
         self._check(self.lib.hdg_set_state(self.ctx, self._dev(u, shp), None if uprev is None else self._dev(uprev, shp),
-                                           None if lam is None else self._dev(lam, (self.n_faces, self.Nf)), t))
+                                           None if lam is None else self._dev(lam, self._tshape), t))
 
     def hdg_get_state(self, u=None, uprev=None, lam=None, want_prev=False):
         """Returns (u, lam, t) or, with want_prev, (u, uprev, lam, t); buffers may be passed in."""

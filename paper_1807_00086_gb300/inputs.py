@@ -94,3 +94,12 @@ def acoustic_3d_workload(N=32, k=3, seed=DEFAULT_SEED):
     h = 1.0 / N
     src = np.array([[0.5 + 0.3 * h, 0.5 + 0.3 * h, 0.5 + 0.3 * h]])
     return dict(vert=vert, elem=elem, k=k, rho=rho, c=c, tau=1.0, sources=src, f0=10.0, t0=1.2 / 10.0)
+
+
+def acoustic_3d_multisource_workload(N=32, k=3, nsrc=64, seed=DEFAULT_SEED):
+    """The 3D acoustic workload with `nsrc` Ricker point sources at seeded uniform interior
+    points of [0.1, 0.9]^3, source i driving right-hand-side column i."""
+    w = acoustic_3d_workload(N=N, k=k, seed=seed)
+    w["sources"] = uniform_points(nsrc, 3, 0.1, 0.9, seed + 64)
+    w["source_cols"] = np.arange(nsrc, dtype=np.int32)
+    return w
