@@ -1,0 +1,178 @@
+"""Pins for the oracle's linear elastodynamics HDG scheme (Sec. 4.1).
+
+* static condensation (Eq. LS) reproduces the uncondensed [A B; C D] solve;
+* the velocity / symmetric-stress form and the paper's velocity / deformation-gradient
+  form (Eqs. eq:sigma_cauchy, eq:HDG_linelas) give the same velocity and trace;
+* S_K is symmetric positive definite;
+* the backward-Euler discrete energy identity (the discrete analogue of the energy
+  identity of Sec. 4.2) holds step by step;
+* a manufactured solution converges at order k + 1 in the velocity, the order the paper's
+  convergence table reports (tests/golden/eoc_linear_elastodyn.txt).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import elastic as el
+from paper_1807_00086_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "eoc_linear_elastodyn.txt")
+
+
+def _problem(dim, N, k, form="sigma", data=True):
+    vert, elem = inputs.unit_square_tri(N) if dim == 2 else inputs.unit_cube_tet(N)
+    ne = elem.shape[0]
+    lam = 1.5 * inputs.lognormal(ne, 1.0, 0.5, 2)
+    mu = inputs.lognormal(ne, 1.0, 0.5, 3)
+    prob = el.build_problem(vert, elem, k, inputs.loguniform(ne, 0.5, 2.0, 4), lam, mu, form=form)
+    if data:
+        prob.dirichlet = lambda x, t: np.stack([np.sin(x[:, 0] + t), np.cos(x[:, 1]), x[:, 0] * x[:, -1]][:dim], axis=1)
+        prob.body_force = lambda x, t: np.stack([np.cos(2 * x[:, 0]), x[:, 1] * t, np.ones(x.shape[0])][:dim], axis=1)
+    return prob
+
+
+def test_compliance_inverts_hooke():
+    for dim in (2, 3):
+        lam, mu = 1.7, 0.6
+        comps = el.sym_components(dim)
+        Q = el.compliance(dim, lam, mu)
+        rng = np.random.default_rng(0)
+        eps = rng.standard_normal((dim, dim))
+        eps = eps + eps.T
+        sig = lam * np.trace(eps) * np.eye(dim) + 2 * mu * eps
+        # (C^{-1} sigma, G_a) = w_a eps_ij
+        svec = np.array([sig[i, j] for (i, j) in comps])
+        want = np.array([(1.0 if i == j else 2.0) * eps[i, j] for (i, j) in comps])
+        assert np.abs(Q @ svec - want).max() < 1e-12
+        # Eq. eq:sigma_cauchy with F = I + H reduces to Hooke's law
+        P = el.stiffness_F(dim, lam, mu)
+        H = rng.standard_normal((dim, dim))
+        sigF = (P @ H.ravel()).reshape(dim, dim)
+        F = np.eye(dim) + H
+        paper = mu * (F + F.T) + (lam * (np.trace(F) - dim) - 2 * mu) * np.eye(dim)
+        assert np.abs(sigF - paper).max() < 1e-12
+
+
+@pytest.mark.parametrize("dim,N,k", [(2, 2, 1), (2, 2, 2), (2, 1, 3), (3, 1, 1), (3, 1, 2)])
+def test_condensed_equals_monolithic(dim, N, k):
+    prob = _problem(dim, N, k)
+    rng = np.random.default_rng(1)
+    h = rng.standard_normal((prob.sk.elem.shape[0], (dim + prob.nt) * prob.Np))
+    for alpha in (0.3, 60.0):
+        cond = el.condense(prob, alpha)
+        u, lam = el.solve_stage(prob, cond, h, 0.3)
+        um, lm = el.solve_monolithic(prob, alpha, h, 0.3)
+        assert np.abs(u - um).max() <= 1e-12 * np.abs(um).max()
+        assert np.abs(lam - lm).max() <= 1e-12 * np.abs(lm).max()
+
+
+@pytest.mark.parametrize("dim,k", [(2, 2), (3, 2)])
+def test_schur_symmetric_positive_definite(dim, k):
+    prob = _problem(dim, 1, k, data=False)
+    for alpha in (0.1, 100.0):
+        for S in el.condense(prob, alpha).S:
+            assert np.abs(S - S.T).max() <= 1e-12 * np.abs(S).max()
+            assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > 0
+
+
+@pytest.mark.parametrize("dim,N", [(2, 2), (3, 1)])
+def test_velocity_sigma_form_equals_deformation_gradient_form(dim, N):
+    k = 2
+    pS = _problem(dim, N, k, "sigma")
+    pF = _problem(dim, N, k, "F")
+    ne, Np = pS.sk.elem.shape[0], pS.Np
+    rng = np.random.default_rng(2)
+    H0 = rng.standard_normal((ne, dim * dim, Np))
+    v0 = rng.standard_normal((ne, dim * Np))
+    uF = np.concatenate([v0, H0.reshape(ne, -1)], axis=1)
+    comps, full = el.sym_components(dim), el.full_components(dim)
+    uS = np.zeros((ne, (dim + len(comps)) * Np))
+    uS[:, :dim * Np] = v0
+    for e in range(ne):
+        sig = el.stiffness_F(dim, pS.lam[e], pS.mu[e]) @ H0[e]
+        for a, (i, j) in enumerate(comps):
+            uS[e, (dim + a) * Np:(dim + a + 1) * Np] = sig[full.index((i, j))]
+    a1 = el.run_bdf(pS, uS, 0.01, 3, 2)
+    a2 = el.run_bdf(pF, uF, 0.01, 3, 2)
+    vS, vF = a1[0][:, :dim * Np], a2[0][:, :dim * Np]
+    assert np.abs(vS - vF).max() <= 1e-12 * np.abs(vS).max()
+    assert np.abs(a1[1] - a2[1]).max() <= 1e-12 * np.abs(a1[1]).max()
+
+
+@pytest.mark.parametrize("dim,N", [(2, 3), (3, 1)])
+def test_backward_euler_energy_identity(dim, N):
+    """E^{n+1} - E^n + 1/2 |u^{n+1} - u^n|_M^2 + dt sum_dK <s (v - v_hat)^2, 1>
+       = dt [(f, v^{n+1}) + <v_hat, sigma_hat n>_{Gamma_D}]."""
+    prob = _problem(dim, N, 2)
+    rng = np.random.default_rng(3)
+    u0 = rng.standard_normal((prob.sk.elem.shape[0], (dim + prob.nt) * prob.Np))
+    dt = 0.01
+    prev = [u0]
+
+    def check(n, t, u, lam):
+        diss, bwork, fv = el.energy_terms(prob, u, lam, t)
+        du = u - prev[-1]
+        lhs = (el.energy(prob, u) - el.energy(prob, prev[-1])
+               + 0.5 * sum(du[e] @ bl.Mw @ du[e] for e, bl in enumerate(prob.blocks)) + dt * diss)
+        assert abs(lhs - dt * (fv + bwork)) <= 1e-11 * (abs(lhs) + dt * abs(diss))
+        prev.append(u)
+
+    el.run_bdf(prob, u0, dt, 3, 1, on_step=check)
+
+
+def _mms_2d(lam, mu, rho, w):
+    """u = sin(w t) s(x) (1, 1), s = sin(pi x) sin(pi y): v, sigma and the body force
+    f = rho v_t - div sigma, with div(C eps(Phi)) = (lam + mu) grad div Phi + mu lap Phi."""
+    pi = math.pi
+
+    def parts(x):
+        sx, sy = np.sin(pi * x[:, 0]), np.sin(pi * x[:, 1])
+        cx, cy = np.cos(pi * x[:, 0]), np.cos(pi * x[:, 1])
+        return sx, sy, cx, cy
+
+    def v(x, t):
+        sx, sy, cx, cy = parts(x)
+        s = w * math.cos(w * t) * sx * sy
+        return np.stack([s, s], axis=1)
+
+    def sigma(x, t):
+        sx, sy, cx, cy = parts(x)
+        e11 = pi * cx * sy
+        e22 = pi * sx * cy
+        e12 = 0.5 * (pi * sx * cy + pi * cx * sy)
+        tr = e11 + e22
+        st = math.sin(w * t)
+        return np.stack([st * (lam * tr + 2 * mu * e11), st * (lam * tr + 2 * mu * e22), st * 2 * mu * e12], axis=1)
+
+    def force(x, t):
+        sx, sy, cx, cy = parts(x)
+        s = sx * sy
+        graddiv = pi * pi * (cx * cy - s)
+        divC = (lam + mu) * graddiv - 2 * mu * pi * pi * s
+        f = -rho * w * w * math.sin(w * t) * s - math.sin(w * t) * divC
+        return np.stack([f, f], axis=1)
+
+    return v, sigma, force
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_manufactured_solution_converges_at_order_k_plus_1(k):
+    lam, mu, rho, w = 1.5, 1.0, 1.0, math.pi * math.sqrt(2.0)
+    v, sigma, force = _mms_2d(lam, mu, rho, w)
+    T = 0.2
+    errs = []
+    for N in (2, 4, 8):
+        vert, elem = inputs.unit_square_tri(N)
+        prob = el.build_problem(vert, elem, k, rho, lam, mu)
+        prob.body_force = force
+        u0 = el.project(prob, lambda x: v(x, 0.0), lambda x: sigma(x, 0.0))
+        nst = 4 * N
+        u, lamh, t = el.run_dirk3(prob, u0, T / nst, nst)
+        errs.append(el.l2_error_velocity(prob, u, lambda x: v(x, T)))
+    rate = math.log2(errs[-2] / errs[-1])
+    # the paper reports e.o.c. close to k + 1 for the velocity on its finest meshes
+    paper = {int(r.split()[0]): float(r.split()[3]) for r in open(GOLDEN) if r.strip() and not r.startswith("#")}
+    assert paper[k] > k + 0.9
+    assert rate > k + 1 - 0.3, (errs, rate)
