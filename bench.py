@@ -25,6 +25,9 @@ import time
 
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
+if "--serve" in sys.argv:
+    # many resident contexts, each on its own stream: give them separate hardware queues
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -371,6 +374,30 @@ def run_apply_only(args):
     print(json.dumps({"mode": "apply", "n_elem": s.n_elem, "applies": args.steps, "max_abs": float(y.abs().max())}))
 
 
+def run_serve(args):
+    """Serving workload: Poisson arrivals (20/s), 2D/3D acoustic requests of mixed mesh size,
+    degree and step count, continuous batching under a device-memory budget."""
+    import torch
+    from paper_1807_00086_gb300.serve import Server, serving_workload
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = serving_workload(n_req=args.serve_requests, rate=args.serve_rate)
+    srv = Server(budget_bytes=int(args.serve_budget_gb * (1 << 30)), R=args.serve_slots, prec=args.prec)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    stats = srv.run(reqs)
+    clk = clocks.stop()
+    srv.close()
+    out = {"metric": METRIC, "mode": "serve", "value": stats["dof_steps_per_s"], "unit": UNIT,
+           "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "mean_ms": stats["mean_ms"],
+           "higher_is_better": True, "dtype": "f64" if args.prec == "fp64" else "f32+f64", "data": "synthetic",
+           "config": {"workload": "serve_acoustic_2d3d_poisson%g" % args.serve_rate, "requests": stats["requests"],
+                      "slots_per_context": args.serve_slots, "budget_gb": args.serve_budget_gb,
+                      "contexts_resident_at_end": stats["contexts_created"], "wall_s": stats["wall_s"],
+                      "precision": args.prec},
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,8 +417,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="step", choices=["step", "apply"],
                     help="apply: profiling driver that only condenses and applies K (no JSON bench line)")
+    ap.add_argument("--serve", action="store_true", help="run the continuous-batching serving workload")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
-    if args.mode == "apply":
+    if args.serve:
+        run_serve(args)
+    elif args.mode == "apply":
         run_apply_only(args)
     elif args.impl == "reference":
         run_reference(args)

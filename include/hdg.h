@@ -80,6 +80,8 @@ typedef struct {
                             /* solved together: every field and trace array below     */
                             /* gains an innermost column index [..][R]; one read of    */
                             /* each S_K serves all R columns                           */
+  int32_t use_graphs;       /* nrhs > 1: replay captured CUDA graphs of Krylov        */
+                            /* iteration chunks (fewer host launches; small problems)  */
 } hdg_options;
 
 typedef struct {
@@ -95,7 +97,8 @@ typedef struct {
   double rel_residual;      /* final ||r|| / ||b|| of the trace system (FP64)         */
 } hdg_solve_info;
 
-/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1. */
+/* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1,
+ * use_graphs 0. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face
@@ -139,13 +142,23 @@ hdg_status hdg_trace_solve(hdg_ctx* ctx, const double* r_dev, double* lam_dev, h
  * faces (boundary entries = Dirichlet trace). F_dev, u_dev: [n_elem][n]. */
 hdg_status hdg_recover(hdg_ctx* ctx, const double* F_dev, const double* lam_dev, double* u_dev);
 
-/* Data of the time-dependent problem. Point sources (pressure equation, Ricker wavelet
- * r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), amplitude amp_host[i]) at
- * positions pos_host [nsrc][dim]; each is attached to the lowest-id element containing
+/* Data of the time-dependent problem. Point sources in the pressure equation at
+ * positions pos_host [nsrc][dim], source i with amplitude amp_host[i] and the Ricker
+ * wavelet r(t - d_i), r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), delayed
+ * by d_i = delay_host[i] (NULL: 0); each is attached to the lowest-id element containing
  * it and acts on right-hand-side column col_host[i] (NULL: column 0). nsrc = 0 removes
  * all sources. */
 hdg_status hdg_set_sources(hdg_ctx* ctx, int32_t nsrc, const double* pos_host, const double* amp_host,
-                           const int32_t* col_host, double f0, double t0);
+                           const int32_t* col_host, const double* delay_host, double f0, double t0);
+
+/* A dedicated non-blocking CUDA stream (cudaStream_t) for one context, e.g. for several
+ * contexts stepping concurrently from different threads; destroy it after the context. */
+hdg_status hdg_stream_create(void** stream_out);
+hdg_status hdg_stream_destroy(void* stream);
+
+/* Zeroes column j of the fields, the previous level and the traces (a column restarted
+ * from rest; used to recycle a finished request's slot). Enqueued on the stream. */
+hdg_status hdg_reset_column(hdg_ctx* ctx, int32_t j);
 
 /* Physical coordinates of the projection quadrature points: which = 0 volume
  * ([n_elem][nq_vol][dim]), which = 1 boundary faces in face order ([n_bnd][nq_face][dim]). */

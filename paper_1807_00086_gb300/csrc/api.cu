@@ -62,7 +62,11 @@ struct hdg_ctx {
          *d_mbb = nullptr, *d_mtol2 = nullptr, *d_mscale = nullptr, *d_mrr2 = nullptr, *d_mbb2 = nullptr;
   int *d_mconv = nullptr, *d_mdone = nullptr, *d_mnconv = nullptr, *d_miters = nullptr;
   int* h_mint = nullptr;                // pinned: [0] done flag, [1] nconv, [2] iterations
+  // CUDA graphs of per-column Krylov iteration chunks, keyed by (vector type, x pointer)
+  std::vector<std::pair<std::pair<int, const void*>, cudaGraphExec_t>> graphs;
   int32_t* d_src_col = nullptr;
+  double* d_src_delay = nullptr;
+  int src_cap = 0;                      // capacity of the per-source buffers (grow-only)
   RefScal* d_rs = nullptr;
   RefScal* h_rs = nullptr;   // pinned
   // time state
@@ -127,6 +131,14 @@ int grid_for(const hdg_ctx* c, int64_t n, int block = 256) {
   int64_t g = (n + block - 1) / block;
   int64_t cap = (int64_t)c->sms * 8;
   return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+SrcArgs srcargs(const hdg_ctx* c, double t) {
+  SrcArgs a;
+  a.ptr = c->nsrc > 0 ? c->d_src_ptr : nullptr;
+  a.phi = c->d_src_phi; a.col = c->d_src_col; a.delay = c->d_src_delay;
+  a.f0 = c->f0; a.t0 = c->t0; a.t = t;
+  return a;
 }
 
 DevMesh devmesh(const hdg_ctx* c) {
@@ -199,17 +211,17 @@ void launch_condense(hdg_ctx* c) {
 }
 
 template <int DIM, int K>
-void launch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double src_rt, const double* lam, double* out) {
+void launch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double t, const double* lam, double* out) {
   using L = LocalCfg<DIM, K>;
   const unsigned grid = (unsigned)((c->sk.ne + L::EPB - 1) / L::EPB);
-  const int32_t* sp = c->nsrc > 0 ? c->d_src_ptr : nullptr;
+  const SrcArgs sa = srcargs(c, t);
   c->n_launch += 1;
   if (mode == 0)
-    local_kernel<DIM, K, 0><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F, hist, sp,
-                                                            c->d_src_phi, src_rt, lam, out);
+    local_kernel<DIM, K, 0><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F, hist, sa, lam,
+                                                            out);
   else
-    local_kernel<DIM, K, 1><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F, hist, sp,
-                                                            c->d_src_phi, src_rt, lam, out);
+    local_kernel<DIM, K, 1><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F, hist, sa, lam,
+                                                            out);
 }
 
 template <int DIM, int K>
@@ -449,17 +461,17 @@ MScal mscal(hdg_ctx* c) {
 }
 
 template <int DIM, int K>
-void mlaunch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double src_rt, const double* lam, double* out) {
+void mlaunch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double t, const double* lam, double* out) {
   using L = LocalMultiCfg<DIM, K>;
   dim3 grid((unsigned)c->sk.ne, (unsigned)((c->R + L::CW - 1) / L::CW));
-  const int32_t* sp = c->nsrc > 0 ? c->d_src_ptr : nullptr;
+  const SrcArgs sa = srcargs(c, t);
   c->n_launch += 1;
   if (mode == 0)
     local_multi_kernel<DIM, K, 0><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, c->R, F,
-                                                                  hist, sp, c->d_src_phi, c->d_src_col, src_rt, lam, out);
+                                                                  hist, sa, lam, out);
   else
     local_multi_kernel<DIM, K, 1><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, c->R, F,
-                                                                  hist, sp, c->d_src_phi, c->d_src_col, src_rt, lam, out);
+                                                                  hist, sa, lam, out);
 }
 
 template <int DIM, int K, typename TV>
@@ -558,22 +570,57 @@ hdg_status mcg(hdg_ctx* c, const TV* b, TV* x, TV* r, TV* z, TV* p, TV* q, TV* s
   c->h_mint[0] = 0;
   CUDA_TRY(c, cudaMemcpyAsync(c->h_mint, c->d_mdone, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  while (!c->h_mint[0] && it < maxit) {
-    const int upto = std::min(maxit, it + (it == 0 ? first : std::min(chk, 3)));
-    for (; it < upto; ++it) {
-      const int par = it & 1;
+  auto issue = [&](int it0, int count) {
+    for (int i = it0; i < it0 + count; ++i) {
+      const int par = i & 1;
       c->n_launch += 5;
       if (sizeof(TV) == 8) {
-        HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)p, (double*)slot, c->d_mdone, it);
+        HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)p, (double*)slot, c->d_mdone, i);
         HDG_DISPATCH(c, mlaunch_face_q64, c, (const double*)slot, (const double*)p, (double*)q);
       } else {
-        HDG_DISPATCH(c, mlaunch_apply32, c, (const float*)p, (float*)slot, c->d_mdone, it);
+        HDG_DISPATCH(c, mlaunch_apply32, c, (const float*)p, (float*)slot, c->d_mdone, i);
         HDG_DISPATCH(c, mlaunch_face_q32, c, (const float*)slot, (const float*)p, (float*)q);
       }
       mcols_alpha<<<1, 256, 0, c->stream>>>(nb, c->R, par, c->d_part, mscal(c));
       mupdate_kernel<TV><<<nb, 256, 0, c->stream>>>(n, c->R, p, q, dinv, x, r, z, c->d_part, mscal(c));
-      mcols_beta<<<1, 256, 0, c->stream>>>(nb, c->R, par, it, maxit, c->d_part, mscal(c), c->d_mbeta);
+      mcols_beta<<<1, 256, 0, c->stream>>>(nb, c->R, par, maxit, c->d_part, mscal(c), c->d_mbeta);
       mdirection_kernel<TV><<<nb, 256, 0, c->stream>>>(n, c->R, z, p, c->d_mbeta, c->d_mdone);
+    }
+  };
+  // graph mode: chunks of GCH iterations (even, so the parity pattern repeats) captured once
+  const int GCH = 4;
+  cudaGraphExec_t gexec = nullptr;
+  if (c->opt.use_graphs && !c->stats_on) {
+    const std::pair<int, const void*> key((int)sizeof(TV), (const void*)x);
+    for (auto& g : c->graphs)
+      if (g.first == key) gexec = g.second;
+    if (!gexec) {
+      // the context's stream must be its own (a stream shared with another context would
+      // capture that context's launches too); the capture is always ended, even on error
+      cudaGraph_t graph = nullptr;
+      CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      issue(0, GCH);
+      const cudaError_t le = cudaGetLastError();
+      cudaError_t ce = cudaStreamEndCapture(c->stream, &graph);
+      if (le != cudaSuccess || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(c, HDG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ce));
+      }
+      ce = cudaGraphInstantiate(&gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return fail(c, HDG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+      c->graphs.push_back({key, gexec});
+    }
+  }
+  while (!c->h_mint[0] && it < maxit) {
+    if (gexec) {
+      const int reps = it == 0 ? std::max(1, (first + GCH - 1) / GCH) : 1;
+      for (int rr = 0; rr < reps; ++rr) CUDA_TRY(c, cudaGraphLaunch(gexec, c->stream));
+      it += reps * GCH;
+    } else {
+      const int upto = std::min(maxit, it + (it == 0 ? first : std::min(chk, 3)));
+      issue(it, upto - it);
+      it = upto;
     }
     if ((s = check_launch(c, "mcg_iter"))) return s;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_mint, c->d_mdone, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -594,8 +641,9 @@ hdg_status msolve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) 
     int it = 0;
     if ((s = mcg<double>(c, b, x, c->d_r, c->d_z, c->d_p, c->d_q, c->d_mslot, c->d_dinv, c->opt.rtol, false, &it))) return s;
     std::vector<double> rr(c->R), bb(c->R);
-    CUDA_TRY(c, cudaMemcpy(rr.data(), c->d_mrr, c->R * 8, cudaMemcpyDeviceToHost));
-    CUDA_TRY(c, cudaMemcpy(bb.data(), c->d_mbb, c->R * 8, cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpyAsync(rr.data(), c->d_mrr, c->R * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(bb.data(), c->d_mbb, c->R * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     double worst = 0.0;
     for (int j = 0; j < c->R; ++j) worst = std::max(worst, bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0);
     if (info) { info->iterations += it; info->sweeps += 1; info->rel_residual = std::max(info->rel_residual, worst); }
@@ -611,8 +659,9 @@ hdg_status msolve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) 
     harvest(c);
     if (c->h_mint[1] == 0 || sweep >= c->opt.max_sweeps) {
       std::vector<double> rr(c->R), bb(c->R);
-      CUDA_TRY(c, cudaMemcpy(rr.data(), c->d_mrr2, c->R * 8, cudaMemcpyDeviceToHost));
-      CUDA_TRY(c, cudaMemcpy(bb.data(), c->d_mbb2, c->R * 8, cudaMemcpyDeviceToHost));
+      CUDA_TRY(c, cudaMemcpyAsync(rr.data(), c->d_mrr2, c->R * 8, cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaMemcpyAsync(bb.data(), c->d_mbb2, c->R * 8, cudaMemcpyDeviceToHost, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
       double worst = 0.0;
       for (int j = 0; j < c->R; ++j) worst = std::max(worst, bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0);
       if (info) { info->iterations += total; info->sweeps += sweep; info->rel_residual = std::max(info->rel_residual, worst); }
@@ -632,11 +681,6 @@ hdg_status msolve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) 
   }
 }
 
-double ricker(double t, double f0, double t0) {
-  const double pi = 3.14159265358979323846;
-  const double a = (pi * f0 * (t - t0)) * (pi * f0 * (t - t0));
-  return (1.0 - 2.0 * a) * std::exp(-a);
-}
 
 // one implicit solve at mass shift alpha: alpha Mw u + f(u, lam, t) = alpha Mw hist
 hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info) {
@@ -646,25 +690,23 @@ hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, 
     c->n_launch += 1;
     mdirichlet_kernel<<<grid_for(c, nbe), 256, 0, c->stream>>>(c->sk.nb, c->Nf, c->R, c->d_bnd_faces, c->d_bnd_coef, fac,
                                                               c->d_lam);
-    const double rt = c->nsrc > 0 ? ricker(tt, c->f0, c->t0) : 0.0;
-    HDG_DISPATCH(c, mlaunch_local, c, 0, (const double*)nullptr, hist, rt, c->d_lam, c->d_mslot);
+    HDG_DISPATCH(c, mlaunch_local, c, 0, (const double*)nullptr, hist, tt, c->d_lam, c->d_mslot);
     HDG_DISPATCH(c, mlaunch_gather, c, (const double*)c->d_mslot, 1.0, c->d_b);
     hdg_status s = check_launch(c, "rhs_multi");
     if (s) return s;
     if ((s = msolve(c, c->d_b, c->d_lam, info))) return s;
-    HDG_DISPATCH(c, mlaunch_local, c, 1, (const double*)nullptr, hist, rt, c->d_lam, uout);
+    HDG_DISPATCH(c, mlaunch_local, c, 1, (const double*)nullptr, hist, tt, c->d_lam, uout);
     return check_launch(c, "recover_multi");
   }
   c->n_launch += 1;
   dirichlet_kernel<<<grid_for(c, c->sk.nb * c->Nf), 256, 0, c->stream>>>(c->sk.nb, c->Nf, c->d_bnd_faces, c->d_bnd_coef, fac,
                                                                          c->d_lam);
-  const double rt = c->nsrc > 0 ? ricker(tt, c->f0, c->t0) : 0.0;
-  HDG_DISPATCH(c, launch_local, c, 0, (const double*)nullptr, hist, rt, c->d_lam, c->d_slot);
+  HDG_DISPATCH(c, launch_local, c, 0, (const double*)nullptr, hist, tt, c->d_lam, c->d_slot);
   hdg_status s = check_launch(c, "rhs");
   if (s) return s;
   if ((s = faces_from_slots(c, 1.0, c->d_b))) return s;
   if ((s = cg_solve(c, c->d_b, c->d_lam, info))) return s;
-  HDG_DISPATCH(c, launch_local, c, 1, (const double*)nullptr, hist, rt, c->d_lam, uout);
+  HDG_DISPATCH(c, launch_local, c, 1, (const double*)nullptr, hist, tt, c->d_lam, uout);
   return check_launch(c, "recover");
 }
 
@@ -708,12 +750,14 @@ void hdg_default_options(hdg_options* o) {
   o->inner_rtol = 1e-4;
   o->max_sweeps = 20;
   o->nrhs = 1;
+  o->use_graphs = 0;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void hdg_destroy(hdg_ctx* c) {
   if (!c) return;
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
@@ -931,12 +975,13 @@ hdg_status hdg_recover(hdg_ctx* c, const double* F, const double* lam, double* u
 }
 
 hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const double* amp, const int32_t* col,
-                           double f0, double t0) {
+                           const double* delay, double f0, double t0) {
   if (!c || nsrc < 0 || (nsrc > 0 && (!pos || !amp))) return fail(c, HDG_EINVAL, "bad source arguments");
   for (int s2 = 0; col && s2 < nsrc; ++s2)
     if (col[s2] < 0 || col[s2] >= c->R) return fail(c, HDG_EINVAL, "source column out of range");
-  dfree(c, c->d_src_ptr); dfree(c, c->d_src_phi); dfree(c, c->d_src_col);
-  c->d_src_ptr = nullptr; c->d_src_phi = nullptr; c->d_src_col = nullptr; c->nsrc = 0;
+  // buffers only grow, so re-setting sources (e.g. a serving loop recycling slots) never
+  // frees device memory (cudaFree would synchronise the whole device)
+  c->nsrc = 0;
   if (nsrc == 0) return HDG_OK;
   const int d = c->dim, nc = c->nfc, Np = c->Np;
   const int64_t ne = c->sk.ne;
@@ -965,18 +1010,28 @@ hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const do
   std::vector<int32_t> ptr(ne + 1, 0);
   std::vector<double> phi((size_t)nsrc * Np);
   std::vector<int32_t> cols(nsrc, 0);
+  std::vector<double> delays(nsrc, 0.0);
   for (size_t i = 0; i < owner.size(); ++i) {
     ptr[owner[i].first + 1]++;
     const int s = owner[i].second;
     cols[i] = col ? col[s] : 0;
+    delays[i] = delay ? delay[s] : 0.0;
     dubiner(d, c->k, &xi_all[(size_t)s * d], 1, &phi[i * Np], nullptr);
     for (int q = 0; q < Np; ++q) phi[i * Np + q] *= amp[s];
   }
   for (int64_t e = 0; e < ne; ++e) ptr[e + 1] += ptr[e];
   hdg_status st;
-  if ((st = dalloc(c, &c->d_src_ptr, (size_t)ne + 1))) return st;
-  if ((st = dalloc(c, &c->d_src_phi, phi.size()))) return st;
-  if ((st = dalloc(c, &c->d_src_col, cols.size()))) return st;
+  if (!c->d_src_ptr && (st = dalloc(c, &c->d_src_ptr, (size_t)ne + 1))) return st;
+  if (nsrc > c->src_cap) {
+    const int cap = std::max(nsrc, 2 * c->src_cap);
+    dfree(c, c->d_src_phi); dfree(c, c->d_src_col); dfree(c, c->d_src_delay);
+    c->d_src_phi = nullptr; c->d_src_col = nullptr; c->d_src_delay = nullptr; c->src_cap = 0;
+    if ((st = dalloc(c, &c->d_src_phi, (size_t)cap * Np))) return st;
+    if ((st = dalloc(c, &c->d_src_col, (size_t)cap))) return st;
+    if ((st = dalloc(c, &c->d_src_delay, (size_t)cap))) return st;
+    c->src_cap = cap;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_src_delay, delays.data(), delays.size() * 8, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_src_col, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_src_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_src_phi, phi.data(), phi.size() * 8, cudaMemcpyHostToDevice, c->stream));
@@ -1169,6 +1224,34 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (info) { info->iterations = si.iterations; info->sweeps = si.sweeps; info->rel_residual = si.rel_residual; }
   return HDG_OK;
+}
+
+hdg_status hdg_stream_create(void** out) {
+  if (!out) return HDG_EINVAL;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return HDG_ECUDA;
+  *out = (void*)st;
+  return HDG_OK;
+}
+
+hdg_status hdg_stream_destroy(void* stream) {
+  if (!stream) return HDG_EINVAL;
+  return cudaStreamDestroy((cudaStream_t)stream) == cudaSuccess ? HDG_OK : HDG_ECUDA;
+}
+
+hdg_status hdg_reset_column(hdg_ctx* c, int32_t j) {
+  if (!c) return HDG_EINVAL;
+  if (j < 0 || j >= c->R) return fail(c, HDG_EINVAL, "column out of range");
+  const int64_t nf = c->sk.ne * c->n, nt = c->sk.nf * c->Nf;
+  for (double* a : {c->d_u, c->d_uprev}) {
+    c->n_launch += 1;
+    zero_column_kernel<<<grid_for(c, nf), 256, 0, c->stream>>>(nf, c->R, j, a);
+  }
+  for (double* a : {c->d_lam, c->d_lam_prev}) {
+    c->n_launch += 1;
+    zero_column_kernel<<<grid_for(c, nt), 256, 0, c->stream>>>(nt, c->R, j, a);
+  }
+  return check_launch(c, "reset_column");
 }
 
 hdg_status hdg_enable_stats(hdg_ctx* c, int32_t enable) {

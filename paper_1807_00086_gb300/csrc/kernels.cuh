@@ -36,6 +36,23 @@ struct DevMesh {
   const int32_t* face_bnd;
 };
 
+// Point sources: CSR by element (ptr[e]..ptr[e+1]), per source the basis values at the
+// point times its amplitude (phi), its right-hand-side column and its time delay; the
+// Ricker wavelet r(t - delay) = (1 - 2a) exp(-a), a = (pi f0 (t - delay - t0))^2.
+struct SrcArgs {
+  const int32_t* ptr;
+  const double* phi;
+  const int32_t* col;
+  const double* delay;
+  double f0, t0, t;
+};
+
+__device__ __forceinline__ double ricker_at(const SrcArgs& s, int q) {
+  const double x = 3.14159265358979323846 * s.f0 * (s.t - s.delay[q] - s.t0);
+  const double a = x * x;
+  return (1.0 - 2.0 * a) * exp(-a);
+}
+
 template <int DIM, int K>
 struct Dims {
   static constexpr int NP = (DIM == 2) ? (K + 1) * (K + 2) / 2 : (K + 1) * (K + 2) * (K + 3) / 6;
@@ -199,9 +216,7 @@ struct LocalCfg {
 template <int DIM, int K, int MODE>
 __global__ void __launch_bounds__(LocalCfg<DIM, K>::NT) local_kernel(DevMesh mesh, Tabs T, const double* __restrict__ Hinv,
                                                                     double alpha, double tau, const double* __restrict__ F,
-                                                                    const double* __restrict__ hist,
-                                                                    const int32_t* __restrict__ src_ptr,
-                                                                    const double* __restrict__ src_phi, double src_rt,
+                                                                    const double* __restrict__ hist, SrcArgs src,
                                                                     const double* __restrict__ lam, double* __restrict__ out) {
   using D = Dims<DIM, K>;
   using L = LocalCfg<DIM, K>;
@@ -269,8 +284,8 @@ __global__ void __launch_bounds__(LocalCfg<DIM, K>::NT) local_kernel(DevMesh mes
         if (hist) {
           const double sc = comp == 0 ? co[el][1] * dJ : b * dJ;
           v = sc * hist[e * N + comp * NP + i];
-          if (comp == 0 && src_ptr)
-            for (int q = src_ptr[e]; q < src_ptr[e + 1]; ++q) v += src_rt * src_phi[(int64_t)q * NP + i];
+          if (comp == 0 && src.ptr)
+            for (int q = src.ptr[e]; q < src.ptr[e + 1]; ++q) v += ricker_at(src, q) * src.phi[(int64_t)q * NP + i];
         } else {
           v = F[e * N + comp * NP + i];
         }

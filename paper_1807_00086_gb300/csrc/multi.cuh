@@ -21,8 +21,7 @@ struct LocalMultiCfg {
 template <int DIM, int K, int MODE>
 __global__ void __launch_bounds__(LocalMultiCfg<DIM, K>::NT)
     local_multi_kernel(DevMesh mesh, Tabs T, const double* __restrict__ Hinv, double alpha, double tau, int R,
-                       const double* __restrict__ F, const double* __restrict__ hist, const int32_t* __restrict__ src_ptr,
-                       const double* __restrict__ src_phi, const int32_t* __restrict__ src_col, double src_rt,
+                       const double* __restrict__ F, const double* __restrict__ hist, SrcArgs src,
                        const double* __restrict__ lam, double* __restrict__ out) {
   using D = Dims<DIM, K>;
   using L = LocalMultiCfg<DIM, K>;
@@ -76,9 +75,9 @@ __global__ void __launch_bounds__(LocalMultiCfg<DIM, K>::NT)
         const int64_t idx = (e * N + comp * NP + i) * R + j;
         if (hist) {
           v = (comp == 0 ? alpha * dJ / (rho * cc * cc) : b * dJ) * hist[idx];
-          if (comp == 0 && src_ptr)
-            for (int q = src_ptr[e]; q < src_ptr[e + 1]; ++q)
-              if (src_col[q] == j) v += src_rt * src_phi[(int64_t)q * NP + i];
+          if (comp == 0 && src.ptr)
+            for (int q = src.ptr[e]; q < src.ptr[e + 1]; ++q)
+              if (src.col[q] == j) v += ricker_at(src, q) * src.phi[(int64_t)q * NP + i];
         } else {
           v = F[idx];
         }
@@ -402,13 +401,15 @@ __global__ void __launch_bounds__(256) mupdate_kernel(int64_t n, int R, const TV
   if (threadIdx.x < R) part[(int64_t)(gridDim.x + blockIdx.x) * R + threadIdx.x] = red[threadIdx.x];
 }
 
-// rho_new, rr per column; convergence; beta (written to alpha slot of the other parity use)
-__global__ void mcols_beta(int nb, int R, int parity, int iter, int maxit, const double* __restrict__ part,
-                           MScal sc, double* __restrict__ beta) {
+// rho_new, rr per column; convergence; beta. Single block: the iteration counter lives on the
+// device (read by every thread before thread 0 advances it), so launches carry no host index.
+__global__ void mcols_beta(int nb, int R, int parity, int maxit, const double* __restrict__ part, MScal sc,
+                           double* __restrict__ beta) {
   __shared__ int notconv;
   if (threadIdx.x == 0) notconv = 0;
   __syncthreads();
   if (*sc.done) return;
+  const int iter = *sc.iters;
   for (int j = threadIdx.x; j < R; j += blockDim.x) {
     double rz = 0.0, rr = 0.0;
     for (int b = 0; b < nb; ++b) { rz += part[(int64_t)b * R + j]; rr += part[(int64_t)(nb + b) * R + j]; }
@@ -617,4 +618,12 @@ __global__ void mproject_volume_kernel(int64_t ne, int NP, int nq, int ncomp, in
   }
 }
 
+}  // namespace hdg
+
+namespace hdg {
+// column j of an [count][R] array <- 0
+__global__ void zero_column_kernel(int64_t count, int R, int j, double* __restrict__ a) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+    a[t * R + j] = 0.0;
+}
 }  // namespace hdg

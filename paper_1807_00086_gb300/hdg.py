@@ -35,7 +35,7 @@ class Material(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32),
-                ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32)]
+                ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32), ("use_graphs", c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -70,7 +70,10 @@ SIGNATURES = {
     "hdg_condensed_rhs": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hdg_trace_solve": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(SolveInfo)]),
     "hdg_recover": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
-    "hdg_set_sources": (c_int32, [c_void_p, c_int32, P_double, P_double, P_int32, c_double, c_double]),
+    "hdg_set_sources": (c_int32, [c_void_p, c_int32, P_double, P_double, P_int32, P_double, c_double, c_double]),
+    "hdg_reset_column": (c_int32, [c_void_p, c_int32]),
+    "hdg_stream_create": (c_int32, [ctypes.POINTER(c_void_p)]),
+    "hdg_stream_destroy": (c_int32, [c_void_p]),
     "hdg_quadrature_points": (c_int32, [c_void_p, c_int32, P_double]),
     "hdg_project_volume": (c_int32, [c_void_p, P_double, c_void_p]),
     "hdg_set_dirichlet": (c_int32, [c_void_p, P_double, c_double, c_double]),
@@ -101,6 +104,23 @@ def load():
     return _lib
 
 
+def own_stream():
+    """A dedicated CUDA stream created by the library (torch.cuda.ExternalStream wrapper).
+    torch.cuda.Stream() draws from a small per-device pool, so many contexts would share
+    streams; the caller must call release_stream() after closing the context."""
+    import torch
+    lib = load()
+    p = ctypes.c_void_p()
+    st = lib.hdg_stream_create(ctypes.byref(p))
+    if st != 0:
+        raise HDGError(st, "hdg_stream_create failed")
+    return torch.cuda.ExternalStream(p.value)
+
+
+def release_stream(stream):
+    load().hdg_stream_destroy(ctypes.c_void_p(stream.cuda_stream))
+
+
 class HDGError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (STATUS.get(status, status), msg))
@@ -119,7 +139,7 @@ class Solver:
     """One HDG problem resident on the current CUDA device (wraps an hdg_ctx)."""
 
     def __init__(self, vert, elem, k, tau, rho, c, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
-                 inner_rtol=None, max_sweeps=None, nrhs=1, stream=None):
+                 inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None):
         import torch
         self.lib = load()
         self.torch = torch
@@ -139,6 +159,7 @@ class Solver:
         if max_sweeps is not None:
             opt.max_sweeps = max_sweeps
         opt.nrhs = nrhs
+        opt.use_graphs = 1 if use_graphs else 0
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -220,15 +241,22 @@ class Solver:
                                          self._dev(lam, self._tshape), self._dev(u, self._fshape)))
         return u
 
-    def hdg_set_sources(self, pos, amp, f0, t0, col=None):
+    def hdg_set_sources(self, pos, amp, f0, t0, col=None, delay=None):
         pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, self.dim))
         amp = np.ascontiguousarray(np.broadcast_to(np.asarray(amp, dtype=np.float64), (pos.shape[0],)))
         colp = None
         if col is not None:
             col = np.ascontiguousarray(np.asarray(col, dtype=np.int32).reshape(-1))
             colp = _np_ptr(col, c_int32)
+        delp = None
+        if delay is not None:
+            delay = np.ascontiguousarray(np.asarray(delay, dtype=np.float64).reshape(-1))
+            delp = _np_ptr(delay, c_double)
         self._check(self.lib.hdg_set_sources(self.ctx, pos.shape[0], _np_ptr(pos, c_double), _np_ptr(amp, c_double),
-                                             colp, f0, t0))
+                                             colp, delp, f0, t0))
+
+    def hdg_reset_column(self, j):
+        self._check(self.lib.hdg_reset_column(self.ctx, j))
 
     def hdg_quadrature_points(self, which):
         nq = self.sizes.nq_vol if which == 0 else self.sizes.nq_face
