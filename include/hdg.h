@@ -2,9 +2,11 @@
  *
  * The library implements the data-parallel hot path of the hybridized DG method of
  * Fernandez, Christophe, Terrana, Nguyen and Peraire, "Hybridized discontinuous Galerkin
- * methods for wave propagation" (arXiv 1807.00086), for first-order acoustics
- * (1/(rho c^2)) p_t + div v = s, rho v_t + grad p = 0 on affine triangles (d = 2) and
- * tetrahedra (d = 3):
+ * methods for wave propagation" (arXiv 1807.00086), on affine triangles (d = 2) and
+ * tetrahedra (d = 3), for first-order acoustics (1/(rho c^2)) p_t + div v = s,
+ * rho v_t + grad p = 0, and for linear elastodynamics (Sec. 4.1) in the velocity /
+ * symmetric-stress form C^{-1} sigma_t = eps(v), rho v_t = div sigma, flux
+ * sigma_hat n = sigma n - s (v - v_hat), s = 2 rho c_s (Eq. eq:stab_matrix_lin):
  *
  *   Sec. 2.2 (Eqs. e:spaces1, e:spaces2)  discontinuous P_k fields, P_k face traces (HDG);
  *   Sec. 2.3 (Eqs. ch5appendx1:eq8-eq10)  the semi-discrete DAE, BDF steps and DIRK stages;
@@ -15,12 +17,16 @@
  *   - element vertices are used in ascending global id; local face j is opposite local
  *     vertex j; a face is parametrised from its vertices in ascending global id;
  *   - faces are numbered 0..n_faces-1 in lexicographic order of their sorted vertex ids;
- *   - element fields: [n_elem][d+1][Np] FP64, components (p, v_1, .., v_d), coefficients
- *     in the orthonormal Dubiner basis of the unit reference simplex (mass = |det J| I);
+ *   - element fields: [n_elem][ncomp][Np] FP64, coefficients in the orthonormal Dubiner basis
+ *     of the unit reference simplex (mass = |det J| I); acoustic components (p, v_1, .., v_d),
+ *     ncomp = d + 1; elastic components (v_1, .., v_d, sigma_11, sigma_22, [sigma_33,
+ *     sigma_23, sigma_13,] sigma_12), ncomp = d + d(d+1)/2;
  *   - face traces: [n_faces][Nf] FP64 in the orthonormal basis of the reference face
  *     (face mass = J_F I, J_F = edge length (d = 2) or twice the face area (d = 3));
- *   - Np = C(k+d, d), Nf = C(k+d-1, d-1), n = (d+1) Np, m = (d+1) Nf;
- *   - boundary faces carry Dirichlet data for p_hat; only interior faces are unknowns.
+ *     acoustic: p_hat, Nf = C(k+d-1, d-1); elastic: v_hat component-major, Nf = d C(k+d-1, d-1);
+ *   - Np = C(k+d, d), n = ncomp Np, m = (d+1) Nf;
+ *   - boundary faces carry Dirichlet data for the trace (elastic: clamped, v_hat = 0); only
+ *     interior faces are unknowns.
  *
  * Memory: pointers named *_dev are device pointers owned by the caller, used on the
  * context's stream and borrowed for the duration of the call (the call returns after
@@ -53,6 +59,7 @@ typedef enum {
 } hdg_status;
 
 typedef enum { HDG_BE = 1, HDG_BDF2 = 2, HDG_DIRK3 = 3 } hdg_scheme;
+typedef enum { HDG_ACOUSTIC = 0, HDG_ELASTIC = 1 } hdg_physics;
 typedef enum { HDG_FP64 = 0, HDG_MIXED = 1 } hdg_precision;
 
 typedef struct {
@@ -63,8 +70,11 @@ typedef struct {
 } hdg_mesh;
 
 typedef struct {
+  hdg_physics phys;         /* HDG_ACOUSTIC (uses rho, c) or HDG_ELASTIC (rho, lam, mu) */
   const double* rho;        /* _host [n_elem] density, > 0                           */
-  const double* c;          /* _host [n_elem] sound speed, > 0                       */
+  const double* c;          /* _host [n_elem] sound speed, > 0 (acoustic)            */
+  const double* lam;        /* _host [n_elem] Lame lambda (elastic), d lam + 2 mu > 0 */
+  const double* mu;         /* _host [n_elem] Lame mu (elastic), > 0                 */
 } hdg_material;
 
 typedef struct {

@@ -14,6 +14,7 @@
 #include "../../include/hdg.h"
 #include "kernels.cuh"
 #include "multi.cuh"
+#include "elastic.cuh"
 #include "mesh.h"
 #include "reftab.h"
 
@@ -24,6 +25,11 @@ struct hdg_ctx {
   cudaStream_t stream = nullptr;
   hdg_options opt{};
   int dim = 0, k = 0, Np = 0, Nf = 0, n = 0, m = 0, nfc = 0;
+  int phys = 0;             // HDG_ACOUSTIC or HDG_ELASTIC
+  int ncomp = 0;            // field components per element
+  int nv = 0;               // size of the factored local block (H^{-1} is nv x nv)
+  double sgn = -1.0;        // the Krylov operator is sgn * K (SPD)
+  double *d_lame = nullptr, *d_mue = nullptr;
   int sms = 148;
   double tau = 1.0;
   Skeleton sk;
@@ -205,13 +211,31 @@ template <int DIM, int K>
 void launch_condense(hdg_ctx* c) {
   constexpr int NT = 128;
   c->n_launch += 2;
+  if (c->phys == HDG_ELASTIC) {
+    const size_t smem = CondElCfg<DIM, K>::SMEM;
+    cudaFuncSetAttribute(condense_el_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    condense_el_kernel<DIM, K><<<(unsigned)c->sk.ne, 256, smem, c->stream>>>(devmesh(c), c->tabs, c->d_lame, c->d_mue,
+                                                                            c->alpha, c->d_S, c->d_Hinv, c->d_err);
+    diag_kernel<ElDims<DIM, K>><<<grid_for(c, c->sk.nf * c->Nf), 256, 0, c->stream>>>(devmesh(c), c->d_S, c->sgn, c->d_dinv);
+    return;
+  }
   condense_kernel<DIM, K, NT><<<(unsigned)c->sk.ne, NT, 0, c->stream>>>(devmesh(c), c->tabs, c->alpha, c->tau, c->d_S,
                                                                        c->d_Hinv, c->d_err);
-  diag_kernel<DIM, K><<<grid_for(c, c->sk.nf * c->Nf), 256, 0, c->stream>>>(devmesh(c), c->d_S, c->d_dinv);
+  diag_kernel<Dims<DIM, K>><<<grid_for(c, c->sk.nf * c->Nf), 256, 0, c->stream>>>(devmesh(c), c->d_S, c->sgn, c->d_dinv);
 }
 
 template <int DIM, int K>
 void launch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double t, const double* lam, double* out) {
+  if (c->phys == HDG_ELASTIC) {
+    c->n_launch += 1;
+    if (mode == 0)
+      local_el_kernel<DIM, K, 0><<<(unsigned)c->sk.ne, 128, 0, c->stream>>>(devmesh(c), c->tabs, c->d_lame, c->d_mue,
+                                                                            c->d_Hinv, c->alpha, F, hist, lam, out);
+    else
+      local_el_kernel<DIM, K, 1><<<(unsigned)c->sk.ne, 128, 0, c->stream>>>(devmesh(c), c->tabs, c->d_lame, c->d_mue,
+                                                                            c->d_Hinv, c->alpha, F, hist, lam, out);
+    return;
+  }
   using L = LocalCfg<DIM, K>;
   const unsigned grid = (unsigned)((c->sk.ne + L::EPB - 1) / L::EPB);
   const SrcArgs sa = srcargs(c, t);
@@ -224,14 +248,20 @@ void launch_local(hdg_ctx* c, int mode, const double* F, const double* hist, dou
                                                             out);
 }
 
-template <int DIM, int K>
-void launch_apply(hdg_ctx* c, const double* x, double* zslot, const int* done, int iter = -1) {
-  using C = ApplyCfg<DIM, K>;
+template <class L>
+void launch_apply_l(hdg_ctx* c, const double* x, double* zslot, const int* done, int iter) {
+  using C = ApplyCfg<L>;
   const unsigned grid = (unsigned)((c->sk.ne + C::EPB - 1) / C::EPB);
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 0, iter);
-  apply_kernel<DIM, K><<<grid, C::NT, 0, c->stream>>>(devmesh(c), c->d_S, x, zslot, done);
+  apply_kernel<L><<<grid, C::NT, 0, c->stream>>>(devmesh(c), c->d_S, x, zslot, done);
   apply_end(c, stop);
+}
+
+template <int DIM, int K>
+void launch_apply(hdg_ctx* c, const double* x, double* zslot, const int* done, int iter = -1) {
+  if (c->phys == HDG_ELASTIC) launch_apply_l<ElDims<DIM, K>>(c, x, zslot, done, iter);
+  else launch_apply_l<Dims<DIM, K>>(c, x, zslot, done, iter);
 }
 
 hdg_status check_launch(hdg_ctx* c, const char* what) {
@@ -250,14 +280,24 @@ void launch_pack32(hdg_ctx* c) {
 
 template <int DIM, int K>
 void launch_face_q64(hdg_ctx* c) {
-  cg_face_q_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->d_face_slot, c->d_face_bnd, c->d_slot, c->d_p,
-                                                             c->d_q, c->d_part, c->d_sc);
+  if (c->phys == HDG_ELASTIC)
+    cg_face_q_kernel<ElDims<DIM, K>><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->sgn, c->d_face_slot, c->d_face_bnd,
+                                                                       c->d_slot, c->d_p, c->d_q, c->d_part, c->d_sc);
+  else
+    cg_face_q_kernel<Dims<DIM, K>><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->sgn, c->d_face_slot, c->d_face_bnd,
+                                                                     c->d_slot, c->d_p, c->d_q, c->d_part, c->d_sc);
 }
 
 template <int DIM, int K>
 void launch_face_q32(hdg_ctx* c) {
-  cg32_face_q_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->d_face_slot, c->d_face_bnd, c->d_slot32,
-                                                               c->d_p32, c->d_q32, c->d_part, c->d_sc);
+  if (c->phys == HDG_ELASTIC)
+    cg32_face_q_kernel<ElDims<DIM, K>><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, (float)c->sgn, c->d_face_slot,
+                                                                         c->d_face_bnd, c->d_slot32, c->d_p32, c->d_q32,
+                                                                         c->d_part, c->d_sc);
+  else
+    cg32_face_q_kernel<Dims<DIM, K>><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, (float)c->sgn, c->d_face_slot,
+                                                                       c->d_face_bnd, c->d_slot32, c->d_p32, c->d_q32,
+                                                                       c->d_part, c->d_sc);
 }
 
 template <int DIM, int K>
@@ -273,6 +313,12 @@ void launch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, in
   const int64_t ngroups = (c->sk.ne + 31) / 32;
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 1, iter);
+  if (c->phys == HDG_ELASTIC) {
+    apply32f_kernel<ElDims<DIM, K>><<<(unsigned)((c->sk.ne + 3) / 4), 128, 0, c->stream>>>(
+        c->sk.ne, c->d_elem_face, c->d_face_bnd, c->d_S32, x, slot, done);
+    apply_end(c, stop);
+    return;
+  }
   apply32_kernel<DIM, K><<<(unsigned)((ngroups + 3) / 4), 128, 0, c->stream>>>(c->sk.ne, c->d_elem_face, c->d_face_bnd,
                                                                               c->d_S32, x, slot, done);
   apply_end(c, stop);
@@ -286,7 +332,11 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
   hdg_status s = check_launch(c, "condense");
   if (s) return s;
   if (c->opt.prec == HDG_MIXED) {
-    if (c->R > 1) {
+    if (c->phys == HDG_ELASTIC) {
+      const int64_t nS = c->sk.ne * (int64_t)c->m * c->m;
+      c->n_launch += 1;
+      to32_copy_kernel<<<grid_for(c, nS), 256, 0, c->stream>>>(nS, c->d_S, c->d_S32);
+    } else if (c->R > 1) {
       HDG_DISPATCH(c, launch_pack32m, c);
     } else {
       HDG_DISPATCH(c, launch_pack32, c);
@@ -363,7 +413,7 @@ hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
   for (int sweep = 0;; ++sweep) {
     HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
     c->n_launch += 2;
-    refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec,
+    refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec,
                                                       c->d_res, c->d_part);
     refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
     if ((s = check_launch(c, "refine_residual"))) return s;
@@ -404,7 +454,7 @@ hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* i
   const int nb = c->nb_red;
   HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
   c->n_launch += 2;
-  cg_init_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec, c->d_dinv, c->d_r,
+  cg_init_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec, c->d_dinv, c->d_r,
                                             c->d_z, c->d_p, c->d_part);
   cg_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->opt.rtol, c->d_sc);
   hdg_status s = check_launch(c, "cg_init");
@@ -704,7 +754,8 @@ hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, 
   HDG_DISPATCH(c, launch_local, c, 0, (const double*)nullptr, hist, tt, c->d_lam, c->d_slot);
   hdg_status s = check_launch(c, "rhs");
   if (s) return s;
-  if ((s = faces_from_slots(c, 1.0, c->d_b))) return s;
+  // Krylov right-hand side b = sgn r = -sgn sum_K C_K A_K^{-1} F~_K
+  if ((s = faces_from_slots(c, -c->sgn, c->d_b))) return s;
   if ((s = cg_solve(c, c->d_b, c->d_lam, info))) return s;
   HDG_DISPATCH(c, launch_local, c, 1, (const double*)nullptr, hist, tt, c->d_lam, uout);
   return check_launch(c, "recover");
@@ -773,7 +824,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   hdg_ctx* c = new (std::nothrow) hdg_ctx();
   if (!c) return HDG_ENOMEM;
   *out = c;
-  if (!mesh || !mat || !mesh->vert || !mesh->elem_vert || !mat->rho || !mat->c)
+  if (!mesh || !mat || !mesh->vert || !mesh->elem_vert || !mat->rho || (mat->phys == HDG_ACOUSTIC && !mat->c))
     return fail(c, HDG_EINVAL, "null mesh or material pointer");
   if (k < 1 || k > 4) return fail(c, HDG_EINVAL, "degree k must be in 1..4");
   if (!(tau > 0.0)) return fail(c, HDG_EINVAL, "tau must be positive");
@@ -786,18 +837,40 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
     return fail(c, HDG_EINVAL, "nrhs must be a power of two in 1..256");
   c->R = c->opt.nrhs;
   std::string err;
+  if (mat->phys != HDG_ACOUSTIC && mat->phys != HDG_ELASTIC) return fail(c, HDG_EINVAL, "unknown physics");
+  c->phys = mat->phys;
+  if (c->phys == HDG_ELASTIC && (!mat->lam || !mat->mu)) return fail(c, HDG_EINVAL, "elastic material needs lam and mu");
+  if (c->phys == HDG_ELASTIC && c->opt.nrhs != 1) return fail(c, HDG_EINVAL, "elastic path supports nrhs = 1 only");
+  if (c->phys == HDG_ELASTIC && mesh->dim == 3 && k == 4)
+    return fail(c, HDG_EINVAL, "elastic path in 3D supports 1 <= k <= 3 (the local block does not fit shared memory)");
   if (!build_skeleton(mesh->dim, mesh->n_vert, mesh->n_elem, mesh->vert, mesh->elem_vert, c->sk, err))
     return fail(c, HDG_EINVAL, err);
-  for (int64_t e = 0; e < mesh->n_elem; ++e)
-    if (!(mat->rho[e] > 0.0) || !(mat->c[e] > 0.0)) return fail(c, HDG_EINVAL, "rho and c must be positive");
+  for (int64_t e = 0; e < mesh->n_elem; ++e) {
+    if (!(mat->rho[e] > 0.0)) return fail(c, HDG_EINVAL, "rho must be positive");
+    if (c->phys == HDG_ACOUSTIC && !(mat->c[e] > 0.0)) return fail(c, HDG_EINVAL, "c must be positive");
+    if (c->phys == HDG_ELASTIC && (!(mat->mu[e] > 0.0) || !(mesh->dim * mat->lam[e] + 2.0 * mat->mu[e] > 0.0)))
+      return fail(c, HDG_EINVAL, "Lame parameters must satisfy mu > 0 and d lam + 2 mu > 0");
+  }
   c->dim = mesh->dim; c->k = k; c->tau = tau;
   try {
     c->T = build_tables(c->dim, k);
   } catch (const std::exception& ex) {
     return fail(c, HDG_EINVAL, ex.what());
   }
-  c->Np = c->T.Np; c->Nf = c->T.Nf; c->nfc = c->dim + 1;
-  c->n = c->nfc * c->Np; c->m = c->nfc * c->Nf;
+  c->Np = c->T.Np; c->nfc = c->dim + 1;
+  if (c->phys == HDG_ELASTIC) {
+    const int nt = c->dim * (c->dim + 1) / 2;
+    c->ncomp = c->dim + nt;
+    c->Nf = c->dim * c->T.Nf;          // trace DOFs per face: d velocity components
+    c->nv = c->dim * c->Np;
+    c->sgn = 1.0;
+  } else {
+    c->ncomp = c->dim + 1;
+    c->Nf = c->T.Nf;
+    c->nv = c->Np;
+    c->sgn = -1.0;
+  }
+  c->n = c->ncomp * c->Np; c->m = c->nfc * c->Nf;
   c->stream = (cudaStream_t)cuda_stream;
   int dev = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
@@ -826,7 +899,15 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if ((s = dalloc(c, &c->d_bnd_faces, (size_t)nb))) return s;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_geo, c->sk.geo.data(), c->sk.geo.size() * 8, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_rho, mat->rho, ne * 8, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_c, mat->c, ne * 8, cudaMemcpyHostToDevice, c->stream));
+  if (c->phys == HDG_ACOUSTIC) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_c, mat->c, ne * 8, cudaMemcpyHostToDevice, c->stream));
+  } else {
+    if ((s = dalloc(c, &c->d_lame, (size_t)ne))) return s;
+    if ((s = dalloc(c, &c->d_mue, (size_t)ne))) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_lame, mat->lam, ne * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_mue, mat->mu, ne * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_c, mat->rho, ne * 8, cudaMemcpyHostToDevice, c->stream));   // sound-speed slot unused
+  }
   CUDA_TRY(c, cudaMemcpyAsync(c->d_elem_face, c->sk.elem_face.data(), c->sk.elem_face.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_face_slot, c->sk.face_slot.data(), c->sk.face_slot.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_face_bnd, c->sk.face_bnd.data(), c->sk.face_bnd.size() * 4, cudaMemcpyHostToDevice, c->stream));
@@ -848,7 +929,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   const size_t nfe = (size_t)nf * c->Nf;
   const size_t R = (size_t)c->R;
   if ((s = dalloc(c, &c->d_S, (size_t)ne * c->m * c->m))) return s;
-  if ((s = dalloc(c, &c->d_Hinv, (size_t)ne * c->Np * c->Np))) return s;
+  if ((s = dalloc(c, &c->d_Hinv, (size_t)ne * c->nv * c->nv))) return s;
   if ((s = dalloc(c, &c->d_dinv, nfe))) return s;
   if ((s = dalloc(c, &c->d_err, 1))) return s;
   for (double** p : {&c->d_r, &c->d_z, &c->d_p, &c->d_q, &c->d_b, &c->d_lam, &c->d_lam_prev, &c->d_lam_x})
@@ -875,7 +956,8 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if (c->opt.prec == HDG_MIXED) {
     const int64_t ngroups = (ne + 31) / 32;
     const int P4 = (c->m * (c->m + 1) / 2 + 3) / 4;
-    if ((s = dalloc(c, &c->d_S32, (size_t)ngroups * P4 * 128))) return s;
+    const size_t nS32 = c->phys == HDG_ELASTIC ? (size_t)ne * c->m * c->m : (size_t)ngroups * P4 * 128;
+    if ((s = dalloc(c, &c->d_S32, nS32))) return s;
     if ((s = dalloc(c, &c->d_slot32, (size_t)ngroups * c->m * 32))) return s;
     c->nfe4 = (int64_t)((nfe + 3) / 4) * 4;
     const size_t n32 = c->R > 1 ? nfe * R : (size_t)c->nfe4;
@@ -950,9 +1032,9 @@ hdg_status hdg_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_i
   if (!c || !r || !lam) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
   if (info) { info->iterations = 0; info->sweeps = 0; info->rel_residual = 0; }
-  // K lam = r  <=>  (-K) lam = -r
+  // K lam = r  <=>  (sgn K) lam = sgn r
   const int64_t nfe = c->sk.nf * c->Nf * (int64_t)c->R;
-  combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, -1.0, r, 0, nullptr, 0, nullptr, 0, nullptr, c->d_b);
+  combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->sgn, r, 0, nullptr, 0, nullptr, 0, nullptr, c->d_b);
   hdg_status s = check_launch(c, "negate");
   if (s) return s;
   if (c->R > 1) {
@@ -979,6 +1061,7 @@ hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const do
   if (!c || nsrc < 0 || (nsrc > 0 && (!pos || !amp))) return fail(c, HDG_EINVAL, "bad source arguments");
   for (int s2 = 0; col && s2 < nsrc; ++s2)
     if (col[s2] < 0 || col[s2] >= c->R) return fail(c, HDG_EINVAL, "source column out of range");
+  if (c->phys == HDG_ELASTIC && nsrc > 0) return fail(c, HDG_EINVAL, "point sources are acoustic only");
   // buffers only grow, so re-setting sources (e.g. a serving loop recycling slots) never
   // frees device memory (cudaFree would synchronise the whole device)
   c->nsrc = 0;
@@ -1077,7 +1160,7 @@ hdg_status hdg_quadrature_points(hdg_ctx* c, int32_t which, double* xyz) {
 
 hdg_status hdg_project_volume(hdg_ctx* c, const double* vals, double* u) {
   if (!c || !vals || !u) return fail(c, HDG_EINVAL, "null argument");
-  const size_t cnt = (size_t)c->sk.ne * c->T.nqv * c->nfc;
+  const size_t cnt = (size_t)c->sk.ne * c->T.nqv * c->ncomp;
   double* dv = nullptr;
   hdg_status s;
   if ((s = dalloc(c, &dv, cnt))) return s;
@@ -1085,10 +1168,10 @@ hdg_status hdg_project_volume(hdg_ctx* c, const double* vals, double* u) {
   if (e1 == cudaSuccess) {
     const int64_t n = c->sk.ne * c->n * (int64_t)c->R;
     if (c->R > 1)
-      mproject_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->nfc, c->R, c->d_qv_w,
+      mproject_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->ncomp, c->R, c->d_qv_w,
                                                                    c->d_qv_phi, dv, u);
     else
-      project_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->nfc, c->d_qv_w, c->d_qv_phi,
+      project_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->ncomp, c->d_qv_w, c->d_qv_phi,
                                                                   dv, u);
     e1 = cudaGetLastError();
   }
@@ -1105,6 +1188,7 @@ hdg_status hdg_set_dirichlet(hdg_ctx* c, const double* vals, double omega, doubl
   c->d_bnd_coef = nullptr;
   c->omega = omega; c->phase = phase;
   if (!vals || c->sk.nb == 0) return HDG_OK;
+  if (c->phys == HDG_ELASTIC) return fail(c, HDG_EINVAL, "elastic path supports clamped boundaries (NULL data) only");
   // lam_f[m] = sum_q w_q g(x_q) mu_m(eta_q)   (face mass J_F I cancels J_F)
   const int nq = c->T.nqf, Nf = c->Nf;
   std::vector<double> coef((size_t)c->sk.nb * Nf, 0.0);

@@ -176,10 +176,10 @@ __global__ void __launch_bounds__(NT) condense_kernel(DevMesh mesh, Tabs T, doub
   }
 }
 
-// Jacobi preconditioner of -K: dinv = -1 / (sum over the face's slots of diag S_K).
-template <int DIM, int K>
-__global__ void diag_kernel(DevMesh mesh, const double* __restrict__ S, double* __restrict__ dinv) {
-  using D = Dims<DIM, K>;
+// Jacobi preconditioner: dinv = sgn / (sum over the face's slots of diag S_K), sgn = -1 for the
+// acoustic convention (K negative definite), +1 for the elastic one (K positive definite).
+template <class D>
+__global__ void diag_kernel(DevMesh mesh, const double* __restrict__ S, double sgn, double* __restrict__ dinv) {
   constexpr int NF = D::NF, M = D::M;
   const int64_t n = mesh.nf * NF;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
@@ -193,7 +193,7 @@ __global__ void diag_kernel(DevMesh mesh, const double* __restrict__ S, double* 
         const int r = (int)(slot % D::NFC) * NF + mm;
         d += S[e * (int64_t)(M * M) + (int64_t)r * M + r];
       }
-      dinv[t] = -1.0 / d;
+      dinv[t] = sgn / d;
     } else {
       dinv[t] = 0.0;
     }
@@ -379,20 +379,19 @@ __global__ void __launch_bounds__(LocalCfg<DIM, K>::NT) local_kernel(DevMesh mes
 // ---------------------------------------------------------------- matrix-free trace apply (d)
 // zslot[e][r] = sum_c S_K[r][c] x_K[c], x gathered from faces (boundary faces read as 0).
 // S_K is symmetric, so thread r reads column r (coalesced across the element's threads).
-template <int DIM, int K>
+template <class L>
 struct ApplyCfg {
-  static constexpr int M = Dims<DIM, K>::M;
+  static constexpr int M = L::M;
   static constexpr int EPB = (128 / M) > 0 ? (128 / M) : 1;
   static constexpr int NT = EPB * M;
 };
 
-template <int DIM, int K>
-__global__ void __launch_bounds__(ApplyCfg<DIM, K>::NT) apply_kernel(DevMesh mesh, const double* __restrict__ S,
-                                                                     const double* __restrict__ x,
-                                                                     double* __restrict__ zslot,
-                                                                     const int* __restrict__ done) {
-  using D = Dims<DIM, K>;
-  using C = ApplyCfg<DIM, K>;
+template <class D>
+__global__ void __launch_bounds__(ApplyCfg<D>::NT) apply_kernel(DevMesh mesh, const double* __restrict__ S,
+                                                                const double* __restrict__ x,
+                                                                double* __restrict__ zslot,
+                                                                const int* __restrict__ done) {
+  using C = ApplyCfg<D>;
   constexpr int NF = D::NF, M = D::M, NFC = D::NFC;
   if (done && *done) return;
   __shared__ double lx[C::EPB][M];
@@ -488,8 +487,8 @@ __global__ void face_gather_kernel(int64_t nf, int NF, const int32_t* __restrict
   }
 }
 
-// r = b - (-K) x0, z = Dinv r, p = z; partials (rz, rr, bb) per block.
-__global__ void cg_init_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_slot,
+// r = b - (sgn K) x0, z = Dinv r, p = z; partials (rz, rr, bb) per block.
+__global__ void cg_init_kernel(int64_t nf, int NF, double sgn, const int32_t* __restrict__ face_slot,
                                const int32_t* __restrict__ face_bnd, const double* __restrict__ zslot,
                                const double* __restrict__ bvec, const double* __restrict__ dinv, double* __restrict__ r,
                                double* __restrict__ z, double* __restrict__ p, double* __restrict__ part) {
@@ -501,7 +500,7 @@ __global__ void cg_init_kernel(int64_t nf, int NF, const int32_t* __restrict__ f
     const int mm = (int)(t % NF);
     double rv = 0, zv = 0;
     if (face_bnd[f] < 0) {
-      const double q = -face_sum(face_slot, zslot, f, mm, NF);
+      const double q = sgn * face_sum(face_slot, zslot, f, mm, NF);
       const double bv = bvec[t];
       rv = bv - q;
       zv = dinv[t] * rv;
@@ -529,14 +528,14 @@ __global__ void cg_init_scalars(int nb, const double* __restrict__ part, double 
   }
 }
 
-// q = (-K) p on faces; partial p.q (NF compile-time)
-template <int DIM, int K>
-__global__ void __launch_bounds__(256) cg_face_q_kernel(int nf, const int32_t* __restrict__ face_slot,
+// q = (-K) p on faces (sgn = -1; +K for sgn = +1); partial p.q (NF compile-time)
+template <class LD>
+__global__ void __launch_bounds__(256) cg_face_q_kernel(int nf, double sgn, const int32_t* __restrict__ face_slot,
                                                         const int32_t* __restrict__ face_bnd,
                                                         const double* __restrict__ zslot, const double* __restrict__ p,
                                                         double* __restrict__ q, double* __restrict__ part,
                                                         const CgScal* __restrict__ sc) {
-  constexpr int NF = Dims<DIM, K>::NF;
+  constexpr int NF = LD::NF;
   if (sc->done) return;
   __shared__ double red[8];
   double pq = 0;
@@ -546,7 +545,7 @@ __global__ void __launch_bounds__(256) cg_face_q_kernel(int nf, const int32_t* _
       const double* s0 = zslot + (int64_t)face_slot[2 * f] * NF;
       const double* s1 = zslot + (int64_t)face_slot[2 * f + 1] * NF;
 #pragma unroll
-      for (int mm = 0; mm < NF; ++mm) qv[mm] = -(s0[mm] + s1[mm]);
+      for (int mm = 0; mm < NF; ++mm) qv[mm] = sgn * (s0[mm] + s1[mm]);
     } else {
 #pragma unroll
       for (int mm = 0; mm < NF; ++mm) qv[mm] = 0.0;
@@ -769,14 +768,14 @@ __global__ void __launch_bounds__(128) apply32_kernel(int64_t ne, const int32_t*
   for (int idx = lane; idx < nvalid * M; idx += 32) dst[idx] = t[(idx / M) * MP + idx % M];
 }
 
-// q = (-K32) p on faces; partial p.q in FP64. NF is compile-time (no integer division).
-template <int DIM, int K>
-__global__ void __launch_bounds__(256) cg32_face_q_kernel(int nf, const int32_t* __restrict__ face_slot,
+// q = sgn K32 p on faces; partial p.q in FP64. NF is compile-time (no integer division).
+template <class LD>
+__global__ void __launch_bounds__(256) cg32_face_q_kernel(int nf, float sgn, const int32_t* __restrict__ face_slot,
                                                           const int32_t* __restrict__ face_bnd,
                                                           const float* __restrict__ slot, const float* __restrict__ p,
                                                           float* __restrict__ q, double* __restrict__ part,
                                                           const CgScal* __restrict__ sc) {
-  constexpr int NF = Dims<DIM, K>::NF;
+  constexpr int NF = LD::NF;
   if (sc->done) return;
   __shared__ double red[8];
   Acc2 pq;
@@ -786,7 +785,7 @@ __global__ void __launch_bounds__(256) cg32_face_q_kernel(int nf, const int32_t*
       const float* s0 = slot + (int64_t)face_slot[2 * f] * NF;
       const float* s1 = slot + (int64_t)face_slot[2 * f + 1] * NF;
 #pragma unroll
-      for (int mm = 0; mm < NF; ++mm) qv[mm] = -(s0[mm] + s1[mm]);
+      for (int mm = 0; mm < NF; ++mm) qv[mm] = sgn * (s0[mm] + s1[mm]);
     } else {
 #pragma unroll
       for (int mm = 0; mm < NF; ++mm) qv[mm] = 0.f;
@@ -906,8 +905,8 @@ __global__ void cg32_direction_kernel(int64_t n4, int nb, int parity, int iter, 
   }
 }
 
-// FP64 refinement residual rho = b - (-K) lam = b + sum slots64 (interior), partial |rho|^2 and |b|^2
-__global__ void refine_residual_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_slot,
+// FP64 refinement residual rho = b - (sgn K) lam = b - sgn sum slots64 (interior), partials |rho|^2, |b|^2
+__global__ void refine_residual_kernel(int64_t nf, int NF, double sgn, const int32_t* __restrict__ face_slot,
                                        const int32_t* __restrict__ face_bnd, const double* __restrict__ zslot,
                                        const double* __restrict__ b, double* __restrict__ rho,
                                        double* __restrict__ part) {
@@ -920,7 +919,7 @@ __global__ void refine_residual_kernel(int64_t nf, int NF, const int32_t* __rest
     double v = 0.0;
     if (face_bnd[f] < 0) {
       const double bv = b[t];
-      v = bv + face_sum(face_slot, zslot, f, mm, NF);
+      v = bv - sgn * face_sum(face_slot, zslot, f, mm, NF);
       bb += bv * bv;
     }
     rho[t] = v;

@@ -30,7 +30,7 @@ class Mesh(ctypes.Structure):
 
 
 class Material(ctypes.Structure):
-    _fields_ = [("rho", P_double), ("c", P_double)]
+    _fields_ = [("phys", c_int32), ("rho", P_double), ("c", P_double), ("lam", P_double), ("mu", P_double)]
 
 
 class Options(ctypes.Structure):
@@ -138,18 +138,27 @@ def _np_ptr(a, ct):
 class Solver:
     """One HDG problem resident on the current CUDA device (wraps an hdg_ctx)."""
 
-    def __init__(self, vert, elem, k, tau, rho, c, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
-                 inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None):
+    def __init__(self, vert, elem, k, tau, rho, c=None, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
+                 inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None, lam=None, mu=None):
+        """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu)."""
         import torch
         self.lib = load()
         self.torch = torch
         vert = np.ascontiguousarray(vert, dtype=np.float64)
         elem = np.ascontiguousarray(elem, dtype=np.int32)
         ne = elem.shape[0]
-        self._rho = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), (ne,)))
-        self._c = np.ascontiguousarray(np.broadcast_to(np.asarray(c, dtype=np.float64), (ne,)))
+        arr = lambda a: np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), (ne,)))
+        self._rho = arr(rho)
+        self.elastic = lam is not None
+        if self.elastic:
+            self._lam, self._mu = arr(lam), arr(mu)
+            self._c = arr(1.0)
+            mat = Material(1, _np_ptr(self._rho, c_double), _np_ptr(self._c, c_double), _np_ptr(self._lam, c_double),
+                           _np_ptr(self._mu, c_double))
+        else:
+            self._c = arr(c)
+            mat = Material(0, _np_ptr(self._rho, c_double), _np_ptr(self._c, c_double), None, None)
         mesh = Mesh(vert.shape[1], vert.shape[0], ne, _np_ptr(vert, c_double), _np_ptr(elem, c_int32))
-        mat = Material(_np_ptr(self._rho, c_double), _np_ptr(self._c, c_double))
         opt = Options()
         self.lib.hdg_default_options(ctypes.byref(opt))
         opt.prec = {"fp64": HDG_FP64, "mixed": HDG_MIXED}[prec]
@@ -267,7 +276,7 @@ class Solver:
 
     def hdg_project_volume(self, vals, u=None):
         vals = np.ascontiguousarray(vals, dtype=np.float64)
-        assert vals.shape == (self.n_elem, self.sizes.nq_vol, self.dim + 1)
+        assert vals.shape == (self.n_elem, self.sizes.nq_vol, self.n // self.Np)
         u = self.empty_fields() if u is None else u
         self._check(self.lib.hdg_project_volume(self.ctx, _np_ptr(vals, c_double), self._dev(u, self._fshape)))
         return u

@@ -64,10 +64,31 @@ def test_setup_rejects_bad_input_on_host(libpath):
     elem = np.array([[0, 1, 2]], dtype=np.int32)
     rho = np.ones(1)
     mesh = hdg.Mesh(2, 3, 1, vert.ctypes.data_as(hdg.P_double), elem.ctypes.data_as(hdg.P_int32))
-    mat = hdg.Material(rho.ctypes.data_as(hdg.P_double), rho.ctypes.data_as(hdg.P_double))
+    mat = hdg.Material(0, rho.ctypes.data_as(hdg.P_double), rho.ctypes.data_as(hdg.P_double), None, None)
     st = lib.hdg_setup(ctypes.byref(mesh), 7, 1.0, ctypes.byref(mat), None, None, ctypes.byref(ctx))
     assert st == -1 and b"degree" in lib.hdg_last_error(ctx)
     lib.hdg_destroy(ctx)
     st = lib.hdg_setup(ctypes.byref(mesh), 2, 1.0, ctypes.byref(mat), None, None, ctypes.byref(ctx))
     assert st == -1 and b"degenerate" in lib.hdg_last_error(ctx)
+    lib.hdg_destroy(ctx)
+
+
+def test_setup_rejects_unsupported_elastic_configurations_on_host(libpath):
+    import numpy as np
+    from paper_1807_00086_gb300 import hdg, inputs
+    lib = hdg.load()
+    vert, elem = inputs.unit_cube_tet(1)
+    ne = elem.shape[0]
+    one = np.ones(ne)
+    mesh = hdg.Mesh(3, vert.shape[0], ne, vert.ctypes.data_as(hdg.P_double), elem.ctypes.data_as(hdg.P_int32))
+    mat = hdg.Material(1, one.ctypes.data_as(hdg.P_double), None, one.ctypes.data_as(hdg.P_double),
+                       one.ctypes.data_as(hdg.P_double))
+    ctx = ctypes.c_void_p()
+    st = lib.hdg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(mat), None, None, ctypes.byref(ctx))
+    assert st == -1 and b"1 <= k <= 3" in lib.hdg_last_error(ctx)
+    lib.hdg_destroy(ctx)
+    bad = -np.ones(ne)
+    mat.mu = bad.ctypes.data_as(hdg.P_double)
+    st = lib.hdg_setup(ctypes.byref(mesh), 2, 1.0, ctypes.byref(mat), None, None, ctypes.byref(ctx))
+    assert st == -1 and b"Lame" in lib.hdg_last_error(ctx)
     lib.hdg_destroy(ctx)
