@@ -179,13 +179,28 @@ def run_ours(args):
             dist.barrier()
 
     R = args.nrhs
-    if R > 1:
+    elastic = args.physics == "elastic"
+    scheme, dt = ("dirk3", 1e-3) if elastic else ("bdf2", DT)
+    if elastic:
+        w = inputs.elastic_3d_workload(N=args.N if args.N != 32 else 24, k=args.k)
+    elif R > 1:
         w = inputs.acoustic_3d_multisource_workload(N=args.N, k=args.k, nsrc=R)
     else:
         w = inputs.acoustic_3d_workload(N=args.N, k=args.k)
     ne = w["elem"].shape[0]
+    u_init = None
 
     def make_solver(prec):
+        nonlocal u_init
+        if elastic:
+            sv = hdg.Solver(w["vert"], w["elem"], w["k"], 1.0, w["rho"], lam=w["lam"], mu=w["mu"], prec=prec,
+                            rtol=args.rtol, inner_rtol=args.inner_rtol)
+            if u_init is None:
+                xq = sv.hdg_quadrature_points(0)
+                u_init = sv.hdg_project_volume(inputs.gaussian_velocity_values(xq, w["center"], w["width"],
+                                                                               sv.n // sv.Np))
+            sv.hdg_set_state(u_init, 0.0)
+            return sv
         sv = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=prec, rtol=args.rtol,
                         inner_rtol=args.inner_rtol, nrhs=R)
         sv.hdg_set_sources(w["sources"], np.ones(len(w["sources"])), w["f0"], w["t0"], col=w.get("source_cols"))
@@ -198,7 +213,7 @@ def run_ours(args):
     stream = s.stream
     # warm-up (includes the condensation for alpha = 3/(2 dt))
     for _ in range(args.warmup):
-        s.hdg_step(DT, "bdf2", 1)
+        s.hdg_step(dt, scheme, 1)
     torch.cuda.synchronize()
     s.hdg_enable_stats(True)
     s.hdg_get_stats(reset=True)
@@ -212,7 +227,7 @@ def run_ours(args):
     iters = 0
     sweeps = 0
     for _ in range(args.steps):
-        info = s.hdg_step(DT, "bdf2", 1)
+        info = s.hdg_step(dt, scheme, 1)
         iters += info["iterations"]
         sweeps += info["sweeps"]
     ev1.record(stream)
@@ -248,7 +263,7 @@ def run_ours(args):
             up_d.copy_(up_h, non_blocking=True)
             l_d.copy_(l_h, non_blocking=True)
         s.hdg_set_state(u_d, t_now, uprev=up_d, lam=l_d)
-        s.hdg_step(DT, "bdf2", 1)
+        s.hdg_step(dt, scheme, 1)
         _, _, _, t_now = s.hdg_get_state(u=u_d, uprev=up_d, lam=l_d, want_prev=True)
         with torch.cuda.stream(stream):
             u_h.copy_(u_d, non_blocking=True)
@@ -313,17 +328,17 @@ def run_ours(args):
         torch.cuda.empty_cache()
         s64 = make_solver("fp64")
         for _ in range(args.warmup):
-            s64.hdg_step(DT, "bdf2", 1)
+            s64.hdg_step(dt, scheme, 1)
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            s64.hdg_step(DT, "bdf2", 1)
+            s64.hdg_step(dt, scheme, 1)
         ev1.record(stream)
         torch.cuda.synchronize()
         ms64 = ev0.elapsed_time(ev1)
         # same steps from the same start; the e2e leg advanced the mixed run by e2e_steps more
         for _ in range(e2e_steps):
-            s64.hdg_step(DT, "bdf2", 1)
+            s64.hdg_step(dt, scheme, 1)
         u64 = s64.hdg_get_state()[0]
         rel = float((u_mixed - u64).abs().max() / u64.abs().max().clamp_min(1e-300))
         fp64 = {"value": dofs * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
@@ -333,6 +348,14 @@ def run_ours(args):
 
     if R > 1:
         roof = roof_multi
+    if elastic and args.prec == "mixed":
+        a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
+        bytes_el = m * m * 4 + 2 * m * 4
+        ach = bytes_el * ne / (a32 / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                "traffic": None, "kernel": "apply32f_kernel<ElDims<3,%d>> (FP32 S_K %dx%d)" % (args.k, m, m),
+                "bytes_per_elem": bytes_el, "launch_ms": a32, "launches": st["apply32_launches"],
+                "fp64_refinement_apply": fp64_view}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -343,9 +366,10 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32+f64",
                "data": "synthetic",
-               "config": {"workload": "acoustic3d_k3_32cube_bdf2" + ("_%dsrc" % R if R > 1 else ""), "n_elem": ne,
+               "config": {"workload": ("elastic3d_k%d_%dcube_dirk3" % (args.k, round((ne / 6) ** (1 / 3))) if elastic else
+                                       "acoustic3d_k3_32cube_bdf2" + ("_%dsrc" % R if R > 1 else "")), "n_elem": ne,
                           "k": args.k, "dofs": dofs, "nrhs": R,
-                          "trace_dofs": int(s.n_faces - s.n_bnd) * s.Nf * R, "dt": DT, "scheme": "BDF2",
+                          "trace_dofs": int(s.n_faces - s.n_bnd) * s.Nf * R, "dt": dt, "scheme": scheme.upper(),
                           "precision": args.prec, "rtol": args.rtol, "parallelism": "replicas",
                           "l2": "inputs larger than L2 (S_K %.2f GB)" % (ne * m * m * 8 / 1e9),
                           "krylov_iters_per_step": iters / args.steps,
@@ -411,6 +435,8 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=1e-4)
     ap.add_argument("--N", type=int, default=32)
     ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--physics", default="acoustic", choices=["acoustic", "elastic"],
+                    help="elastic: the 3D linear elastodynamics workload (24^3 x 6 tets, DIRK3)")
     ap.add_argument("--nrhs", type=int, default=1,
                     help="right-hand-side columns solved together (64: the multi-source workload)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -103,3 +103,21 @@ def acoustic_3d_multisource_workload(N=32, k=3, nsrc=64, seed=DEFAULT_SEED):
     w["sources"] = uniform_points(nsrc, 3, 0.1, 0.9, seed + 64)
     w["source_cols"] = np.arange(nsrc, dtype=np.int32)
     return w
+
+
+def elastic_3d_workload(N=24, k=3, seed=DEFAULT_SEED):
+    """3D linear elastodynamics workload: unit cube, 6 N^3 tets, rho = 1, Lame parameters
+    lognormal per element (sigma 0.5; medians lam = 1.5, mu = 1), clamped boundary, initial
+    velocity e_z exp(-|x - x_c|^2 / (2 * 0.05^2)) with x_c the cube centre, zero stress."""
+    vert, elem = unit_cube_tet(N)
+    ne = elem.shape[0]
+    return dict(vert=vert, elem=elem, k=k, rho=np.ones(ne), lam=lognormal(ne, 1.5, 0.5, seed),
+                mu=lognormal(ne, 1.0, 0.5, seed + 1), center=np.array([0.5, 0.5, 0.5]), width=0.05)
+
+
+def gaussian_velocity_values(xq, center, width, ncomp):
+    """Point values [.., ncomp] of the elastic initial data at points xq [.., 3]: v_z bump."""
+    r2 = np.sum((xq - center) ** 2, axis=-1)
+    vals = np.zeros(xq.shape[:-1] + (ncomp,))
+    vals[..., 2] = np.exp(-r2 / (2.0 * width * width))
+    return vals
