@@ -319,6 +319,12 @@ def run_ours(args):
                 "kernel": "apply32_kernel<3,3> (FP32 packed-symmetric S_K x lambda_K)",
                 "peak_source": src + " (hbm_gbs: copy)", "bytes_per_elem": bytes_el,
                 "launch_ms": a32, "launches": st["apply32_launches"], "fp64_refinement_apply": fp64_view}
+        if st.get("applydf_launches"):
+            adf = st["applydf_ms"] / st["applydf_launches"]
+            roof["df_refinement_apply"] = {
+                "kernel": "apply_df_kernel<3,3> (double-float hi + lo, diagonal-major per element)", "launches": st["applydf_launches"],
+                "launch_ms": adf, "bytes_per_elem": 2 * p4 * 16 + m * 8 + m * 8,
+                "achieved_gbs": (2 * p4 * 16 + 2 * m * 8) * ne / (adf / 1e3) / 1e9}
 
     # the plain FP64 GPU path on the same workload and steps, for the mixed-vs-FP64 comparison
     fp64 = None

@@ -238,6 +238,8 @@ typedef struct {
   double apply_ms;          /* summed device time of those launches (CUDA events)      */
   int64_t apply32_launches; /* launches of the FP32 (mixed precision) trace apply      */
   double apply32_ms;        /* summed device time of those launches                    */
+  int64_t applydf_launches; /* launches of the double-float refinement-residual apply   */
+  double applydf_ms;        /* summed device time of those launches                    */
 } hdg_stats;
 hdg_status hdg_enable_stats(hdg_ctx* ctx, int32_t enable);
 hdg_status hdg_get_stats(hdg_ctx* ctx, hdg_stats* out, int32_t reset);

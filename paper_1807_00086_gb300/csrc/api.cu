@@ -54,6 +54,7 @@ struct hdg_ctx {
   int nb_red = 0;
   // mixed precision
   float *d_S32 = nullptr, *d_dinv32 = nullptr, *d_slot32 = nullptr;
+  float* d_Sdf = nullptr;       // double-float diagonal-major copy of S_K (refinement apply)
   float *d_r32 = nullptr, *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_x32 = nullptr, *d_b32 = nullptr;
   double* d_res = nullptr;   // FP64 refinement residual
   int64_t nfe4 = 0;          // FP32 face vectors padded to a multiple of 4 entries
@@ -91,8 +92,8 @@ struct hdg_ctx {
   std::vector<void*> allocs;
   // instrumentation
   bool stats_on = false;
-  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0;
-  double apply_ms = 0.0, apply32_ms = 0.0;
+  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0, n_applydf = 0;
+  double apply_ms = 0.0, apply32_ms = 0.0, applydf_ms = 0.0;
   std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
   std::vector<char> ev_kind;          // per pair: 0 FP64 apply, 1 FP32 apply
   std::vector<int> ev_iter;           // per pair: Krylov iteration index (-1: always live)
@@ -186,7 +187,8 @@ void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
     float ms = 0.f;
     if (c->ev_iter[i / 2] >= live_iters) continue;
     if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
-      if (c->ev_kind[i / 2]) { c->apply32_ms += ms; c->n_apply32 += 1; }
+      if (c->ev_kind[i / 2] == 1) { c->apply32_ms += ms; c->n_apply32 += 1; }
+      else if (c->ev_kind[i / 2] == 2) { c->applydf_ms += ms; c->n_applydf += 1; }
       else { c->apply_ms += ms; c->n_apply += 1; }
     }
   }
@@ -301,6 +303,25 @@ void launch_face_q32(hdg_ctx* c) {
 }
 
 template <int DIM, int K>
+void launch_packdf(hdg_ctx* c) {
+  using PK = Packed<DIM, K>;
+  const int64_t n = c->sk.ne * PK::P4 * 4;
+  c->n_launch += 1;
+  packdf_kernel<DIM, K><<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->d_S, c->d_Sdf);
+}
+
+template <int DIM, int K>
+void launch_apply_df(hdg_ctx* c, const double* x, double* zslot) {
+  using C = ApplyDfCfg<DIM, K>;
+  const unsigned grid = (unsigned)((c->sk.ne + C::EPB - 1) / C::EPB);
+  c->n_launch += 1;
+  cudaFuncSetAttribute(apply_df_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  cudaEvent_t stop = apply_begin(c, 2, -1);
+  apply_df_kernel<DIM, K><<<grid, C::NT, C::SMEM, c->stream>>>(devmesh(c), c->d_Sdf, x, zslot);
+  apply_end(c, stop);
+}
+
+template <int DIM, int K>
 void launch_pack32m(hdg_ctx* c) {
   using PK = Packed<DIM, K>;
   const int64_t n = c->sk.ne * PK::P4 * 4;
@@ -340,6 +361,7 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
       HDG_DISPATCH(c, launch_pack32m, c);
     } else {
       HDG_DISPATCH(c, launch_pack32, c);
+      HDG_DISPATCH(c, launch_packdf, c);
     }
     const int64_t nfe = c->sk.nf * c->Nf;
     c->n_launch += 1;
@@ -411,7 +433,11 @@ hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
   hdg_status s;
   double rel = 0.0;
   for (int sweep = 0;; ++sweep) {
-    HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
+    if (c->d_Sdf) {
+      HDG_DISPATCH(c, launch_apply_df, c, x, c->d_slot);
+    } else {
+      HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
+    }
     c->n_launch += 2;
     refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec,
                                                       c->d_res, c->d_part);
@@ -967,6 +993,12 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
       CUDA_TRY(c, cudaMemsetAsync(*p, 0, cnt * 4, c->stream));
     }
     if (c->R > 1 && (s = dalloc(c, &c->d_mslot32, (size_t)ne * c->m * R))) return s;
+    if (c->R == 1 && c->phys == HDG_ACOUSTIC) {
+      // whole 32-element groups, so the per-CTA staging copy never runs past the end
+      const size_t nSdf = (size_t)ngroups * 32 * 2 * P4 * 4;
+      if ((s = dalloc(c, &c->d_Sdf, nSdf))) return s;
+      CUDA_TRY(c, cudaMemsetAsync(c->d_Sdf, 0, nSdf * 4, c->stream));
+    }
     if ((s = dalloc(c, &c->d_res, nfe * R))) return s;
     if ((s = dalloc(c, &c->d_rs, 1))) return s;
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_rs, sizeof(RefScal)));
@@ -1355,7 +1387,12 @@ hdg_status hdg_get_stats(hdg_ctx* c, hdg_stats* o, int32_t reset) {
   o->apply_ms = c->apply_ms;
   o->apply32_launches = c->n_apply32;
   o->apply32_ms = c->apply32_ms;
-  if (reset) { c->n_launch = 0; c->n_apply = 0; c->apply_ms = 0.0; c->n_apply32 = 0; c->apply32_ms = 0.0; }
+  o->applydf_launches = c->n_applydf;
+  o->applydf_ms = c->applydf_ms;
+  if (reset) {
+    c->n_launch = 0; c->n_apply = 0; c->apply_ms = 0.0; c->n_apply32 = 0; c->apply32_ms = 0.0;
+    c->n_applydf = 0; c->applydf_ms = 0.0;
+  }
   return HDG_OK;
 }
 

@@ -968,3 +968,125 @@ __global__ void to32_kernel(int64_t n, const double* __restrict__ a, float* __re
 }
 
 }  // namespace hdg
+
+namespace hdg {
+
+// ================================================================ double-float (FP64-class on the FP32 pipe)
+// A value is the unevaluated sum h + l of two floats (|l| <= ulp(h)/2): about 48 significant
+// bits. Products use the exact FMA error of h*h, sums the TwoSum error, so dot products keep
+// the accuracy of FP64 evaluation to ~1e-14 relative on GB300's 58x faster FP32 pipe.
+struct df2 {
+  float h, l;
+};
+
+__device__ __forceinline__ df2 df_from(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(df2 a) { return (double)a.h + (double)a.l; }
+
+// compensated accumulator of sum_i a_i b_i with a_i, b_i double-floats
+struct DfAcc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void fma(df2 a, df2 b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+    const float t = s + p;
+    const float bb = t - s;
+    c += ((s - (t - bb)) + (p - bb)) + e;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Double-float copy of S_K for the refinement apply, element-contiguous and diagonal-major:
+// element e holds [hi | lo], each PD = 4 * P4 floats, entry (r, r + s) of the upper triangle at
+// off(s) + r with off(s) = packed_index(M, s, s) (the s-th superdiagonal follows the first s
+// ones). hi = fl32(S), lo = fl32(S - hi).
+__host__ __device__ constexpr int diag_off(int M, int s) { return packed_index(M, s, s); }
+
+template <int DIM, int K>
+__global__ void packdf_kernel(int64_t ne, const double* __restrict__ S, float* __restrict__ Sdf) {
+  using PK = Packed<DIM, K>;
+  constexpr int M = PK::M, PD = PK::P4 * 4;
+  const int64_t n = ne * PD;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / PD;
+    const int pos = (int)(t - e * PD);
+    float hi = 0.f, lo = 0.f;
+    if (pos < PK::P) {
+      int s = 0;
+      while (s < M - 1 && diag_off(M, s + 1) <= pos) ++s;
+      const int r = pos - diag_off(M, s);
+      const double v = S[e * (int64_t)(M * M) + r * M + r + s];
+      hi = __double2float_rn(v);
+      lo = __double2float_rn(v - (double)hi);
+    }
+    Sdf[e * 2 * PD + pos] = hi;
+    Sdf[e * 2 * PD + PD + pos] = lo;
+  }
+}
+
+// FP64-accurate refinement apply on the FP32 pipe: zslot[e][r] = sum_c S_K[r][c] x_K[c] with
+// S_K = hi + lo from the diagonal-major copy and x split into double-floats. CTA = EPB
+// elements, one thread per (element, row); the elements' copies are staged in shared memory
+// with 16-byte asynchronous copies. At step s thread r takes column c = (r + s) mod M: the
+// superdiagonal s at row r when c >= r, else the superdiagonal M - s at row c, so the threads
+// of an element read two runs of consecutive words.
+template <int DIM, int K>
+struct ApplyDfCfg {
+  static constexpr int M = Dims<DIM, K>::M;
+  static constexpr int EPB = 4;
+  static constexpr int NT = EPB * M;
+  static constexpr int PD = Packed<DIM, K>::P4 * 4;
+  static constexpr int CH = EPB * 2 * PD / 4;                   // 16-byte chunks per CTA
+  static constexpr size_t SMEM = sizeof(float) * EPB * 2 * PD + sizeof(df2) * EPB * M;
+};
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(ApplyDfCfg<DIM, K>::NT) apply_df_kernel(DevMesh mesh, const float* __restrict__ Sdf,
+                                                                         const double* __restrict__ x,
+                                                                         double* __restrict__ zslot) {
+  using D = Dims<DIM, K>;
+  using C = ApplyDfCfg<DIM, K>;
+  constexpr int NF = D::NF, M = D::M, NFC = D::NFC, EPB = C::EPB, PD = C::PD;
+  extern __shared__ __align__(16) float dsm[];
+  df2* lx = reinterpret_cast<df2*>(dsm + EPB * 2 * PD);   // [EPB][M]
+  const int64_t e0 = (int64_t)blockIdx.x * EPB;
+  {
+    // the copy is padded to a whole number of CTAs, so every chunk is in bounds
+    const char* src = reinterpret_cast<const char*>(Sdf + e0 * 2 * PD);
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(dsm);
+    for (int i = threadIdx.x; i < C::CH; i += C::NT)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * i), "l"(src + 16 * i) : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  const int el = threadIdx.x / M, r = threadIdx.x % M;
+  const int64_t e = e0 + el;
+  {
+    double v = 0.0;
+    if (e < mesh.ne) {
+      const int f = mesh.elem_face[e * NFC + r / NF];
+      if (mesh.face_bnd[f] < 0) v = x[(int64_t)f * NF + r % NF];
+    }
+    lx[el * M + r] = df_from(v);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  if (e >= mesh.ne) return;
+  const float* hi = dsm + el * 2 * PD;
+  const float* lo = hi + PD;
+  const df2* ex = lx + el * M;
+  DfAcc acc;
+#pragma unroll
+  for (int s = 0; s < M; ++s) {
+    const int c = r + s;
+    const bool up = c < M;
+    const int pos = up ? diag_off(M, s) + r : diag_off(M, M - s) + (c - M);
+    acc.fma(df2{hi[pos], lo[pos]}, ex[up ? c : c - M]);
+  }
+  zslot[e * M + r] = acc.value();
+}
+
+}  // namespace hdg

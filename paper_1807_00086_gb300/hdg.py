@@ -53,7 +53,8 @@ class SolveInfo(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", c_int64), ("apply_launches", c_int64), ("apply_ms", c_double),
-                ("apply32_launches", c_int64), ("apply32_ms", c_double)]
+                ("apply32_launches", c_int64), ("apply32_ms", c_double), ("applydf_launches", c_int64),
+                ("applydf_ms", c_double)]
 
 
 # exported entry points: name -> (restype, argtypes)
@@ -312,7 +313,8 @@ class Solver:
         st = Stats()
         self._check(self.lib.hdg_get_stats(self.ctx, ctypes.byref(st), 1 if reset else 0))
         return {"kernel_launches": st.kernel_launches, "apply_launches": st.apply_launches, "apply_ms": st.apply_ms,
-                "apply32_launches": st.apply32_launches, "apply32_ms": st.apply32_ms}
+                "apply32_launches": st.apply32_launches, "apply32_ms": st.apply32_ms,
+                "applydf_launches": st.applydf_launches, "applydf_ms": st.applydf_ms}
 
     def hdg_step(self, dt, scheme, nsteps=1):
         info = SolveInfo()

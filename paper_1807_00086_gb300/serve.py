@@ -62,6 +62,8 @@ def estimate_bytes(dim, N, k, R, prec="mixed"):
     per_elem = m * m * 8 + Np * Np * 8 + 320 + m * 8 + 7 * n * 8 * R + m * 8 * R
     if prec == "mixed":
         per_elem += p4 * 16 + m * 4 * R
+        if R == 1:
+            per_elem += p4 * 32         # double-float copy for the refinement apply
     per_face = Nf * R * (9 * 8 + 8 * 4 + 8) + 16
     return int(ne * per_elem + nf * per_face + (1 << 20))
 
