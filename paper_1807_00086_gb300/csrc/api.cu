@@ -13,6 +13,7 @@
 
 #include "../../include/hdg.h"
 #include "kernels.cuh"
+#include "dflocal.cuh"
 #include "multi.cuh"
 #include "elastic.cuh"
 #include "mesh.h"
@@ -55,6 +56,8 @@ struct hdg_ctx {
   // mixed precision
   float *d_S32 = nullptr, *d_dinv32 = nullptr, *d_slot32 = nullptr;
   float* d_Sdf = nullptr;       // double-float diagonal-major copy of S_K (refinement apply)
+  df2 *d_Hinvdf = nullptr, *d_geodf = nullptr, *d_tabdf = nullptr;   // double-float local solves
+  TabsDf tabsdf{};
   float *d_r32 = nullptr, *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_x32 = nullptr, *d_b32 = nullptr;
   double* d_res = nullptr;   // FP64 refinement residual
   int64_t nfe4 = 0;          // FP32 face vectors padded to a multiple of 4 entries
@@ -238,10 +241,23 @@ void launch_local(hdg_ctx* c, int mode, const double* F, const double* hist, dou
                                                                             c->d_Hinv, c->alpha, F, hist, lam, out);
     return;
   }
-  using L = LocalCfg<DIM, K>;
-  const unsigned grid = (unsigned)((c->sk.ne + L::EPB - 1) / L::EPB);
   const SrcArgs sa = srcargs(c, t);
   c->n_launch += 1;
+  if (c->d_Hinvdf) {
+    using LD = LocalDfCfg<DIM, K>;
+    const unsigned gd = (unsigned)((c->sk.ne + LD::EPB - 1) / LD::EPB);
+    const float th = (float)c->tau;
+    const df2 tau{th, (float)(c->tau - (double)th)};
+    if (mode == 0)
+      local_df_kernel<DIM, K, 0><<<gd, LD::NT, 0, c->stream>>>(devmesh(c), c->tabsdf, c->d_geodf, c->d_Hinvdf, c->alpha,
+                                                               tau, F, hist, sa, lam, out);
+    else
+      local_df_kernel<DIM, K, 1><<<gd, LD::NT, 0, c->stream>>>(devmesh(c), c->tabsdf, c->d_geodf, c->d_Hinvdf, c->alpha,
+                                                               tau, F, hist, sa, lam, out);
+    return;
+  }
+  using L = LocalCfg<DIM, K>;
+  const unsigned grid = (unsigned)((c->sk.ne + L::EPB - 1) / L::EPB);
   if (mode == 0)
     local_kernel<DIM, K, 0><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, F, hist, sa, lam,
                                                             out);
@@ -362,6 +378,9 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
     } else {
       HDG_DISPATCH(c, launch_pack32, c);
       HDG_DISPATCH(c, launch_packdf, c);
+      const int64_t nH = c->sk.ne * (int64_t)c->nv * c->nv;
+      c->n_launch += 1;
+      to_df_kernel<<<grid_for(c, nH), 256, 0, c->stream>>>(nH, c->d_Hinv, c->d_Hinvdf);
     }
     const int64_t nfe = c->sk.nf * c->Nf;
     c->n_launch += 1;
@@ -998,6 +1017,35 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
       const size_t nSdf = (size_t)ngroups * 32 * 2 * P4 * 4;
       if ((s = dalloc(c, &c->d_Sdf, nSdf))) return s;
       CUDA_TRY(c, cudaMemsetAsync(c->d_Sdf, 0, nSdf * 4, c->stream));
+      // double-float local solves: H^{-1} (filled at each condensation), geometry, tables
+      if ((s = dalloc(c, &c->d_Hinvdf, (size_t)ne * c->nv * c->nv))) return s;
+      if ((s = dalloc(c, &c->d_geodf, (size_t)ne * GEO_STRIDE))) return s;
+      c->n_launch += 1;
+      to_df_kernel<<<grid_for(c, ne * GEO_STRIDE), 256, 0, c->stream>>>(ne * GEO_STRIDE, c->d_geo, c->d_geodf);
+      const int NP = c->nv, NF = c->Nf, D = c->dim, NFC = c->dim + 1;
+      std::vector<df2> td((size_t)2 * D * NP * NP + 2 * NFC * NP * NF);
+      auto split = [](double v) { const float h = (float)v; return df2{h, (float)(v - (double)h)}; };
+      df2* DrT = td.data();
+      df2* Drd = DrT + D * NP * NP;
+      df2* FfT = Drd + D * NP * NP;
+      df2* Ffd = FfT + NFC * NP * NF;
+      for (int r = 0; r < D; ++r)
+        for (int l = 0; l < NP; ++l)
+          for (int i = 0; i < NP; ++i) {
+            DrT[(r * NP + l) * NP + i] = split(c->T.Dr[(r * NP + i) * NP + l]);
+            Drd[(r * NP + l) * NP + i] = split(c->T.Dr[(r * NP + l) * NP + i]);
+          }
+      for (int f = 0; f < NFC; ++f)
+        for (int i = 0; i < NP; ++i)
+          for (int mm = 0; mm < NF; ++mm) {
+            FfT[(f * NF + mm) * NP + i] = split(c->T.Ff[(f * NP + i) * NF + mm]);
+            Ffd[(f * NP + i) * NF + mm] = split(c->T.Ff[(f * NP + i) * NF + mm]);
+          }
+      if ((s = dalloc(c, &c->d_tabdf, td.size()))) return s;
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_tabdf, td.data(), td.size() * sizeof(df2), cudaMemcpyHostToDevice, c->stream));
+      // the host copy is released below only after the stream has consumed it
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      c->tabsdf = TabsDf{c->d_tabdf, c->d_tabdf + (Drd - DrT), c->d_tabdf + (FfT - DrT), c->d_tabdf + (Ffd - DrT)};
     }
     if ((s = dalloc(c, &c->d_res, nfe * R))) return s;
     if ((s = dalloc(c, &c->d_rs, 1))) return s;
