@@ -9,7 +9,7 @@ c ~ logU[1, 3] per element (seeded), rho = 1, BDF2 dt = 2e-3, Ricker point sourc
 f0 = 10. Inputs are seeded and synthetic; the per-element operators (S_K: 2.5 GB FP64)
 are far larger than L2, so no flush is needed between steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64|mixed|mixed16] [--impl ours|reference]
 
 `--impl reference` times the CPU oracle on a bounded sample of the same workload.
 Under torchrun (N > 1) every rank runs an independent replica (the path does not shard
@@ -285,17 +285,17 @@ def run_ours(args):
     if R > 1:
         # multi-column apply: S_K read once per element, the R-column trace blocks gathered twice
         # (once per neighbour) and the slot products written once
-        a32 = (st["apply32_ms"] / max(1, st["apply32_launches"])) if args.prec == "mixed" else apply_avg_ms
-        ebytes = 4 if args.prec == "mixed" else 8
-        sbytes = ((m * (m + 1) // 2 + 3) // 4) * 16 if args.prec == "mixed" else m * m * 8
+        a32 = (st["apply32_ms"] / max(1, st["apply32_launches"])) if args.prec != "fp64" else apply_avg_ms
+        ebytes = 4 if args.prec != "fp64" else 8
+        sbytes = ((m * (m + 1) // 2 + 3) // 4) * 16 if args.prec != "fp64" else m * m * 8
         bytes_el = sbytes + 2 * m * R * ebytes
         ach = bytes_el * ne / (a32 / 1e3) / 1e9
         peaks, src = load_peaks()
         roof_multi = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                       "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                      "kernel": "apply_multi_kernel<3,3,%s> (%d columns)" % ("float" if args.prec == "mixed" else "double", R),
+                      "kernel": "apply_multi_kernel<3,3,%s> (%d columns)" % ("float" if args.prec != "fp64" else "double", R),
                       "bytes_per_elem": bytes_el, "launch_ms": a32,
-                      "launches": st["apply32_launches"] if args.prec == "mixed" else st["apply_launches"],
+                      "launches": st["apply32_launches"] if args.prec != "fp64" else st["apply_launches"],
                       "flops_per_elem": 2 * m * m * R}
     fp64_view = {"kernel": "apply_kernel<3,3> (FP64 S_K x lambda_K)", "launches": st["apply_launches"],
                  "launch_ms": apply_avg_ms,
@@ -313,12 +313,24 @@ def run_ours(args):
         a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
         p4 = (m * (m + 1) // 2 + 3) // 4
         bytes_el = p4 * 16 + 2 * m * 4
-        ach = bytes_el * ne / (a32 / 1e3) / 1e9
+        ach = bytes_el * ne / (a32 / 1e3) / 1e9 if a32 > 0 else None
         roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": None,
                 "kernel": "apply32_kernel<3,3> (FP32 packed-symmetric S_K x lambda_K)",
                 "peak_source": src + " (hbm_gbs: copy)", "bytes_per_elem": bytes_el,
                 "launch_ms": a32, "launches": st["apply32_launches"], "fp64_refinement_apply": fp64_view}
+        if st.get("apply16_launches"):
+            # FP16 inner operator: packed halves + one FP32 scale per element, FP32 trace gather/slots
+            a16 = st["apply16_ms"] / st["apply16_launches"]
+            p8 = (m * (m + 1) // 2 + 7) // 8
+            b16 = p8 * 16 + 4 + 2 * m * 4
+            ach16 = b16 * ne / (a16 / 1e3) / 1e9
+            fp32_view = {k: roof[k] for k in ("kernel", "bytes_per_elem", "launch_ms", "launches")}
+            fp32_view["achieved_gbs"] = ach if st["apply32_launches"] else None
+            roof.update({"achieved": ach16, "frac": ach16 / peaks["hbm_gbs"],
+                         "kernel": "apply16_kernel<3,3> (FP16 packed-symmetric S_K, per-element scale)",
+                         "bytes_per_elem": b16, "launch_ms": a16, "launches": st["apply16_launches"],
+                         "fp32_apply": fp32_view})
         if st.get("applydf_launches"):
             adf = st["applydf_ms"] / st["applydf_launches"]
             roof["df_refinement_apply"] = {
@@ -328,7 +340,7 @@ def run_ours(args):
 
     # the plain FP64 GPU path on the same workload and steps, for the mixed-vs-FP64 comparison
     fp64 = None
-    if args.prec == "mixed" and not args.no_fp64_compare:
+    if args.prec != "fp64" and not args.no_fp64_compare:
         u_mixed = s.hdg_get_state()[0]
         s.close()
         torch.cuda.empty_cache()
@@ -354,7 +366,7 @@ def run_ours(args):
 
     if R > 1:
         roof = roof_multi
-    if elastic and args.prec == "mixed":
+    if elastic and args.prec != "fp64":
         a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
         bytes_el = m * m * 4 + 2 * m * 4
         ach = bytes_el * ne / (a32 / 1e3) / 1e9
@@ -370,7 +382,7 @@ def run_ours(args):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else "f32+f64",
+               "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "mixed16": "f16+f32+f64"}[args.prec],
                "data": "synthetic",
                "config": {"workload": ("elastic3d_k%d_%dcube_dirk3" % (args.k, round((ne / 6) ** (1 / 3))) if elastic else
                                        "acoustic3d_k3_32cube_bdf2" + ("_%dsrc" % R if R > 1 else "")), "n_elem": ne,
@@ -379,8 +391,8 @@ def run_ours(args):
                           "precision": args.prec, "rtol": args.rtol, "parallelism": "replicas",
                           "l2": "inputs larger than L2 (S_K %.2f GB)" % (ne * m * m * 8 / 1e9),
                           "krylov_iters_per_step": iters / args.steps,
-                          "refinement_sweeps_per_step": sweeps / args.steps if args.prec == "mixed" else None,
-                          "inner_rtol": args.inner_rtol if args.prec == "mixed" else None},
+                          "refinement_sweeps_per_step": sweeps / args.steps if args.prec != "fp64" else None,
+                          "inner_rtol": args.inner_rtol if args.prec != "fp64" else None},
                "roofline": roof, "cpu_baseline": cpu, "fp64_gpu": fp64,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * field_bytes + trace_bytes,
                        "d2h_bytes_per_step": 2 * field_bytes + trace_bytes, "steps": e2e_steps},
@@ -419,7 +431,7 @@ def run_serve(args):
     srv.close()
     out = {"metric": METRIC, "mode": "serve", "value": stats["dof_steps_per_s"], "unit": UNIT,
            "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "mean_ms": stats["mean_ms"],
-           "higher_is_better": True, "dtype": "f64" if args.prec == "fp64" else "f32+f64", "data": "synthetic",
+           "higher_is_better": True, "dtype": {"fp64": "f64", "mixed": "f32+f64", "mixed16": "f16+f32+f64"}[args.prec], "data": "synthetic",
            "config": {"workload": "serve_acoustic_2d3d_poisson%g" % args.serve_rate, "requests": stats["requests"],
                       "slots_per_context": args.serve_slots, "budget_gb": args.serve_budget_gb,
                       "contexts_resident_at_end": stats["contexts_created"], "wall_s": stats["wall_s"],
@@ -434,7 +446,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed", "mixed16"])
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain FP64 comparison run that follows a mixed-precision measurement")
     ap.add_argument("--rtol", type=float, default=1e-12)

@@ -60,7 +60,7 @@ typedef enum {
 
 typedef enum { HDG_BE = 1, HDG_BDF2 = 2, HDG_DIRK3 = 3 } hdg_scheme;
 typedef enum { HDG_ACOUSTIC = 0, HDG_ELASTIC = 1 } hdg_physics;
-typedef enum { HDG_FP64 = 0, HDG_MIXED = 1 } hdg_precision;
+typedef enum { HDG_FP64 = 0, HDG_MIXED = 1, HDG_MIXED16 = 2 } hdg_precision;
 
 typedef struct {
   int32_t dim;              /* 2 or 3                                                */
@@ -80,7 +80,12 @@ typedef struct {
 typedef struct {
   hdg_precision prec;       /* HDG_FP64: everything FP64. HDG_MIXED: the Krylov       */
                             /* iterations apply an FP32 copy of S_K inside FP64        */
-                            /* iterative refinement of the trace system                */
+                            /* iterative refinement of the trace system.               */
+                            /* HDG_MIXED16: as MIXED with an FP16 copy of S_K (one     */
+                            /* FP32 scale per element) in the Krylov iterations; a     */
+                            /* sweep that gains less than 10x switches the rest of     */
+                            /* that solve to the FP32 copy. Acoustic, nrhs = 1; other  */
+                            /* configurations run as HDG_MIXED                         */
   double rtol;              /* relative residual target of the trace solve (FP64)     */
   int32_t maxit;            /* Krylov iteration cap per solve (per sweep if MIXED)    */
   int32_t check_every;      /* host polls the device convergence flag this often      */
@@ -240,6 +245,8 @@ typedef struct {
   double apply32_ms;        /* summed device time of those launches                    */
   int64_t applydf_launches; /* launches of the double-float refinement-residual apply   */
   double applydf_ms;        /* summed device time of those launches                    */
+  int64_t apply16_launches; /* launches of the FP16 apply (HDG_MIXED16 Krylov iterations) */
+  double apply16_ms;        /* summed device time of those launches                    */
 } hdg_stats;
 hdg_status hdg_enable_stats(hdg_ctx* ctx, int32_t enable);
 hdg_status hdg_get_stats(hdg_ctx* ctx, hdg_stats* out, int32_t reset);

@@ -58,10 +58,15 @@ struct hdg_ctx {
   float* d_Sdf = nullptr;       // double-float diagonal-major copy of S_K (refinement apply)
   df2 *d_Hinvdf = nullptr, *d_geodf = nullptr, *d_tabdf = nullptr;   // double-float local solves
   TabsDf tabsdf{};
+  __half* d_S16 = nullptr;      // FP16 packed S_K (inner Krylov operator of HDG_MIXED16)
+  float* d_sc16 = nullptr;      // its per-element scales
+  double *d_pqpart = nullptr, *d_pq = nullptr;   // p.q block partials and result of the FP32/FP16 apply
+  unsigned* d_ticket = nullptr;                   // last-block counter of that reduction
   float *d_r32 = nullptr, *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_x32 = nullptr, *d_b32 = nullptr;
   double* d_res = nullptr;   // FP64 refinement residual
   int64_t nfe4 = 0;          // FP32 face vectors padded to a multiple of 4 entries
   int last_it32 = 16, last_it64 = 16;   // iteration counts of the previous solves (poll schedule)
+  int last_sweep_it[8] = {16, 16, 16, 16, 16, 16, 16, 16};   // the same per refinement sweep
   double *d_lam_prev = nullptr, *d_lam_x = nullptr;  // trace history for the extrapolated guess
   bool have_lam_prev = false;
   // multiple right-hand sides (R columns, innermost index)
@@ -95,10 +100,10 @@ struct hdg_ctx {
   std::vector<void*> allocs;
   // instrumentation
   bool stats_on = false;
-  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0, n_applydf = 0;
-  double apply_ms = 0.0, apply32_ms = 0.0, applydf_ms = 0.0;
+  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0, n_applydf = 0, n_apply16 = 0;
+  double apply_ms = 0.0, apply32_ms = 0.0, applydf_ms = 0.0, apply16_ms = 0.0;
   std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
-  std::vector<char> ev_kind;          // per pair: 0 FP64 apply, 1 FP32 apply
+  std::vector<char> ev_kind;          // per pair: 0 FP64, 1 FP32, 2 double-float, 3 FP16 apply
   std::vector<int> ev_iter;           // per pair: Krylov iteration index (-1: always live)
   size_t ev_used = 0;
 };
@@ -192,6 +197,7 @@ void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
     if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
       if (c->ev_kind[i / 2] == 1) { c->apply32_ms += ms; c->n_apply32 += 1; }
       else if (c->ev_kind[i / 2] == 2) { c->applydf_ms += ms; c->n_applydf += 1; }
+      else if (c->ev_kind[i / 2] == 3) { c->apply16_ms += ms; c->n_apply16 += 1; }
       else { c->apply_ms += ms; c->n_apply += 1; }
     }
   }
@@ -306,6 +312,17 @@ void launch_face_q64(hdg_ctx* c) {
                                                                      c->d_slot, c->d_p, c->d_q, c->d_part, c->d_sc);
 }
 
+// p.q reduction target of the single-column FP32/FP16 applies
+PqOut pq_out(hdg_ctx* c) { return PqOut{c->d_pqpart, c->d_ticket, c->d_pq, (float)c->sgn}; }
+
+template <int DIM, int K>
+void launch_update_f32(hdg_ctx* c, int par) {
+  cg32_update_f_kernel<Dims<DIM, K>><<<c->nb_red, 256, 0, c->stream>>>(
+      c->nfe4 / 4, c->sk.nf * c->Nf, (float)c->sgn, par, c->d_face_slot, c->d_face_bnd, c->d_slot32,
+      (const float4*)c->d_p32, (const float4*)c->d_dinv32, (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
+      c->d_pq, c->d_part + c->nb_red, c->d_sc);
+}
+
 template <int DIM, int K>
 void launch_face_q32(hdg_ctx* c) {
   if (c->phys == HDG_ELASTIC)
@@ -324,6 +341,27 @@ void launch_packdf(hdg_ctx* c) {
   const int64_t n = c->sk.ne * PK::P4 * 4;
   c->n_launch += 1;
   packdf_kernel<DIM, K><<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->d_S, c->d_Sdf);
+}
+
+template <int DIM, int K>
+void launch_pack16(hdg_ctx* c) {
+  using PK = Packed16<DIM, K>;
+  const int64_t ne = c->sk.ne;
+  c->n_launch += 2;
+  scale16_kernel<DIM, K><<<grid_for(c, ne * 32), 256, 0, c->stream>>>(ne, c->d_S, c->d_sc16);
+  pack16_kernel<DIM, K><<<grid_for(c, ((ne + 31) / 32) * PK::P8 * 256), 256, 0, c->stream>>>(ne, c->d_S, c->d_sc16,
+                                                                                               c->d_S16);
+}
+
+template <int DIM, int K>
+void launch_apply16(hdg_ctx* c, const float* x, float* slot, const int* done, int iter) {
+  const int64_t ngroups = (c->sk.ne + 31) / 32;
+  c->n_launch += 1;
+  cudaEvent_t stop = apply_begin(c, 3, iter);
+  apply16_kernel<DIM, K><<<(unsigned)((ngroups + 3) / 4), 128, 0, c->stream>>>(c->sk.ne, c->d_elem_face, c->d_face_bnd,
+                                                                              c->d_S16, c->d_sc16, x, slot, done,
+                                                                              pq_out(c));
+  apply_end(c, stop);
 }
 
 template <int DIM, int K>
@@ -357,7 +395,7 @@ void launch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, in
     return;
   }
   apply32_kernel<DIM, K><<<(unsigned)((ngroups + 3) / 4), 128, 0, c->stream>>>(c->sk.ne, c->d_elem_face, c->d_face_bnd,
-                                                                              c->d_S32, x, slot, done);
+                                                                              c->d_S32, x, slot, done, pq_out(c));
   apply_end(c, stop);
 }
 
@@ -368,7 +406,7 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
   HDG_DISPATCH(c, launch_condense, c);
   hdg_status s = check_launch(c, "condense");
   if (s) return s;
-  if (c->opt.prec == HDG_MIXED) {
+  if (c->opt.prec != HDG_FP64) {
     if (c->phys == HDG_ELASTIC) {
       const int64_t nS = c->sk.ne * (int64_t)c->m * c->m;
       c->n_launch += 1;
@@ -378,6 +416,7 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
     } else {
       HDG_DISPATCH(c, launch_pack32, c);
       HDG_DISPATCH(c, launch_packdf, c);
+      if (c->d_S16) HDG_DISPATCH(c, launch_pack16, c);
       const int64_t nH = c->sk.ne * (int64_t)c->nv * c->nv;
       c->n_launch += 1;
       to_df_kernel<<<grid_for(c, nH), 256, 0, c->stream>>>(nH, c->d_Hinv, c->d_Hinvdf);
@@ -404,31 +443,42 @@ hdg_status faces_from_slots(hdg_ctx* c, double scale, double* out) {
 }
 
 // FP32 PCG on (-K32) x32 = b32 from x32 = 0 (inner solve of the mixed path).
-hdg_status cg32_inner(hdg_ctx* c, int* iters) {
+hdg_status cg32_inner(hdg_ctx* c, int* iters, double tol, int* last, bool use16) {
   const int64_t nfe = c->sk.nf * c->Nf;
   const int nb = c->nb_red;
   const int64_t n4 = c->nfe4 / 4;
   c->n_launch += 2;
   cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32, (float4*)c->d_x32,
                                               (float4*)c->d_r32, (float4*)c->d_z32, (float4*)c->d_p32, c->d_part);
-  cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->opt.inner_rtol, c->d_sc);
+  cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, tol, c->d_sc);
   hdg_status s = check_launch(c, "cg32_init");
   if (s) return s;
   int it = 0;
   const int maxit = c->opt.maxit;
   const int chk = std::max(1, c->opt.check_every);
   c->h_sc->done = 0;
-  const int first = std::max(2, std::min(chk, c->last_it32 - 1));   // first poll near the last solve's count
+  const int first = std::max(2, std::min(chk, *last - 1));   // first poll near the last solve's count
   while (!c->h_sc->done && it < maxit) {
     const int upto = std::min(maxit, it + (it == 0 ? first : std::min(chk, 3)));
     for (; it < upto; ++it) {
       const int par = it & 1;
-      HDG_DISPATCH(c, launch_apply32, c, c->d_p32, c->d_slot32, &c->d_sc->done, it);
-      c->n_launch += 3;
-      HDG_DISPATCH(c, launch_face_q32, c);
-      cg32_update_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, c->d_part, (const float4*)c->d_p32, (const float4*)c->d_q32,
-                                                    (const float4*)c->d_dinv32, (float4*)c->d_x32, (float4*)c->d_r32,
-                                                    (float4*)c->d_z32, c->d_part + nb, c->d_sc);
+      if (use16) {
+        HDG_DISPATCH(c, launch_apply16, c, c->d_p32, c->d_slot32, &c->d_sc->done, it);
+      } else {
+        HDG_DISPATCH(c, launch_apply32, c, c->d_p32, c->d_slot32, &c->d_sc->done, it);
+      }
+      if (c->phys == HDG_ELASTIC) {
+        c->n_launch += 3;
+        HDG_DISPATCH(c, launch_face_q32, c);
+        cg32_update_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, c->d_part, (const float4*)c->d_p32,
+                                                      (const float4*)c->d_q32, (const float4*)c->d_dinv32,
+                                                      (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
+                                                      c->d_part + nb, c->d_sc);
+      } else {
+        // p.q comes from the apply; the update forms q from the slots
+        c->n_launch += 2;
+        HDG_DISPATCH(c, launch_update_f32, c, par);
+      }
       cg32_direction_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, it, c->d_part + nb, (const float4*)c->d_z32,
                                                        (float4*)c->d_p32, c->d_sc, maxit);
     }
@@ -438,7 +488,7 @@ hdg_status cg32_inner(hdg_ctx* c, int* iters) {
     harvest(c, c->h_sc->done ? c->h_sc->iters : (1 << 30));
   }
   *iters = c->h_sc->iters;
-  c->last_it32 = std::max(1, c->h_sc->iters);
+  *last = std::max(1, c->h_sc->iters);
   return HDG_OK;
 }
 
@@ -450,7 +500,8 @@ hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
   const int nb = c->nb_red;
   int total_it = 0;
   hdg_status s;
-  double rel = 0.0;
+  double rel = 0.0, rel_prev = 0.0;
+  bool use16 = c->d_S16 != nullptr;   // FP16 inner operator until a sweep contracts poorly
   for (int sweep = 0;; ++sweep) {
     if (c->d_Sdf) {
       HDG_DISPATCH(c, launch_apply_df, c, x, c->d_slot);
@@ -472,7 +523,11 @@ hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
       if (info) { info->rel_residual = 0.0; info->sweeps += sweep; }
       return check_launch(c, "zero_interior");
     }
+    rel_prev = rel;
     rel = std::sqrt(r.rr / r.bb);
+    // the FP16 operator's rounding bounds the contraction of a sweep; if it gained less than
+    // a factor 10, the remaining sweeps use the FP32 copy
+    if (use16 && sweep > 0 && rel > 0.1 * rel_prev) use16 = false;
     if (rel <= c->opt.rtol) {
       if (info) { info->iterations += total_it; info->sweeps += sweep; info->rel_residual = rel; }
       return HDG_OK;
@@ -480,8 +535,11 @@ hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
     if (sweep >= c->opt.max_sweeps) break;
     c->n_launch += 1;
     to32_scaled_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_res, c->d_rs, c->d_b32);
+    // the inner solve needs to gain only what is left to rtol (with a margin): the last sweep
+    // stops early instead of over-solving to inner_rtol
+    const double tol = std::min(0.5, std::max(c->opt.inner_rtol, 0.25 * c->opt.rtol / rel));
     int it = 0;
-    if ((s = cg32_inner(c, &it))) return s;
+    if ((s = cg32_inner(c, &it, tol, &c->last_sweep_it[std::min(sweep, 7)], use16))) return s;
     total_it += it;
     c->n_launch += 1;
     refine_update_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_bnd, c->d_x32, c->d_rs, x);
@@ -494,7 +552,7 @@ hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
 
 // PCG on (-K) x = bvec over interior faces; x holds the initial guess (interior entries).
 hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
-  if (c->opt.prec == HDG_MIXED) return solve_mixed(c, bvec, x, info);
+  if (c->opt.prec != HDG_FP64) return solve_mixed(c, bvec, x, info);
   const int64_t nfe = c->sk.nf * c->Nf;
   const int nb = c->nb_red;
   HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr);
@@ -874,9 +932,10 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if (k < 1 || k > 4) return fail(c, HDG_EINVAL, "degree k must be in 1..4");
   if (!(tau > 0.0)) return fail(c, HDG_EINVAL, "tau must be positive");
   if (opt) c->opt = *opt; else hdg_default_options(&c->opt);
-  if (c->opt.prec != HDG_FP64 && c->opt.prec != HDG_MIXED) return fail(c, HDG_EINVAL, "unknown precision mode");
+  if (c->opt.prec != HDG_FP64 && c->opt.prec != HDG_MIXED && c->opt.prec != HDG_MIXED16)
+    return fail(c, HDG_EINVAL, "unknown precision mode");
   if (!(c->opt.rtol > 0.0) || c->opt.maxit < 1) return fail(c, HDG_EINVAL, "rtol must be > 0 and maxit >= 1");
-  if (c->opt.prec == HDG_MIXED && (!(c->opt.inner_rtol > 0.0) || !(c->opt.inner_rtol < 1.0) || c->opt.max_sweeps < 1))
+  if (c->opt.prec != HDG_FP64 && (!(c->opt.inner_rtol > 0.0) || !(c->opt.inner_rtol < 1.0) || c->opt.max_sweeps < 1))
     return fail(c, HDG_EINVAL, "mixed precision needs 0 < inner_rtol < 1 and max_sweeps >= 1");
   if (c->opt.nrhs < 1 || c->opt.nrhs > 256 || (c->opt.nrhs & (c->opt.nrhs - 1)))
     return fail(c, HDG_EINVAL, "nrhs must be a power of two in 1..256");
@@ -998,7 +1057,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   std::memset(c->h_sc, 0, sizeof(CgScal));
   for (double** p : {&c->d_u, &c->d_uprev, &c->d_h, &c->d_unew, &c->d_stage[0], &c->d_stage[1], &c->d_stage[2]})
     if ((s = dalloc(c, p, (size_t)ne * c->n * R))) return s;
-  if (c->opt.prec == HDG_MIXED) {
+  if (c->opt.prec != HDG_FP64) {
     const int64_t ngroups = (ne + 31) / 32;
     const int P4 = (c->m * (c->m + 1) / 2 + 3) / 4;
     const size_t nS32 = c->phys == HDG_ELASTIC ? (size_t)ne * c->m * c->m : (size_t)ngroups * P4 * 128;
@@ -1012,10 +1071,21 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
       CUDA_TRY(c, cudaMemsetAsync(*p, 0, cnt * 4, c->stream));
     }
     if (c->R > 1 && (s = dalloc(c, &c->d_mslot32, (size_t)ne * c->m * R))) return s;
+    if ((s = dalloc(c, &c->d_pqpart, (size_t)(ngroups + 3) / 4))) return s;
+    if ((s = dalloc(c, &c->d_pq, 1))) return s;
+    if ((s = dalloc(c, &c->d_ticket, 1))) return s;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream));
     if (c->R == 1 && c->phys == HDG_ACOUSTIC) {
       // whole 32-element groups, so the per-CTA staging copy never runs past the end
       const size_t nSdf = (size_t)ngroups * 32 * 2 * P4 * 4;
       if ((s = dalloc(c, &c->d_Sdf, nSdf))) return s;
+      if (c->opt.prec == HDG_MIXED16) {
+        const int P8 = (c->m * (c->m + 1) / 2 + 7) / 8;
+        const size_t n16 = (size_t)ngroups * P8 * 256;
+        if ((s = dalloc(c, &c->d_S16, n16))) return s;
+        if ((s = dalloc(c, &c->d_sc16, (size_t)ngroups * 32))) return s;
+        CUDA_TRY(c, cudaMemsetAsync(c->d_sc16, 0, (size_t)ngroups * 32 * 4, c->stream));
+      }
       CUDA_TRY(c, cudaMemsetAsync(c->d_Sdf, 0, nSdf * 4, c->stream));
       // double-float local solves: H^{-1} (filled at each condensation), geometry, tables
       if ((s = dalloc(c, &c->d_Hinvdf, (size_t)ne * c->nv * c->nv))) return s;
@@ -1437,9 +1507,11 @@ hdg_status hdg_get_stats(hdg_ctx* c, hdg_stats* o, int32_t reset) {
   o->apply32_ms = c->apply32_ms;
   o->applydf_launches = c->n_applydf;
   o->applydf_ms = c->applydf_ms;
+  o->apply16_launches = c->n_apply16;
+  o->apply16_ms = c->apply16_ms;
   if (reset) {
     c->n_launch = 0; c->n_apply = 0; c->apply_ms = 0.0; c->n_apply32 = 0; c->apply32_ms = 0.0;
-    c->n_applydf = 0; c->applydf_ms = 0.0;
+    c->n_applydf = 0; c->applydf_ms = 0.0; c->n_apply16 = 0; c->apply16_ms = 0.0;
   }
   return HDG_OK;
 }

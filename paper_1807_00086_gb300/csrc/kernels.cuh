@@ -14,6 +14,8 @@
 //   S_K = Bt^T H^{-1} Bt + D_K - (1/(b dJ)) [J_f J_g (n_f . n_g) Ff_f^T Ff_g]_{fg},
 //   Bt_f = -J_f (tau Ff_f + (1/b) sum_r (n_f . Jinv[r]) Dr_r Ff_f).
 #pragma once
+
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -718,13 +720,50 @@ __global__ void pack32_kernel(int64_t ne, const double* __restrict__ S, float* _
   }
 }
 
+// p.q of the Krylov iteration, formed inside the element apply: with q = sgn K p and K the
+// sum of the element blocks, p.q = sgn sum_K p_K . (S_K p_K) (boundary entries of p are zero
+// on both sides). Each 4-warp block writes its partial; the last block to finish (ticket
+// counter, no waiting) sums the partials in index order and resets the counter.
+struct PqOut {
+  double* part;       // [gridDim.x] block partials
+  unsigned* ticket;   // zero between launches
+  double* pq;         // result
+  float sgn;
+};
+
+__device__ __forceinline__ void pq_epilogue(const PqOut& o, double v) {
+  __shared__ double wsum[4];
+  __shared__ bool last;
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wsum[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    o.part[blockIdx.x] = ((wsum[0] + wsum[1]) + (wsum[2] + wsum[3]));
+    __threadfence();
+    last = atomicAdd(o.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(o.part + i);
+  s = warp_sum(s);
+  if (lane == 0) wsum[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *o.pq = (double)o.sgn * ((wsum[0] + wsum[1]) + (wsum[2] + wsum[3]));
+    *o.ticket = 0u;
+  }
+}
+
 // slot32 layout: [e][M] floats (element-major, like the FP64 slots); the warp transposes
 // its 32 x M products through shared memory so that the stores are contiguous float4s.
 template <int DIM, int K>
-__global__ void __launch_bounds__(128) apply32_kernel(int64_t ne, const int32_t* __restrict__ elem_face,
+__global__ void __launch_bounds__(128, 4) apply32_kernel(int64_t ne, const int32_t* __restrict__ elem_face,
                                                       const int32_t* __restrict__ face_bnd,
                                                       const float* __restrict__ S32, const float* __restrict__ x,
-                                                      float* __restrict__ slot, const int* __restrict__ done) {
+                                                      float* __restrict__ slot, const int* __restrict__ done, PqOut pqo) {
   using D = Dims<DIM, K>;
   using PK = Packed<DIM, K>;
   constexpr int NF = D::NF, M = D::M, NFC = D::NFC, P4 = PK::P4;
@@ -732,9 +771,10 @@ __global__ void __launch_bounds__(128) apply32_kernel(int64_t ne, const int32_t*
   __shared__ float tr[4][32 * MP];
   if (done && *done) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t g = (int64_t)blockIdx.x * 4 + wid;
-  const int64_t e = g * 32 + lane;
-  if (g * 32 >= ne) return;
+  const int64_t g0 = (int64_t)blockIdx.x * 4 + wid;
+  const bool wact = g0 * 32 < ne;                 // the last block may hold idle warps
+  const int64_t g = wact ? g0 : 0;
+  const int64_t e = g0 * 32 + lane;
   float xl[M], y[M];
 #pragma unroll
   for (int f = 0; f < NFC; ++f) {
@@ -763,9 +803,141 @@ __global__ void __launch_bounds__(128) apply32_kernel(int64_t ne, const int32_t*
 #pragma unroll
   for (int r = 0; r < M; ++r) t[lane * MP + r] = y[r];
   __syncwarp();
-  const int64_t nvalid = (ne - g * 32) < 32 ? (ne - g * 32) : 32;
-  float* dst = slot + g * 32 * (int64_t)M;
-  for (int idx = lane; idx < nvalid * M; idx += 32) dst[idx] = t[(idx / M) * MP + idx % M];
+  if (wact) {
+    const int64_t nvalid = (ne - g * 32) < 32 ? (ne - g * 32) : 32;
+    float* dst = slot + g * 32 * (int64_t)M;
+    for (int idx = lane; idx < nvalid * M; idx += 32) dst[idx] = t[(idx / M) * MP + idx % M];
+  }
+  if (pqo.part) {
+    Acc2 a;
+#pragma unroll
+    for (int r = 0; r < M; ++r) a.dot(xl[r], y[r]);
+    pq_epilogue(pqo, a.value());
+  }
+}
+
+// ---------------------------------------------------------------- FP16 operator copy
+// Packed symmetric S_K in binary16 with one FP32 scale per element: S_K ~ sc16[e] * S16,
+// sc16[e] = max |S_K| (so every stored value lies in [-1, 1]). Layout [group][P8][lane][8]:
+// one 16-byte load per lane carries 8 consecutive packed entries.
+template <int DIM, int K>
+struct Packed16 {
+  static constexpr int M = Dims<DIM, K>::M;
+  static constexpr int P = M * (M + 1) / 2;
+  static constexpr int P8 = (P + 7) / 8;
+};
+
+template <int DIM, int K>
+__global__ void scale16_kernel(int64_t ne, const double* __restrict__ S, float* __restrict__ sc16) {
+  constexpr int M = Dims<DIM, K>::M;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = w; e < ne; e += nw) {
+    double m = 0.0;
+    for (int i = lane; i < M * M; i += 32) m = fmax(m, fabs(S[e * (int64_t)(M * M) + i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // round the scale up so that |S / sc| <= 1 holds after the FP32 rounding of sc
+    if (lane == 0) sc16[e] = m > 0.0 ? __double2float_ru(m) : 1.f;
+  }
+}
+
+template <int DIM, int K>
+__global__ void pack16_kernel(int64_t ne, const double* __restrict__ S, const float* __restrict__ sc16,
+                              __half* __restrict__ S16) {
+  using PK = Packed16<DIM, K>;
+  constexpr int M = PK::M, P8 = PK::P8;
+  const int64_t ngroups = (ne + 31) / 32;
+  const int64_t n = ngroups * P8 * 32 * 8;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t & 7);
+    const int lane = (int)((t >> 3) & 31);
+    const int64_t q = (t >> 8) % P8;
+    const int64_t g = (t >> 8) / P8;
+    const int64_t e = g * 32 + lane;
+    const int p = (int)(q * 8 + j);
+    float v = 0.f;
+    if (e < ne && p < PK::P) {
+      int r = 0;
+      while (packed_index(M, r, M - 1) < p) ++r;
+      const int c = r + (p - packed_index(M, r, r));
+      v = (float)(S[e * (int64_t)(M * M) + r * M + c] / (double)sc16[e]);
+    }
+    S16[t] = __float2half_rn(v);
+  }
+}
+
+// slot = S_K x_K with the FP16 copy; the same thread-per-element structure as apply32_kernel
+// (FP32 accumulation, the element scale applied once at the end).
+template <int DIM, int K>
+__global__ void __launch_bounds__(128, 4) apply16_kernel(int64_t ne, const int32_t* __restrict__ elem_face,
+                                                      const int32_t* __restrict__ face_bnd,
+                                                      const __half* __restrict__ S16, const float* __restrict__ sc16,
+                                                      const float* __restrict__ x, float* __restrict__ slot,
+                                                      const int* __restrict__ done, PqOut pqo) {
+  using D = Dims<DIM, K>;
+  using PK = Packed16<DIM, K>;
+  constexpr int NF = D::NF, M = D::M, NFC = D::NFC, P8 = PK::P8;
+  constexpr int MP = M + 1;
+  __shared__ float tr[4][32 * MP];
+  if (done && *done) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t g0 = (int64_t)blockIdx.x * 4 + wid;
+  const bool wact = g0 * 32 < ne;
+  const int64_t g = wact ? g0 : 0;
+  const int64_t e = g0 * 32 + lane;
+  float xl[M], y[M];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    int fid = -1;
+    if (e < ne) fid = elem_face[e * NFC + f];
+    const bool use = fid >= 0 && face_bnd[fid] < 0;
+#pragma unroll
+    for (int mm = 0; mm < NF; ++mm) xl[f * NF + mm] = use ? x[(int64_t)fid * NF + mm] : 0.f;
+  }
+#pragma unroll
+  for (int r = 0; r < M; ++r) y[r] = 0.f;
+  const uint4* Sg = reinterpret_cast<const uint4*>(S16) + g * (int64_t)P8 * 32 + lane;
+  float sv[8];
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+#pragma unroll
+    for (int c = r; c < M; ++c) {
+      const int p = packed_index(M, r, c);
+      if ((p & 7) == 0) {
+        const uint4 u = __ldcs(Sg + (p >> 3) * 32);
+        const unsigned w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&w4[h]));
+          sv[2 * h] = f2.x;
+          sv[2 * h + 1] = f2.y;
+        }
+      }
+      const float s = sv[p & 7];
+      y[r] = fmaf(s, xl[c], y[r]);
+      if (c != r) y[c] = fmaf(s, xl[r], y[c]);
+    }
+  }
+  const float scl = e < ne ? sc16[e] : 0.f;
+  float* t = tr[wid];
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    y[r] *= scl;
+    t[lane * MP + r] = y[r];
+  }
+  __syncwarp();
+  if (wact) {
+    const int64_t nvalid = (ne - g * 32) < 32 ? (ne - g * 32) : 32;
+    float* dst = slot + g * 32 * (int64_t)M;
+    for (int idx = lane; idx < nvalid * M; idx += 32) dst[idx] = t[(idx / M) * MP + idx % M];
+  }
+  if (pqo.part) {
+    Acc2 a;
+#pragma unroll
+    for (int r = 0; r < M; ++r) a.dot(xl[r], y[r]);
+    pq_epilogue(pqo, a.value());
+  }
 }
 
 // q = sgn K32 p on faces; partial p.q in FP64. NF is compile-time (no integer division).
@@ -870,6 +1042,57 @@ __global__ void cg32_update_kernel(int64_t n4, int nb, int parity, const double*
     const float4 zv1 = f4mul(dinv[t], rv1);
     r[t] = rv1; z[t] = zv1;
     rz.dot4(rv1, zv1); rr.dot4(rv1, rv1);
+  }
+  double s;
+  s = block_sum256(rz.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 0] = s;
+  s = block_sum256(rr.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
+}
+
+// The update of the Krylov iteration with q = sgn K p formed from the slots (the face pass
+// is folded in): q = sgn (slot0 + slot1) on interior faces (0 on the boundary),
+// x += alpha p, r -= alpha q, z = Dinv r; partials (r.z, r.r). alpha = rho / pq with pq
+// from the apply's reduction. Vectors are processed as float4 (coalesced); the two slot
+// values of each entry are gathered per entry (runs of NF consecutive floats).
+template <class LD>
+__device__ __forceinline__ float q_entry(int64_t d, int64_t nfe, float sgn, const int32_t* __restrict__ face_slot,
+                                         const int32_t* __restrict__ face_bnd, const float* __restrict__ slot) {
+  constexpr int NF = LD::NF;
+  if (d >= nfe) return 0.f;
+  const int f = (int)(d / NF);
+  const int mm = (int)(d - (int64_t)f * NF);
+  if (face_bnd[f] >= 0) return 0.f;
+  return sgn * (slot[(int64_t)face_slot[2 * f] * NF + mm] + slot[(int64_t)face_slot[2 * f + 1] * NF + mm]);
+}
+
+template <class LD>
+__global__ void __launch_bounds__(256) cg32_update_f_kernel(int64_t n4, int64_t nfe, float sgn, int parity,
+                                                            const int32_t* __restrict__ face_slot,
+                                                            const int32_t* __restrict__ face_bnd,
+                                                            const float* __restrict__ slot,
+                                                            const float4* __restrict__ p,
+                                                            const float4* __restrict__ dinv, float4* __restrict__ x,
+                                                            float4* __restrict__ r, float4* __restrict__ z,
+                                                            const double* __restrict__ pq_in,
+                                                            double* __restrict__ part, const CgScal* __restrict__ sc) {
+  if (sc->done) return;
+  __shared__ double red[8];
+  const float al = (float)(sc->rho[parity] / *pq_in);
+  Acc2 rz, rr;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += stride) {
+    const float4 pv = p[t], xv = x[t], rv = r[t], dv = dinv[t];
+    float4 qv;
+    qv.x = q_entry<LD>(4 * t + 0, nfe, sgn, face_slot, face_bnd, slot);
+    qv.y = q_entry<LD>(4 * t + 1, nfe, sgn, face_slot, face_bnd, slot);
+    qv.z = q_entry<LD>(4 * t + 2, nfe, sgn, face_slot, face_bnd, slot);
+    qv.w = q_entry<LD>(4 * t + 3, nfe, sgn, face_slot, face_bnd, slot);
+    x[t] = f4fma(al, pv, xv);
+    const float4 rn = f4fma(-al, qv, rv);
+    const float4 zn = f4mul(dv, rn);
+    r[t] = rn;
+    z[t] = zn;
+    rz.dot4(rn, zn);
+    rr.dot4(rn, rn);
   }
   double s;
   s = block_sum256(rz.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 0] = s;

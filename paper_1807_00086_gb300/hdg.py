@@ -18,7 +18,7 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 P_double, P_int32 = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
 
 HDG_BE, HDG_BDF2, HDG_DIRK3 = 1, 2, 3
-HDG_FP64, HDG_MIXED = 0, 1
+HDG_FP64, HDG_MIXED, HDG_MIXED16 = 0, 1, 2
 SCHEMES = {"be": HDG_BE, "bdf2": HDG_BDF2, "dirk3": HDG_DIRK3}
 STATUS = {0: "HDG_OK", -1: "HDG_EINVAL", -2: "HDG_ENOMEM", -3: "HDG_ECUDA", -4: "HDG_ENOCONV",
           -5: "HDG_ETIMEOUT", -6: "HDG_ESTATE"}
@@ -54,7 +54,7 @@ class SolveInfo(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", c_int64), ("apply_launches", c_int64), ("apply_ms", c_double),
                 ("apply32_launches", c_int64), ("apply32_ms", c_double), ("applydf_launches", c_int64),
-                ("applydf_ms", c_double)]
+                ("applydf_ms", c_double), ("apply16_launches", c_int64), ("apply16_ms", c_double)]
 
 
 # exported entry points: name -> (restype, argtypes)
@@ -162,7 +162,7 @@ class Solver:
         mesh = Mesh(vert.shape[1], vert.shape[0], ne, _np_ptr(vert, c_double), _np_ptr(elem, c_int32))
         opt = Options()
         self.lib.hdg_default_options(ctypes.byref(opt))
-        opt.prec = {"fp64": HDG_FP64, "mixed": HDG_MIXED}[prec]
+        opt.prec = {"fp64": HDG_FP64, "mixed": HDG_MIXED, "mixed16": HDG_MIXED16}[prec]
         opt.rtol, opt.maxit, opt.check_every = rtol, maxit, check_every
         if inner_rtol is not None:
             opt.inner_rtol = inner_rtol
@@ -314,7 +314,8 @@ class Solver:
         self._check(self.lib.hdg_get_stats(self.ctx, ctypes.byref(st), 1 if reset else 0))
         return {"kernel_launches": st.kernel_launches, "apply_launches": st.apply_launches, "apply_ms": st.apply_ms,
                 "apply32_launches": st.apply32_launches, "apply32_ms": st.apply32_ms,
-                "applydf_launches": st.applydf_launches, "applydf_ms": st.applydf_ms}
+                "applydf_launches": st.applydf_launches, "applydf_ms": st.applydf_ms,
+                "apply16_launches": st.apply16_launches, "apply16_ms": st.apply16_ms}
 
     def hdg_step(self, dt, scheme, nsteps=1):
         info = SolveInfo()
