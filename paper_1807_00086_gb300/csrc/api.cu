@@ -67,8 +67,8 @@ struct hdg_ctx {
   int64_t nfe4 = 0;          // FP32 face vectors padded to a multiple of 4 entries
   int last_it32 = 16, last_it64 = 16;   // iteration counts of the previous solves (poll schedule)
   int last_sweep_it[8] = {16, 16, 16, 16, 16, 16, 16, 16};   // the same per refinement sweep
-  double *d_lam_prev = nullptr, *d_lam_x = nullptr;  // trace history for the extrapolated guess
-  bool have_lam_prev = false;
+  double *d_lam_prev = nullptr, *d_lam_prev2 = nullptr, *d_lam_x = nullptr;  // trace history (initial guess)
+  int n_lam_hist = 0;           // valid entries of that history (lam^{n-1}, lam^{n-2})
   // multiple right-hand sides (R columns, innermost index)
   int R = 1;
   double *d_mslot = nullptr;            // FP64 slots [ne][m][R]
@@ -1036,7 +1036,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if ((s = dalloc(c, &c->d_Hinv, (size_t)ne * c->nv * c->nv))) return s;
   if ((s = dalloc(c, &c->d_dinv, nfe))) return s;
   if ((s = dalloc(c, &c->d_err, 1))) return s;
-  for (double** p : {&c->d_r, &c->d_z, &c->d_p, &c->d_q, &c->d_b, &c->d_lam, &c->d_lam_prev, &c->d_lam_x})
+  for (double** p : {&c->d_r, &c->d_z, &c->d_p, &c->d_q, &c->d_b, &c->d_lam, &c->d_lam_prev, &c->d_lam_prev2, &c->d_lam_x})
     if ((s = dalloc(c, p, nfe * R))) return s;
   if ((s = dalloc(c, &c->d_slot, (size_t)ne * std::max(c->m, 1)))) return s;
   if ((s = dalloc(c, &c->d_part, (size_t)c->nb_red * 3 * R))) return s;
@@ -1368,7 +1368,7 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->t = t;
   c->have_state = true;
-  c->have_lam_prev = false;
+  c->n_lam_hist = 0;
   return HDG_OK;
 }
 
@@ -1403,23 +1403,33 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
         combine(c, c->d_h, 4.0 / 3.0, c->d_u, -1.0 / 3.0, c->d_uprev);
       }
       if ((s = ensure_alpha(c, alpha))) return s;
-      // initial guess of the trace solve: 2 lam^n - lam^{n-1} (lam^n alone on the first step)
+      // initial guess of the trace solve: polynomial extrapolation of the last traces,
+      // 3 lam^n - 3 lam^{n-1} + lam^{n-2} (quadratic; linear / constant while the history fills)
       const int64_t nfe = c->sk.nf * c->Nf * (int64_t)c->R;
-      if (c->have_lam_prev) {
+      if (c->n_lam_hist >= 1) {
         c->n_launch += 1;
-        combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, 2.0, c->d_lam, -1.0, c->d_lam_prev, 0, nullptr, 0,
-                                                                nullptr, c->d_lam_x);
-        std::swap(c->d_lam_prev, c->d_lam);
-        std::swap(c->d_lam, c->d_lam_x);
+        if (c->n_lam_hist >= 2)
+          combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, 3.0, c->d_lam, -3.0, c->d_lam_prev, 1.0,
+                                                                  c->d_lam_prev2, 0, nullptr, c->d_lam_x);
+        else
+          combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, 2.0, c->d_lam, -1.0, c->d_lam_prev, 0, nullptr, 0,
+                                                                  nullptr, c->d_lam_x);
+        // rotate: lam^{n-2} <- lam^{n-1} <- lam^n, lam <- guess
+        double* t = c->d_lam_prev2;
+        c->d_lam_prev2 = c->d_lam_prev;
+        c->d_lam_prev = c->d_lam;
+        c->d_lam = c->d_lam_x;
+        c->d_lam_x = t;
+        c->n_lam_hist = 2;
       } else {
         CUDA_TRY(c, cudaMemcpyAsync(c->d_lam_prev, c->d_lam, nfe * 8, cudaMemcpyDeviceToDevice, c->stream));
-        c->have_lam_prev = true;
+        c->n_lam_hist = 1;
       }
       if ((s = stage_solve(c, c->d_h, tn + dt, c->d_unew, &si))) return s;
       std::swap(c->d_uprev, c->d_u);   // u^{n-1} <- u^n
       std::swap(c->d_u, c->d_unew);    // u^n <- u^{n+1}
     } else {
-      c->have_lam_prev = false;
+      c->n_lam_hist = 0;
       double a[3][3], b[3], cc[3];
       dirk3(a, b, cc);
       // d = a^{-1} (lower triangular)
@@ -1481,7 +1491,7 @@ hdg_status hdg_reset_column(hdg_ctx* c, int32_t j) {
     c->n_launch += 1;
     zero_column_kernel<<<grid_for(c, nf), 256, 0, c->stream>>>(nf, c->R, j, a);
   }
-  for (double* a : {c->d_lam, c->d_lam_prev}) {
+  for (double* a : {c->d_lam, c->d_lam_prev, c->d_lam_prev2}) {
     c->n_launch += 1;
     zero_column_kernel<<<grid_for(c, nt), 256, 0, c->stream>>>(nt, c->R, j, a);
   }
