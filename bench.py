@@ -446,11 +446,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="mixed", choices=["fp64", "mixed", "mixed16"])
+    ap.add_argument("--prec", default=None, choices=["fp64", "mixed", "mixed16"],
+                    help="default: mixed16 for the single-source acoustic workload, else mixed")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain FP64 comparison run that follows a mixed-precision measurement")
     ap.add_argument("--rtol", type=float, default=1e-12)
-    ap.add_argument("--inner-rtol", type=float, default=1e-4)
+    ap.add_argument("--inner-rtol", type=float, default=None,
+                    help="default: 3e-4 (FP16 operator: its rounding bounds a sweep near that), "
+                         "3e-6 (FP32 operator, one right-hand side), 1e-4 (FP32, many)")
     ap.add_argument("--N", type=int, default=32)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--physics", default="acoustic", choices=["acoustic", "elastic"],
@@ -467,6 +470,10 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
+    if args.prec is None:
+        args.prec = "mixed16" if (args.physics == "acoustic" and args.nrhs == 1 and not args.serve) else "mixed"
+    if args.inner_rtol is None:
+        args.inner_rtol = 3e-4 if args.prec == "mixed16" else (1e-4 if args.nrhs > 1 else 3e-6)
     if args.serve:
         run_serve(args)
     elif args.mode == "apply":

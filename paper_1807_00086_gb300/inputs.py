@@ -105,6 +105,18 @@ def acoustic_3d_multisource_workload(N=32, k=3, nsrc=64, seed=DEFAULT_SEED):
     return w
 
 
+def element_degrees(ne, kmin=1, kmax=4, seed=DEFAULT_SEED):
+    """Per-element polynomial degree drawn uniformly from {kmin..kmax} (int32)."""
+    return np.random.default_rng(seed).integers(kmin, kmax + 1, size=ne).astype(np.int32)
+
+
+def elastic_3d_mixed_workload(N=24, seed=DEFAULT_SEED):
+    """The elastic workload with a per-element degree drawn uniformly from {1, 2, 3, 4}."""
+    w = elastic_3d_workload(N=N, k=4, seed=seed)
+    w["elem_k"] = element_degrees(w["elem"].shape[0], 1, 4, seed + 7)
+    return w
+
+
 def elastic_3d_workload(N=24, k=3, seed=DEFAULT_SEED):
     """3D linear elastodynamics workload: unit cube, 6 N^3 tets, rho = 1, Lame parameters
     lognormal per element (sigma 0.5; medians lam = 1.5, mu = 1), clamped boundary, initial
