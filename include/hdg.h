@@ -67,6 +67,15 @@ typedef struct {
   int64_t n_vert, n_elem;
   const double* vert;       /* _host [n_vert][dim]                                   */
   const int32_t* elem_vert; /* _host [n_elem][dim+1], any vertex order               */
+  const int32_t* elem_k;    /* _host [n_elem] per-element degree in 1..4, or NULL for */
+                            /* the uniform degree k of hdg_setup. 3D elastic only:    */
+                            /* v_h, sigma_h in P_{k_K}(K), the trace on a face in     */
+                            /* P_{k_F}, k_F = max over the face's elements. Fields    */
+                            /* and traces are then flat (sizes field_entries /        */
+                            /* trace_entries of hdg_sizes): element K holds its       */
+                            /* 9 N_p(k_K) coefficients [comp][mode] in element order, */
+                            /* face F its 3 N_f(k_F) trace values [comp][mode] in     */
+                            /* face order. Boundary faces are clamped (v_hat = 0)     */
 } hdg_mesh;
 
 typedef struct {
@@ -104,6 +113,11 @@ typedef struct {
   int64_t n_elem, n_faces, n_bnd_faces;
   int32_t nq_vol, nq_face;  /* projection quadrature points per element / face       */
   int64_t device_bytes;     /* device memory held by the context                     */
+  int64_t field_entries;    /* entries of one field column: n_elem x n_local, or the */
+                            /* sum of the elements' own sizes (per-element degrees)   */
+  int64_t trace_entries;    /* entries of one trace column: n_faces x the trace DOFs */
+                            /* of a face (N_f, or 3 N_f elastic); with per-element    */
+                            /* degrees the sum of the faces' own sizes                */
 } hdg_sizes;
 
 typedef struct {

@@ -21,202 +21,9 @@
 
 using namespace hdg;
 
-struct hdg_ctx {
-  std::string err;
-  cudaStream_t stream = nullptr;
-  hdg_options opt{};
-  int dim = 0, k = 0, Np = 0, Nf = 0, n = 0, m = 0, nfc = 0;
-  int phys = 0;             // HDG_ACOUSTIC or HDG_ELASTIC
-  int ncomp = 0;            // field components per element
-  int nv = 0;               // size of the factored local block (H^{-1} is nv x nv)
-  double sgn = -1.0;        // the Krylov operator is sgn * K (SPD)
-  double *d_lame = nullptr, *d_mue = nullptr;
-  int sms = 148;
-  double tau = 1.0;
-  Skeleton sk;
-  RefTables T;
-  std::vector<double> h_vert_elem;   // [ne][d+1][d] element vertex coordinates (sorted order)
-  // device: mesh and tables
-  double *d_geo = nullptr, *d_rho = nullptr, *d_c = nullptr, *d_tab = nullptr;
-  int32_t *d_elem_face = nullptr, *d_face_slot = nullptr, *d_face_bnd = nullptr;
-  int64_t* d_bnd_faces = nullptr;
-  Tabs tabs{};
-  double *d_qv_w = nullptr, *d_qv_phi = nullptr;
-  // condensed operators
-  double *d_S = nullptr, *d_Hinv = nullptr, *d_dinv = nullptr;
-  double alpha = 0.0;
-  bool condensed = false;
-  int* d_err = nullptr;
-  // Krylov workspace
-  double *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_b = nullptr, *d_slot = nullptr;
-  double* d_part = nullptr;
-  CgScal* d_sc = nullptr;
-  CgScal* h_sc = nullptr;   // pinned
-  int nb_red = 0;
-  // mixed precision
-  float *d_S32 = nullptr, *d_dinv32 = nullptr, *d_slot32 = nullptr;
-  float* d_Sdf = nullptr;       // double-float diagonal-major copy of S_K (refinement apply)
-  df2 *d_Hinvdf = nullptr, *d_geodf = nullptr, *d_tabdf = nullptr;   // double-float local solves
-  TabsDf tabsdf{};
-  __half* d_S16 = nullptr;      // FP16 packed S_K (inner Krylov operator of HDG_MIXED16)
-  float* d_sc16 = nullptr;      // its per-element scales
-  double *d_pqpart = nullptr, *d_pq = nullptr;   // p.q block partials and result of the FP32/FP16 apply
-  unsigned* d_ticket = nullptr;                   // last-block counter of that reduction
-  float *d_r32 = nullptr, *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_x32 = nullptr, *d_b32 = nullptr;
-  double* d_res = nullptr;   // FP64 refinement residual
-  int64_t nfe4 = 0;          // FP32 face vectors padded to a multiple of 4 entries
-  int last_it32 = 16, last_it64 = 16;   // iteration counts of the previous solves (poll schedule)
-  int last_sweep_it[8] = {16, 16, 16, 16, 16, 16, 16, 16};   // the same per refinement sweep
-  double *d_lam_prev = nullptr, *d_lam_prev2 = nullptr, *d_lam_x = nullptr;  // trace history (initial guess)
-  int n_lam_hist = 0;           // valid entries of that history (lam^{n-1}, lam^{n-2})
-  // multiple right-hand sides (R columns, innermost index)
-  int R = 1;
-  double *d_mslot = nullptr;            // FP64 slots [ne][m][R]
-  float *d_mslot32 = nullptr;           // FP32 slots [ne][m][R]
-  double *d_mrho0 = nullptr, *d_mrho1 = nullptr, *d_malpha = nullptr, *d_mbeta = nullptr, *d_mrr = nullptr,
-         *d_mbb = nullptr, *d_mtol2 = nullptr, *d_mscale = nullptr, *d_mrr2 = nullptr, *d_mbb2 = nullptr;
-  int *d_mconv = nullptr, *d_mdone = nullptr, *d_mnconv = nullptr, *d_miters = nullptr;
-  int* h_mint = nullptr;                // pinned: [0] done flag, [1] nconv, [2] iterations
-  // CUDA graphs of per-column Krylov iteration chunks, keyed by (vector type, x pointer)
-  std::vector<std::pair<std::pair<int, const void*>, cudaGraphExec_t>> graphs;
-  int32_t* d_src_col = nullptr;
-  double* d_src_delay = nullptr;
-  int src_cap = 0;                      // capacity of the per-source buffers (grow-only)
-  RefScal* d_rs = nullptr;
-  RefScal* h_rs = nullptr;   // pinned
-  // time state
-  double *d_u = nullptr, *d_uprev = nullptr, *d_lam = nullptr, *d_h = nullptr, *d_unew = nullptr;
-  double* d_stage[3] = {nullptr, nullptr, nullptr};
-  double t = 0.0;
-  bool have_state = false;
-  // data
-  int nsrc = 0;
-  int32_t* d_src_ptr = nullptr;
-  double* d_src_phi = nullptr;
-  double f0 = 0.0, t0 = 0.0;
-  double* d_bnd_coef = nullptr;
-  double omega = 0.0, phase = 0.0;
-  int64_t bytes = 0;
-  std::vector<void*> allocs;
-  // instrumentation
-  bool stats_on = false;
-  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0, n_applydf = 0, n_apply16 = 0;
-  double apply_ms = 0.0, apply32_ms = 0.0, applydf_ms = 0.0, apply16_ms = 0.0;
-  std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
-  std::vector<char> ev_kind;          // per pair: 0 FP64, 1 FP32, 2 double-float, 3 FP16 apply
-  std::vector<int> ev_iter;           // per pair: Krylov iteration index (-1: always live)
-  size_t ev_used = 0;
-};
+#include "ctx.cuh"
 
 namespace {
-
-hdg_status fail(hdg_ctx* c, hdg_status s, const std::string& msg) {
-  if (c) c->err = msg;
-  return s;
-}
-
-#define CUDA_TRY(ctx, call)                                                                       \
-  do {                                                                                            \
-    cudaError_t e_ = (call);                                                                      \
-    if (e_ != cudaSuccess) return fail(ctx, HDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-
-template <typename T>
-hdg_status dalloc(hdg_ctx* c, T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return fail(c, HDG_ENOMEM, std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) + "): " + cudaGetErrorString(e));
-  }
-  c->allocs.push_back(*p);
-  c->bytes += (int64_t)(count * sizeof(T));
-  return HDG_OK;
-}
-
-void dfree(hdg_ctx* c, void* p) {
-  if (!p) return;
-  cudaFree(p);
-  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
-  if (it != c->allocs.end()) c->allocs.erase(it);
-}
-
-int grid_for(const hdg_ctx* c, int64_t n, int block = 256) {
-  int64_t g = (n + block - 1) / block;
-  int64_t cap = (int64_t)c->sms * 8;
-  return (int)std::max<int64_t>(1, std::min(g, cap));
-}
-
-SrcArgs srcargs(const hdg_ctx* c, double t) {
-  SrcArgs a;
-  a.ptr = c->nsrc > 0 ? c->d_src_ptr : nullptr;
-  a.phi = c->d_src_phi; a.col = c->d_src_col; a.delay = c->d_src_delay;
-  a.f0 = c->f0; a.t0 = c->t0; a.t = t;
-  return a;
-}
-
-DevMesh devmesh(const hdg_ctx* c) {
-  DevMesh m;
-  m.ne = c->sk.ne; m.nf = c->sk.nf;
-  m.geo = c->d_geo; m.rho = c->d_rho; m.c = c->d_c;
-  m.elem_face = c->d_elem_face; m.face_slot = c->d_face_slot; m.face_bnd = c->d_face_bnd;
-  return m;
-}
-
-// Event pair around one apply launch (instrumentation); returns the stop event or null.
-cudaEvent_t apply_begin(hdg_ctx* c, int kind = 0, int iter = -1) {
-  if (!c->stats_on) return nullptr;
-  if (c->ev_used + 2 > c->ev_pool.size()) {
-    for (int i = 0; i < 64; ++i) {
-      cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-      c->ev_pool.push_back(e);
-    }
-    c->ev_kind.resize(c->ev_pool.size() / 2 + 1);
-    c->ev_iter.resize(c->ev_pool.size() / 2 + 1);
-  }
-  cudaEvent_t a = c->ev_pool[c->ev_used];
-  c->ev_kind[c->ev_used / 2] = (char)kind;
-  c->ev_iter[c->ev_used / 2] = iter;
-  cudaEventRecord(a, c->stream);
-  return c->ev_pool[c->ev_used + 1];
-}
-void apply_end(hdg_ctx* c, cudaEvent_t stop) {
-  if (!stop) return;
-  cudaEventRecord(stop, c->stream);
-  c->ev_used += 2;
-}
-// Harvests the recorded pairs (call after a stream synchronisation). Launches of Krylov
-// iterations at or beyond live_iters returned early (the solve had converged) and are
-// dropped, so the statistics time only launches that did the work.
-void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
-  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
-    float ms = 0.f;
-    if (c->ev_iter[i / 2] >= live_iters) continue;
-    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
-      if (c->ev_kind[i / 2] == 1) { c->apply32_ms += ms; c->n_apply32 += 1; }
-      else if (c->ev_kind[i / 2] == 2) { c->applydf_ms += ms; c->n_applydf += 1; }
-      else if (c->ev_kind[i / 2] == 3) { c->apply16_ms += ms; c->n_apply16 += 1; }
-      else { c->apply_ms += ms; c->n_apply += 1; }
-    }
-  }
-  c->ev_used = 0;
-}
-
-// ---- dispatch on (dim, k)
-#define HDG_DISPATCH(c, FN, ...)                     \
-  switch ((c)->dim * 10 + (c)->k) {                  \
-    case 21: FN<2, 1>(__VA_ARGS__); break;           \
-    case 22: FN<2, 2>(__VA_ARGS__); break;           \
-    case 23: FN<2, 3>(__VA_ARGS__); break;           \
-    case 24: FN<2, 4>(__VA_ARGS__); break;           \
-    case 31: FN<3, 1>(__VA_ARGS__); break;           \
-    case 32: FN<3, 2>(__VA_ARGS__); break;           \
-    case 33: FN<3, 3>(__VA_ARGS__); break;           \
-    case 34: FN<3, 4>(__VA_ARGS__); break;           \
-    default: break;                                  \
-  }
 
 template <int DIM, int K>
 void launch_condense(hdg_ctx* c) {
@@ -286,12 +93,6 @@ template <int DIM, int K>
 void launch_apply(hdg_ctx* c, const double* x, double* zslot, const int* done, int iter = -1) {
   if (c->phys == HDG_ELASTIC) launch_apply_l<ElDims<DIM, K>>(c, x, zslot, done, iter);
   else launch_apply_l<Dims<DIM, K>>(c, x, zslot, done, iter);
-}
-
-hdg_status check_launch(hdg_ctx* c, const char* what) {
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(c, HDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-  return HDG_OK;
 }
 
 template <int DIM, int K>
@@ -400,6 +201,7 @@ void launch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, in
 }
 
 hdg_status do_condense(hdg_ctx* c, double alpha) {
+  if (c->vd) return vd_condense(c, alpha);
   if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(c, HDG_EINVAL, "alpha must be positive and finite");
   c->alpha = alpha;
   CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
@@ -837,6 +639,7 @@ hdg_status msolve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) 
 
 // one implicit solve at mass shift alpha: alpha Mw u + f(u, lam, t) = alpha Mw hist
 hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info) {
+  if (c->vd) return vd_stage_solve(c, hist, tt, uout, info);
   const double fac = std::cos(c->omega * tt + c->phase);
   if (c->R > 1) {
     const int64_t nbe = c->sk.nb * c->Nf * (int64_t)c->R;
@@ -871,7 +674,7 @@ hdg_status ensure_alpha(hdg_ctx* c, double alpha) {
 
 void combine(hdg_ctx* c, double* out, double c0, const double* i0, double c1 = 0, const double* i1 = nullptr,
              double c2 = 0, const double* i2 = nullptr, double c3 = 0, const double* i3 = nullptr) {
-  const int64_t n = c->sk.ne * c->n * (int64_t)c->R;
+  const int64_t n = c->nfld * (int64_t)c->R;
   c->n_launch += 1;
   combine_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c0, i0, c1, i1, c2, i2, c3, i3, out);
 }
@@ -917,6 +720,7 @@ void hdg_destroy(hdg_ctx* c) {
   if (c->h_sc) cudaFreeHost(c->h_sc);
   if (c->h_rs) cudaFreeHost(c->h_rs);
   if (c->h_mint) cudaFreeHost(c->h_mint);
+  vd_destroy(c);
   delete c;
 }
 
@@ -945,8 +749,16 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   c->phys = mat->phys;
   if (c->phys == HDG_ELASTIC && (!mat->lam || !mat->mu)) return fail(c, HDG_EINVAL, "elastic material needs lam and mu");
   if (c->phys == HDG_ELASTIC && c->opt.nrhs != 1) return fail(c, HDG_EINVAL, "elastic path supports nrhs = 1 only");
-  if (c->phys == HDG_ELASTIC && mesh->dim == 3 && k == 4)
-    return fail(c, HDG_EINVAL, "elastic path in 3D supports 1 <= k <= 3 (the local block does not fit shared memory)");
+  // uniform degree 4 in 3D elastic runs through the per-element-degree path (its local
+  // velocity block does not fit shared memory in the uniform condensation kernel)
+  std::vector<int32_t> k4;
+  const int32_t* elem_k = mesh->elem_k;
+  if (!elem_k && mat->phys == HDG_ELASTIC && mesh->dim == 3 && k == 4) {
+    k4.assign((size_t)std::max<int64_t>(mesh->n_elem, 0), 4);
+    elem_k = k4.data();
+  }
+  if (elem_k && (mat->phys != HDG_ELASTIC || mesh->dim != 3))
+    return fail(c, HDG_EINVAL, "per-element degrees: 3D elastic meshes only");
   if (!build_skeleton(mesh->dim, mesh->n_vert, mesh->n_elem, mesh->vert, mesh->elem_vert, c->sk, err))
     return fail(c, HDG_EINVAL, err);
   for (int64_t e = 0; e < mesh->n_elem; ++e) {
@@ -1016,6 +828,15 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   CUDA_TRY(c, cudaMemcpyAsync(c->d_face_slot, c->sk.face_slot.data(), c->sk.face_slot.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_face_bnd, c->sk.face_bnd.data(), c->sk.face_bnd.size() * 4, cudaMemcpyHostToDevice, c->stream));
   if (nb) CUDA_TRY(c, cudaMemcpyAsync(c->d_bnd_faces, c->sk.bnd_faces.data(), nb * 8, cudaMemcpyHostToDevice, c->stream));
+  if (elem_k) {
+    if ((s = vd_setup(c, elem_k))) return s;
+    c->k = 0;
+    for (int64_t e = 0; e < ne; ++e) c->k = std::max(c->k, (int)elem_k[e]);
+    c->n = 0; c->m = 0;   // no common local size: fields and traces are flat (nfld, ntr entries)
+    return HDG_OK;
+  }
+  c->nfld = ne * (int64_t)c->n;
+  c->ntr = nf * (int64_t)c->Nf;
   // reference tables packed in one buffer
   std::vector<double> tab;
   size_t off[6];
@@ -1135,6 +956,8 @@ hdg_status hdg_get_sizes(const hdg_ctx* c, hdg_sizes* o) {
   o->n_elem = c->sk.ne; o->n_faces = c->sk.nf; o->n_bnd_faces = c->sk.nb;
   o->nq_vol = c->T.nqv; o->nq_face = c->T.nqf;
   o->device_bytes = c->bytes;
+  o->field_entries = c->nfld;
+  o->trace_entries = c->ntr;
   return HDG_OK;
 }
 
@@ -1144,6 +967,7 @@ hdg_status hdg_condense(hdg_ctx* c, double alpha) {
 }
 
 hdg_status hdg_get_schur(hdg_ctx* c, double* S_dev) {
+  if (c && c->vd) return fail(c, HDG_EINVAL, "not available with per-element degrees");
   if (!c || !S_dev) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
   CUDA_TRY(c, cudaMemcpyAsync(S_dev, c->d_S, (size_t)c->sk.ne * c->m * c->m * 8, cudaMemcpyDeviceToDevice, c->stream));
@@ -1153,6 +977,7 @@ hdg_status hdg_get_schur(hdg_ctx* c, double* S_dev) {
 hdg_status hdg_trace_apply(hdg_ctx* c, const double* x, double* y) {
   if (!c || !x || !y) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  if (c->vd) return vd_trace_apply(c, x, y);
   if (c->R > 1) {
     HDG_DISPATCH(c, mlaunch_apply64, c, x, c->d_mslot, (const int*)nullptr, -1);
     HDG_DISPATCH(c, mlaunch_gather, c, (const double*)c->d_mslot, 1.0, y);
@@ -1167,6 +992,7 @@ hdg_status hdg_trace_apply(hdg_ctx* c, const double* x, double* y) {
 hdg_status hdg_condensed_rhs(hdg_ctx* c, const double* F, const double* lamD, double* r) {
   if (!c || !F || !r) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  if (c->vd) return vd_condensed_rhs(c, F, lamD, r);
   if (c->R > 1) {
     HDG_DISPATCH(c, mlaunch_local, c, 0, F, (const double*)nullptr, 0.0, lamD, c->d_mslot);
     HDG_DISPATCH(c, mlaunch_gather, c, (const double*)c->d_mslot, -1.0, r);
@@ -1182,6 +1008,7 @@ hdg_status hdg_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_i
   if (!c || !r || !lam) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
   if (info) { info->iterations = 0; info->sweeps = 0; info->rel_residual = 0; }
+  if (c->vd) return vd_trace_solve(c, r, lam, info);
   // K lam = r  <=>  (sgn K) lam = sgn r
   const int64_t nfe = c->sk.nf * c->Nf * (int64_t)c->R;
   combine_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->sgn, r, 0, nullptr, 0, nullptr, 0, nullptr, c->d_b);
@@ -1198,6 +1025,7 @@ hdg_status hdg_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_i
 hdg_status hdg_recover(hdg_ctx* c, const double* F, const double* lam, double* u) {
   if (!c || !F || !lam || !u) return fail(c, HDG_EINVAL, "null argument");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  if (c->vd) return vd_recover(c, F, lam, u);
   if (c->R > 1) {
     HDG_DISPATCH(c, mlaunch_local, c, 1, F, (const double*)nullptr, 0.0, lam, u);
     return check_launch(c, "recover_multi");
@@ -1274,6 +1102,7 @@ hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const do
 }
 
 hdg_status hdg_quadrature_points(hdg_ctx* c, int32_t which, double* xyz) {
+  if (c && c->vd) return fail(c, HDG_EINVAL, "not available with per-element degrees");
   if (!c || !xyz || (which != 0 && which != 1)) return fail(c, HDG_EINVAL, "bad arguments");
   const int d = c->dim, nc = c->nfc;
   if (which == 0) {
@@ -1309,6 +1138,7 @@ hdg_status hdg_quadrature_points(hdg_ctx* c, int32_t which, double* xyz) {
 }
 
 hdg_status hdg_project_volume(hdg_ctx* c, const double* vals, double* u) {
+  if (c && c->vd) return fail(c, HDG_EINVAL, "not available with per-element degrees");
   if (!c || !vals || !u) return fail(c, HDG_EINVAL, "null argument");
   const size_t cnt = (size_t)c->sk.ne * c->T.nqv * c->ncomp;
   double* dv = nullptr;
@@ -1316,7 +1146,7 @@ hdg_status hdg_project_volume(hdg_ctx* c, const double* vals, double* u) {
   if ((s = dalloc(c, &dv, cnt))) return s;
   cudaError_t e1 = cudaMemcpyAsync(dv, vals, cnt * 8, cudaMemcpyHostToDevice, c->stream);
   if (e1 == cudaSuccess) {
-    const int64_t n = c->sk.ne * c->n * (int64_t)c->R;
+    const int64_t n = c->nfld * (int64_t)c->R;
     if (c->R > 1)
       mproject_volume_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.ne, c->Np, c->T.nqv, c->ncomp, c->R, c->d_qv_w,
                                                                    c->d_qv_phi, dv, u);
@@ -1333,6 +1163,7 @@ hdg_status hdg_project_volume(hdg_ctx* c, const double* vals, double* u) {
 }
 
 hdg_status hdg_set_dirichlet(hdg_ctx* c, const double* vals, double omega, double phase) {
+  if (c && c->vd && vals) return fail(c, HDG_EINVAL, "per-element degrees: homogeneous (clamped) boundary only");
   if (!c) return HDG_EINVAL;
   dfree(c, c->d_bnd_coef);
   c->d_bnd_coef = nullptr;
@@ -1357,8 +1188,8 @@ hdg_status hdg_set_dirichlet(hdg_ctx* c, const double* vals, double omega, doubl
 
 hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const double* lam, double t) {
   if (!c || !u) return fail(c, HDG_EINVAL, "null argument");
-  const size_t bytes = (size_t)c->sk.ne * c->n * c->R * 8;
-  const size_t tbytes = (size_t)c->sk.nf * c->Nf * c->R * 8;
+  const size_t bytes = (size_t)c->nfld * c->R * 8;
+  const size_t tbytes = (size_t)c->ntr * c->R * 8;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_u, u, bytes, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_uprev, uprev ? uprev : u, bytes, cudaMemcpyDeviceToDevice, c->stream));
   if (lam)
@@ -1374,10 +1205,10 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
 
 hdg_status hdg_get_state(hdg_ctx* c, double* u, double* uprev, double* lam, double* t) {
   if (!c) return HDG_EINVAL;
-  const size_t bytes = (size_t)c->sk.ne * c->n * c->R * 8;
+  const size_t bytes = (size_t)c->nfld * c->R * 8;
   if (u) CUDA_TRY(c, cudaMemcpyAsync(u, c->d_u, bytes, cudaMemcpyDeviceToDevice, c->stream));
   if (uprev) CUDA_TRY(c, cudaMemcpyAsync(uprev, c->d_uprev, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  if (lam) CUDA_TRY(c, cudaMemcpyAsync(lam, c->d_lam, (size_t)c->sk.nf * c->Nf * c->R * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (lam) CUDA_TRY(c, cudaMemcpyAsync(lam, c->d_lam, (size_t)c->ntr * c->R * 8, cudaMemcpyDeviceToDevice, c->stream));
   if (t) *t = c->t;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return HDG_OK;
@@ -1405,7 +1236,7 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
       if ((s = ensure_alpha(c, alpha))) return s;
       // initial guess of the trace solve: polynomial extrapolation of the last traces,
       // 3 lam^n - 3 lam^{n-1} + lam^{n-2} (quadratic; linear / constant while the history fills)
-      const int64_t nfe = c->sk.nf * c->Nf * (int64_t)c->R;
+      const int64_t nfe = c->ntr * (int64_t)c->R;
       if (c->n_lam_hist >= 1) {
         c->n_launch += 1;
         if (c->n_lam_hist >= 2)
@@ -1486,7 +1317,7 @@ hdg_status hdg_stream_destroy(void* stream) {
 hdg_status hdg_reset_column(hdg_ctx* c, int32_t j) {
   if (!c) return HDG_EINVAL;
   if (j < 0 || j >= c->R) return fail(c, HDG_EINVAL, "column out of range");
-  const int64_t nf = c->sk.ne * c->n, nt = c->sk.nf * c->Nf;
+  const int64_t nf = c->nfld, nt = c->ntr;
   for (double* a : {c->d_u, c->d_uprev}) {
     c->n_launch += 1;
     zero_column_kernel<<<grid_for(c, nf), 256, 0, c->stream>>>(nf, c->R, j, a);

@@ -1,0 +1,240 @@
+// The library context (hdg_ctx) and the host helpers shared by the translation units of
+// the library: errors, device allocation, launch sizing, instrumentation, (dim, k) dispatch.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/hdg.h"
+#include "kernels.cuh"
+#include "dflocal.cuh"
+#include "mesh.h"
+#include "reftab.h"
+
+using namespace hdg;
+
+struct VarDeg;   // variable-degree (per-element k) data of an elastic context
+
+struct hdg_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  hdg_options opt{};
+  int dim = 0, k = 0, Np = 0, Nf = 0, n = 0, m = 0, nfc = 0;
+  int phys = 0;             // HDG_ACOUSTIC or HDG_ELASTIC
+  int ncomp = 0;            // field components per element
+  int nv = 0;               // size of the factored local block (H^{-1} is nv x nv)
+  double sgn = -1.0;        // the Krylov operator is sgn * K (SPD)
+  double *d_lame = nullptr, *d_mue = nullptr;
+  int sms = 148;
+  double tau = 1.0;
+  Skeleton sk;
+  RefTables T;
+  std::vector<double> h_vert_elem;   // [ne][d+1][d] element vertex coordinates (sorted order)
+  // device: mesh and tables
+  double *d_geo = nullptr, *d_rho = nullptr, *d_c = nullptr, *d_tab = nullptr;
+  int32_t *d_elem_face = nullptr, *d_face_slot = nullptr, *d_face_bnd = nullptr;
+  int64_t* d_bnd_faces = nullptr;
+  Tabs tabs{};
+  double *d_qv_w = nullptr, *d_qv_phi = nullptr;
+  // condensed operators
+  double *d_S = nullptr, *d_Hinv = nullptr, *d_dinv = nullptr;
+  double alpha = 0.0;
+  bool condensed = false;
+  int* d_err = nullptr;
+  // Krylov workspace
+  double *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_b = nullptr, *d_slot = nullptr;
+  double* d_part = nullptr;
+  CgScal* d_sc = nullptr;
+  CgScal* h_sc = nullptr;   // pinned
+  int nb_red = 0;
+  // mixed precision
+  float *d_S32 = nullptr, *d_dinv32 = nullptr, *d_slot32 = nullptr;
+  float* d_Sdf = nullptr;       // double-float diagonal-major copy of S_K (refinement apply)
+  df2 *d_Hinvdf = nullptr, *d_geodf = nullptr, *d_tabdf = nullptr;   // double-float local solves
+  TabsDf tabsdf{};
+  __half* d_S16 = nullptr;      // FP16 packed S_K (inner Krylov operator of HDG_MIXED16)
+  float* d_sc16 = nullptr;      // its per-element scales
+  double *d_pqpart = nullptr, *d_pq = nullptr;   // p.q block partials and result of the FP32/FP16 apply
+  unsigned* d_ticket = nullptr;                   // last-block counter of that reduction
+  float *d_r32 = nullptr, *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_x32 = nullptr, *d_b32 = nullptr;
+  double* d_res = nullptr;   // FP64 refinement residual
+  int64_t nfe4 = 0;          // FP32 face vectors padded to a multiple of 4 entries
+  int last_it32 = 16, last_it64 = 16;   // iteration counts of the previous solves (poll schedule)
+  int last_sweep_it[8] = {16, 16, 16, 16, 16, 16, 16, 16};   // the same per refinement sweep
+  double *d_lam_prev = nullptr, *d_lam_prev2 = nullptr, *d_lam_x = nullptr;  // trace history (initial guess)
+  int n_lam_hist = 0;           // valid entries of that history (lam^{n-1}, lam^{n-2})
+  // multiple right-hand sides (R columns, innermost index)
+  int R = 1;
+  double *d_mslot = nullptr;            // FP64 slots [ne][m][R]
+  float *d_mslot32 = nullptr;           // FP32 slots [ne][m][R]
+  double *d_mrho0 = nullptr, *d_mrho1 = nullptr, *d_malpha = nullptr, *d_mbeta = nullptr, *d_mrr = nullptr,
+         *d_mbb = nullptr, *d_mtol2 = nullptr, *d_mscale = nullptr, *d_mrr2 = nullptr, *d_mbb2 = nullptr;
+  int *d_mconv = nullptr, *d_mdone = nullptr, *d_mnconv = nullptr, *d_miters = nullptr;
+  int* h_mint = nullptr;                // pinned: [0] done flag, [1] nconv, [2] iterations
+  // CUDA graphs of per-column Krylov iteration chunks, keyed by (vector type, x pointer)
+  std::vector<std::pair<std::pair<int, const void*>, cudaGraphExec_t>> graphs;
+  int32_t* d_src_col = nullptr;
+  double* d_src_delay = nullptr;
+  int src_cap = 0;                      // capacity of the per-source buffers (grow-only)
+  RefScal* d_rs = nullptr;
+  RefScal* h_rs = nullptr;   // pinned
+  // time state
+  double *d_u = nullptr, *d_uprev = nullptr, *d_lam = nullptr, *d_h = nullptr, *d_unew = nullptr;
+  double* d_stage[3] = {nullptr, nullptr, nullptr};
+  double t = 0.0;
+  bool have_state = false;
+  // data
+  int nsrc = 0;
+  int32_t* d_src_ptr = nullptr;
+  double* d_src_phi = nullptr;
+  double f0 = 0.0, t0 = 0.0;
+  double* d_bnd_coef = nullptr;
+  double omega = 0.0, phase = 0.0;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+  // instrumentation
+  bool stats_on = false;
+  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0, n_applydf = 0, n_apply16 = 0;
+  double apply_ms = 0.0, apply32_ms = 0.0, applydf_ms = 0.0, apply16_ms = 0.0;
+  std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
+  std::vector<char> ev_kind;          // per pair: 0 FP64, 1 FP32, 2 double-float, 3 FP16 apply
+  std::vector<int> ev_iter;           // per pair: Krylov iteration index (-1: always live)
+  size_t ev_used = 0;
+  // entries of one field / trace column (n N_e and N_f N_faces for one degree; sums of the
+  // per-element / per-face sizes on a variable-degree mesh)
+  int64_t nfld = 0, ntr = 0;
+  VarDeg* vd = nullptr;
+};
+
+namespace {
+
+hdg_status fail(hdg_ctx* c, hdg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                       \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(ctx, HDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+hdg_status dalloc(hdg_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(c, HDG_ENOMEM, std::string("cudaMalloc(") + std::to_string(count * sizeof(T)) + "): " + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(*p);
+  c->bytes += (int64_t)(count * sizeof(T));
+  return HDG_OK;
+}
+
+void dfree(hdg_ctx* c, void* p) {
+  if (!p) return;
+  cudaFree(p);
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+}
+
+hdg_status check_launch(hdg_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, HDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return HDG_OK;
+}
+
+int grid_for(const hdg_ctx* c, int64_t n, int block = 256) {
+  int64_t g = (n + block - 1) / block;
+  int64_t cap = (int64_t)c->sms * 8;
+  return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+SrcArgs srcargs(const hdg_ctx* c, double t) {
+  SrcArgs a;
+  a.ptr = c->nsrc > 0 ? c->d_src_ptr : nullptr;
+  a.phi = c->d_src_phi; a.col = c->d_src_col; a.delay = c->d_src_delay;
+  a.f0 = c->f0; a.t0 = c->t0; a.t = t;
+  return a;
+}
+
+DevMesh devmesh(const hdg_ctx* c) {
+  DevMesh m;
+  m.ne = c->sk.ne; m.nf = c->sk.nf;
+  m.geo = c->d_geo; m.rho = c->d_rho; m.c = c->d_c;
+  m.elem_face = c->d_elem_face; m.face_slot = c->d_face_slot; m.face_bnd = c->d_face_bnd;
+  return m;
+}
+
+// Event pair around one apply launch (instrumentation); returns the stop event or null.
+cudaEvent_t apply_begin(hdg_ctx* c, int kind = 0, int iter = -1) {
+  if (!c->stats_on) return nullptr;
+  if (c->ev_used + 2 > c->ev_pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      c->ev_pool.push_back(e);
+    }
+    c->ev_kind.resize(c->ev_pool.size() / 2 + 1);
+    c->ev_iter.resize(c->ev_pool.size() / 2 + 1);
+  }
+  cudaEvent_t a = c->ev_pool[c->ev_used];
+  c->ev_kind[c->ev_used / 2] = (char)kind;
+  c->ev_iter[c->ev_used / 2] = iter;
+  cudaEventRecord(a, c->stream);
+  return c->ev_pool[c->ev_used + 1];
+}
+void apply_end(hdg_ctx* c, cudaEvent_t stop) {
+  if (!stop) return;
+  cudaEventRecord(stop, c->stream);
+  c->ev_used += 2;
+}
+// Harvests the recorded pairs (call after a stream synchronisation). Launches of Krylov
+// iterations at or beyond live_iters returned early (the solve had converged) and are
+// dropped, so the statistics time only launches that did the work.
+void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    if (c->ev_iter[i / 2] >= live_iters) continue;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
+      if (c->ev_kind[i / 2] == 1) { c->apply32_ms += ms; c->n_apply32 += 1; }
+      else if (c->ev_kind[i / 2] == 2) { c->applydf_ms += ms; c->n_applydf += 1; }
+      else if (c->ev_kind[i / 2] == 3) { c->apply16_ms += ms; c->n_apply16 += 1; }
+      else { c->apply_ms += ms; c->n_apply += 1; }
+    }
+  }
+  c->ev_used = 0;
+}
+
+// ---- dispatch on (dim, k)
+#define HDG_DISPATCH(c, FN, ...)                     \
+  switch ((c)->dim * 10 + (c)->k) {                  \
+    case 21: FN<2, 1>(__VA_ARGS__); break;           \
+    case 22: FN<2, 2>(__VA_ARGS__); break;           \
+    case 23: FN<2, 3>(__VA_ARGS__); break;           \
+    case 24: FN<2, 4>(__VA_ARGS__); break;           \
+    case 31: FN<3, 1>(__VA_ARGS__); break;           \
+    case 32: FN<3, 2>(__VA_ARGS__); break;           \
+    case 33: FN<3, 3>(__VA_ARGS__); break;           \
+    case 34: FN<3, 4>(__VA_ARGS__); break;           \
+    default: break;                                  \
+  }
+
+}  // namespace
+
+// variable-degree elastic path (vardeg.cu)
+hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k);
+hdg_status vd_condense(hdg_ctx* c, double alpha);
+hdg_status vd_stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info);
+hdg_status vd_trace_apply(hdg_ctx* c, const double* x, double* y);
+hdg_status vd_condensed_rhs(hdg_ctx* c, const double* F, const double* lamD, double* r);
+hdg_status vd_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_info* info);
+hdg_status vd_recover(hdg_ctx* c, const double* F, const double* lam, double* u);
+void vd_destroy(hdg_ctx* c);

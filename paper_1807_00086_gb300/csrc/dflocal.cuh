@@ -54,7 +54,7 @@ struct LocalDfCfg {
 };
 
 // Double-float copy of an FP64 array (H^{-1} after each condensation, the element geometry).
-__global__ void to_df_kernel(int64_t n, const double* __restrict__ a, df2* __restrict__ out) {
+static __global__ void to_df_kernel(int64_t n, const double* __restrict__ a, df2* __restrict__ out) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     out[t] = df_from(a[t]);
 }

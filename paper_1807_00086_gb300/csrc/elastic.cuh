@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(128) apply32f_kernel(int64_t ne, const int32_t
   }
 }
 
-__global__ void to32_copy_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+static __global__ void to32_copy_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     b[t] = (float)a[t];
 }

@@ -478,7 +478,7 @@ __device__ __forceinline__ double face_sum(const int32_t* __restrict__ face_slot
 }
 
 // b = sum of slots (interior), 0 on boundary; optional scale.
-__global__ void face_gather_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_slot,
+static __global__ void face_gather_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_slot,
                                    const int32_t* __restrict__ face_bnd, const double* __restrict__ zslot,
                                    double scale, double* __restrict__ out) {
   const int64_t n = nf * NF;
@@ -490,7 +490,7 @@ __global__ void face_gather_kernel(int64_t nf, int NF, const int32_t* __restrict
 }
 
 // r = b - (sgn K) x0, z = Dinv r, p = z; partials (rz, rr, bb) per block.
-__global__ void cg_init_kernel(int64_t nf, int NF, double sgn, const int32_t* __restrict__ face_slot,
+static __global__ void cg_init_kernel(int64_t nf, int NF, double sgn, const int32_t* __restrict__ face_slot,
                                const int32_t* __restrict__ face_bnd, const double* __restrict__ zslot,
                                const double* __restrict__ bvec, const double* __restrict__ dinv, double* __restrict__ r,
                                double* __restrict__ z, double* __restrict__ p, double* __restrict__ part) {
@@ -517,7 +517,7 @@ __global__ void cg_init_kernel(int64_t nf, int NF, double sgn, const int32_t* __
   s = block_sum256(bb, red); if (threadIdx.x == 0) part[blockIdx.x * 3 + 2] = s;
 }
 
-__global__ void cg_init_scalars(int nb, const double* __restrict__ part, double rtol, CgScal* sc) {
+static __global__ void cg_init_scalars(int nb, const double* __restrict__ part, double rtol, CgScal* sc) {
   __shared__ double red[8];
   const double rz = reduce_partials(part + 0, nb, 3, red);
   const double rr = reduce_partials(part + 1, nb, 3, red);
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(256) cg_face_q_kernel(int nf, double sgn, cons
 }
 
 // alpha = rho/pq; x += alpha p; r -= alpha q; z = Dinv r; partials (rz, rr)
-__global__ void cg_update_kernel(int64_t n, int nb, int parity, const double* __restrict__ part_pq,
+static __global__ void cg_update_kernel(int64_t n, int nb, int parity, const double* __restrict__ part_pq,
                                  const double* __restrict__ p, const double* __restrict__ q,
                                  const double* __restrict__ dinv, double* __restrict__ x, double* __restrict__ r,
                                  double* __restrict__ z, double* __restrict__ part, const CgScal* __restrict__ sc) {
@@ -604,7 +604,7 @@ __global__ void cg_update_kernel(int64_t n, int nb, int parity, const double* __
 }
 
 // beta = rz_new / rho; p = z + beta p; convergence test.
-__global__ void cg_direction_kernel(int64_t n, int nb, int parity, int iter, const double* __restrict__ part,
+static __global__ void cg_direction_kernel(int64_t n, int nb, int parity, int iter, const double* __restrict__ part,
                                     const double* __restrict__ z, double* __restrict__ p, CgScal* sc, int maxit) {
   if (sc->done) return;
   __shared__ double red[8];
@@ -635,7 +635,7 @@ __global__ void cg_direction_kernel(int64_t n, int nb, int parity, int iter, con
 }
 
 // out = sum_q c_q in_q (up to four inputs), elementwise.
-__global__ void combine_kernel(int64_t n, double c0, const double* __restrict__ i0, double c1,
+static __global__ void combine_kernel(int64_t n, double c0, const double* __restrict__ i0, double c1,
                                const double* __restrict__ i1, double c2, const double* __restrict__ i2, double c3,
                                const double* __restrict__ i3, double* __restrict__ out) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
@@ -648,7 +648,7 @@ __global__ void combine_kernel(int64_t n, double c0, const double* __restrict__ 
 }
 
 // boundary entries of lam <- coef[b] * fac (Dirichlet trace at the current time).
-__global__ void dirichlet_kernel(int64_t nb, int NF, const int64_t* __restrict__ bnd_faces,
+static __global__ void dirichlet_kernel(int64_t nb, int NF, const int64_t* __restrict__ bnd_faces,
                                  const double* __restrict__ coef, double fac, double* __restrict__ lam) {
   const int64_t n = nb * NF;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
@@ -658,14 +658,14 @@ __global__ void dirichlet_kernel(int64_t nb, int NF, const int64_t* __restrict__
 }
 
 // interior entries of x <- 0
-__global__ void zero_interior_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_bnd, double* __restrict__ x) {
+static __global__ void zero_interior_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_bnd, double* __restrict__ x) {
   const int64_t n = nf * NF;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     if (face_bnd[t / NF] < 0) x[t] = 0.0;
 }
 
 // volume projection: u[e][c*NP+i] = sum_q w_q vals[e][q][c] phi_i(xi_q)  (mass = dJ I cancels dJ)
-__global__ void project_volume_kernel(int64_t ne, int NP, int nq, int ncomp, const double* __restrict__ w,
+static __global__ void project_volume_kernel(int64_t ne, int NP, int nq, int ncomp, const double* __restrict__ w,
                                       const double* __restrict__ phi, const double* __restrict__ vals,
                                       double* __restrict__ u) {
   const int64_t n = ne * ncomp * NP;
@@ -981,7 +981,7 @@ __device__ __forceinline__ float4 f4mul(float4 a, float4 b) { return make_float4
 
 
 // inner solve start from x = 0: r = b, z = Dinv r, p = z; partials (rz, rr)
-__global__ void cg32_init_kernel(int64_t n4, const float4* __restrict__ b, const float4* __restrict__ dinv,
+static __global__ void cg32_init_kernel(int64_t n4, const float4* __restrict__ b, const float4* __restrict__ dinv,
                                  float4* __restrict__ x, float4* __restrict__ r, float4* __restrict__ z,
                                  float4* __restrict__ p, double* __restrict__ part) {
   __shared__ double red[8];
@@ -997,7 +997,7 @@ __global__ void cg32_init_kernel(int64_t n4, const float4* __restrict__ b, const
   s = block_sum256(rr.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
 }
 
-__global__ void cg32_init_scalars(int nb, const double* __restrict__ part, double rtol, CgScal* sc) {
+static __global__ void cg32_init_scalars(int nb, const double* __restrict__ part, double rtol, CgScal* sc) {
   __shared__ double red[8];
   const double rz = reduce_partials(part + 0, nb, 2, red);
   const double rr = reduce_partials(part + 1, nb, 2, red);
@@ -1009,7 +1009,7 @@ __global__ void cg32_init_scalars(int nb, const double* __restrict__ part, doubl
   }
 }
 
-__global__ void cg32_update_kernel(int64_t n4, int nb, int parity, const double* __restrict__ part_pq,
+static __global__ void cg32_update_kernel(int64_t n4, int nb, int parity, const double* __restrict__ part_pq,
                                    const float4* __restrict__ p, const float4* __restrict__ q,
                                    const float4* __restrict__ dinv, float4* __restrict__ x, float4* __restrict__ r,
                                    float4* __restrict__ z, double* __restrict__ part, const CgScal* __restrict__ sc) {
@@ -1099,7 +1099,7 @@ __global__ void __launch_bounds__(256) cg32_update_f_kernel(int64_t n4, int64_t 
   s = block_sum256(rr.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
 }
 
-__global__ void cg32_direction_kernel(int64_t n4, int nb, int parity, int iter, const double* __restrict__ part,
+static __global__ void cg32_direction_kernel(int64_t n4, int nb, int parity, int iter, const double* __restrict__ part,
                                       const float4* __restrict__ z, float4* __restrict__ p, CgScal* sc, int maxit) {
   if (sc->done) return;
   __shared__ double red[8];
@@ -1129,7 +1129,7 @@ __global__ void cg32_direction_kernel(int64_t n4, int nb, int parity, int iter, 
 }
 
 // FP64 refinement residual rho = b - (sgn K) lam = b - sgn sum slots64 (interior), partials |rho|^2, |b|^2
-__global__ void refine_residual_kernel(int64_t nf, int NF, double sgn, const int32_t* __restrict__ face_slot,
+static __global__ void refine_residual_kernel(int64_t nf, int NF, double sgn, const int32_t* __restrict__ face_slot,
                                        const int32_t* __restrict__ face_bnd, const double* __restrict__ zslot,
                                        const double* __restrict__ b, double* __restrict__ rho,
                                        double* __restrict__ part) {
@@ -1157,7 +1157,7 @@ struct RefScal {
   double rr, bb, scale;
 };
 
-__global__ void refine_scalars(int nb, const double* __restrict__ part, RefScal* rs) {
+static __global__ void refine_scalars(int nb, const double* __restrict__ part, RefScal* rs) {
   __shared__ double red[8];
   const double rr = reduce_partials(part + 0, nb, 2, red);
   const double bb = reduce_partials(part + 1, nb, 2, red);
@@ -1168,7 +1168,7 @@ __global__ void refine_scalars(int nb, const double* __restrict__ part, RefScal*
 }
 
 // b32 = rho * scale (inner right-hand side of unit norm)
-__global__ void to32_scaled_kernel(int64_t n, const double* __restrict__ rho, const RefScal* __restrict__ rs,
+static __global__ void to32_scaled_kernel(int64_t n, const double* __restrict__ rho, const RefScal* __restrict__ rs,
                                    float* __restrict__ b32) {
   const double s = rs->scale;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -1176,7 +1176,7 @@ __global__ void to32_scaled_kernel(int64_t n, const double* __restrict__ rho, co
 }
 
 // lam += delta / scale on interior faces (delta is zero on boundary faces)
-__global__ void refine_update_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_bnd,
+static __global__ void refine_update_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_bnd,
                                      const float* __restrict__ delta, const RefScal* __restrict__ rs,
                                      double* __restrict__ lam) {
   const double inv = 1.0 / rs->scale;
@@ -1185,7 +1185,7 @@ __global__ void refine_update_kernel(int64_t nf, int NF, const int32_t* __restri
     if (face_bnd[t / NF] < 0) lam[t] += (double)delta[t] * inv;
 }
 
-__global__ void to32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+static __global__ void to32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     b[t] = (float)a[t];
 }

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(256) mface_q_kernel(int nf, int R, const int32
 }
 
 // alpha_j = rho_j / pq_j (0 for converged columns)
-__global__ void mcols_alpha(int nb, int R, int parity, const double* __restrict__ part, MScal sc) {
+static __global__ void mcols_alpha(int nb, int R, int parity, const double* __restrict__ part, MScal sc) {
   for (int j = threadIdx.x; j < R; j += blockDim.x) {
     if (*sc.done) return;
     double s = 0.0;
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(256) mupdate_kernel(int64_t n, int R, const TV
 
 // rho_new, rr per column; convergence; beta. Single block: the iteration counter lives on the
 // device (read by every thread before thread 0 advances it), so launches carry no host index.
-__global__ void mcols_beta(int nb, int R, int parity, int maxit, const double* __restrict__ part, MScal sc,
+static __global__ void mcols_beta(int nb, int R, int parity, int maxit, const double* __restrict__ part, MScal sc,
                            double* __restrict__ beta) {
   __shared__ int notconv;
   if (threadIdx.x == 0) notconv = 0;
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(256) minit_kernel(int nf, int R, const int32_t
 }
 
 // column scalars after minit: rho0 = rz, rr, bb, tol2 = rtol^2 * (bb or rr when bb_from_rr)
-__global__ void mcols_init(int nb, int R, double rtol, int tol_from_rr, const double* __restrict__ part, MScal sc) {
+static __global__ void mcols_init(int nb, int R, double rtol, int tol_from_rr, const double* __restrict__ part, MScal sc) {
   __shared__ int notconv;
   if (threadIdx.x == 0) notconv = 0;
   __syncthreads();
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(256) mrefine_residual_kernel(int nf, int R, co
 }
 
 // per column: rr, bb, scale = 1/|rho| (0 -> column converged: its inner right-hand side is zero)
-__global__ void mrefine_scalars(int nb, int R, double rtol, const double* __restrict__ part, double* __restrict__ rr,
+static __global__ void mrefine_scalars(int nb, int R, double rtol, const double* __restrict__ part, double* __restrict__ rr,
                                 double* __restrict__ bb, double* __restrict__ scale, int* __restrict__ nconv) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
@@ -548,13 +548,13 @@ __global__ void mrefine_scalars(int nb, int R, double rtol, const double* __rest
   if (threadIdx.x == 0) *nconv = cnt;
 }
 
-__global__ void mto32_scaled_kernel(int64_t n, int R, const double* __restrict__ res, const double* __restrict__ scale,
+static __global__ void mto32_scaled_kernel(int64_t n, int R, const double* __restrict__ res, const double* __restrict__ scale,
                                     float* __restrict__ b32) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     b32[t] = (float)(res[t] * scale[t & (R - 1)]);
 }
 
-__global__ void mrefine_update_kernel(int64_t n, int R, int NF, const int32_t* __restrict__ face_bnd,
+static __global__ void mrefine_update_kernel(int64_t n, int R, int NF, const int32_t* __restrict__ face_bnd,
                                       const float* __restrict__ delta, const double* __restrict__ scale,
                                       double* __restrict__ lam) {
   const int lg = __ffs(R) - 1;
@@ -565,7 +565,7 @@ __global__ void mrefine_update_kernel(int64_t n, int R, int NF, const int32_t* _
 }
 
 // boundary entries of lam (all columns) <- coef[b] * fac
-__global__ void mdirichlet_kernel(int64_t nb, int NF, int R, const int64_t* __restrict__ bnd_faces,
+static __global__ void mdirichlet_kernel(int64_t nb, int NF, int R, const int64_t* __restrict__ bnd_faces,
                                   const double* __restrict__ coef, double fac, double* __restrict__ lam) {
   const int64_t n = nb * NF * R;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
@@ -596,7 +596,7 @@ __global__ void mface_gather_kernel(int nf, int R, const int32_t* __restrict__ f
 }
 
 // interior entries (all columns) <- 0
-__global__ void mzero_interior_kernel(int64_t n, int R, int NF, const int32_t* __restrict__ face_bnd,
+static __global__ void mzero_interior_kernel(int64_t n, int R, int NF, const int32_t* __restrict__ face_bnd,
                                       double* __restrict__ x) {
   const int lg = __ffs(R) - 1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -604,7 +604,7 @@ __global__ void mzero_interior_kernel(int64_t n, int R, int NF, const int32_t* _
 }
 
 // volume projection replicated over R columns: u[e][c*NP+i][j] = sum_q w_q vals[e][q][c] phi_i(xi_q)
-__global__ void mproject_volume_kernel(int64_t ne, int NP, int nq, int ncomp, int R, const double* __restrict__ w,
+static __global__ void mproject_volume_kernel(int64_t ne, int NP, int nq, int ncomp, int R, const double* __restrict__ w,
                                        const double* __restrict__ phi, const double* __restrict__ vals,
                                        double* __restrict__ u) {
   const int64_t n = ne * ncomp * NP * R;
@@ -622,7 +622,7 @@ __global__ void mproject_volume_kernel(int64_t ne, int NP, int nq, int ncomp, in
 
 namespace hdg {
 // column j of an [count][R] array <- 0
-__global__ void zero_column_kernel(int64_t count, int R, int j, double* __restrict__ a) {
+static __global__ void zero_column_kernel(int64_t count, int R, int j, double* __restrict__ a) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
     a[t * R + j] = 0.0;
 }

@@ -149,15 +149,30 @@ void dubiner(int dim, int k, const double* pts, int np, double* val, double* gra
   }
 }
 
-RefTables build_tables(int dim, int k) {
-  if (dim < 2 || dim > 3 || k < 1 || k > 4) throw std::invalid_argument("dim must be 2/3 and 1 <= k <= 4");
+std::vector<int> face_mode_degrees(int dim, int kf) {
+  std::vector<int> d;
+  if (dim == 2) {
+    for (int i = 0; i <= kf; ++i) d.push_back(i);
+  } else {
+    for (int i = 0; i <= kf; ++i)
+      for (int j = 0; i + j <= kf; ++j) d.push_back(i + j);
+  }
+  return d;
+}
+
+RefTables build_tables(int dim, int k) { return build_tables_pair(dim, k, k); }
+
+RefTables build_tables_pair(int dim, int k, int kf) {
+  if (dim < 2 || dim > 3 || k < 1 || k > 4 || kf < k || kf > 4)
+    throw std::invalid_argument("dim must be 2/3 and 1 <= k <= kf <= 4");
   RefTables T;
   T.dim = dim; T.k = k;
   const int Np = T.Np = n_modes(dim, k);
-  const int Nf = T.Nf = n_modes(dim - 1, k);
+  const int Nf = T.Nf = n_modes(dim - 1, kf);
   const int nfc = dim + 1;
+  const int kq = kf;   // kf >= k: rules exact for the face products of degree k + kf
   // volume rule and derivative matrices
-  simplex_rule(dim, k + 2, T.qv_pts, T.qv_w);
+  simplex_rule(dim, kq + 2, T.qv_pts, T.qv_w);
   const int nqv = T.nqv = (int)T.qv_w.size();
   T.qv_phi.resize((size_t)nqv * Np);
   std::vector<double> grad((size_t)nqv * Np * dim);
@@ -171,10 +186,10 @@ RefTables build_tables(int dim, int k) {
         T.Dr[((size_t)r * Np + i) * Np + l] = s;
       }
   // face rule and face-trace coupling: local face j has the reference vertices {0..d}\{j}
-  simplex_rule(dim - 1, k + 2, T.qf_pts, T.qf_w);
+  simplex_rule(dim - 1, kq + 2, T.qf_pts, T.qf_w);
   const int nqf = T.nqf = (int)T.qf_w.size();
   T.qf_mu.resize((size_t)nqf * Nf);
-  dubiner(dim - 1, k, T.qf_pts.data(), nqf, T.qf_mu.data(), nullptr);
+  dubiner(dim - 1, kf, T.qf_pts.data(), nqf, T.qf_mu.data(), nullptr);
   T.Ff.assign((size_t)nfc * Np * Nf, 0.0);
   std::vector<double> vref((size_t)(dim + 1) * dim, 0.0);  // reference vertices
   for (int r = 0; r < dim; ++r) vref[(size_t)(r + 1) * dim + r] = 1.0;

@@ -29,5 +29,11 @@ struct RefTables {
 };
 
 RefTables build_tables(int dim, int k);
+// Tables of a volume degree kv whose faces carry traces of degree kf >= kv (variable-degree
+// meshes): Np = Np(kv), Nf = Nf(kf); the rules take max(kv, kf) + 2 points per direction.
+// build_tables(dim, k) == build_tables_pair(dim, k, k).
+RefTables build_tables_pair(int dim, int kv, int kf);
+// total degree of each face mode of degree kf, in the face basis order
+std::vector<int> face_mode_degrees(int dim, int kf);
 
 }  // namespace hdg

@@ -26,7 +26,7 @@ STATUS = {0: "HDG_OK", -1: "HDG_EINVAL", -2: "HDG_ENOMEM", -3: "HDG_ECUDA", -4: 
 
 class Mesh(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("n_vert", c_int64), ("n_elem", c_int64), ("vert", P_double),
-                ("elem_vert", P_int32)]
+                ("elem_vert", P_int32), ("elem_k", P_int32)]
 
 
 class Material(ctypes.Structure):
@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
 class Sizes(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("k", c_int32), ("Np", c_int32), ("Nf", c_int32), ("n_local", c_int32),
                 ("n_trace_local", c_int32), ("n_elem", c_int64), ("n_faces", c_int64), ("n_bnd_faces", c_int64),
-                ("nq_vol", c_int32), ("nq_face", c_int32), ("device_bytes", c_int64)]
+                ("nq_vol", c_int32), ("nq_face", c_int32), ("device_bytes", c_int64), ("field_entries", c_int64),
+                ("trace_entries", c_int64)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -140,8 +141,10 @@ class Solver:
     """One HDG problem resident on the current CUDA device (wraps an hdg_ctx)."""
 
     def __init__(self, vert, elem, k, tau, rho, c=None, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
-                 inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None, lam=None, mu=None):
-        """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu)."""
+                 inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None, lam=None, mu=None,
+                 elem_k=None):
+        """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu).
+        elem_k: per-element degrees (3D elastic); fields and traces are then flat vectors."""
         import torch
         self.lib = load()
         self.torch = torch
@@ -159,7 +162,9 @@ class Solver:
         else:
             self._c = arr(c)
             mat = Material(0, _np_ptr(self._rho, c_double), _np_ptr(self._c, c_double), None, None)
-        mesh = Mesh(vert.shape[1], vert.shape[0], ne, _np_ptr(vert, c_double), _np_ptr(elem, c_int32))
+        self._ek = None if elem_k is None else np.ascontiguousarray(elem_k, dtype=np.int32)
+        mesh = Mesh(vert.shape[1], vert.shape[0], ne, _np_ptr(vert, c_double), _np_ptr(elem, c_int32),
+                    None if self._ek is None else _np_ptr(self._ek, c_int32))
         opt = Options()
         self.lib.hdg_default_options(ctypes.byref(opt))
         opt.prec = {"fp64": HDG_FP64, "mixed": HDG_MIXED, "mixed16": HDG_MIXED16}[prec]
@@ -186,8 +191,12 @@ class Solver:
         self.n, self.m = sz.n_local, sz.n_trace_local
         self.n_elem, self.n_faces, self.n_bnd = sz.n_elem, sz.n_faces, sz.n_bnd_faces
         self.R = nrhs
-        self._fshape = (self.n_elem, self.n) if nrhs == 1 else (self.n_elem, self.n, nrhs)
-        self._tshape = (self.n_faces, self.Nf) if nrhs == 1 else (self.n_faces, self.Nf, nrhs)
+        self.vardeg = self.n == 0
+        if self.vardeg:
+            self._fshape, self._tshape = (sz.field_entries,), (sz.trace_entries,)
+        else:
+            self._fshape = (self.n_elem, self.n) if nrhs == 1 else (self.n_elem, self.n, nrhs)
+            self._tshape = (self.n_faces, self.Nf) if nrhs == 1 else (self.n_faces, self.Nf, nrhs)
 
     def _check(self, st):
         if st != 0:
