@@ -181,7 +181,10 @@ def run_ours(args):
     R = args.nrhs
     elastic = args.physics == "elastic"
     scheme, dt = ("dirk3", 1e-3) if elastic else ("bdf2", DT)
-    if elastic:
+    vardeg = elastic and args.mixed_degree
+    if vardeg:
+        w = inputs.elastic_3d_mixed_workload(N=args.N if args.N != 32 else 24)
+    elif elastic:
         w = inputs.elastic_3d_workload(N=args.N if args.N != 32 else 24, k=args.k)
     elif R > 1:
         w = inputs.acoustic_3d_multisource_workload(N=args.N, k=args.k, nsrc=R)
@@ -194,11 +197,10 @@ def run_ours(args):
         nonlocal u_init
         if elastic:
             sv = hdg.Solver(w["vert"], w["elem"], w["k"], 1.0, w["rho"], lam=w["lam"], mu=w["mu"], prec=prec,
-                            rtol=args.rtol, inner_rtol=args.inner_rtol)
+                            rtol=args.rtol, inner_rtol=args.inner_rtol, elem_k=w.get("elem_k"))
             if u_init is None:
                 xq = sv.hdg_quadrature_points(0)
-                u_init = sv.hdg_project_volume(inputs.gaussian_velocity_values(xq, w["center"], w["width"],
-                                                                               sv.n // sv.Np))
+                u_init = sv.hdg_project_volume(inputs.gaussian_velocity_values(xq, w["center"], w["width"], 9))
             sv.hdg_set_state(u_init, 0.0)
             return sv
         sv = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=prec, rtol=args.rtol,
@@ -209,7 +211,7 @@ def run_ours(args):
         return sv
 
     s = make_solver(args.prec)
-    dofs = ne * s.n * R
+    dofs = int(np.prod(s._fshape))
     stream = s.stream
     # warm-up (includes the condensation for alpha = 3/(2 dt))
     for _ in range(args.warmup):
@@ -275,8 +277,9 @@ def run_ours(args):
     if dist is not None:
         dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
     e2e_value = world * dofs * e2e_steps / float(t_e.item())
-    field_bytes = ne * s.n * R * 8
-    trace_bytes = s.n_faces * s.Nf * R * 8
+    field_bytes = int(np.prod(s._fshape)) * 8
+    trace_bytes = int(np.prod(s._tshape)) * 8
+    nschur, nslot = s.sizes.schur_entries, s.sizes.slot_entries
 
     # roofline of the dominant kernel (matrix-free trace apply)
     peaks, src = load_peaks()
@@ -366,7 +369,28 @@ def run_ours(args):
 
     if R > 1:
         roof = roof_multi
-    if elastic and args.prec != "fp64":
+    if vardeg:
+        # per launch: every compact S_K (FP32, or FP64 for the plain path), the trace gather and
+        # the slot products
+        if args.prec != "fp64":
+            a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
+            byt = nschur * 4 + 2 * nslot * 4
+            ach = byt / (a32 / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                    "kernel": "apply_vd_kernel<float> (compact FP32 S_K, per-element m_K)",
+                    "peak_source": src + " (hbm_gbs: copy)",
+                    "bytes_per_launch": byt, "launch_ms": a32, "launches": st["apply32_launches"],
+                    "fp64_refinement_apply": {"launch_ms": apply_avg_ms, "launches": st["apply_launches"],
+                                              "achieved_tflops": 2 * nschur / (apply_avg_ms / 1e3) / 1e12
+                                              if st["apply_launches"] else None}}
+        else:
+            ach = 2 * nschur / (apply_avg_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                    "traffic": None, "kernel": "apply_vd_kernel<double> (compact FP64 S_K)",
+                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s", "flops_per_launch": 2 * nschur,
+                    "launch_ms": apply_avg_ms, "launches": st["apply_launches"]}
+    elif elastic and args.prec != "fp64":
         a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
         bytes_el = m * m * 4 + 2 * m * 4
         ach = bytes_el * ne / (a32 / 1e3) / 1e9
@@ -384,12 +408,13 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "mixed16": "f16+f32+f64"}[args.prec],
                "data": "synthetic",
-               "config": {"workload": ("elastic3d_k%d_%dcube_dirk3" % (args.k, round((ne / 6) ** (1 / 3))) if elastic else
+               "config": {"workload": ("elastic3d_k%s_%dcube_dirk3" % ("mix1to4" if vardeg else args.k,
+                                                                    round((ne / 6) ** (1 / 3))) if elastic else
                                        "acoustic3d_k3_32cube_bdf2" + ("_%dsrc" % R if R > 1 else "")), "n_elem": ne,
-                          "k": args.k, "dofs": dofs, "nrhs": R,
-                          "trace_dofs": int(s.n_faces - s.n_bnd) * s.Nf * R, "dt": dt, "scheme": scheme.upper(),
+                          "k": "U{1..4} per element" if vardeg else args.k, "dofs": dofs, "nrhs": R,
+                          "trace_dofs": int(s.sizes.trace_entries) * R, "dt": dt, "scheme": scheme.upper(),
                           "precision": args.prec, "rtol": args.rtol, "parallelism": "replicas",
-                          "l2": "inputs larger than L2 (S_K %.2f GB)" % (ne * m * m * 8 / 1e9),
+                          "l2": "inputs larger than L2 (S_K %.2f GB)" % (nschur * 8 / 1e9),
                           "krylov_iters_per_step": iters / args.steps,
                           "refinement_sweeps_per_step": sweeps / args.steps if args.prec != "fp64" else None,
                           "inner_rtol": args.inner_rtol if args.prec != "fp64" else None},
@@ -458,6 +483,8 @@ def main():
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--physics", default="acoustic", choices=["acoustic", "elastic"],
                     help="elastic: the 3D linear elastodynamics workload (24^3 x 6 tets, DIRK3)")
+    ap.add_argument("--mixed-degree", action="store_true",
+                    help="elastic: per-element degree uniform in {1..4} (the mixed-degree workload)")
     ap.add_argument("--nrhs", type=int, default=1,
                     help="right-hand-side columns solved together (64: the multi-source workload)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -118,6 +118,8 @@ typedef struct {
   int64_t trace_entries;    /* entries of one trace column: n_faces x the trace DOFs */
                             /* of a face (N_f, or 3 N_f elastic); with per-element    */
                             /* degrees the sum of the faces' own sizes                */
+  int64_t schur_entries;    /* stored S_K entries summed over the elements (m^2 each) */
+  int64_t slot_entries;     /* element trace entries summed over the elements (m each) */
 } hdg_sizes;
 
 typedef struct {
@@ -190,11 +192,15 @@ hdg_status hdg_stream_destroy(void* stream);
 hdg_status hdg_reset_column(hdg_ctx* ctx, int32_t j);
 
 /* Physical coordinates of the projection quadrature points: which = 0 volume
- * ([n_elem][nq_vol][dim]), which = 1 boundary faces in face order ([n_bnd][nq_face][dim]). */
+ * ([n_elem][nq_vol][dim]), which = 1 boundary faces in face order ([n_bnd][nq_face][dim]).
+ * With per-element degrees (which = 0 only): element K has its own rule of (k_K + 2)^dim
+ * points and the elements' points are concatenated in element order. */
 hdg_status hdg_quadrature_points(hdg_ctx* ctx, int32_t which, double* xyz_host);
 
-/* Element-wise L2 projection of point values vals_host [n_elem][nq_vol][d+1] (p, v) at
- * the volume quadrature points into u_dev [n_elem][n]. */
+/* Element-wise L2 projection of point values vals_host [n_elem][nq_vol][ncomp] at the
+ * volume quadrature points into u_dev [n_elem][n] (ncomp = d + 1 acoustic (p, v), d + d(d+1)/2
+ * elastic (v, sigma)); with per-element degrees vals_host is [total points][ncomp] in the order
+ * of hdg_quadrature_points and u_dev the flat field array. */
 hdg_status hdg_project_volume(hdg_ctx* ctx, const double* vals_host, double* u_dev);
 
 /* Dirichlet trace p_hat = g(x) cos(omega t + phase) on all boundary faces; vals_host

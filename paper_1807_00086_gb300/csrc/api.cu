@@ -759,6 +759,9 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   }
   if (elem_k && (mat->phys != HDG_ELASTIC || mesh->dim != 3))
     return fail(c, HDG_EINVAL, "per-element degrees: 3D elastic meshes only");
+  if (elem_k && c->opt.nrhs != 1) return fail(c, HDG_EINVAL, "per-element degrees: nrhs = 1 only");
+  for (int64_t e = 0; elem_k && e < mesh->n_elem; ++e)
+    if (elem_k[e] < 1 || elem_k[e] > 4) return fail(c, HDG_EINVAL, "per-element degree must be in 1..4");
   if (!build_skeleton(mesh->dim, mesh->n_vert, mesh->n_elem, mesh->vert, mesh->elem_vert, c->sk, err))
     return fail(c, HDG_EINVAL, err);
   for (int64_t e = 0; e < mesh->n_elem; ++e) {
@@ -837,6 +840,8 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   }
   c->nfld = ne * (int64_t)c->n;
   c->ntr = nf * (int64_t)c->Nf;
+  c->nschur = ne * (int64_t)c->m * c->m;
+  c->nslot = ne * (int64_t)c->m;
   // reference tables packed in one buffer
   std::vector<double> tab;
   size_t off[6];
@@ -958,6 +963,8 @@ hdg_status hdg_get_sizes(const hdg_ctx* c, hdg_sizes* o) {
   o->device_bytes = c->bytes;
   o->field_entries = c->nfld;
   o->trace_entries = c->ntr;
+  o->schur_entries = c->nschur;
+  o->slot_entries = c->nslot;
   return HDG_OK;
 }
 
@@ -1102,8 +1109,8 @@ hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const do
 }
 
 hdg_status hdg_quadrature_points(hdg_ctx* c, int32_t which, double* xyz) {
-  if (c && c->vd) return fail(c, HDG_EINVAL, "not available with per-element degrees");
   if (!c || !xyz || (which != 0 && which != 1)) return fail(c, HDG_EINVAL, "bad arguments");
+  if (c->vd) return vd_quadrature_points(c, which, xyz);
   const int d = c->dim, nc = c->nfc;
   if (which == 0) {
     const int nq = c->T.nqv;
@@ -1138,8 +1145,8 @@ hdg_status hdg_quadrature_points(hdg_ctx* c, int32_t which, double* xyz) {
 }
 
 hdg_status hdg_project_volume(hdg_ctx* c, const double* vals, double* u) {
-  if (c && c->vd) return fail(c, HDG_EINVAL, "not available with per-element degrees");
   if (!c || !vals || !u) return fail(c, HDG_EINVAL, "null argument");
+  if (c->vd) return vd_project_volume(c, vals, u);
   const size_t cnt = (size_t)c->sk.ne * c->T.nqv * c->ncomp;
   double* dv = nullptr;
   hdg_status s;

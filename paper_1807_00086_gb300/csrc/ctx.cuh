@@ -108,6 +108,7 @@ struct hdg_ctx {
   // entries of one field / trace column (n N_e and N_f N_faces for one degree; sums of the
   // per-element / per-face sizes on a variable-degree mesh)
   int64_t nfld = 0, ntr = 0;
+  int64_t nschur = 0, nslot = 0;   // S_K entries and element trace entries summed over the elements
   VarDeg* vd = nullptr;
 };
 
@@ -237,4 +238,6 @@ hdg_status vd_trace_apply(hdg_ctx* c, const double* x, double* y);
 hdg_status vd_condensed_rhs(hdg_ctx* c, const double* F, const double* lamD, double* r);
 hdg_status vd_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_info* info);
 hdg_status vd_recover(hdg_ctx* c, const double* F, const double* lam, double* u);
+hdg_status vd_quadrature_points(hdg_ctx* c, int32_t which, double* xyz);
+hdg_status vd_project_volume(hdg_ctx* c, const double* vals, double* u);
 void vd_destroy(hdg_ctx* c);

@@ -28,6 +28,14 @@ struct VarDeg {
   int64_t scr_blocks = 0;
   int64_t m_tot = 0, s_tot = 0, h_tot = 0;
   float* d_S32 = nullptr;
+  // per-degree volume rules (initial-data projection) and per-element degree / point offsets
+  std::vector<RefTables> rule;        // index k = 1..4
+  std::vector<int32_t> ek;
+  std::vector<int64_t> q_off;
+  int32_t* d_ek = nullptr;
+  int64_t* d_q_off = nullptr;
+  double* d_qtab = nullptr;
+  VdQuad quad{};
 };
 
 namespace {
@@ -290,6 +298,8 @@ hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k) {
   }
   c->nfld = u_off[ne];
   v->m_tot = m_off[ne]; v->s_tot = s_off[ne]; v->h_tot = h_off[ne];
+  c->nschur = v->s_tot;
+  c->nslot = v->m_tot;
   // compact local entries: faces in local order, components, active modes in the padded order
   std::vector<std::vector<int>> mdeg(5);
   for (int k = 1; k <= 4; ++k) mdeg[k] = face_mode_degrees(dim, k);
@@ -382,6 +392,32 @@ hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k) {
   CUDA_TRY(c, up(v->d_pidx, pidx.data(), pidx.size() * 2));
   CUDA_TRY(c, up(v->d_sdiag, sdiag.data(), sdiag.size() * 8));
   CUDA_TRY(c, up(v->d_dslot, dslot.data(), dslot.size() * 4));
+  // volume rules of each degree and per-element point offsets (initial-data projection)
+  v->rule.resize(5);
+  std::vector<double> qtab;
+  size_t qw_off[5] = {0}, qp_off[5] = {0};
+  for (int k = 1; k <= 4; ++k) {
+    v->rule[k] = build_tables(dim, k);
+    qw_off[k] = qtab.size();
+    qtab.insert(qtab.end(), v->rule[k].qv_w.begin(), v->rule[k].qv_w.end());
+    qp_off[k] = qtab.size();
+    qtab.insert(qtab.end(), v->rule[k].qv_phi.begin(), v->rule[k].qv_phi.end());
+    v->quad.nq[k] = v->rule[k].nqv;
+    v->quad.np[k] = v->rule[k].Np;
+  }
+  v->ek.assign(elem_k, elem_k + ne);
+  v->q_off.assign(ne + 1, 0);
+  for (int64_t e = 0; e < ne; ++e) v->q_off[e + 1] = v->q_off[e] + v->rule[elem_k[e]].nqv;
+  if ((s = dalloc(c, &v->d_qtab, qtab.size()))) return s;
+  if ((s = dalloc(c, &v->d_ek, (size_t)ne))) return s;
+  if ((s = dalloc(c, &v->d_q_off, (size_t)ne + 1))) return s;
+  for (int k = 1; k <= 4; ++k) {
+    v->quad.qw[k] = v->d_qtab + qw_off[k];
+    v->quad.qphi[k] = v->d_qtab + qp_off[k];
+  }
+  CUDA_TRY(c, up(v->d_qtab, qtab.data(), qtab.size() * 8));
+  CUDA_TRY(c, up(v->d_ek, v->ek.data(), v->ek.size() * 4));
+  CUDA_TRY(c, up(v->d_q_off, v->q_off.data(), v->q_off.size() * 8));
   // operators and workspaces
   const size_t ntr = (size_t)c->ntr, nfld = (size_t)c->nfld;
   {
@@ -483,6 +519,43 @@ hdg_status vd_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_in
 hdg_status vd_recover(hdg_ctx* c, const double* F, const double* lam, double* u) {
   vd_local(c, 1, F, nullptr, lam, u);
   return check_launch(c, "vd_recover");
+}
+
+hdg_status vd_quadrature_points(hdg_ctx* c, int32_t which, double* xyz) {
+  if (which != 0) return fail(c, HDG_EINVAL, "per-element degrees: clamped boundary, no face points");
+  const int d = c->dim, nc = c->nfc;
+  const VarDeg* v = c->vd;
+  for (int64_t e = 0; e < c->sk.ne; ++e) {
+    const RefTables& T = v->rule[v->ek[e]];
+    const double* X = &c->h_vert_elem[(size_t)e * nc * d];
+    for (int q = 0; q < T.nqv; ++q)
+      for (int j = 0; j < d; ++j) {
+        double val = X[j];
+        for (int r = 0; r < d; ++r) val += T.qv_pts[(size_t)q * d + r] * (X[(r + 1) * d + j] - X[j]);
+        xyz[((size_t)v->q_off[e] + q) * d + j] = val;
+      }
+  }
+  return HDG_OK;
+}
+
+hdg_status vd_project_volume(hdg_ctx* c, const double* vals, double* u) {
+  VarDeg* v = c->vd;
+  const size_t cnt = (size_t)v->q_off[c->sk.ne] * c->ncomp;
+  double* dv = nullptr;
+  hdg_status s;
+  if ((s = dalloc(c, &dv, cnt))) return s;
+  cudaError_t e1 = cudaMemcpyAsync(dv, vals, cnt * 8, cudaMemcpyHostToDevice, c->stream);
+  if (e1 == cudaSuccess) {
+    c->n_launch += 1;
+    project_vd_kernel<<<grid_for(c, c->sk.ne * 128, 128), 128, 0, c->stream>>>(c->sk.ne, c->ncomp, v->d_ek, v->d_q_off,
+                                                                               v->d_u_off, v->quad, dv, u);
+    e1 = cudaGetLastError();
+  }
+  if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(c->stream);
+  dfree(c, dv);
+  c->bytes -= (int64_t)(cnt * 8);
+  if (e1 != cudaSuccess) return fail(c, HDG_ECUDA, std::string("project_volume: ") + cudaGetErrorString(e1));
+  return HDG_OK;
 }
 
 void vd_destroy(hdg_ctx* c) {

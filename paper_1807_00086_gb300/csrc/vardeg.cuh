@@ -405,6 +405,32 @@ __global__ void __launch_bounds__(128) apply_vd_kernel(int64_t ne, const int64_t
   }
 }
 
+// L2 projection of point values at each element's own volume rule (degree k_K, (k_K + 2)^3
+// points): u_K[c][i] = sum_q w_q vals[q][c] phi_i(xi_q) (orthonormal basis: the mass |J| I
+// cancels |J| in the load). Block per element; tables per degree at qw[k], qphi[k].
+struct VdQuad {
+  const double* qw[5];
+  const double* qphi[5];
+  int nq[5], np[5];
+};
+
+static __global__ void project_vd_kernel(int64_t ne, int ncomp, const int32_t* __restrict__ ek,
+                                         const int64_t* __restrict__ q_off, const int64_t* __restrict__ u_off,
+                                         VdQuad Q, const double* __restrict__ vals, double* __restrict__ u) {
+  for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+    const int k = ek[e], nq = Q.nq[k], np = Q.np[k];
+    const double* w = Q.qw[k];
+    const double* phi = Q.qphi[k];
+    const double* v = vals + q_off[e] * ncomp;
+    for (int t = threadIdx.x; t < ncomp * np; t += blockDim.x) {
+      const int c = t / np, i = t % np;
+      double s = 0.0;
+      for (int q = 0; q < nq; ++q) s += w[q] * v[q * ncomp + c] * phi[q * np + i];
+      u[u_off[e] + t] = s;
+    }
+  }
+}
+
 // ---- trace-entry passes through the slot map (generic over the per-face size)
 template <typename TV>
 __device__ __forceinline__ TV vd_sum(const int32_t* __restrict__ dslot, const TV* __restrict__ slot, int64_t d) {

@@ -42,7 +42,7 @@ class Sizes(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("k", c_int32), ("Np", c_int32), ("Nf", c_int32), ("n_local", c_int32),
                 ("n_trace_local", c_int32), ("n_elem", c_int64), ("n_faces", c_int64), ("n_bnd_faces", c_int64),
                 ("nq_vol", c_int32), ("nq_face", c_int32), ("device_bytes", c_int64), ("field_entries", c_int64),
-                ("trace_entries", c_int64)]
+                ("trace_entries", c_int64), ("schur_entries", c_int64), ("slot_entries", c_int64)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -277,7 +277,18 @@ class Solver:
     def hdg_reset_column(self, j):
         self._check(self.lib.hdg_reset_column(self.ctx, j))
 
+    def vol_points_per_element(self):
+        """Volume quadrature points of each element ((k_K + 2)^dim with per-element degrees)."""
+        if self.vardeg:
+            return (self._ek.astype(np.int64) + 2) ** self.dim if self._ek is not None else \
+                np.full(self.n_elem, (self.k + 2) ** self.dim)
+        return np.full(self.n_elem, self.sizes.nq_vol)
+
     def hdg_quadrature_points(self, which):
+        if self.vardeg and which == 0:
+            out = np.zeros((int(self.vol_points_per_element().sum()), self.dim))
+            self._check(self.lib.hdg_quadrature_points(self.ctx, which, _np_ptr(out, c_double)))
+            return out
         nq = self.sizes.nq_vol if which == 0 else self.sizes.nq_face
         cnt = self.n_elem if which == 0 else self.n_bnd
         out = np.zeros((cnt, nq, self.dim))
@@ -286,7 +297,11 @@ class Solver:
 
     def hdg_project_volume(self, vals, u=None):
         vals = np.ascontiguousarray(vals, dtype=np.float64)
-        assert vals.shape == (self.n_elem, self.sizes.nq_vol, self.n // self.Np)
+        ncomp = (self.dim + self.dim * (self.dim + 1) // 2) if self.elastic else self.dim + 1
+        if self.vardeg:
+            assert vals.shape == (int(self.vol_points_per_element().sum()), ncomp)
+        else:
+            assert vals.shape == (self.n_elem, self.sizes.nq_vol, ncomp)
         u = self.empty_fields() if u is None else u
         self._check(self.lib.hdg_project_volume(self.ctx, _np_ptr(vals, c_double), self._dev(u, self._fshape)))
         return u

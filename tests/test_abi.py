@@ -84,9 +84,19 @@ def test_setup_rejects_unsupported_elastic_configurations_on_host(libpath):
     mat = hdg.Material(1, one.ctypes.data_as(hdg.P_double), None, one.ctypes.data_as(hdg.P_double),
                        one.ctypes.data_as(hdg.P_double))
     ctx = ctypes.c_void_p()
+    # per-element degrees: each in 1..4, 3D elastic only
+    ks = np.full(ne, 2, dtype=np.int32)
+    ks[3] = 5
+    mesh.elem_k = ks.ctypes.data_as(hdg.P_int32)
     st = lib.hdg_setup(ctypes.byref(mesh), 4, 1.0, ctypes.byref(mat), None, None, ctypes.byref(ctx))
-    assert st == -1 and b"1 <= k <= 3" in lib.hdg_last_error(ctx)
+    assert st == -1 and b"1..4" in lib.hdg_last_error(ctx)
     lib.hdg_destroy(ctx)
+    ks[3] = 1
+    amat = hdg.Material(0, one.ctypes.data_as(hdg.P_double), one.ctypes.data_as(hdg.P_double), None, None)
+    st = lib.hdg_setup(ctypes.byref(mesh), 2, 1.0, ctypes.byref(amat), None, None, ctypes.byref(ctx))
+    assert st == -1 and b"3D elastic" in lib.hdg_last_error(ctx)
+    lib.hdg_destroy(ctx)
+    mesh.elem_k = None
     bad = -np.ones(ne)
     mat.mu = bad.ctypes.data_as(hdg.P_double)
     st = lib.hdg_setup(ctypes.byref(mesh), 2, 1.0, ctypes.byref(mat), None, None, ctypes.byref(ctx))
