@@ -343,8 +343,10 @@ def run_ours(args):
 
     # the plain FP64 GPU path on the same workload and steps, for the mixed-vs-FP64 comparison
     fp64 = None
+    tiles = s.hdg_get_tuning() if vardeg else None
     if args.prec != "fp64" and not args.no_fp64_compare:
         u_mixed = s.hdg_get_state()[0]
+        tiles = s.hdg_get_tuning() if vardeg else None
         s.close()
         torch.cuda.empty_cache()
         s64 = make_solver("fp64")
@@ -384,6 +386,12 @@ def run_ours(args):
                     "fp64_refinement_apply": {"launch_ms": apply_avg_ms, "launches": st["apply_launches"],
                                               "achieved_tflops": 2 * nschur / (apply_avg_ms / 1e3) / 1e12
                                               if st["apply_launches"] else None}}
+            if st.get("applydf_launches"):
+                adf = st["applydf_ms"] / st["applydf_launches"]
+                roof["df_refinement_apply"] = {
+                    "kernel": "apply_vd_df_kernel (double-float hi + lo compact S_K)", "launches": st["applydf_launches"],
+                    "launch_ms": adf, "bytes_per_launch": nschur * 8 + nslot * 16,
+                    "achieved_gbs": (nschur * 8 + nslot * 16) / (adf / 1e3) / 1e9}
         else:
             ach = 2 * nschur / (apply_avg_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
@@ -422,6 +430,8 @@ def run_ours(args):
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * field_bytes + trace_bytes,
                        "d2h_bytes_per_step": 2 * field_bytes + trace_bytes, "steps": e2e_steps},
                "gpu_launches": st["kernel_launches"], "clocks": clk}
+        if vardeg:
+            out["config"]["autotuned_tiles"] = tiles
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -254,6 +254,24 @@ hdg_status hdg_trace_apply_noalloc(int32_t dim, int32_t k, int64_t n_elem, int64
                                    const int32_t* face_bnd_dev, const double* x_dev, double* y_dev,
                                    void* cuda_stream, char* err, int32_t err_len);
 
+/* Tiles of the per-element-degree (elastic, elem_k) kernels, chosen by the library's
+ * autotuner on the context's own data: at the first hdg_condense it times each candidate tile
+ * of the matrix-free apply (warps per block in {4, 8} x columns in flight in {4, 8, 16}) on
+ * the condensed operator: apply64 is the FP64-accurate apply (the FP64 kernel, or with mixed
+ * precision the double-float refinement-residual kernel), apply32 the FP32 inner apply
+ * (mixed precision). At the first local solve of
+ * each kind it times the block size of the one-launch element-local solve (64, 128 or 256
+ * threads per element). tuned = 0 before the first condensation; local_threads are 0 until
+ * the first condensed right-hand side (index 0) / recovery (index 1). HDG_EINVAL for a
+ * context without per-element degrees. */
+typedef struct {
+  int32_t tuned;
+  int32_t apply32_warps, apply32_unroll;
+  int32_t apply64_warps, apply64_unroll;
+  int32_t local_threads[2];
+} hdg_tuning;
+hdg_status hdg_get_tuning(const hdg_ctx* ctx, hdg_tuning* out);
+
 /* Instrumentation (not part of the method). When enabled, the context counts its kernel
  * launches and times every launch of the matrix-free trace apply with CUDA events on the
  * context stream; hdg_get_stats returns the totals since the last reset. */

@@ -1336,6 +1336,12 @@ hdg_status hdg_reset_column(hdg_ctx* c, int32_t j) {
   return check_launch(c, "reset_column");
 }
 
+hdg_status hdg_get_tuning(const hdg_ctx* c, hdg_tuning* out) {
+  if (!c || !out) return HDG_EINVAL;
+  if (!c->vd) return HDG_EINVAL;
+  return vd_get_tuning(c, out);
+}
+
 hdg_status hdg_enable_stats(hdg_ctx* c, int32_t enable) {
   if (!c) return HDG_EINVAL;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));

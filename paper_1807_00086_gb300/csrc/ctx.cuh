@@ -240,4 +240,5 @@ hdg_status vd_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_in
 hdg_status vd_recover(hdg_ctx* c, const double* F, const double* lam, double* u);
 hdg_status vd_quadrature_points(hdg_ctx* c, int32_t which, double* xyz);
 hdg_status vd_project_volume(hdg_ctx* c, const double* vals, double* u);
+hdg_status vd_get_tuning(const hdg_ctx* c, hdg_tuning* out);
 void vd_destroy(hdg_ctx* c);

@@ -28,6 +28,7 @@ struct VarDeg {
   int64_t scr_blocks = 0;
   int64_t m_tot = 0, s_tot = 0, h_tot = 0;
   float* d_S32 = nullptr;
+  float* d_S32lo = nullptr;       // remainder of S_K beyond its FP32 copy (double-float residual apply)
   // per-degree volume rules (initial-data projection) and per-element degree / point offsets
   std::vector<RefTables> rule;        // index k = 1..4
   std::vector<int32_t> ek;
@@ -36,6 +37,11 @@ struct VarDeg {
   int64_t* d_q_off = nullptr;
   double* d_qtab = nullptr;
   VdQuad quad{};
+  // one-launch local solves and the autotuned tiles
+  VdClassTable table{};
+  size_t local_smem = 0;
+  int tile32 = -1, tile64 = -1, tiledf = -1;   // index into kApplyTiles (-1: not tuned yet)
+  int local_nth[2] = {0, 0};      // threads per element of the MODE 0 / MODE 1 launch (0: not tuned)
 };
 
 namespace {
@@ -70,6 +76,11 @@ VdIndex vd_index(const hdg_ctx* c, const VarDeg::Cls& k) {
   }
 
 template <int K, int KT>
+void vd_local_smem(size_t& s) {
+  s = std::max(s, sizeof(double) * (size_t)LocalVdSmem<3, K, KT>::TOTAL);
+}
+
+template <int K, int KT>
 void vd_launch_condense(hdg_ctx* c, const VarDeg::Cls& k) {
   using C = CondVdCfg<3, K, KT>;
   cudaFuncSetAttribute(condense_vd_kernel<3, K, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
@@ -86,37 +97,140 @@ void vd_launch_condense(hdg_ctx* c, const VarDeg::Cls& k) {
   }
 }
 
-template <int K, int KT>
-void vd_launch_local(hdg_ctx* c, const VarDeg::Cls& k, int mode, const double* F, const double* hist,
-                     const double* lam, double* out) {
-  c->n_launch += 1;
-  if (mode == 0)
-    local_vd_kernel<3, K, KT, 0><<<(unsigned)k.count, 128, 0, c->stream>>>(devmesh(c), k.tabs, c->d_lame, c->d_mue,
-                                                                          c->d_Hinv, c->alpha, vd_index(c, k), F, hist,
-                                                                          lam, out);
-  else
-    local_vd_kernel<3, K, KT, 1><<<(unsigned)k.count, 128, 0, c->stream>>>(devmesh(c), k.tabs, c->d_lame, c->d_mue,
-                                                                          c->d_Hinv, c->alpha, vd_index(c, k), F, hist,
-                                                                          lam, out);
+constexpr int kApplyTiles[6][2] = {{4, 4}, {4, 8}, {4, 16}, {8, 4}, {8, 8}, {8, 16}};   // (warps, unroll)
+constexpr int kLocalThreads[3] = {64, 128, 256};
+
+template <typename TV, int WPB, int UNR>
+void vd_apply_tile(hdg_ctx* c, const TV* S, const TV* x, TV* slot, const int* done) {
+  apply_vd_kernel<TV, VD_MMAX, WPB, UNR><<<(unsigned)((c->sk.ne + WPB - 1) / WPB), 32 * WPB, 0, c->stream>>>(
+      c->sk.ne, c->vd->d_s_off, c->vd->d_m_off, c->vd->d_gint, S, x, slot, done);
 }
 
+template <typename TV>
+void vd_apply_variant(hdg_ctx* c, int tile, const TV* S, const TV* x, TV* slot, const int* done) {
+  switch (tile) {
+    case 0: vd_apply_tile<TV, 4, 4>(c, S, x, slot, done); break;
+    case 1: vd_apply_tile<TV, 4, 8>(c, S, x, slot, done); break;
+    case 2: vd_apply_tile<TV, 4, 16>(c, S, x, slot, done); break;
+    case 3: vd_apply_tile<TV, 8, 4>(c, S, x, slot, done); break;
+    case 4: vd_apply_tile<TV, 8, 8>(c, S, x, slot, done); break;
+    default: vd_apply_tile<TV, 8, 16>(c, S, x, slot, done); break;
+  }
+}
+
+template <int WPB, int UNR>
+void vd_apply_df_tile(hdg_ctx* c, const double* x, double* slot) {
+  apply_vd_df_kernel<VD_MMAX, WPB, UNR><<<(unsigned)((c->sk.ne + WPB - 1) / WPB), 32 * WPB, 0, c->stream>>>(
+      c->sk.ne, c->vd->d_s_off, c->vd->d_m_off, c->vd->d_gint, c->vd->d_S32, c->vd->d_S32lo, x, slot);
+}
+
+void vd_apply_df_variant(hdg_ctx* c, int tile, const double* x, double* slot) {
+  switch (tile) {
+    case 0: vd_apply_df_tile<4, 4>(c, x, slot); break;
+    case 1: vd_apply_df_tile<4, 8>(c, x, slot); break;
+    case 2: vd_apply_df_tile<4, 16>(c, x, slot); break;
+    case 3: vd_apply_df_tile<8, 4>(c, x, slot); break;
+    case 4: vd_apply_df_tile<8, 8>(c, x, slot); break;
+    default: vd_apply_df_tile<8, 16>(c, x, slot); break;
+  }
+}
+
+// Autotuner: times every candidate tile (run(t) launches candidate t) on the context's own
+// operator (the slot output is a workspace that the next use overwrites) and keeps the
+// fastest; 3 timed launches each after one untimed launch.
+template <typename RUN>
+int vd_tune(hdg_ctx* c, RUN run) {
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return 1;
+  if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return 1; }
+  int best = 1;
+  float best_ms = 1e30f;
+  for (int t = 0; t < 6; ++t) {
+    run(t);
+    cudaEventRecord(a, c->stream);
+    for (int r = 0; r < 3; ++r) run(t);
+    cudaEventRecord(b, c->stream);
+    float ms = 0.f;
+    if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  c->n_launch += 24;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+template <int MODE>
+void vd_local_launch(hdg_ctx* c, int nth, const double* F, const double* hist, const double* lam, double* out) {
+  const VarDeg* v = c->vd;
+  const VdIndex X{v->d_elist, v->d_u_off, v->d_h_off, v->d_s_off, v->d_m_off, v->d_gidx, v->d_pidx};
+  const unsigned grid = (unsigned)c->sk.ne;
+  c->n_launch += 1;
+  if (nth == 64)
+    local_vd_all_kernel<MODE, 64><<<grid, 64, v->local_smem, c->stream>>>(devmesh(c), v->table, c->d_lame, c->d_mue,
+                                                                          c->d_Hinv, c->alpha, X, F, hist, lam, out);
+  else if (nth == 128)
+    local_vd_all_kernel<MODE, 128><<<grid, 128, v->local_smem, c->stream>>>(devmesh(c), v->table, c->d_lame, c->d_mue,
+                                                                            c->d_Hinv, c->alpha, X, F, hist, lam, out);
+  else
+    local_vd_all_kernel<MODE, 256><<<grid, 256, v->local_smem, c->stream>>>(devmesh(c), v->table, c->d_lame, c->d_mue,
+                                                                            c->d_Hinv, c->alpha, X, F, hist, lam, out);
+}
+
+// The element-local solves of every class in one launch. The first call of each mode times
+// the block sizes on the live inputs (each candidate writes the same output) and keeps the
+// fastest.
 void vd_local(hdg_ctx* c, int mode, const double* F, const double* hist, const double* lam, double* out) {
-  for (const auto& k : c->vd->cls) VD_DISPATCH(k.K, k.KT, vd_launch_local, c, k, mode, F, hist, lam, out);
+  VarDeg* v = c->vd;
+  auto run = [&](int nth) {
+    if (mode == 0) vd_local_launch<0>(c, nth, F, hist, lam, out);
+    else vd_local_launch<1>(c, nth, F, hist, lam, out);
+  };
+  if (v->local_nth[mode] == 0) {
+    cudaEvent_t a, b;
+    int best = 128;
+    float best_ms = 1e30f;
+    if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
+      for (int nth : kLocalThreads) {
+        run(nth);   // untimed first launch
+        cudaEventRecord(a, c->stream);
+        run(nth);
+        cudaEventRecord(b, c->stream);
+        float ms = 0.f;
+        if (cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best = nth;
+        }
+      }
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+    v->local_nth[mode] = best;
+  }
+  run(v->local_nth[mode]);
 }
 
 void vd_apply64(hdg_ctx* c, const double* x, double* slot, const int* done, int iter) {
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 0, iter);
-  apply_vd_kernel<double, VD_MMAX><<<(unsigned)((c->sk.ne + 3) / 4), 128, 0, c->stream>>>(
-      c->sk.ne, c->vd->d_s_off, c->vd->d_m_off, c->vd->d_gint, c->d_S, x, slot, done);
+  vd_apply_variant<double>(c, c->vd->tile64 < 0 ? 1 : c->vd->tile64, c->d_S, x, slot, done);
+  apply_end(c, stop);
+}
+
+// FP64-accurate residual apply of the mixed path (double-float on the FP32 pipe)
+void vd_apply_df(hdg_ctx* c, const double* x, double* slot) {
+  c->n_launch += 1;
+  cudaEvent_t stop = apply_begin(c, 2, -1);
+  vd_apply_df_variant(c, c->vd->tiledf < 0 ? 1 : c->vd->tiledf, x, slot);
   apply_end(c, stop);
 }
 
 void vd_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, int iter) {
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 1, iter);
-  apply_vd_kernel<float, VD_MMAX><<<(unsigned)((c->sk.ne + 3) / 4), 128, 0, c->stream>>>(
-      c->sk.ne, c->vd->d_s_off, c->vd->d_m_off, c->vd->d_gint, c->vd->d_S32, x, slot, done);
+  vd_apply_variant<float>(c, c->vd->tile32 < 0 ? 1 : c->vd->tile32, c->vd->d_S32, x, slot, done);
   apply_end(c, stop);
 }
 
@@ -219,7 +333,7 @@ hdg_status vd_refine(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* 
   double rel = 0.0;
   hdg_status s;
   for (int sweep = 0;; ++sweep) {
-    vd_apply64(c, x, c->d_slot, nullptr, -1);
+    vd_apply_df(c, x, c->d_slot);
     c->n_launch += 2;
     vd_refine_residual_kernel<<<nb, 256, 0, c->stream>>>(n, c->sgn, c->vd->d_dslot, c->d_slot, bvec, c->d_res,
                                                          c->d_part);
@@ -338,7 +452,9 @@ hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k) {
   std::vector<int32_t> elist;
   std::vector<double> tab;
   std::vector<std::array<size_t, 6>> toff;
-  for (auto& g : groups) {
+  // heaviest classes first (descending 10 K + KT): the one-launch local solves start them first
+  for (auto it = groups.rbegin(); it != groups.rend(); ++it) {
+    auto& g = *it;
     VarDeg::Cls k;
     k.K = g.first / 10; k.KT = g.first % 10;
     k.first = (int64_t)elist.size(); k.count = (int64_t)g.second.size();
@@ -362,6 +478,14 @@ hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k) {
     T.Dr = v->d_tab + toff[i][0]; T.Ff = v->d_tab + toff[i][1]; T.Ef = v->d_tab + toff[i][2];
     T.Trs = v->d_tab + toff[i][3]; T.DFrf = v->d_tab + toff[i][4]; T.Pfg = v->d_tab + toff[i][5];
   }
+  v->table.n = (int)v->cls.size();
+  for (size_t i = 0; i < v->cls.size(); ++i) {
+    v->table.start[i] = v->cls[i].first;
+    v->table.key[i] = v->cls[i].K * 10 + v->cls[i].KT;
+    v->table.tabs[i] = v->cls[i].tabs;
+    VD_DISPATCH(v->cls[i].K, v->cls[i].KT, vd_local_smem, v->local_smem);
+  }
+  v->table.start[v->cls.size()] = ne;
   // scratch of the classes whose H does not fit shared memory
   v->scr_blocks = 0;
   size_t scr = 0;
@@ -441,6 +565,7 @@ hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k) {
     if ((s = dalloc(c, p, nfld))) return s;
   if (c->opt.prec != HDG_FP64) {
     if ((s = dalloc(c, &v->d_S32, (size_t)v->s_tot))) return s;
+    if ((s = dalloc(c, &v->d_S32lo, (size_t)v->s_tot))) return s;
     if ((s = dalloc(c, &c->d_slot32, (size_t)v->m_tot))) return s;
     c->nfe4 = (int64_t)((ntr + 3) / 4) * 4;
     for (float** p : {&c->d_dinv32, &c->d_r32, &c->d_z32, &c->d_p32, &c->d_q32, &c->d_x32, &c->d_b32}) {
@@ -473,9 +598,22 @@ hdg_status vd_condense(hdg_ctx* c, double alpha) {
   if (c->opt.prec != HDG_FP64) {
     c->n_launch += 2;
     to32_copy_kernel<<<grid_for(c, c->vd->s_tot), 256, 0, c->stream>>>(c->vd->s_tot, c->d_S, c->vd->d_S32);
+    c->n_launch += 1;
+    lo32_kernel<<<grid_for(c, c->vd->s_tot), 256, 0, c->stream>>>(c->vd->s_tot, c->d_S, c->vd->d_S32, c->vd->d_S32lo);
     to32_kernel<<<grid_for(c, c->ntr), 256, 0, c->stream>>>(c->ntr, c->d_dinv, c->d_dinv32);
   }
   if ((s = check_launch(c, "vd_diag"))) return s;
+  // tiles of the applies, tuned once per context on its own operator
+  VarDeg* v = c->vd;
+  if (c->opt.prec == HDG_FP64) {
+    if (v->tile64 < 0)
+      v->tile64 = vd_tune(c, [&](int t) { vd_apply_variant<double>(c, t, c->d_S, c->d_lam, c->d_slot, nullptr); });
+  } else {
+    if (v->tile32 < 0)
+      v->tile32 = vd_tune(c, [&](int t) { vd_apply_variant<float>(c, t, v->d_S32, c->d_p32, c->d_slot32, nullptr); });
+    if (v->tiledf < 0) v->tiledf = vd_tune(c, [&](int t) { vd_apply_df_variant(c, t, c->d_lam, c->d_slot); });
+  }
+  if ((s = check_launch(c, "vd_tune"))) return s;
   int herr = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -555,6 +693,22 @@ hdg_status vd_project_volume(hdg_ctx* c, const double* vals, double* u) {
   dfree(c, dv);
   c->bytes -= (int64_t)(cnt * 8);
   if (e1 != cudaSuccess) return fail(c, HDG_ECUDA, std::string("project_volume: ") + cudaGetErrorString(e1));
+  return HDG_OK;
+}
+
+hdg_status vd_get_tuning(const hdg_ctx* c, hdg_tuning* o) {
+  const VarDeg* v = c->vd;
+  // the FP64-accurate apply is the FP64 kernel on the plain path and the double-float kernel
+  // (residual of the refinement) on the mixed path
+  const int tr = c->opt.prec == HDG_FP64 ? v->tile64 : v->tiledf;
+  o->tuned = tr >= 0 ? 1 : 0;
+  const int t32 = v->tile32 < 0 ? 1 : v->tile32, t64 = tr < 0 ? 1 : tr;
+  o->apply32_warps = kApplyTiles[t32][0];
+  o->apply32_unroll = kApplyTiles[t32][1];
+  o->apply64_warps = kApplyTiles[t64][0];
+  o->apply64_unroll = kApplyTiles[t64][1];
+  o->local_threads[0] = v->local_nth[0];
+  o->local_threads[1] = v->local_nth[1];
   return HDG_OK;
 }
 

@@ -205,26 +205,35 @@ __global__ void __launch_bounds__(256) condense_vd_kernel(DevMesh mesh, Tabs T, 
   }
 }
 
-// Element-local solves of one class. MODE 0: out[m_off[e] + a] = (C_K A_K^{-1}(F_K - B_K lamD_K))
-// at the compact entries; MODE 1: out[u_off[e] ..] = A_K^{-1}(F_K - B_K lam_K). F_K = F[u_off[e] ..]
-// or alpha Mw_K hist[u_off[e] ..].
-template <int DIM, int K, int KT, int MODE>
-__global__ void __launch_bounds__(128) local_vd_kernel(DevMesh mesh, Tabs T, const double* __restrict__ lamv,
-                                                        const double* __restrict__ muv, const double* __restrict__ Hinv,
-                                                        double alpha, VdIndex X, const double* __restrict__ F,
-                                                        const double* __restrict__ hist, const double* __restrict__ lamt,
-                                                        double* __restrict__ out) {
+// Shared workspace of one element of class (K, KT) in the local solves (offsets in doubles).
+template <int DIM, int K, int KT>
+struct LocalVdSmem {
   using D = VdDims<DIM, K, KT>;
+  static constexpr int G = 0, LL = G + GEO_STRIDE, FL = LL + D::M, RV = FL + D::NFC * DIM * D::NP,
+                       RS = RV + D::NV, Y = RS + D::NT * D::NP, TT = Y + D::NT * D::NP,
+                       RHS = TT + DIM * DIM * D::NP, V = RHS + D::NV, Z = V + D::NV, W = Z + DIM * DIM * D::NP,
+                       SG = W + D::NT * D::NP, CM = SG + D::NT * D::NP, QM = CM + D::NT * D::NT,
+                       FUSE = QM + D::NT * D::NT, TOTAL = FUSE + 4;
+};
+
+// Element-local solves of one element of class (K, KT), NTH threads. MODE 0:
+// out[m_off[e] + a] = (C_K A_K^{-1}(F_K - B_K lamD_K)) at the compact entries; MODE 1:
+// out[u_off[e] ..] = A_K^{-1}(F_K - B_K lam_K). F_K = F[u_off[e] ..] or alpha Mw_K hist[u_off[e] ..].
+template <int DIM, int K, int KT, int MODE, int NTH>
+__device__ __forceinline__ void local_vd_body(const DevMesh& mesh, const Tabs& T, const double* __restrict__ lamv,
+                                              const double* __restrict__ muv, const double* __restrict__ Hinv,
+                                              double alpha, const VdIndex& X, int64_t e, const double* __restrict__ F,
+                                              const double* __restrict__ hist, const double* __restrict__ lamt,
+                                              double* __restrict__ out, double* sm) {
+  using D = VdDims<DIM, K, KT>;
+  using SM = LocalVdSmem<DIM, K, KT>;
   constexpr int NP = D::NP, NFP = D::NFP, NF = D::NF, NFC = D::NFC, NT = D::NT, NV = D::NV, M = D::M, N = D::N;
-  constexpr int NTH = 128;
-  __shared__ double g[GEO_STRIDE];
-  __shared__ double ll[M];
-  __shared__ int fuse[NFC];
-  __shared__ double Fl[NFC * DIM * NP];
-  __shared__ double rv[NV], rs[NT * NP], y[NT * NP], tt[DIM * DIM * NP], rhs[NV], v[NV], z[DIM * DIM * NP];
-  __shared__ double w[NT * NP], sg[NT * NP];
-  __shared__ double Cm[NT * NT], Qm[NT * NT];
-  const int64_t e = X.elist[blockIdx.x];
+  double* g = sm + SM::G;
+  double* ll = sm + SM::LL;
+  double* Fl = sm + SM::FL;
+  double *rv = sm + SM::RV, *rs = sm + SM::RS, *y = sm + SM::Y, *tt = sm + SM::TT, *rhs = sm + SM::RHS,
+         *v = sm + SM::V, *z = sm + SM::Z, *w = sm + SM::W, *sg = sm + SM::SG, *Cm = sm + SM::CM, *Qm = sm + SM::QM;
+  int* fuse = reinterpret_cast<int*>(sm + SM::FUSE);
   const int tid = threadIdx.x;
   const double rho = mesh.rho[e], lam = lamv[e], mu = muv[e];
   const double s = 2.0 * sqrt(rho * mu);
@@ -364,20 +373,62 @@ __global__ void __launch_bounds__(128) local_vd_kernel(DevMesh mesh, Tabs T, con
   }
 }
 
+// All classes of a variable-degree mesh in one launch: block b handles element elist[b]; the
+// element list is grouped by class, heaviest classes first, and the class ranges are
+// [start[c], start[c + 1]). The shared workspace is the largest class's (dynamic).
+struct VdClassTable {
+  int n;
+  int64_t start[11];
+  int key[10];     // 10 K + KT
+  Tabs tabs[10];
+};
+
+template <int MODE, int NTH>
+__global__ void __launch_bounds__(NTH) local_vd_all_kernel(DevMesh mesh, VdClassTable C, const double* __restrict__ lamv,
+                                                           const double* __restrict__ muv,
+                                                           const double* __restrict__ Hinv, double alpha, VdIndex X,
+                                                           const double* __restrict__ F, const double* __restrict__ hist,
+                                                           const double* __restrict__ lamt, double* __restrict__ out) {
+  extern __shared__ double sm[];
+  const int64_t b = blockIdx.x;
+  int c = 0;
+  while (c + 1 < C.n && b >= C.start[c + 1]) ++c;
+  const int64_t e = X.elist[b];
+#define HDG_VD_BODY(KK, KKT)                                                                                      \
+  case KK * 10 + KKT:                                                                                             \
+    local_vd_body<3, KK, KKT, MODE, NTH>(mesh, C.tabs[c], lamv, muv, Hinv, alpha, X, e, F, hist, lamt, out, sm); \
+    break;
+  switch (C.key[c]) {
+    HDG_VD_BODY(4, 4)
+    HDG_VD_BODY(3, 4)
+    HDG_VD_BODY(3, 3)
+    HDG_VD_BODY(2, 4)
+    HDG_VD_BODY(2, 3)
+    HDG_VD_BODY(2, 2)
+    HDG_VD_BODY(1, 4)
+    HDG_VD_BODY(1, 3)
+    HDG_VD_BODY(1, 2)
+    HDG_VD_BODY(1, 1)
+    default: break;
+  }
+#undef HDG_VD_BODY
+}
+
 // slot[m_off[e] + r] = sum_c S_e[r][c] x[gint[m_off[e] + c]] (boundary entries read as 0).
-// Warp per element, lane handles rows lane + 32 q; S_e is symmetric, so column r is read as
-// row r (coalesced). MMAX bounds m_e.
-template <typename TV, int MMAX>
-__global__ void __launch_bounds__(128) apply_vd_kernel(int64_t ne, const int64_t* __restrict__ s_off,
-                                                       const int32_t* __restrict__ m_off,
-                                                       const int32_t* __restrict__ gint, const TV* __restrict__ S,
-                                                       const TV* __restrict__ x, TV* __restrict__ slot,
-                                                       const int* __restrict__ done) {
+// Warp per element, WPB warps per block, lane handles rows lane + 32 q; S_e is symmetric, so
+// column r is read as row r (coalesced); UNR columns are in flight per step. MMAX bounds m_e.
+// (WPB, UNR) is the tile the autotuner picks per context.
+template <typename TV, int MMAX, int WPB, int UNR>
+__global__ void __launch_bounds__(32 * WPB) apply_vd_kernel(int64_t ne, const int64_t* __restrict__ s_off,
+                                                            const int32_t* __restrict__ m_off,
+                                                            const int32_t* __restrict__ gint, const TV* __restrict__ S,
+                                                            const TV* __restrict__ x, TV* __restrict__ slot,
+                                                            const int* __restrict__ done) {
   constexpr int RPL = (MMAX + 31) / 32;
-  __shared__ TV lx[4][MMAX];
+  __shared__ TV lx[WPB][MMAX];
   if (done && *done) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t e = (int64_t)blockIdx.x * 4 + w;
+  const int64_t e = (int64_t)blockIdx.x * WPB + w;
   if (e >= ne) return;
   const int m0 = m_off[e], me = m_off[e + 1] - m0;
   for (int c = lane; c < me; c += 32) {
@@ -389,7 +440,7 @@ __global__ void __launch_bounds__(128) apply_vd_kernel(int64_t ne, const int64_t
 #pragma unroll
   for (int q = 0; q < RPL; ++q) acc[q] = TV(0);
   const TV* Se = S + s_off[e];
-#pragma unroll 4
+#pragma unroll UNR
   for (int c = 0; c < me; ++c) {
     const TV xc = lx[w][c];
 #pragma unroll
@@ -403,6 +454,55 @@ __global__ void __launch_bounds__(128) apply_vd_kernel(int64_t ne, const int64_t
     const int r = lane + 32 * q;
     if (r < me) slot[m0 + r] = acc[q];
   }
+}
+
+// FP64-accurate refinement apply on the FP32 pipe: S_e = hi + lo (hi = the FP32 copy, lo =
+// fl32(S - hi)), x split into double-floats, compensated accumulation (same tile structure as
+// apply_vd_kernel; the FP64 slot is written).
+template <int MMAX, int WPB, int UNR>
+__global__ void __launch_bounds__(32 * WPB) apply_vd_df_kernel(int64_t ne, const int64_t* __restrict__ s_off,
+                                                               const int32_t* __restrict__ m_off,
+                                                               const int32_t* __restrict__ gint,
+                                                               const float* __restrict__ Shi,
+                                                               const float* __restrict__ Slo,
+                                                               const double* __restrict__ x, double* __restrict__ slot) {
+  constexpr int RPL = (MMAX + 31) / 32;
+  __shared__ df2 lx[WPB][MMAX];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * WPB + w;
+  if (e >= ne) return;
+  const int m0 = m_off[e], me = m_off[e + 1] - m0;
+  for (int c = lane; c < me; c += 32) {
+    const int gi = gint[m0 + c];
+    lx[w][c] = df_from(gi >= 0 ? x[gi] : 0.0);
+  }
+  __syncwarp();
+  DfAcc acc[RPL];
+  const int64_t so = s_off[e];
+#pragma unroll UNR
+  for (int c = 0; c < me; ++c) {
+    const df2 xc = lx[w][c];
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+      const int r = lane + 32 * q;
+      if (r < me) {
+        const int64_t o = so + (int64_t)c * me + r;
+        acc[q].fma(df2{__ldcs(Shi + o), __ldcs(Slo + o)}, xc);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < RPL; ++q) {
+    const int r = lane + 32 * q;
+    if (r < me) slot[m0 + r] = acc[q].value();
+  }
+}
+
+// lo = fl32(S - hi): the part of each FP64 entry that its FP32 copy does not hold
+static __global__ void lo32_kernel(int64_t n, const double* __restrict__ S, const float* __restrict__ hi,
+                                   float* __restrict__ lo) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    lo[t] = __double2float_rn(S[t] - (double)hi[t]);
 }
 
 // L2 projection of point values at each element's own volume rule (degree k_K, (k_K + 2)^3

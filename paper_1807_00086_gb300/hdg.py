@@ -58,6 +58,11 @@ class Stats(ctypes.Structure):
                 ("applydf_ms", c_double), ("apply16_launches", c_int64), ("apply16_ms", c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("tuned", c_int32), ("apply32_warps", c_int32), ("apply32_unroll", c_int32),
+                ("apply64_warps", c_int32), ("apply64_unroll", c_int32), ("local_threads", c_int32 * 2)]
+
+
 # exported entry points: name -> (restype, argtypes)
 SIGNATURES = {
     "hdg_default_options": (None, [ctypes.POINTER(Options)]),
@@ -86,6 +91,7 @@ SIGNATURES = {
                                           c_void_p, c_void_p, c_void_p, ctypes.c_char_p, c_int32]),
     "hdg_enable_stats": (c_int32, [c_void_p, c_int32]),
     "hdg_get_stats": (c_int32, [c_void_p, ctypes.POINTER(Stats), c_int32]),
+    "hdg_get_tuning": (c_int32, [c_void_p, ctypes.POINTER(Tuning)]),
 }
 
 _lib = None
@@ -340,6 +346,13 @@ class Solver:
                 "apply32_launches": st.apply32_launches, "apply32_ms": st.apply32_ms,
                 "applydf_launches": st.applydf_launches, "applydf_ms": st.applydf_ms,
                 "apply16_launches": st.apply16_launches, "apply16_ms": st.apply16_ms}
+
+    def hdg_get_tuning(self):
+        """Autotuned tiles of a per-element-degree context (see hdg_tuning in include/hdg.h)."""
+        t = Tuning()
+        self._check(self.lib.hdg_get_tuning(self.ctx, ctypes.byref(t)))
+        return {"tuned": t.tuned, "apply32_tile": (t.apply32_warps, t.apply32_unroll),
+                "apply64_tile": (t.apply64_warps, t.apply64_unroll), "local_threads": tuple(t.local_threads)}
 
     def hdg_step(self, dt, scheme, nsteps=1):
         info = SolveInfo()

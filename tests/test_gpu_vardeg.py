@@ -87,6 +87,9 @@ def test_vardeg_dirk3_steps_match_oracle(prec, tol):
         u, lam, t = s.hdg_get_state()
         assert relerr(u.cpu().numpy(), uo_steps[n][0]) < tol
         assert relerr(lam.cpu().numpy(), uo_steps[n][1]) < tol
+    tun = s.hdg_get_tuning()
+    assert tun["tuned"] == 1 and all(nth in (64, 128, 256) for nth in tun["local_threads"])
+    assert tun["apply64_tile"][0] in (4, 8) and tun["apply64_tile"][1] in (4, 8, 16)
 
 
 def test_uniform_degree_4_elastic_matches_uniform_oracle():
