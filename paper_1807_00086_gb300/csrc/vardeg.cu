@@ -29,6 +29,8 @@ struct VarDeg {
   int64_t m_tot = 0, s_tot = 0, h_tot = 0;
   float* d_S32 = nullptr;
   float* d_S32lo = nullptr;       // remainder of S_K beyond its FP32 copy (double-float residual apply)
+  __half* d_S16 = nullptr;        // FP16 copy (HDG_MIXED16 inner operator) and its per-element scales
+  float* d_sc16 = nullptr;
   // per-degree volume rules (initial-data projection) and per-element degree / point offsets
   std::vector<RefTables> rule;        // index k = 1..4
   std::vector<int32_t> ek;
@@ -40,7 +42,7 @@ struct VarDeg {
   // one-launch local solves and the autotuned tiles
   VdClassTable table{};
   size_t local_smem = 0;
-  int tile32 = -1, tile64 = -1, tiledf = -1;   // index into kApplyTiles (-1: not tuned yet)
+  int tile32 = -1, tile64 = -1, tiledf = -1, tile16 = -1;   // index into kApplyTiles (-1: not tuned yet)
   int local_nth[2] = {0, 0};      // threads per element of the MODE 0 / MODE 1 launch (0: not tuned)
 };
 
@@ -100,21 +102,22 @@ void vd_launch_condense(hdg_ctx* c, const VarDeg::Cls& k) {
 constexpr int kApplyTiles[6][2] = {{4, 4}, {4, 8}, {4, 16}, {8, 4}, {8, 8}, {8, 16}};   // (warps, unroll)
 constexpr int kLocalThreads[3] = {64, 128, 256};
 
-template <typename TV, int WPB, int UNR>
-void vd_apply_tile(hdg_ctx* c, const TV* S, const TV* x, TV* slot, const int* done) {
-  apply_vd_kernel<TV, VD_MMAX, WPB, UNR><<<(unsigned)((c->sk.ne + WPB - 1) / WPB), 32 * WPB, 0, c->stream>>>(
-      c->sk.ne, c->vd->d_s_off, c->vd->d_m_off, c->vd->d_gint, S, x, slot, done);
+template <typename TV, typename ST, int WPB, int UNR>
+void vd_apply_tile(hdg_ctx* c, const ST* S, const float* sc, const TV* x, TV* slot, const int* done) {
+  apply_vd_kernel<TV, ST, VD_MMAX, WPB, UNR><<<(unsigned)((c->sk.ne + WPB - 1) / WPB), 32 * WPB, 0, c->stream>>>(
+      c->sk.ne, c->vd->d_s_off, c->vd->d_m_off, c->vd->d_gint, S, sc, x, slot, done);
 }
 
-template <typename TV>
-void vd_apply_variant(hdg_ctx* c, int tile, const TV* S, const TV* x, TV* slot, const int* done) {
+template <typename TV, typename ST = TV>
+void vd_apply_variant(hdg_ctx* c, int tile, const ST* S, const TV* x, TV* slot, const int* done,
+                      const float* sc = nullptr) {
   switch (tile) {
-    case 0: vd_apply_tile<TV, 4, 4>(c, S, x, slot, done); break;
-    case 1: vd_apply_tile<TV, 4, 8>(c, S, x, slot, done); break;
-    case 2: vd_apply_tile<TV, 4, 16>(c, S, x, slot, done); break;
-    case 3: vd_apply_tile<TV, 8, 4>(c, S, x, slot, done); break;
-    case 4: vd_apply_tile<TV, 8, 8>(c, S, x, slot, done); break;
-    default: vd_apply_tile<TV, 8, 16>(c, S, x, slot, done); break;
+    case 0: vd_apply_tile<TV, ST, 4, 4>(c, S, sc, x, slot, done); break;
+    case 1: vd_apply_tile<TV, ST, 4, 8>(c, S, sc, x, slot, done); break;
+    case 2: vd_apply_tile<TV, ST, 4, 16>(c, S, sc, x, slot, done); break;
+    case 3: vd_apply_tile<TV, ST, 8, 4>(c, S, sc, x, slot, done); break;
+    case 4: vd_apply_tile<TV, ST, 8, 8>(c, S, sc, x, slot, done); break;
+    default: vd_apply_tile<TV, ST, 8, 16>(c, S, sc, x, slot, done); break;
   }
 }
 
@@ -234,6 +237,14 @@ void vd_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, int it
   apply_end(c, stop);
 }
 
+void vd_apply16(hdg_ctx* c, const float* x, float* slot, const int* done, int iter) {
+  c->n_launch += 1;
+  cudaEvent_t stop = apply_begin(c, 3, iter);
+  vd_apply_variant<float, __half>(c, c->vd->tile16 < 0 ? 1 : c->vd->tile16, c->vd->d_S16, x, slot, done,
+                                  c->vd->d_sc16);
+  apply_end(c, stop);
+}
+
 hdg_status vd_gather(hdg_ctx* c, const double* slot, double scale, double* out) {
   c->n_launch += 1;
   vd_face_gather_kernel<<<grid_for(c, c->ntr), 256, 0, c->stream>>>(c->ntr, c->vd->d_dslot, slot, scale, out);
@@ -287,7 +298,7 @@ hdg_status vd_cg(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info
 }
 
 // FP32 PCG on (sgn K32) x32 = b32 from x32 = 0 (inner solve of the refinement).
-hdg_status vd_cg32(hdg_ctx* c, double tol, int* iters) {
+hdg_status vd_cg32(hdg_ctx* c, double tol, int* iters, bool use16) {
   const int64_t n = c->ntr;
   const int nb = c->nb_red;
   const int64_t n4 = c->nfe4 / 4;
@@ -305,7 +316,8 @@ hdg_status vd_cg32(hdg_ctx* c, double tol, int* iters) {
     const int upto = std::min(maxit, it + chk);
     for (; it < upto; ++it) {
       const int par = it & 1;
-      vd_apply32(c, c->d_p32, c->d_slot32, &c->d_sc->done, it);
+      if (use16) vd_apply16(c, c->d_p32, c->d_slot32, &c->d_sc->done, it);
+      else vd_apply32(c, c->d_p32, c->d_slot32, &c->d_sc->done, it);
       c->n_launch += 3;
       vd_face_q_kernel<float><<<nb, 256, 0, c->stream>>>(n, (float)c->sgn, c->vd->d_dslot, c->d_slot32, c->d_p32,
                                                          c->d_q32, c->d_part, c->d_sc);
@@ -330,8 +342,9 @@ hdg_status vd_refine(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* 
   const int64_t n = c->ntr;
   const int nb = c->nb_red;
   int total_it = 0;
-  double rel = 0.0;
+  double rel = 0.0, rel_prev = 0.0;
   hdg_status s;
+  bool use16 = c->vd->d_S16 != nullptr;   // FP16 inner operator until a sweep contracts poorly
   for (int sweep = 0;; ++sweep) {
     vd_apply_df(c, x, c->d_slot);
     c->n_launch += 2;
@@ -349,7 +362,10 @@ hdg_status vd_refine(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* 
       if (info) { info->rel_residual = 0.0; info->sweeps += sweep; }
       return check_launch(c, "vd_zero_interior");
     }
+    rel_prev = rel;
     rel = std::sqrt(r.rr / r.bb);
+    // a sweep that gained less than 10x with the FP16 operator hands the rest to the FP32 copy
+    if (use16 && sweep > 0 && rel > 0.1 * rel_prev) use16 = false;
     if (rel <= c->opt.rtol) {
       if (info) { info->iterations += total_it; info->sweeps += sweep; info->rel_residual = rel; }
       return HDG_OK;
@@ -359,7 +375,7 @@ hdg_status vd_refine(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* 
     to32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_res, c->d_rs, c->d_b32);
     const double tol = std::min(0.5, std::max(c->opt.inner_rtol, 0.25 * c->opt.rtol / rel));
     int it = 0;
-    if ((s = vd_cg32(c, tol, &it))) return s;
+    if ((s = vd_cg32(c, tol, &it, use16))) return s;
     total_it += it;
     c->n_launch += 1;
     vd_refine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->vd->d_dslot, c->d_x32, c->d_rs, x);
@@ -566,6 +582,10 @@ hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k) {
   if (c->opt.prec != HDG_FP64) {
     if ((s = dalloc(c, &v->d_S32, (size_t)v->s_tot))) return s;
     if ((s = dalloc(c, &v->d_S32lo, (size_t)v->s_tot))) return s;
+    if (c->opt.prec == HDG_MIXED16) {
+      if ((s = dalloc(c, &v->d_S16, (size_t)v->s_tot))) return s;
+      if ((s = dalloc(c, &v->d_sc16, (size_t)ne))) return s;
+    }
     if ((s = dalloc(c, &c->d_slot32, (size_t)v->m_tot))) return s;
     c->nfe4 = (int64_t)((ntr + 3) / 4) * 4;
     for (float** p : {&c->d_dinv32, &c->d_r32, &c->d_z32, &c->d_p32, &c->d_q32, &c->d_x32, &c->d_b32}) {
@@ -600,6 +620,11 @@ hdg_status vd_condense(hdg_ctx* c, double alpha) {
     to32_copy_kernel<<<grid_for(c, c->vd->s_tot), 256, 0, c->stream>>>(c->vd->s_tot, c->d_S, c->vd->d_S32);
     c->n_launch += 1;
     lo32_kernel<<<grid_for(c, c->vd->s_tot), 256, 0, c->stream>>>(c->vd->s_tot, c->d_S, c->vd->d_S32, c->vd->d_S32lo);
+    if (c->vd->d_S16) {
+      c->n_launch += 1;
+      pack16_vd_kernel<<<grid_for(c, c->sk.ne * 32), 256, 0, c->stream>>>(c->sk.ne, c->vd->d_s_off, c->d_S,
+                                                                          c->vd->d_sc16, c->vd->d_S16);
+    }
     to32_kernel<<<grid_for(c, c->ntr), 256, 0, c->stream>>>(c->ntr, c->d_dinv, c->d_dinv32);
   }
   if ((s = check_launch(c, "vd_diag"))) return s;
@@ -612,6 +637,10 @@ hdg_status vd_condense(hdg_ctx* c, double alpha) {
     if (v->tile32 < 0)
       v->tile32 = vd_tune(c, [&](int t) { vd_apply_variant<float>(c, t, v->d_S32, c->d_p32, c->d_slot32, nullptr); });
     if (v->tiledf < 0) v->tiledf = vd_tune(c, [&](int t) { vd_apply_df_variant(c, t, c->d_lam, c->d_slot); });
+    if (v->d_S16 && v->tile16 < 0)
+      v->tile16 = vd_tune(c, [&](int t) {
+        vd_apply_variant<float, __half>(c, t, v->d_S16, c->d_p32, c->d_slot32, nullptr, v->d_sc16);
+      });
   }
   if ((s = check_launch(c, "vd_tune"))) return s;
   int herr = 0;

@@ -418,12 +418,17 @@ __global__ void __launch_bounds__(NTH) local_vd_all_kernel(DevMesh mesh, VdClass
 // Warp per element, WPB warps per block, lane handles rows lane + 32 q; S_e is symmetric, so
 // column r is read as row r (coalesced); UNR columns are in flight per step. MMAX bounds m_e.
 // (WPB, UNR) is the tile the autotuner picks per context.
-template <typename TV, int MMAX, int WPB, int UNR>
+__device__ __forceinline__ double vd_val(double s) { return s; }
+__device__ __forceinline__ float vd_val(float s) { return s; }
+__device__ __forceinline__ float vd_val(__half s) { return __half2float(s); }
+
+// ST: storage type of S_K (double, float, or __half with a per-element scale sc[e]).
+template <typename TV, typename ST, int MMAX, int WPB, int UNR>
 __global__ void __launch_bounds__(32 * WPB) apply_vd_kernel(int64_t ne, const int64_t* __restrict__ s_off,
                                                             const int32_t* __restrict__ m_off,
-                                                            const int32_t* __restrict__ gint, const TV* __restrict__ S,
-                                                            const TV* __restrict__ x, TV* __restrict__ slot,
-                                                            const int* __restrict__ done) {
+                                                            const int32_t* __restrict__ gint, const ST* __restrict__ S,
+                                                            const float* __restrict__ sc, const TV* __restrict__ x,
+                                                            TV* __restrict__ slot, const int* __restrict__ done) {
   constexpr int RPL = (MMAX + 31) / 32;
   __shared__ TV lx[WPB][MMAX];
   if (done && *done) return;
@@ -439,20 +444,39 @@ __global__ void __launch_bounds__(32 * WPB) apply_vd_kernel(int64_t ne, const in
   TV acc[RPL];
 #pragma unroll
   for (int q = 0; q < RPL; ++q) acc[q] = TV(0);
-  const TV* Se = S + s_off[e];
+  const ST* Se = S + s_off[e];
 #pragma unroll UNR
   for (int c = 0; c < me; ++c) {
     const TV xc = lx[w][c];
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
       const int r = lane + 32 * q;
-      if (r < me) acc[q] += __ldcs(Se + (int64_t)c * me + r) * xc;
+      if (r < me) acc[q] += (TV)vd_val(__ldcs(Se + (int64_t)c * me + r)) * xc;
     }
   }
+  const TV scl = sc ? (TV)sc[e] : TV(1);
 #pragma unroll
   for (int q = 0; q < RPL; ++q) {
     const int r = lane + 32 * q;
-    if (r < me) slot[m0 + r] = acc[q];
+    if (r < me) slot[m0 + r] = scl * acc[q];
+  }
+}
+
+// FP16 copy of the compact S_K blocks with one scale per element (max |S_K|, rounded up so
+// every stored value lies in [-1, 1]). Warp per element.
+static __global__ void pack16_vd_kernel(int64_t ne, const int64_t* __restrict__ s_off, const double* __restrict__ S,
+                                        float* __restrict__ sc, __half* __restrict__ S16) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = w; e < ne; e += nw) {
+    const int64_t a = s_off[e], b = s_off[e + 1];
+    double m = 0.0;
+    for (int64_t t = a + lane; t < b; t += 32) m = fmax(m, fabs(S[t]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const float s = m > 0.0 ? __double2float_ru(m) : 1.f;
+    if (lane == 0) sc[e] = s;
+    for (int64_t t = a + lane; t < b; t += 32) S16[t] = __float2half_rn((float)(S[t] / (double)s));
   }
 }
 
