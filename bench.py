@@ -375,14 +375,18 @@ def run_ours(args):
         # per launch: every compact S_K (FP32, or FP64 for the plain path), the trace gather and
         # the slot products
         if args.prec != "fp64":
-            a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
-            byt = nschur * 4 + 2 * nslot * 4
+            f16 = st.get("apply16_launches", 0) > 0
+            a32 = (st["apply16_ms"] / st["apply16_launches"]) if f16 else \
+                st["apply32_ms"] / max(1, st["apply32_launches"])
+            byt = (nschur * 2 + ne * 4 if f16 else nschur * 4) + 2 * nslot * 4
             ach = byt / (a32 / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                    "kernel": "apply_vd_kernel<float> (compact FP32 S_K, per-element m_K)",
+                    "kernel": ("apply_vd_kernel<float, __half> (compact FP16 S_K, per-element scale)" if f16 else
+                               "apply_vd_kernel<float> (compact FP32 S_K, per-element m_K)"),
                     "peak_source": src + " (hbm_gbs: copy)",
-                    "bytes_per_launch": byt, "launch_ms": a32, "launches": st["apply32_launches"],
+                    "bytes_per_launch": byt, "launch_ms": a32,
+                    "launches": st["apply16_launches"] if f16 else st["apply32_launches"],
                     "fp64_refinement_apply": {"launch_ms": apply_avg_ms, "launches": st["apply_launches"],
                                               "achieved_tflops": 2 * nschur / (apply_avg_ms / 1e3) / 1e12
                                               if st["apply_launches"] else None}}

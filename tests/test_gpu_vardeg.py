@@ -69,7 +69,7 @@ def test_vardeg_trace_operators_match_oracle(N, seed):
     assert relerr(u, uo) < 1e-12
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 1e-9)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 1e-9), ("mixed16", 1e-9)])
 def test_vardeg_dirk3_steps_match_oracle(prec, tol):
     import torch
     N, seed = 2, 5
