@@ -213,8 +213,10 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
       const int64_t nS = c->sk.ne * (int64_t)c->m * c->m;
       c->n_launch += 1;
       to32_copy_kernel<<<grid_for(c, nS), 256, 0, c->stream>>>(nS, c->d_S, c->d_S32);
-    } else if (c->R > 1) {
+    } else if (c->R >= 32) {
       HDG_DISPATCH(c, launch_pack32m, c);
+    } else if (c->R > 1) {
+      HDG_DISPATCH(c, launch_pack32, c);   // group layout, read by the narrow multi-column apply
     } else {
       HDG_DISPATCH(c, launch_pack32, c);
       HDG_DISPATCH(c, launch_packdf, c);
@@ -415,27 +417,48 @@ MScal mscal(hdg_ctx* c) {
   return m;
 }
 
+template <int DIM, int K, int CWW>
+void mlaunch_local_cw(hdg_ctx* c, int mode, const double* F, const double* hist, const SrcArgs& sa, const double* lam,
+                      double* out) {
+  using L = LocalMultiCfg<DIM, K, CWW>;
+  dim3 grid((unsigned)c->sk.ne, (unsigned)((c->R + L::CW - 1) / L::CW));
+  if (mode == 0)
+    local_multi_kernel<DIM, K, 0, CWW><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau,
+                                                                       c->R, F, hist, sa, lam, out);
+  else
+    local_multi_kernel<DIM, K, 1, CWW><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau,
+                                                                       c->R, F, hist, sa, lam, out);
+}
+
 template <int DIM, int K>
 void mlaunch_local(hdg_ctx* c, int mode, const double* F, const double* hist, double t, const double* lam, double* out) {
-  using L = LocalMultiCfg<DIM, K>;
-  dim3 grid((unsigned)c->sk.ne, (unsigned)((c->R + L::CW - 1) / L::CW));
   const SrcArgs sa = srcargs(c, t);
   c->n_launch += 1;
-  if (mode == 0)
-    local_multi_kernel<DIM, K, 0><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, c->R, F,
-                                                                  hist, sa, lam, out);
-  else
-    local_multi_kernel<DIM, K, 1><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau, c->R, F,
-                                                                  hist, sa, lam, out);
+  // as many columns per CTA as the batch has (up to the kernel's width)
+  if (c->R <= 2) mlaunch_local_cw<DIM, K, 2>(c, mode, F, hist, sa, lam, out);
+  else if (c->R <= 4) mlaunch_local_cw<DIM, K, 4>(c, mode, F, hist, sa, lam, out);
+  else if (c->R <= 8) mlaunch_local_cw<DIM, K, 8>(c, mode, F, hist, sa, lam, out);
+  else if (c->R <= 16) mlaunch_local_cw<DIM, K, 16>(c, mode, F, hist, sa, lam, out);
+  else mlaunch_local_cw<DIM, K, 32>(c, mode, F, hist, sa, lam, out);
+}
+
+template <int DIM, int K, typename TV, int CWN>
+void mlaunch_apply_cw(hdg_ctx* c, const TV* x, TV* slot, const int* done) {
+  constexpr int EPB = 4 * (32 / CWN);   // elements per 4-warp block
+  dim3 grid((unsigned)((c->sk.ne + EPB - 1) / EPB), (unsigned)((c->R + CWN - 1) / CWN));
+  apply_multi_kernel<DIM, K, TV, CWN><<<grid, 128, 0, c->stream>>>(c->sk.ne, c->R, c->d_elem_face, c->d_face_bnd,
+                                                                   c->d_S32, c->d_S, x, slot, done);
 }
 
 template <int DIM, int K, typename TV>
 void mlaunch_apply(hdg_ctx* c, const TV* x, TV* slot, const int* done, int iter) {
-  dim3 grid((unsigned)((c->sk.ne + 3) / 4), (unsigned)((c->R + 31) / 32));
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, sizeof(TV) == 4 ? 1 : 0, iter);
-  apply_multi_kernel<DIM, K, TV><<<grid, 128, 0, c->stream>>>(c->sk.ne, c->R, c->d_elem_face, c->d_face_bnd, c->d_S32,
-                                                              c->d_S, x, slot, done);
+  if (c->R <= 2) mlaunch_apply_cw<DIM, K, TV, 2>(c, x, slot, done);
+  else if (c->R <= 4) mlaunch_apply_cw<DIM, K, TV, 4>(c, x, slot, done);
+  else if (c->R <= 8) mlaunch_apply_cw<DIM, K, TV, 8>(c, x, slot, done);
+  else if (c->R <= 16) mlaunch_apply_cw<DIM, K, TV, 16>(c, x, slot, done);
+  else mlaunch_apply_cw<DIM, K, TV, 32>(c, x, slot, done);
   apply_end(c, stop);
 }
 template <int DIM, int K>
@@ -444,6 +467,11 @@ void mlaunch_apply64(hdg_ctx* c, const double* x, double* slot, const int* done,
 }
 template <int DIM, int K>
 void mlaunch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, int iter) {
+  // fewer than 32 columns: several elements per warp over the group-layout FP32 S_K
+  if (c->R < 32) {
+    mlaunch_apply<DIM, K, float>(c, x, slot, done, iter);
+    return;
+  }
   using AC = Apply32mCfg<DIM, K>;
   const unsigned grid = (unsigned)((c->sk.ne + AC::EPB - 1) / AC::EPB);
   c->n_launch += 1;

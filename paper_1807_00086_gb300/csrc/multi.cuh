@@ -9,22 +9,24 @@
 namespace hdg {
 
 // ------------------------------------------------------------------ element-local solves, R columns
-// CTA = one element x CW columns x NP rows; warp = one row over 32 columns, so table,
-// geometry and H^{-1} reads are warp-uniform and field reads are coalesced along columns.
-template <int DIM, int K>
+// CTA = one element x CW columns x NP rows; with CW = 32 a warp is one row over 32 columns, so
+// table, geometry and H^{-1} reads are warp-uniform and field reads are coalesced along columns.
+// CW = columns per CTA: min(R, 32) (16 when N_p > 32), so a narrow batch (a few serving slots)
+// keeps every thread busy.
+template <int DIM, int K, int CWW = 32>
 struct LocalMultiCfg {
   static constexpr int NP = Dims<DIM, K>::NP;
-  static constexpr int CW = NP <= 32 ? 32 : 16;
+  static constexpr int CW = (NP <= 32 ? 32 : 16) < CWW ? (NP <= 32 ? 32 : 16) : CWW;
   static constexpr int NT = NP * CW;
 };
 
-template <int DIM, int K, int MODE>
-__global__ void __launch_bounds__(LocalMultiCfg<DIM, K>::NT)
+template <int DIM, int K, int MODE, int CWW = 32>
+__global__ void __launch_bounds__(LocalMultiCfg<DIM, K, CWW>::NT)
     local_multi_kernel(DevMesh mesh, Tabs T, const double* __restrict__ Hinv, double alpha, double tau, int R,
                        const double* __restrict__ F, const double* __restrict__ hist, SrcArgs src,
                        const double* __restrict__ lam, double* __restrict__ out) {
   using D = Dims<DIM, K>;
-  using L = LocalMultiCfg<DIM, K>;
+  using L = LocalMultiCfg<DIM, K, CWW>;
   constexpr int NP = D::NP, NF = D::NF, M = D::M, NFC = D::NFC, N = D::N, CW = L::CW;
   __shared__ double g[GEO_STRIDE];
   __shared__ double Tr[DIM * NP][CW];
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(LocalMultiCfg<DIM, K>::NT)
   const int jl = threadIdx.x % CW, i = threadIdx.x / CW;
   const int j = blockIdx.y * CW + jl;
   const bool col = j < R;
-  if (threadIdx.x < GEO_STRIDE) g[threadIdx.x] = mesh.geo[e * GEO_STRIDE + threadIdx.x];
+  for (int t = threadIdx.x; t < GEO_STRIDE; t += L::NT) g[t] = mesh.geo[e * GEO_STRIDE + t];   // NT may be < 32
   if (threadIdx.x < NFC) {
     int use = 0;
     if (lam) {
@@ -166,7 +168,10 @@ __global__ void __launch_bounds__(LocalMultiCfg<DIM, K>::NT)
 // ------------------------------------------------------------------ trace apply, R columns
 // warp = (element, 32-column group); lane = column. S_K entries are warp-uniform loads.
 // FP32: S from the packed group layout of pack32_kernel. FP64: S from [e][M][M].
-template <int DIM, int K, typename TV>
+// Warp = 32 / CWN elements x CWN columns (CWN = min(R, 32)); the FP32 S_K is read from the
+// 32-element group layout of the single-column path (consecutive elements of a warp read
+// consecutive float4s), the FP64 S_K from [e][m][m].
+template <int DIM, int K, typename TV, int CWN = 32>
 __global__ void __launch_bounds__(128) apply_multi_kernel(int64_t ne, int R, const int32_t* __restrict__ elem_face,
                                                           const int32_t* __restrict__ face_bnd,
                                                           const float* __restrict__ S32, const double* __restrict__ S64,
@@ -174,11 +179,11 @@ __global__ void __launch_bounds__(128) apply_multi_kernel(int64_t ne, int R, con
                                                           const int* __restrict__ done) {
   using Dm = Dims<DIM, K>;
   using PK = Packed<DIM, K>;
-  constexpr int NF = Dm::NF, M = Dm::M, NFC = Dm::NFC, P4 = PK::P4;
+  constexpr int NF = Dm::NF, M = Dm::M, NFC = Dm::NFC, P4 = PK::P4, EPW = 32 / CWN;
   if (done && *done) return;
   const int lane = threadIdx.x & 31;
-  const int64_t e = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int j = blockIdx.y * 32 + lane;
+  const int64_t e = ((int64_t)blockIdx.x * 4 + (threadIdx.x >> 5)) * EPW + lane / CWN;
+  const int j = blockIdx.y * CWN + lane % CWN;
   if (e >= ne) return;
   const bool col = j < R;
   TV xl[M], y[M];
