@@ -338,6 +338,17 @@ __device__ __forceinline__ void block_cols(double v, int R, double* red /*[256]*
   }
 }
 
+// Per-column sums of block partials part[(b0 + b) * R + j] (b < nb) by the whole block (256
+// threads, R a power of two <= 256): 256 / R threads per column, fixed partition and tree,
+// so the sums are deterministic; column j's sum is left in red[j].
+__device__ __forceinline__ void col_partials(const double* __restrict__ part, int nb, int R, int64_t b0,
+                                             double* red /*[256]*/) {
+  const int G = 256 / R, j = threadIdx.x & (R - 1), g = threadIdx.x / R;
+  double s = 0.0;
+  for (int b = g; b < nb; b += G) s += part[(b0 + b) * R + j];
+  block_cols(s, R, red);
+}
+
 struct MScal {              // per-column Krylov scalars, arrays of R entries
   double *rho0, *rho1, *alpha, *rr, *bb, *tol2;
   int* conv;                // per column: converged
@@ -374,10 +385,11 @@ __global__ void __launch_bounds__(256) mface_q_kernel(int nf, int R, const int32
 
 // alpha_j = rho_j / pq_j (0 for converged columns)
 static __global__ void mcols_alpha(int nb, int R, int parity, const double* __restrict__ part, MScal sc) {
+  __shared__ double red[256];
+  if (*sc.done) return;
+  col_partials(part, nb, R, 0, red);
   for (int j = threadIdx.x; j < R; j += blockDim.x) {
-    if (*sc.done) return;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * R + j];
+    const double s = red[j];
     const double rho = parity ? sc.rho1[j] : sc.rho0[j];
     sc.alpha[j] = (sc.conv[j] || s == 0.0) ? 0.0 : rho / s;
   }
@@ -415,9 +427,12 @@ static __global__ void mcols_beta(int nb, int R, int parity, int maxit, const do
   __syncthreads();
   if (*sc.done) return;
   const int iter = *sc.iters;
+  __shared__ double red[256], rzs[256];
+  col_partials(part, nb, R, 0, red);
+  if (threadIdx.x < R) rzs[threadIdx.x] = red[threadIdx.x];
+  col_partials(part, nb, R, nb, red);   // starts with a barrier: rzs is complete
   for (int j = threadIdx.x; j < R; j += blockDim.x) {
-    double rz = 0.0, rr = 0.0;
-    for (int b = 0; b < nb; ++b) { rz += part[(int64_t)b * R + j]; rr += part[(int64_t)(nb + b) * R + j]; }
+    const double rz = rzs[j], rr = red[j];
     const double rho = parity ? sc.rho1[j] : sc.rho0[j];
     const int c = sc.conv[j] || rr <= sc.tol2[j];
     beta[j] = c ? 0.0 : rz / rho;
@@ -484,13 +499,14 @@ static __global__ void mcols_init(int nb, int R, double rtol, int tol_from_rr, c
   __shared__ int notconv;
   if (threadIdx.x == 0) notconv = 0;
   __syncthreads();
+  __shared__ double red[256], rzs[256], rrs[256];
+  col_partials(part, nb, R, 0, red);
+  if (threadIdx.x < R) rzs[threadIdx.x] = red[threadIdx.x];
+  col_partials(part, nb, R, nb, red);
+  if (threadIdx.x < R) rrs[threadIdx.x] = red[threadIdx.x];
+  col_partials(part, nb, R, 2 * (int64_t)nb, red);
   for (int j = threadIdx.x; j < R; j += blockDim.x) {
-    double rz = 0.0, rr = 0.0, bb = 0.0;
-    for (int b = 0; b < nb; ++b) {
-      rz += part[(int64_t)b * R + j];
-      rr += part[(int64_t)(nb + b) * R + j];
-      bb += part[(int64_t)(2 * nb + b) * R + j];
-    }
+    const double rz = rzs[j], rr = rrs[j], bb = red[j];
     sc.rho0[j] = rz; sc.rho1[j] = 0.0; sc.rr[j] = rr; sc.bb[j] = bb;
     sc.tol2[j] = rtol * rtol * (tol_from_rr ? rr : bb);
     const int c = rr <= sc.tol2[j];
@@ -541,9 +557,12 @@ static __global__ void mrefine_scalars(int nb, int R, double rtol, const double*
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
+  __shared__ double red[256], as[256];
+  col_partials(part, nb, R, 0, red);
+  if (threadIdx.x < R) as[threadIdx.x] = red[threadIdx.x];
+  col_partials(part, nb, R, nb, red);
   for (int j = threadIdx.x; j < R; j += blockDim.x) {
-    double a = 0.0, c = 0.0;
-    for (int b = 0; b < nb; ++b) { a += part[(int64_t)b * R + j]; c += part[(int64_t)(nb + b) * R + j]; }
+    const double a = as[j], c = red[j];
     rr[j] = a; bb[j] = c;
     const bool ok = a <= rtol * rtol * c;
     scale[j] = (ok || a == 0.0) ? 0.0 : 1.0 / sqrt(a);
