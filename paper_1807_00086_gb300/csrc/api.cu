@@ -213,10 +213,18 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
       const int64_t nS = c->sk.ne * (int64_t)c->m * c->m;
       c->n_launch += 1;
       to32_copy_kernel<<<grid_for(c, nS), 256, 0, c->stream>>>(nS, c->d_S, c->d_S32);
-    } else if (c->R >= 32) {
-      HDG_DISPATCH(c, launch_pack32m, c);
     } else if (c->R > 1) {
-      HDG_DISPATCH(c, launch_pack32, c);   // group layout, read by the narrow multi-column apply
+      if (c->R >= 32) {
+        HDG_DISPATCH(c, launch_pack32m, c);
+      } else {
+        HDG_DISPATCH(c, launch_pack32, c);   // group layout, read by the narrow multi-column apply
+      }
+      const int64_t nS = c->sk.ne * (int64_t)c->m * c->m;
+      c->n_launch += 1;
+      split_df_kernel<<<grid_for(c, nS), 256, 0, c->stream>>>(nS, c->d_S, c->d_mShi, c->d_mSlo);
+      const int64_t nH = c->sk.ne * (int64_t)c->nv * c->nv;
+      c->n_launch += 1;
+      to_df_kernel<<<grid_for(c, nH), 256, 0, c->stream>>>(nH, c->d_Hinv, c->d_Hinvdf);
     } else {
       HDG_DISPATCH(c, launch_pack32, c);
       HDG_DISPATCH(c, launch_packdf, c);
@@ -422,6 +430,17 @@ void mlaunch_local_cw(hdg_ctx* c, int mode, const double* F, const double* hist,
                       double* out) {
   using L = LocalMultiCfg<DIM, K, CWW>;
   dim3 grid((unsigned)c->sk.ne, (unsigned)((c->R + L::CW - 1) / L::CW));
+  if (c->d_Hinvdf) {   // mixed precision: double-float on the FP32 pipe
+    const float th = (float)c->tau;
+    const df2 tau{th, (float)(c->tau - (double)th)};
+    if (mode == 0)
+      local_df_multi_kernel<DIM, K, 0, CWW><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabsdf, c->d_geodf, c->d_Hinvdf,
+                                                                           c->alpha, tau, c->R, F, hist, sa, lam, out);
+    else
+      local_df_multi_kernel<DIM, K, 1, CWW><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabsdf, c->d_geodf, c->d_Hinvdf,
+                                                                           c->alpha, tau, c->R, F, hist, sa, lam, out);
+    return;
+  }
   if (mode == 0)
     local_multi_kernel<DIM, K, 0, CWW><<<grid, L::NT, 0, c->stream>>>(devmesh(c), c->tabs, c->d_Hinv, c->alpha, c->tau,
                                                                        c->R, F, hist, sa, lam, out);
@@ -461,6 +480,27 @@ void mlaunch_apply(hdg_ctx* c, const TV* x, TV* slot, const int* done, int iter)
   else mlaunch_apply_cw<DIM, K, TV, 32>(c, x, slot, done);
   apply_end(c, stop);
 }
+template <int DIM, int K, int CWN>
+void mlaunch_apply_df_cw(hdg_ctx* c, const double* x, double* slot) {
+  constexpr int EPB = ApplyDfMCfg<DIM, K>::WPB * (32 / CWN);
+  dim3 grid((unsigned)((c->sk.ne + EPB - 1) / EPB), (unsigned)((c->R + CWN - 1) / CWN));
+  apply_df_multi_kernel<DIM, K, CWN><<<grid, 32 * ApplyDfMCfg<DIM, K>::WPB, 0, c->stream>>>(
+      c->sk.ne, c->R, c->d_elem_face, c->d_face_bnd, c->d_mShi, c->d_mSlo, x, slot);
+}
+
+// FP64-accurate R-column apply of the mixed refinement (double-float on the FP32 pipe)
+template <int DIM, int K>
+void mlaunch_apply_df(hdg_ctx* c, const double* x, double* slot) {
+  c->n_launch += 1;
+  cudaEvent_t stop = apply_begin(c, 2, -1);
+  if (c->R <= 2) mlaunch_apply_df_cw<DIM, K, 2>(c, x, slot);
+  else if (c->R <= 4) mlaunch_apply_df_cw<DIM, K, 4>(c, x, slot);
+  else if (c->R <= 8) mlaunch_apply_df_cw<DIM, K, 8>(c, x, slot);
+  else if (c->R <= 16) mlaunch_apply_df_cw<DIM, K, 16>(c, x, slot);
+  else mlaunch_apply_df_cw<DIM, K, 32>(c, x, slot);
+  apply_end(c, stop);
+}
+
 template <int DIM, int K>
 void mlaunch_apply64(hdg_ctx* c, const double* x, double* slot, const int* done, int iter) {
   mlaunch_apply<DIM, K, double>(c, x, slot, done, iter);
@@ -634,7 +674,7 @@ hdg_status msolve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) 
   }
   int total = 0;
   for (int sweep = 0;; ++sweep) {
-    HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)x, c->d_mslot, (const int*)nullptr, -1);
+    HDG_DISPATCH(c, mlaunch_apply_df, c, (const double*)x, c->d_mslot);
     HDG_DISPATCH(c, mlaunch_refres, c, b);
     if ((s = check_launch(c, "mrefine_residual"))) return s;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_mint + 1, c->d_mnconv, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -925,6 +965,8 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
       CUDA_TRY(c, cudaMemsetAsync(*p, 0, cnt * 4, c->stream));
     }
     if (c->R > 1 && (s = dalloc(c, &c->d_mslot32, (size_t)ne * c->m * R))) return s;
+    if (c->R > 1 && (s = dalloc(c, &c->d_mShi, (size_t)ne * c->m * c->m))) return s;
+    if (c->R > 1 && (s = dalloc(c, &c->d_mSlo, (size_t)ne * c->m * c->m))) return s;
     if ((s = dalloc(c, &c->d_pqpart, (size_t)(ngroups + 3) / 4))) return s;
     if ((s = dalloc(c, &c->d_pq, 1))) return s;
     if ((s = dalloc(c, &c->d_ticket, 1))) return s;
@@ -941,6 +983,8 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
         CUDA_TRY(c, cudaMemsetAsync(c->d_sc16, 0, (size_t)ngroups * 32 * 4, c->stream));
       }
       CUDA_TRY(c, cudaMemsetAsync(c->d_Sdf, 0, nSdf * 4, c->stream));
+    }
+    if (c->phys == HDG_ACOUSTIC) {
       // double-float local solves: H^{-1} (filled at each condensation), geometry, tables
       if ((s = dalloc(c, &c->d_Hinvdf, (size_t)ne * c->nv * c->nv))) return s;
       if ((s = dalloc(c, &c->d_geodf, (size_t)ne * GEO_STRIDE))) return s;

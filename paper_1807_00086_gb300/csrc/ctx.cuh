@@ -72,6 +72,7 @@ struct hdg_ctx {
   int R = 1;
   double *d_mslot = nullptr;            // FP64 slots [ne][m][R]
   float *d_mslot32 = nullptr;           // FP32 slots [ne][m][R]
+  float *d_mShi = nullptr, *d_mSlo = nullptr;   // S_K as FP32 pairs [ne][m][m] (double-float residual apply)
   double *d_mrho0 = nullptr, *d_mrho1 = nullptr, *d_malpha = nullptr, *d_mbeta = nullptr, *d_mrr = nullptr,
          *d_mbb = nullptr, *d_mtol2 = nullptr, *d_mscale = nullptr, *d_mrr2 = nullptr, *d_mbb2 = nullptr;
   int *d_mconv = nullptr, *d_mdone = nullptr, *d_mnconv = nullptr, *d_miters = nullptr;

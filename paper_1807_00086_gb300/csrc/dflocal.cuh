@@ -11,6 +11,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "multi.cuh"
 
 namespace hdg {
 
@@ -246,6 +247,169 @@ __global__ void __launch_bounds__(LocalDfCfg<DIM, K>::NT)
 #pragma unroll 4
     for (int q = 0; q < NP; ++q) s.fma(T.Ff[(f * NP + q) * NF + mm], wf[q]);
     out[e2 * M + r] = df_to(df_mul(g[el2][D::OJF + f], df_of(s)));
+  }
+}
+
+
+// R-column version (the multi-source and serving batches): CTA = one element x CW columns x
+// NP rows, the layouts and work split of local_multi_kernel, every operation as in
+// local_df_kernel (double-float products and sums on the FP32 pipe).
+template <int DIM, int K, int MODE, int CWW>
+__global__ void __launch_bounds__(LocalMultiCfg<DIM, K, CWW>::NT)
+    local_df_multi_kernel(DevMesh mesh, TabsDf T, const df2* __restrict__ geo, const df2* __restrict__ Hinv,
+                          double alpha, df2 tau, int R, const double* __restrict__ F, const double* __restrict__ hist,
+                          SrcArgs src, const double* __restrict__ lam, double* __restrict__ out) {
+  using D = Dims<DIM, K>;
+  using L = LocalMultiCfg<DIM, K, CWW>;
+  constexpr int NP = D::NP, NF = D::NF, M = D::M, NFC = D::NFC, N = D::N, CW = L::CW;
+  __shared__ df2 g[GEO_STRIDE];
+  __shared__ df2 Tr[DIM * NP][CW];
+  __shared__ df2 rp[NP][CW];
+  __shared__ df2 pp[NP][CW];
+  __shared__ df2 ll[M][CW];
+  __shared__ df2 co[4];   // 1/b, a' dJ, b dJ, 1/(b dJ) with b = alpha rho, a' = alpha/(rho c^2)
+  __shared__ int fuse[NFC];
+  const int64_t e = blockIdx.x;
+  const int jl = threadIdx.x % CW, i = threadIdx.x / CW;
+  const int j = blockIdx.y * CW + jl;
+  const bool col = j < R;
+  for (int t = threadIdx.x; t < GEO_STRIDE; t += L::NT) g[t] = geo[e * GEO_STRIDE + t];
+  if (threadIdx.x < NFC) {
+    int use = 0;
+    if (lam) {
+      const int f = mesh.elem_face[e * NFC + threadIdx.x];
+      use = (MODE == 1) || (mesh.face_bnd[f] >= 0);
+    }
+    fuse[threadIdx.x] = use;
+  }
+  if (threadIdx.x == 0) {
+    const double rho = mesh.rho[e], cc = mesh.c[e], dJ = mesh.geo[e * GEO_STRIDE];
+    const double b = alpha * rho, ap = alpha / (rho * cc * cc);
+    co[0] = df_from(1.0 / b);
+    co[1] = df_from(ap * dJ);
+    co[2] = df_from(b * dJ);
+    co[3] = df_from(1.0 / (b * dJ));
+  }
+  for (int t = threadIdx.x; t < M * CW; t += L::NT) {
+    const int r = t / CW, jj = blockIdx.y * CW + t % CW;
+    double v = 0.0;
+    if (lam && jj < R) {
+      const int f = mesh.elem_face[e * NFC + r / NF];
+      if ((MODE == 1) || (mesh.face_bnd[f] >= 0)) v = lam[((int64_t)f * NF + r % NF) * R + jj];
+    }
+    ll[r][t % CW] = df_from(v);
+  }
+  __syncthreads();
+  const df2 ib = co[0];
+  df2 Fu[DIM + 1];
+  {
+    df2 Fl[NFC];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      DfAcc s;
+      if (fuse[f])
+        for (int mm = 0; mm < NF; ++mm) s.fma(T.FfT[(f * NF + mm) * NP + i], ll[f * NF + mm][jl]);
+      Fl[f] = df_of(s);
+    }
+#pragma unroll
+    for (int comp = 0; comp <= DIM; ++comp) {
+      df2 v{0.f, 0.f};
+      if (col) {
+        const int64_t idx = (e * N + comp * NP + i) * R + j;
+        if (hist) {
+          v = df_mul(co[comp == 0 ? 1 : 2], df_from(hist[idx]));
+          if (comp == 0 && src.ptr && src.ptr[e] < src.ptr[e + 1]) {
+            double sv = 0.0;
+            for (int q = src.ptr[e]; q < src.ptr[e + 1]; ++q)
+              if (src.col[q] == j) sv += ricker_at(src, q) * src.phi[(int64_t)q * NP + i];
+            v = df_add(v, df_from(sv));
+          }
+        } else {
+          v = df_from(F[idx]);
+        }
+      }
+      DfAcc bl;
+      if (comp == 0) {
+#pragma unroll
+        for (int f = 0; f < NFC; ++f) bl.fma(g[D::OJF + f], Fl[f]);
+        v = df_add(v, df_mul(tau, df_of(bl)));
+      } else {
+#pragma unroll
+        for (int f = 0; f < NFC; ++f) bl.fma(df_mul(g[D::ON + f * DIM + comp - 1], g[D::OJF + f]), Fl[f]);
+        v = df_add(v, df_neg(df_of(bl)));
+      }
+      Fu[comp] = v;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) {
+    DfAcc s;
+#pragma unroll
+    for (int jj = 0; jj < DIM; ++jj) s.fma(g[1 + r * DIM + jj], Fu[jj + 1]);
+    Tr[r * NP + i][jl] = df_of(s);
+  }
+  __syncthreads();
+  {
+    DfAcc s;
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+      for (int l = 0; l < NP; ++l) s.fma(T.DrT[(r * NP + l) * NP + i], Tr[r * NP + l][jl]);
+    rp[i][jl] = df_add(Fu[0], df_neg(df_mul(df_of(s), ib)));
+  }
+  __syncthreads();
+  {
+    const df2* He = Hinv + e * (int64_t)(NP * NP);
+    DfAcc s;
+    for (int l = 0; l < NP; ++l) s.fma(He[l * NP + i], rp[l][jl]);
+    pp[i][jl] = df_of(s);
+  }
+  __syncthreads();
+  df2 vv[DIM];
+  {
+    df2 qd[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      DfAcc s;
+      for (int l = 0; l < NP; ++l) s.fma(T.Dr[(r * NP + l) * NP + i], pp[l][jl]);
+      qd[r] = df_of(s);
+    }
+#pragma unroll
+    for (int jj = 0; jj < DIM; ++jj) {
+      DfAcc s;
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) s.fma(g[1 + r * DIM + jj], qd[r]);
+      vv[jj] = df_add(df_mul(Fu[jj + 1], co[3]), df_mul(df_of(s), ib));
+    }
+  }
+  if (MODE == 1) {
+    if (col) {
+      out[(e * N + i) * R + j] = df_to(pp[i][jl]);
+#pragma unroll
+      for (int jj = 0; jj < DIM; ++jj) out[(e * N + (jj + 1) * NP + i) * R + j] = df_to(vv[jj]);
+    }
+    return;
+  }
+  __syncthreads();   // all reads of Tr done: reuse it (and rp) for the face weights
+  {
+    const df2 tp = df_mul(tau, pp[i][jl]);
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      DfAcc s;
+#pragma unroll
+      for (int jj = 0; jj < DIM; ++jj) s.fma(g[D::ON + f * DIM + jj], vv[jj]);
+      const df2 wv = df_add(tp, df_of(s));
+      if (f < DIM) Tr[f * NP + i][jl] = wv;
+      else rp[i][jl] = wv;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < M * CW; t += L::NT) {
+    const int r = t / CW, jj2 = t % CW, f = r / NF, mm = r % NF;
+    const int jc = blockIdx.y * CW + jj2;
+    if (jc >= R) continue;
+    DfAcc s;
+    for (int q = 0; q < NP; ++q) s.fma(T.Ff[(f * NP + q) * NF + mm], f < DIM ? Tr[f * NP + q][jj2] : rp[q][jj2]);
+    out[(e * M + r) * R + jc] = df_to(df_mul(g[D::OJF + f], df_of(s)));
   }
 }
 

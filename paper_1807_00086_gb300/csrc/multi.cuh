@@ -228,6 +228,57 @@ __global__ void __launch_bounds__(128) apply_multi_kernel(int64_t ne, int R, con
   }
 }
 
+// FP64-accurate R-column apply on the FP32 pipe (the refinement residual of the mixed
+// multi-column path): S_K = hi + lo as full row-major FP32 pairs [e][m][m], x split into
+// double-floats and staged lane-contiguous in shared memory, one compensated accumulator per
+// (row, lane). Warp = 32 / CWN elements x CWN columns.
+template <int DIM, int K>
+struct ApplyDfMCfg {   // warps per block: the staged x (M x 32 double-floats per warp) stays under 48 KB
+  static constexpr int WPB = Dims<DIM, K>::M * 32 * 8 * 4 <= 48 * 1024 ? 4 : 2;
+};
+
+template <int DIM, int K, int CWN>
+__global__ void __launch_bounds__(32 * ApplyDfMCfg<DIM, K>::WPB) apply_df_multi_kernel(int64_t ne, int R, const int32_t* __restrict__ elem_face,
+                                                             const int32_t* __restrict__ face_bnd,
+                                                             const float* __restrict__ Shi,
+                                                             const float* __restrict__ Slo,
+                                                             const double* __restrict__ x, double* __restrict__ slot) {
+  using Dm = Dims<DIM, K>;
+  constexpr int NF = Dm::NF, M = Dm::M, NFC = Dm::NFC, EPW = 32 / CWN, WPB = ApplyDfMCfg<DIM, K>::WPB;
+  __shared__ df2 xs[WPB][M][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = ((int64_t)blockIdx.x * WPB + w) * EPW + lane / CWN;
+  const int j = blockIdx.y * CWN + lane % CWN;
+  const bool live = e < ne && j < R;
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    const int fid = live ? elem_face[e * NFC + f] : 0;
+    const bool use = live && face_bnd[fid] < 0;
+#pragma unroll
+    for (int mm = 0; mm < NF; ++mm) xs[w][f * NF + mm][lane] = df_from(use ? x[((int64_t)fid * NF + mm) * R + j] : 0.0);
+  }
+  __syncwarp();
+  if (!live) return;
+  const float* Sh = Shi + e * (int64_t)(M * M);
+  const float* Sl = Slo + e * (int64_t)(M * M);
+  for (int r = 0; r < M; ++r) {
+    DfAcc acc;
+#pragma unroll 8
+    for (int c = 0; c < M; ++c) acc.fma(df2{__ldg(Sh + r * M + c), __ldg(Sl + r * M + c)}, xs[w][c][lane]);
+    slot[(e * M + r) * R + j] = acc.value();
+  }
+}
+
+// hi = fl32(S), lo = fl32(S - hi), full [e][m][m]
+static __global__ void split_df_kernel(int64_t n, const double* __restrict__ S, float* __restrict__ hi,
+                                       float* __restrict__ lo) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const float h = __double2float_rn(S[t]);
+    hi[t] = h;
+    lo[t] = __double2float_rn(S[t] - (double)h);
+  }
+}
+
 // FP32 S for the multi-column path: element-major packed upper triangles [e][P4] float4, so a
 // CTA streams its elements' blocks contiguously into shared memory.
 template <int DIM, int K>

@@ -62,6 +62,9 @@ def estimate_bytes(dim, N, k, R, prec="mixed"):
     per_elem = m * m * 8 + Np * Np * 8 + 320 + m * 8 + 7 * n * 8 * R + m * 8 * R
     if prec == "mixed":
         per_elem += p4 * 16 + m * 4 * R
+        if R > 1:
+            per_elem += m * m * 8          # FP32 pairs of S_K for the double-float residual
+        per_elem += Np * Np * 8 + 256      # double-float H^-1 and geometry (local solves)
         if R == 1:
             per_elem += p4 * 32         # double-float copy for the refinement apply
     per_face = Nf * R * (9 * 8 + 8 * 4 + 8) + 16
