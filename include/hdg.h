@@ -106,6 +106,13 @@ typedef struct {
                             /* each S_K serves all R columns                           */
   int32_t use_graphs;       /* nrhs > 1: replay captured CUDA graphs of Krylov        */
                             /* iteration chunks (fewer host launches; small problems)  */
+  int32_t guess_history;    /* nrhs = 1, hdg_step: number q of earlier stage solutions */
+                            /* (0..8) whose span gives the initial guess of each trace */
+                            /* solve: lam0 = sum c_i lam_i minimising |b - K lam0|     */
+                            /* (K lam_i = b_i at convergence, so only the stored right- */
+                            /* hand sides enter; damped normal equations, Sec. 2.4's   */
+                            /* least-squares guess over earlier solutions). 0: the     */
+                            /* polynomial extrapolation of the last traces (BDF only)  */
 } hdg_options;
 
 typedef struct {
@@ -129,7 +136,7 @@ typedef struct {
 } hdg_solve_info;
 
 /* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1,
- * use_graphs 0. */
+ * use_graphs 0, guess_history 6. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face

@@ -201,6 +201,7 @@ void launch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, in
 }
 
 hdg_status do_condense(hdg_ctx* c, double alpha) {
+  c->g_n = c->g_next = 0;   // the stored stage solutions belong to the previous operator
   if (c->vd) return vd_condense(c, alpha);
   if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(c, HDG_EINVAL, "alpha must be positive and finite");
   c->alpha = alpha;
@@ -730,7 +731,9 @@ hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, 
   if (s) return s;
   // Krylov right-hand side b = sgn r = -sgn sum_K C_K A_K^{-1} F~_K
   if ((s = faces_from_slots(c, -c->sgn, c->d_b))) return s;
+  if ((s = guess_before(c))) return s;
   if ((s = cg_solve(c, c->d_b, c->d_lam, info))) return s;
+  if ((s = guess_after(c))) return s;
   HDG_DISPATCH(c, launch_local, c, 1, (const double*)nullptr, hist, tt, c->d_lam, uout);
   return check_launch(c, "recover");
 }
@@ -764,6 +767,88 @@ void dirk3(double a[3][3], double b[3], double cc[3]) {
 
 }  // namespace
 
+// ---- least-squares initial guess over earlier stage solutions (same alpha)
+// The stored pairs satisfy K lam_i = b_i to the solver tolerance, so minimising
+// |b - K sum c_i lam_i| over the span needs only the Gram matrix of the stored b_i and their
+// dot products with the new b: damped normal equations (G + mu I) c = g, solved on the host.
+hdg_status guess_setup(hdg_ctx* c, const uint8_t* host_mask) {
+  c->g_q = 0;
+  if (c->opt.guess_history <= 0 || c->R != 1) return HDG_OK;
+  const int q = std::min(c->opt.guess_history, 8);
+  const size_t n = (size_t)c->ntr;
+  hdg_status s;
+  if ((s = dalloc(c, &c->d_gb, q * n))) return s;
+  if ((s = dalloc(c, &c->d_gl, q * n))) return s;
+  if ((s = dalloc(c, &c->d_gdots, 9))) return s;
+  if ((s = dalloc(c, &c->d_gpart, (size_t)c->nb_red * 9))) return s;
+  if ((s = dalloc(c, &c->d_intmask, n))) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_intmask, host_mask, n, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->g_q = q;
+  c->g_n = c->g_next = 0;
+  return HDG_OK;
+}
+
+hdg_status guess_before(hdg_ctx* c) {
+  if (!c->g_q) return HDG_OK;
+  const int64_t n = c->ntr;
+  const int m = c->g_n, nb = c->nb_red;
+  c->n_launch += 2;
+  dots_ring_kernel<<<nb, 256, 0, c->stream>>>(n, m, n, c->d_gb, c->d_b, c->d_gpart);
+  dots_final_kernel<<<1, 256, 0, c->stream>>>(nb, m, c->d_gpart, c->d_gdots);
+  double dots[9];
+  CUDA_TRY(c, cudaMemcpyAsync(dots, c->d_gdots, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int i = 0; i <= m; ++i) c->g_dots[i] = dots[i];
+  if (m == 0) return HDG_OK;
+  // (G + mu I) x = g by Cholesky; mu relative to the largest diagonal entry
+  double G[8][8], L[8][8] = {}, y[8], x[8], dmax = 0.0;
+  for (int i = 0; i < m; ++i) dmax = std::max(dmax, c->g_gram[i][i]);
+  if (!(dmax > 0.0)) return HDG_OK;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) G[i][j] = c->g_gram[i][j] + (i == j ? 1e-13 * dmax : 0.0);
+  for (int j = 0; j < m; ++j) {
+    double d = G[j][j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0)) return HDG_OK;   // keep the current guess
+    L[j][j] = std::sqrt(d);
+    for (int i = j + 1; i < m; ++i) {
+      double v = G[i][j];
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+      L[i][j] = v / L[j][j];
+    }
+  }
+  for (int i = 0; i < m; ++i) {
+    double v = dots[i];
+    for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
+    y[i] = v / L[i][i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int k = i + 1; k < m; ++k) v -= L[k][i] * x[k];
+    x[i] = v / L[i][i];
+  }
+  Coef8 cf{};
+  for (int i = 0; i < m; ++i) cf.c[i] = x[i];
+  c->n_launch += 1;
+  lincomb_ring_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, m, n, c->d_gl, cf, c->d_intmask, c->d_lam);
+  return check_launch(c, "guess");
+}
+
+hdg_status guess_after(hdg_ctx* c) {
+  if (!c->g_q) return HDG_OK;
+  const int64_t n = c->ntr;
+  const int s = c->g_next;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_gb + (int64_t)s * n, c->d_b, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_gl + (int64_t)s * n, c->d_lam, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  for (int i = 0; i < c->g_n; ++i)
+    if (i != s) c->g_gram[s][i] = c->g_gram[i][s] = c->g_dots[i];
+  c->g_gram[s][s] = c->g_dots[c->g_n];
+  c->g_next = (s + 1) % c->g_q;
+  c->g_n = std::min(c->g_n + 1, c->g_q);
+  return HDG_OK;
+}
+
 extern "C" {
 
 void hdg_default_options(hdg_options* o) {
@@ -776,6 +861,7 @@ void hdg_default_options(hdg_options* o) {
   o->max_sweeps = 20;
   o->nrhs = 1;
   o->use_graphs = 0;
+  o->guess_history = 6;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -1023,6 +1109,12 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   CUDA_TRY(c, cudaMemsetAsync(c->d_u, 0, (size_t)ne * c->n * R * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_uprev, 0, (size_t)ne * c->n * R * 8, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  {
+    std::vector<uint8_t> mask((size_t)c->ntr);
+    for (int64_t f = 0; f < nf; ++f)
+      for (int mm = 0; mm < c->Nf; ++mm) mask[(size_t)f * c->Nf + mm] = c->sk.face_bnd[f] < 0 ? 1 : 0;
+    if ((s = guess_setup(c, mask.data()))) return s;
+  }
   c->have_state = true;
   return HDG_OK;
 }
@@ -1279,6 +1371,7 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
   c->t = t;
   c->have_state = true;
   c->n_lam_hist = 0;
+  c->g_n = c->g_next = 0;
   return HDG_OK;
 }
 

@@ -110,6 +110,13 @@ struct hdg_ctx {
   // per-element / per-face sizes on a variable-degree mesh)
   int64_t nfld = 0, ntr = 0;
   int64_t nschur = 0, nslot = 0;   // S_K entries and element trace entries summed over the elements
+  // least-squares initial guess: ring of the last q stage right-hand sides b_i and solutions
+  // lam_i (same alpha), their Gram matrix on the host, the interior-entry mask
+  double *d_gb = nullptr, *d_gl = nullptr, *d_gdots = nullptr, *d_gpart = nullptr;
+  uint8_t* d_intmask = nullptr;
+  int g_q = 0, g_n = 0, g_next = 0;   // capacity, stored pairs, next slot
+  double g_gram[8][8] = {};
+  double g_dots[9] = {};   // dots of the current b with the stored b_i, then (b, b)
   VarDeg* vd = nullptr;
 };
 
@@ -233,6 +240,10 @@ void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
 
 // variable-degree elastic path (vardeg.cu)
 hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k);
+// least-squares initial guess around a stage solve (api.cu); both are no-ops when disabled
+hdg_status guess_setup(hdg_ctx* c, const uint8_t* host_mask);
+hdg_status guess_before(hdg_ctx* c);
+hdg_status guess_after(hdg_ctx* c);
 hdg_status vd_condense(hdg_ctx* c, double alpha);
 hdg_status vd_stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info);
 hdg_status vd_trace_apply(hdg_ctx* c, const double* x, double* y);

@@ -634,6 +634,47 @@ static __global__ void cg_direction_kernel(int64_t n, int nb, int parity, int it
   }
 }
 
+// Least-squares initial guess over stored stage solutions. ring: [Q][n] contiguous.
+// dots_ring_kernel: block partials of (v_i, w) for i < q and of (w, w), part[blk][q + 1].
+static __global__ void dots_ring_kernel(int64_t n, int q, int64_t stride, const double* __restrict__ ring,
+                                        const double* __restrict__ w, double* __restrict__ part) {
+  __shared__ double red[8];
+  double acc[9];
+  for (int i = 0; i <= q; ++i) acc[i] = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double wv = w[t];
+    for (int i = 0; i < q; ++i) acc[i] += ring[i * stride + t] * wv;
+    acc[q] += wv * wv;
+  }
+  for (int i = 0; i <= q; ++i) {
+    const double s = block_sum256(acc[i], red);
+    if (threadIdx.x == 0) part[blockIdx.x * (q + 1) + i] = s;
+  }
+}
+
+static __global__ void dots_final_kernel(int nb, int q, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double red[8];
+  for (int i = 0; i <= q; ++i) {
+    const double s = reduce_partials(part + i, nb, q + 1, red);
+    if (threadIdx.x == 0) out[i] = s;
+  }
+}
+
+struct Coef8 {
+  double c[8];
+};
+
+// out[t] = sum_i c_i ring[i][t] on interior trace entries (mask != 0); boundary entries untouched
+static __global__ void lincomb_ring_kernel(int64_t n, int q, int64_t stride, const double* __restrict__ ring, Coef8 c,
+                                           const uint8_t* __restrict__ mask, double* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    if (!mask[t]) continue;
+    double s = 0.0;
+    for (int i = 0; i < q; ++i) s += c.c[i] * ring[i * stride + t];
+    out[t] = s;
+  }
+}
+
 // out = sum_q c_q in_q (up to four inputs), elementwise.
 static __global__ void combine_kernel(int64_t n, double c0, const double* __restrict__ i0, double c1,
                                const double* __restrict__ i1, double c2, const double* __restrict__ i2, double c3,

@@ -601,6 +601,11 @@ hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k) {
   CUDA_TRY(c, cudaMemsetAsync(c->d_uprev, 0, nfld * 8, c->stream));
   // the host index arrays above are released at return: wait for their uploads
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  {
+    std::vector<uint8_t> mask((size_t)c->ntr);
+    for (int64_t d = 0; d < c->ntr; ++d) mask[d] = dslot[2 * d] >= 0 ? 1 : 0;
+    if ((s = guess_setup(c, mask.data()))) return s;
+  }
   c->have_state = true;
   return HDG_OK;
 }
@@ -657,7 +662,9 @@ hdg_status vd_stage_solve(hdg_ctx* c, const double* hist, double tt, double* uou
   hdg_status s = check_launch(c, "vd_rhs");
   if (s) return s;
   if ((s = vd_gather(c, c->d_slot, -c->sgn, c->d_b))) return s;
+  if ((s = guess_before(c))) return s;
   if ((s = vd_solve(c, c->d_b, c->d_lam, info))) return s;
+  if ((s = guess_after(c))) return s;
   vd_local(c, 1, nullptr, hist, c->d_lam, uout);
   return check_launch(c, "vd_recover");
 }

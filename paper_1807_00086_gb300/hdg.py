@@ -35,7 +35,8 @@ class Material(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32),
-                ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32), ("use_graphs", c_int32)]
+                ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32), ("use_graphs", c_int32),
+                ("guess_history", c_int32)]
 
 
 class Sizes(ctypes.Structure):
