@@ -136,7 +136,7 @@ typedef struct {
 } hdg_solve_info;
 
 /* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1,
- * use_graphs 0, guess_history 6. */
+ * use_graphs 0, guess_history 8. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face

@@ -861,7 +861,7 @@ void hdg_default_options(hdg_options* o) {
   o->max_sweeps = 20;
   o->nrhs = 1;
   o->use_graphs = 0;
-  o->guess_history = 6;
+  o->guess_history = 8;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }

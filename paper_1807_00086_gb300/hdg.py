@@ -149,7 +149,7 @@ class Solver:
 
     def __init__(self, vert, elem, k, tau, rho, c=None, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
                  inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None, lam=None, mu=None,
-                 elem_k=None):
+                 elem_k=None, guess_history=None):
         """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu).
         elem_k: per-element degrees (3D elastic); fields and traces are then flat vectors."""
         import torch
@@ -182,6 +182,8 @@ class Solver:
             opt.max_sweeps = max_sweeps
         opt.nrhs = nrhs
         opt.use_graphs = 1 if use_graphs else 0
+        if guess_history is not None:
+            opt.guess_history = guess_history
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream()
