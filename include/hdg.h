@@ -106,13 +106,15 @@ typedef struct {
                             /* each S_K serves all R columns                           */
   int32_t use_graphs;       /* nrhs > 1: replay captured CUDA graphs of Krylov        */
                             /* iteration chunks (fewer host launches; small problems)  */
-  int32_t guess_history;    /* nrhs = 1, hdg_step: number q of earlier stage solutions */
+  int32_t guess_history;    /* hdg_step: number q of earlier stage solutions per column */
                             /* (0..8) whose span gives the initial guess of each trace */
                             /* solve: lam0 = sum c_i lam_i minimising |b - K lam0|     */
                             /* (K lam_i = b_i at convergence, so only the stored right- */
                             /* hand sides enter; damped normal equations, Sec. 2.4's   */
-                            /* least-squares guess over earlier solutions). 0: the     */
-                            /* polynomial extrapolation of the last traces (BDF only)  */
+                            /* least-squares guess over earlier solutions); with R     */
+                            /* columns each column has its own fit; hdg_reset_column  */
+                            /* drops a column's pairs. 0: the polynomial extrapolation */
+                            /* of the last traces (BDF only)                           */
 } hdg_options;
 
 typedef struct {

@@ -719,7 +719,9 @@ hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, 
     HDG_DISPATCH(c, mlaunch_gather, c, (const double*)c->d_mslot, 1.0, c->d_b);
     hdg_status s = check_launch(c, "rhs_multi");
     if (s) return s;
+    if ((s = guess_before(c))) return s;
     if ((s = msolve(c, c->d_b, c->d_lam, info))) return s;
+    if ((s = guess_after(c))) return s;
     HDG_DISPATCH(c, mlaunch_local, c, 1, (const double*)nullptr, hist, tt, c->d_lam, uout);
     return check_launch(c, "recover_multi");
   }
@@ -770,56 +772,54 @@ void dirk3(double a[3][3], double b[3], double cc[3]) {
 // ---- least-squares initial guess over earlier stage solutions (same alpha)
 // The stored pairs satisfy K lam_i = b_i to the solver tolerance, so minimising
 // |b - K sum c_i lam_i| over the span needs only the Gram matrix of the stored b_i and their
-// dot products with the new b: damped normal equations (G + mu I) c = g, solved on the host.
+// dot products with the new b: damped normal equations (G + mu I) c = g, solved on the host,
+// per column when there are several right-hand sides.
 hdg_status guess_setup(hdg_ctx* c, const uint8_t* host_mask) {
   c->g_q = 0;
-  if (c->opt.guess_history <= 0 || c->R != 1) return HDG_OK;
-  const int q = std::min(c->opt.guess_history, 8);
-  const size_t n = (size_t)c->ntr;
+  if (c->opt.guess_history <= 0) return HDG_OK;
+  const int q = std::min(c->opt.guess_history, 8), R = c->R;
+  const size_t n = (size_t)c->ntr * R;
   hdg_status s;
   if ((s = dalloc(c, &c->d_gb, q * n))) return s;
   if ((s = dalloc(c, &c->d_gl, q * n))) return s;
-  if ((s = dalloc(c, &c->d_gdots, 9))) return s;
-  if ((s = dalloc(c, &c->d_gpart, (size_t)c->nb_red * 9))) return s;
-  if ((s = dalloc(c, &c->d_intmask, n))) return s;
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_intmask, host_mask, n, cudaMemcpyHostToDevice, c->stream));
+  if ((s = dalloc(c, &c->d_gdots, (size_t)9 * R))) return s;
+  if ((s = dalloc(c, &c->d_gpart, (size_t)c->nb_red * 9 * R))) return s;
+  if ((s = dalloc(c, &c->d_intmask, (size_t)c->ntr))) return s;
+  if (R > 1) {
+    if ((s = dalloc(c, &c->d_gcoef, (size_t)8 * R))) return s;
+    c->gm_gram.assign((size_t)R * 64, 0.0);
+    c->gm_dots.assign((size_t)9 * R, 0.0);
+    c->gm_coef.assign((size_t)8 * R, 0.0);
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_intmask, host_mask, (size_t)c->ntr, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_gb, 0, q * n * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_gl, 0, q * n * 8, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->g_q = q;
   c->g_n = c->g_next = 0;
   return HDG_OK;
 }
 
-hdg_status guess_before(hdg_ctx* c) {
-  if (!c->g_q) return HDG_OK;
-  const int64_t n = c->ntr;
-  const int m = c->g_n, nb = c->nb_red;
-  c->n_launch += 2;
-  dots_ring_kernel<<<nb, 256, 0, c->stream>>>(n, m, n, c->d_gb, c->d_b, c->d_gpart);
-  dots_final_kernel<<<1, 256, 0, c->stream>>>(nb, m, c->d_gpart, c->d_gdots);
-  double dots[9];
-  CUDA_TRY(c, cudaMemcpyAsync(dots, c->d_gdots, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  for (int i = 0; i <= m; ++i) c->g_dots[i] = dots[i];
-  if (m == 0) return HDG_OK;
-  // (G + mu I) x = g by Cholesky; mu relative to the largest diagonal entry
-  double G[8][8], L[8][8] = {}, y[8], x[8], dmax = 0.0;
-  for (int i = 0; i < m; ++i) dmax = std::max(dmax, c->g_gram[i][i]);
-  if (!(dmax > 0.0)) return HDG_OK;
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) G[i][j] = c->g_gram[i][j] + (i == j ? 1e-13 * dmax : 0.0);
+namespace {
+// (G + mu I) x = g for an m x m Gram matrix G (row stride 8), mu = 1e-13 max diag; false when
+// G is zero or the factorisation breaks down (the caller keeps its current guess)
+bool ls_solve(int m, const double* G, const double* g, double* x) {
+  double L[8][8] = {}, y[8], dmax = 0.0;
+  for (int i = 0; i < m; ++i) dmax = std::max(dmax, G[i * 8 + i]);
+  if (!(dmax > 0.0)) return false;
   for (int j = 0; j < m; ++j) {
-    double d = G[j][j];
+    double d = G[j * 8 + j] + 1e-13 * dmax;
     for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-    if (!(d > 0.0)) return HDG_OK;   // keep the current guess
+    if (!(d > 0.0)) return false;
     L[j][j] = std::sqrt(d);
     for (int i = j + 1; i < m; ++i) {
-      double v = G[i][j];
+      double v = G[i * 8 + j];
       for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
       L[i][j] = v / L[j][j];
     }
   }
   for (int i = 0; i < m; ++i) {
-    double v = dots[i];
+    double v = g[i];
     for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
     y[i] = v / L[i][i];
   }
@@ -828,25 +828,90 @@ hdg_status guess_before(hdg_ctx* c) {
     for (int k = i + 1; k < m; ++k) v -= L[k][i] * x[k];
     x[i] = v / L[i][i];
   }
-  Coef8 cf{};
-  for (int i = 0; i < m; ++i) cf.c[i] = x[i];
+  return true;
+}
+}  // namespace
+
+hdg_status guess_before(hdg_ctx* c) {
+  if (!c->g_q) return HDG_OK;
+  const int R = c->R, m = c->g_n, nb = c->nb_red;
+  const int64_t n = c->ntr * (int64_t)R;
+  if (R == 1) {
+    c->n_launch += 2;
+    dots_ring_kernel<<<nb, 256, 0, c->stream>>>(n, m, n, c->d_gb, c->d_b, c->d_gpart);
+    dots_final_kernel<<<1, 256, 0, c->stream>>>(nb, m, c->d_gpart, c->d_gdots);
+    CUDA_TRY(c, cudaMemcpyAsync(c->g_dots, c->d_gdots, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (m == 0) return HDG_OK;
+    double x[8];
+    if (!ls_solve(m, &c->g_gram[0][0], c->g_dots, x)) return HDG_OK;
+    Coef8 cf{};
+    for (int i = 0; i < m; ++i) cf.c[i] = x[i];
+    c->n_launch += 1;
+    lincomb_ring_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, m, n, c->d_gl, cf, c->d_intmask, c->d_lam);
+    return check_launch(c, "guess");
+  }
+  c->n_launch += 2;
+  mdots_ring_kernel<<<nb, 256, 0, c->stream>>>(n, R, m, n, c->d_gb, c->d_b, c->d_gpart);
+  mdots_final_kernel<<<1, 256, 0, c->stream>>>(nb, R, m, c->d_gpart, c->d_gdots);
+  CUDA_TRY(c, cudaMemcpyAsync(c->gm_dots.data(), c->d_gdots, (size_t)(m + 1) * R * sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (m == 0) return HDG_OK;
+  bool any = false;
+  for (int j = 0; j < R; ++j) {
+    double g[8], x[8];
+    for (int i = 0; i < m; ++i) g[i] = c->gm_dots[(size_t)i * R + j];
+    const bool ok = ls_solve(m, &c->gm_gram[(size_t)j * 64], g, x);
+    any = any || ok;
+    // a column without a usable history (all its pairs reset) keeps its current guess: NaN
+    // in its first coefficient tells the combination kernel to skip it
+    for (int i = 0; i < 8; ++i) c->gm_coef[(size_t)i * R + j] = ok && i < m ? x[i] : 0.0;
+    if (!ok) c->gm_coef[(size_t)0 * R + j] = std::nan("");
+  }
+  if (!any) return HDG_OK;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_gcoef, c->gm_coef.data(), (size_t)8 * R * sizeof(double), cudaMemcpyHostToDevice,
+                              c->stream));
   c->n_launch += 1;
-  lincomb_ring_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, m, n, c->d_gl, cf, c->d_intmask, c->d_lam);
-  return check_launch(c, "guess");
+  mlincomb_ring_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, R, m, n, c->d_gl, c->d_gcoef, c->d_intmask, c->d_lam);
+  return check_launch(c, "guess_multi");
 }
 
 hdg_status guess_after(hdg_ctx* c) {
   if (!c->g_q) return HDG_OK;
-  const int64_t n = c->ntr;
+  const int R = c->R;
+  const int64_t n = c->ntr * (int64_t)R;
   const int s = c->g_next;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_gb + (int64_t)s * n, c->d_b, n * 8, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_gl + (int64_t)s * n, c->d_lam, n * 8, cudaMemcpyDeviceToDevice, c->stream));
-  for (int i = 0; i < c->g_n; ++i)
-    if (i != s) c->g_gram[s][i] = c->g_gram[i][s] = c->g_dots[i];
-  c->g_gram[s][s] = c->g_dots[c->g_n];
+  if (R == 1) {
+    for (int i = 0; i < c->g_n; ++i)
+      if (i != s) c->g_gram[s][i] = c->g_gram[i][s] = c->g_dots[i];
+    c->g_gram[s][s] = c->g_dots[c->g_n];
+  } else {
+    for (int j = 0; j < R; ++j) {
+      double* G = &c->gm_gram[(size_t)j * 64];
+      for (int i = 0; i < c->g_n; ++i)
+        if (i != s) G[s * 8 + i] = G[i * 8 + s] = c->gm_dots[(size_t)i * R + j];
+      G[s * 8 + s] = c->gm_dots[(size_t)c->g_n * R + j];
+    }
+  }
   c->g_next = (s + 1) % c->g_q;
   c->g_n = std::min(c->g_n + 1, c->g_q);
   return HDG_OK;
+}
+
+// a column that restarts (serving: a new request in a slot) drops its stored pairs
+void guess_reset_column(hdg_ctx* c, int j) {
+  if (!c->g_q || c->R == 1) return;
+  // zero_column_kernel takes the entries of one column (ntr); a slot holds ntr x R values
+  const int64_t per_col = c->ntr, slot = c->ntr * (int64_t)c->R;
+  for (int i = 0; i < c->g_q; ++i) {
+    c->n_launch += 2;
+    zero_column_kernel<<<grid_for(c, per_col), 256, 0, c->stream>>>(per_col, c->R, j, c->d_gb + (int64_t)i * slot);
+    zero_column_kernel<<<grid_for(c, per_col), 256, 0, c->stream>>>(per_col, c->R, j, c->d_gl + (int64_t)i * slot);
+  }
+  std::fill(c->gm_gram.begin() + (size_t)j * 64, c->gm_gram.begin() + (size_t)(j + 1) * 64, 0.0);
 }
 
 extern "C" {
@@ -1498,6 +1563,7 @@ hdg_status hdg_reset_column(hdg_ctx* c, int32_t j) {
     c->n_launch += 1;
     zero_column_kernel<<<grid_for(c, nt), 256, 0, c->stream>>>(nt, c->R, j, a);
   }
+  guess_reset_column(c, j);
   return check_launch(c, "reset_column");
 }
 

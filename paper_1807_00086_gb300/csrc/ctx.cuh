@@ -117,6 +117,9 @@ struct hdg_ctx {
   int g_q = 0, g_n = 0, g_next = 0;   // capacity, stored pairs, next slot
   double g_gram[8][8] = {};
   double g_dots[9] = {};   // dots of the current b with the stored b_i, then (b, b)
+  // the same per column (nrhs > 1): Gram matrices [R][8][8], dots [9][R], coefficients [8][R]
+  std::vector<double> gm_gram, gm_dots, gm_coef;
+  double* d_gcoef = nullptr;
   VarDeg* vd = nullptr;
 };
 
@@ -244,6 +247,7 @@ hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k);
 hdg_status guess_setup(hdg_ctx* c, const uint8_t* host_mask);
 hdg_status guess_before(hdg_ctx* c);
 hdg_status guess_after(hdg_ctx* c);
+void guess_reset_column(hdg_ctx* c, int j);
 hdg_status vd_condense(hdg_ctx* c, double alpha);
 hdg_status vd_stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info);
 hdg_status vd_trace_apply(hdg_ctx* c, const double* x, double* y);

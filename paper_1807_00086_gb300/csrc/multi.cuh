@@ -400,6 +400,55 @@ __device__ __forceinline__ void col_partials(const double* __restrict__ part, in
   block_cols(s, R, red);
 }
 
+// Per-column least-squares initial guess over stored pairs (b_i, lam_i), i < q, ring
+// [q][n R] (column innermost). mdots_ring_kernel: block partials of (b_i, w)_j and (w, w)_j
+// per column, part[blk][q + 1][R]; the grid stride is a multiple of R, so each thread keeps
+// one column.
+static __global__ void mdots_ring_kernel(int64_t n, int R, int q, int64_t stride, const double* __restrict__ ring,
+                                         const double* __restrict__ w, double* __restrict__ part) {
+  __shared__ double red[256];
+  double acc[9];
+  for (int i = 0; i <= q; ++i) acc[i] = 0.0;
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256) {
+    const double wv = w[t];
+    for (int i = 0; i < q; ++i) acc[i] += ring[i * stride + t] * wv;
+    acc[q] += wv * wv;
+  }
+  for (int i = 0; i <= q; ++i) {
+    block_cols(acc[i], R, red);
+    if (threadIdx.x < R) part[((int64_t)blockIdx.x * (q + 1) + i) * R + threadIdx.x] = red[threadIdx.x];
+  }
+}
+
+static __global__ void mdots_final_kernel(int nb, int R, int q, const double* __restrict__ part,
+                                          double* __restrict__ out) {
+  __shared__ double red[256];
+  for (int i = 0; i <= q; ++i) {
+    // column sums of part[b][i][j] over b: stride (q + 1) R between blocks
+    const int G = 256 / R, j = threadIdx.x & (R - 1), g = threadIdx.x / R;
+    double s = 0.0;
+    for (int b = g; b < nb; b += G) s += part[((int64_t)b * (q + 1) + i) * R + j];
+    block_cols(s, R, red);
+    if (threadIdx.x < R) out[i * R + threadIdx.x] = red[threadIdx.x];
+  }
+}
+
+// out[t] = sum_i coef[i][j] ring[i][t] (j = t mod R) on interior entries (mask per trace entry);
+// a column whose coef[0][j] is NaN (no usable history) keeps its current values
+static __global__ void mlincomb_ring_kernel(int64_t n, int R, int q, int64_t stride, const double* __restrict__ ring,
+                                            const double* __restrict__ coef, const uint8_t* __restrict__ mask,
+                                            double* __restrict__ out) {
+  const int lg = __ffs(R) - 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    if (!mask[t >> lg]) continue;
+    const int j = (int)(t & (R - 1));
+    if (isnan(coef[j])) continue;
+    double s = 0.0;
+    for (int i = 0; i < q; ++i) s += coef[i * R + j] * ring[i * stride + t];
+    out[t] = s;
+  }
+}
+
 struct MScal {              // per-column Krylov scalars, arrays of R entries
   double *rho0, *rho1, *alpha, *rr, *bb, *tol2;
   int* conv;                // per column: converged

@@ -68,6 +68,7 @@ def estimate_bytes(dim, N, k, R, prec="mixed"):
         if R == 1:
             per_elem += p4 * 32         # double-float copy for the refinement apply
     per_face = Nf * R * (9 * 8 + 8 * 4 + 8) + 16
+    per_face += Nf * R * 8 * 2 * 8          # least-squares guess: 8 stored (b, lam) pairs
     return int(ne * per_elem + nf * per_face + (1 << 20))
 
 
