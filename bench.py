@@ -488,7 +488,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default=None, choices=["fp64", "mixed", "mixed16"],
-                    help="default: mixed16 for the single-source acoustic workload, else mixed")
+                    help="default: mixed16 for the single-source acoustic and the mixed-degree elastic workloads, "
+                         "else mixed")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the plain FP64 comparison run that follows a mixed-precision measurement")
     ap.add_argument("--rtol", type=float, default=1e-12)
@@ -516,7 +517,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.prec is None:
-        args.prec = "mixed16" if (args.physics == "acoustic" and args.nrhs == 1 and not args.serve) else "mixed"
+        args.prec = "mixed16" if ((args.physics == "acoustic" and args.nrhs == 1 and not args.serve) or
+                                  (args.physics == "elastic" and args.mixed_degree)) else "mixed"
     if args.inner_rtol is None:
         args.inner_rtol = 1e-3 if args.prec == "mixed16" else (1e-4 if args.nrhs > 1 else 3e-6)
     if args.serve:

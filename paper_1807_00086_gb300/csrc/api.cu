@@ -584,7 +584,11 @@ hdg_status mcg(hdg_ctx* c, const TV* b, TV* x, TV* r, TV* z, TV* p, TV* q, TV* s
   } else {
     HDG_DISPATCH(c, mlaunch_init32, c, nullptr, (const float*)b, (const float*)dinv, (float*)r, (float*)z, (float*)p);
   }
-  mcols_init<<<1, 256, 0, c->stream>>>(nb, c->R, rtol, x0_zero ? 1 : 0, c->d_part, mscal(c));
+  if (sizeof(TV) == 4)   // inner solve of a refinement sweep: per-column relaxed tolerance
+    mcols_init<<<1, 256, 0, c->stream>>>(nb, c->R, rtol, x0_zero ? 1 : 0, c->d_part, mscal(c), c->d_mrr2, c->d_mbb2,
+                                         c->opt.rtol);
+  else
+    mcols_init<<<1, 256, 0, c->stream>>>(nb, c->R, rtol, x0_zero ? 1 : 0, c->d_part, mscal(c));
   if ((s = check_launch(c, "mcg_init"))) return s;
   const int maxit = c->opt.maxit;
   const int chk = std::max(1, c->opt.check_every);

@@ -595,7 +595,12 @@ __global__ void __launch_bounds__(256) minit_kernel(int nf, int R, const int32_t
 }
 
 // column scalars after minit: rho0 = rz, rr, bb, tol2 = rtol^2 * (bb or rr when bb_from_rr)
-static __global__ void mcols_init(int nb, int R, double rtol, int tol_from_rr, const double* __restrict__ part, MScal sc) {
+// With outer_rr / outer_bb (the columns' refinement residual and right-hand side norms, the
+// inner solve of a refinement sweep), a column's inner tolerance is relaxed to
+// min(0.5, max(rtol, 0.25 outer_rtol / |r|/|b|)): the last sweep gains only what is left.
+static __global__ void mcols_init(int nb, int R, double rtol, int tol_from_rr, const double* __restrict__ part, MScal sc,
+                                  const double* __restrict__ outer_rr = nullptr,
+                                  const double* __restrict__ outer_bb = nullptr, double outer_rtol = 0.0) {
   __shared__ int notconv;
   if (threadIdx.x == 0) notconv = 0;
   __syncthreads();
@@ -608,7 +613,10 @@ static __global__ void mcols_init(int nb, int R, double rtol, int tol_from_rr, c
   for (int j = threadIdx.x; j < R; j += blockDim.x) {
     const double rz = rzs[j], rr = rrs[j], bb = red[j];
     sc.rho0[j] = rz; sc.rho1[j] = 0.0; sc.rr[j] = rr; sc.bb[j] = bb;
-    sc.tol2[j] = rtol * rtol * (tol_from_rr ? rr : bb);
+    double tol = rtol;
+    if (outer_rr && outer_bb[j] > 0.0 && outer_rr[j] > 0.0)
+      tol = fmin(0.5, fmax(rtol, 0.25 * outer_rtol / sqrt(outer_rr[j] / outer_bb[j])));
+    sc.tol2[j] = tol * tol * (tol_from_rr ? rr : bb);
     const int c = rr <= sc.tol2[j];
     sc.conv[j] = c;
     if (!c) atomicAdd(&notconv, 1);
