@@ -548,3 +548,68 @@ def standing_mode(dim):
         return out
 
     return fields
+
+
+# ----------------------------------------------------------------------------- local post-processing
+
+def postprocess_pressure(prob, u, lam):
+    """Element-local post-processed pressure p* in P_{k+1}(K) (Sec. 1: the HDG local
+    post-processing step that gives a superconvergent scalar; the paper names the step but
+    writes no formula for this scheme).
+
+    Reading (the standard HDG post-processing with the method's own discrete gradient):
+      1. q_h in [P_k(K)]^d is the gradient of (p_h, p_hat_h) that the local momentum
+         equation defines: (q_h, r)_K = -(p_h, div r)_K + <p_hat_h, r.n>_dK for every
+         r in [P_k(K)]^d, so that rho dv_h/dt = -q_h;
+      2. p* solves (grad p*, grad w)_K = (q_h, grad w)_K for every w in P_{k+1}(K) and
+         (p*, 1)_K = (p_h, 1)_K (the constant mode of the Neumann problem).
+    u: [Ne, (d+1) Np] fields (pressure block first); lam: [Nfaces, Nf] traces including the
+    Dirichlet values on boundary faces. Returns [Ne, Np(k+1)] coefficients of p* in the
+    orthonormal degree-(k+1) basis of oracle/reference.py.
+    """
+    dim, k, Np, Nf = prob.sk.dim, prob.k, prob.Np, prob.Nf
+    Np1 = ref.n_modes(dim, k + 1)
+    xi, wq = ref.simplex_rule(dim, k + 3)
+    V, G = ref.basis(dim, k, xi)
+    V1, G1 = ref.basis(dim, k + 1, xi)
+    eta, wf = ref.simplex_rule(dim - 1, k + 3)
+    U, _ = ref.basis(dim - 1, k, eta)
+    out = np.zeros((prob.sk.elem.shape[0], Np1))
+    for e, bl in enumerate(prob.blocks):
+        Gx = np.einsum("qir,rj->qij", G, bl.Jinv)       # grad phi_i at the points, [nq, Np, d]
+        G1x = np.einsum("qir,rj->qij", G1, bl.Jinv)
+        w = wq * bl.detJ
+        ph = V @ u[e, :Np]                              # p_h at the points
+        # step 1: the discrete gradient q_h, one component at a time
+        M = np.einsum("q,qi,ql->il", w, V, V)
+        q = np.zeros((dim, Np))
+        for j in range(dim):
+            rhs = -np.einsum("q,q,qi->i", w, ph, Gx[:, :, j])
+            for f in range(dim + 1):
+                Y = bl.X[face_local_vertices(dim, f)]
+                xq = Y[0] + eta @ (Y[1:] - Y[0])
+                Vf, _ = ref.basis(dim, k, (xq - bl.X[0]) @ bl.Jinv.T)
+                phat = U @ lam[prob.sk.elem_face[e, f]]
+                rhs += bl.normal[f, j] * np.einsum("q,q,qi->i", wf * face_frame(Y), phat, Vf)
+            q[j] = np.linalg.solve(M, rhs)
+        qx = V @ q.T                                    # q_h at the points, [nq, d]
+        # step 2: Neumann problem in P_{k+1}; the constant mode's row (all zero in the
+        # stiffness) carries the mean condition instead
+        A = np.einsum("q,qid,qld->il", w, G1x, G1x)
+        b = np.einsum("q,qd,qid->i", w, qx, G1x)
+        A[0] = np.einsum("q,ql->l", w, V1)
+        b[0] = np.sum(w * ph)
+        out[e] = np.linalg.solve(A, b)
+    return out
+
+
+def l2_error_post(prob, pstar, exact, nq=None):
+    """|| p* - exact(x)[0] ||_{L2(Omega)} for degree-(k+1) coefficients p*."""
+    dim, k = prob.sk.dim, prob.k
+    xi, wq = ref.simplex_rule(dim, nq or k + 5)
+    V1, _ = ref.basis(dim, k + 1, xi)
+    err = 0.0
+    for e, bl in enumerate(prob.blocks):
+        x = bl.X[0] + xi @ (bl.X[1:] - bl.X[0])
+        err += np.sum(wq * bl.detJ * (V1 @ pstar[e] - exact(x)[:, 0]) ** 2)
+    return math.sqrt(err)
