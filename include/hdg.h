@@ -182,6 +182,22 @@ hdg_status hdg_trace_solve(hdg_ctx* ctx, const double* r_dev, double* lam_dev, h
  * faces (boundary entries = Dirichlet trace). F_dev, u_dev: [n_elem][n]. */
 hdg_status hdg_recover(hdg_ctx* ctx, const double* F_dev, const double* lam_dev, double* u_dev);
 
+/* Element-local post-processing of the acoustic pressure into P_{k+1} (the local,
+ * superconvergent post-processing step of HDG methods, Sec. 1; the paper writes no formula
+ * for this scheme, so this is the standard one with the method's own discrete gradient).
+ * For every element K, p* in P_{k+1}(K) solves
+ *   (grad p*, grad w)_K = (q_h, grad w)_K  for all w in P_{k+1}(K),  (p*, 1)_K = (p_h, 1)_K,
+ * where q_h in [P_k(K)]^d is given by the local momentum equation,
+ *   (q_h, r)_K = -(p_h, div r)_K + <p_hat_h, r.n>_dK  for all r in [P_k(K)]^d.
+ * u_dev: fields [n_elem][n] (pressure block first); lam_dev: traces [n_faces][Nf] with the
+ * Dirichlet values on boundary faces (as hdg_get_state returns them); pstar_dev:
+ * [n_elem][Np(k+1)] coefficients of p* in the orthonormal degree-(k+1) basis (same
+ * construction and mode order as the degree-k basis). All device memory, caller-owned,
+ * stream-ordered on the context's stream. Acoustic contexts with nrhs = 1 only
+ * (HDG_EINVAL otherwise). The first call builds and uploads small reference tables
+ * (one allocation, then a stream synchronisation). */
+hdg_status hdg_postprocess(hdg_ctx* ctx, const double* u_dev, const double* lam_dev, double* pstar_dev);
+
 /* Data of the time-dependent problem. Point sources in the pressure equation at
  * positions pos_host [nsrc][dim], source i with amplitude amp_host[i] and the Ricker
  * wavelet r(t - d_i), r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), delayed

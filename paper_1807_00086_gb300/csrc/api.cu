@@ -13,6 +13,7 @@
 
 #include "../../include/hdg.h"
 #include "kernels.cuh"
+#include "post.cuh"
 #include "dflocal.cuh"
 #include "multi.cuh"
 #include "elastic.cuh"
@@ -918,6 +919,16 @@ void guess_reset_column(hdg_ctx* c, int j) {
   std::fill(c->gm_gram.begin() + (size_t)j * 64, c->gm_gram.begin() + (size_t)(j + 1) * 64, 0.0);
 }
 
+namespace {
+template <int DIM, int K>
+void launch_post(hdg_ctx* c, const double* u, const double* lam, double* pstar) {
+  const PostTabs P{c->d_post, c->d_post + c->post_k1};
+  c->n_launch += 1;
+  post_kernel<DIM, K><<<grid_for(c, c->sk.ne * PostCfg<DIM, K>::NT, PostCfg<DIM, K>::NT), PostCfg<DIM, K>::NT, 0,
+                        c->stream>>>(devmesh(c), c->tabs, P, u, lam, pstar);
+}
+}  // namespace
+
 extern "C" {
 
 void hdg_default_options(hdg_options* o) {
@@ -1272,6 +1283,29 @@ hdg_status hdg_recover(hdg_ctx* c, const double* F, const double* lam, double* u
   }
   HDG_DISPATCH(c, launch_local, c, 1, F, (const double*)nullptr, 0.0, lam, u);
   return check_launch(c, "recover");
+}
+
+hdg_status hdg_postprocess(hdg_ctx* c, const double* u, const double* lam, double* pstar) {
+  if (!c || !u || !lam || !pstar) return fail(c, HDG_EINVAL, "null argument");
+  if (c->phys != HDG_ACOUSTIC || c->vd || c->R != 1)
+    return fail(c, HDG_EINVAL, "post-processing is defined for acoustic contexts with nrhs = 1");
+  if (!c->d_post) {
+    PostTables P;
+    try {
+      P = build_post_tables(c->dim, c->k);
+    } catch (const std::exception& ex) {
+      return fail(c, HDG_EINVAL, std::string("post-processing tables: ") + ex.what());
+    }
+    std::vector<double> tab(P.K1);
+    tab.insert(tab.end(), P.E1.begin(), P.E1.end());
+    hdg_status s;
+    if ((s = dalloc(c, &c->d_post, tab.size()))) return s;
+    c->post_k1 = (int64_t)P.K1.size();
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_post, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // tab is released at return
+  }
+  HDG_DISPATCH(c, launch_post, c, u, lam, pstar);
+  return check_launch(c, "postprocess");
 }
 
 hdg_status hdg_set_sources(hdg_ctx* c, int32_t nsrc, const double* pos, const double* amp, const int32_t* col,

@@ -56,6 +56,8 @@ struct hdg_ctx {
   float *d_S32 = nullptr, *d_dinv32 = nullptr, *d_slot32 = nullptr;
   float* d_Sdf = nullptr;       // double-float diagonal-major copy of S_K (refinement apply)
   df2 *d_Hinvdf = nullptr, *d_geodf = nullptr, *d_tabdf = nullptr;   // double-float local solves
+  double* d_post = nullptr;       // post-processing tables K1 | E1 (built at the first hdg_postprocess)
+  int64_t post_k1 = 0;            // entries of K1
   TabsDf tabsdf{};
   __half* d_S16 = nullptr;      // FP16 packed S_K (inner Krylov operator of HDG_MIXED16)
   float* d_sc16 = nullptr;      // its per-element scales

@@ -250,4 +250,39 @@ RefTables build_tables_pair(int dim, int k, int kf) {
   return T;
 }
 
+PostTables build_post_tables(int dim, int k) {
+  if (dim < 2 || dim > 3 || k < 1 || k > 4) throw std::invalid_argument("dim must be 2/3 and 1 <= k <= 4");
+  PostTables T;
+  T.dim = dim; T.k = k;
+  const int Np = T.Np = n_modes(dim, k), Np1 = T.Np1 = n_modes(dim, k + 1);
+  std::vector<double> pts, w;
+  simplex_rule(dim, k + 3, pts, w);
+  const int nq = (int)w.size();
+  std::vector<double> phi((size_t)nq * Np), psi((size_t)nq * Np1), dpsi((size_t)nq * Np1 * dim);
+  dubiner(dim, k, pts.data(), nq, phi.data(), nullptr);
+  dubiner(dim, k + 1, pts.data(), nq, psi.data(), dpsi.data());
+  double c00 = 0.0;
+  for (int q = 0; q < nq; ++q) c00 += w[q] * psi[(size_t)q * Np1] * phi[(size_t)q * Np];
+  if (std::fabs(c00 - 1.0) > 1e-12) throw std::logic_error("constant modes of degrees k and k+1 differ");
+  T.K1.assign((size_t)dim * dim * Np1 * Np1, 0.0);
+  for (int r = 0; r < dim; ++r)
+    for (int s2 = 0; s2 < dim; ++s2)
+      for (int i = 0; i < Np1; ++i)
+        for (int l = 0; l < Np1; ++l) {
+          double s = 0.0;
+          for (int q = 0; q < nq; ++q)
+            s += w[q] * dpsi[((size_t)q * Np1 + i) * dim + r] * dpsi[((size_t)q * Np1 + l) * dim + s2];
+          T.K1[(((size_t)r * dim + s2) * Np1 + i) * Np1 + l] = s;
+        }
+  T.E1.assign((size_t)dim * Np1 * Np, 0.0);
+  for (int r = 0; r < dim; ++r)
+    for (int i = 0; i < Np1; ++i)
+      for (int l = 0; l < Np; ++l) {
+        double s = 0.0;
+        for (int q = 0; q < nq; ++q) s += w[q] * dpsi[((size_t)q * Np1 + i) * dim + r] * phi[(size_t)q * Np + l];
+        T.E1[((size_t)r * Np1 + i) * Np + l] = s;
+      }
+  return T;
+}
+
 }  // namespace hdg

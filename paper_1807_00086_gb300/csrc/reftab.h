@@ -36,4 +36,15 @@ RefTables build_tables_pair(int dim, int kv, int kf);
 // total degree of each face mode of degree kf, in the face basis order
 std::vector<int> face_mode_degrees(int dim, int kf);
 
+// Tables of the local post-processing into P_{k+1} (psi: orthonormal degree-(k+1) basis,
+// phi: degree k; volume rule of k + 3 points per direction, exact for both products):
+//   K1[r][s][i][l] = int d_r psi_i d_s psi_l      [dim][dim][Np1][Np1]
+//   E1[r][i][l]    = int d_r psi_i phi_l          [dim][Np1][Np]
+// psi_0 = phi_0 (the same constant); build_post_tables checks it.
+struct PostTables {
+  int dim = 0, k = 0, Np = 0, Np1 = 0;
+  std::vector<double> K1, E1;
+};
+PostTables build_post_tables(int dim, int k);
+
 }  // namespace hdg

@@ -7,6 +7,7 @@ Names follow include/hdg.h: hdg_setup, hdg_condense, hdg_trace_apply, hdg_conden
 hdg_trace_solve, hdg_recover, hdg_step, ...
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -78,6 +79,7 @@ SIGNATURES = {
     "hdg_condensed_rhs": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hdg_trace_solve": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(SolveInfo)]),
     "hdg_recover": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hdg_postprocess": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hdg_set_sources": (c_int32, [c_void_p, c_int32, P_double, P_double, P_int32, P_double, c_double, c_double]),
     "hdg_reset_column": (c_int32, [c_void_p, c_int32]),
     "hdg_stream_create": (c_int32, [ctypes.POINTER(c_void_p)]),
@@ -268,6 +270,15 @@ class Solver:
         self._check(self.lib.hdg_recover(self.ctx, self._dev(F, self._fshape),
                                          self._dev(lam, self._tshape), self._dev(u, self._fshape)))
         return u
+
+    def hdg_postprocess(self, u, lam, pstar=None):
+        """Post-processed pressure p* in P_{k+1} per element, [n_elem, Np(k+1)]."""
+        np1 = math.comb(self.k + 1 + self.dim, self.dim)
+        if pstar is None:
+            pstar = self.torch.zeros((self.n_elem, np1), dtype=self.torch.float64, device=self.device)
+        self._check(self.lib.hdg_postprocess(self.ctx, self._dev(u, self._fshape), self._dev(lam, self._tshape),
+                                             self._dev(pstar, (self.n_elem, np1))))
+        return pstar
 
     def hdg_set_sources(self, pos, amp, f0, t0, col=None, delay=None):
         pos = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, self.dim))
