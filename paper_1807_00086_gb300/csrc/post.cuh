@@ -10,8 +10,8 @@
 //     A_il = sum_{r,s} (Jinv Jinv^T)[r][s] K1[r][s][i][l],  b_i = sum_{j,r} Jinv[r][j] (E1[r] q^j)_i;
 //   the mean condition (p*, 1)_K = (p, 1)_K fixes the constant mode: p*_0 = p_0 (psi_0 = phi_0),
 //   and psi_0 has no gradient, so A' c' = b' on the modes 1..Np1-1 (SPD) gives the rest.
-// One CTA per element (grid-stride), A' in shared memory, right-looking Cholesky, then the two
-// triangular solves by one warp. FP64 throughout: the step runs once per output time.
+// One warp per element, A' in shared memory, right-looking Cholesky and the two triangular
+// solves by the same warp. FP64 throughout: the step runs once per output time.
 #pragma once
 
 #include "kernels.cuh"
@@ -28,36 +28,50 @@ struct PostCfg {
   static constexpr int NP = Dims<DIM, K>::NP;
   static constexpr int NP1 = Dims<DIM, K + 1>::NP;
   static constexpr int NA = NP1 - 1;
-  static constexpr int NT = 128;
+  // per-warp shared memory (doubles): A' [NA][NA+1], geometry, p, traces, q, b, metric
+  static constexpr int SM_W = NA * (NA + 1) + GEO_STRIDE + NP + (DIM + 1) * Dims<DIM, K>::NF + DIM * NP + NA + DIM * DIM;
+  static constexpr int WPB = SM_W * 8 * 4 <= 46 * 1024 ? 4 : (SM_W * 8 * 2 <= 46 * 1024 ? 2 : 1);
+  static constexpr int NT = 32 * WPB;
+  // CTAs per SM the registers are budgeted for (the shared memory admits at least this many)
+  static constexpr int MINB = WPB == 4 ? 3 : 2;
 };
 
+// One warp per element (WPB independent warps per CTA, warp-stride over the elements), all
+// synchronisation by __syncwarp, so many elements are in flight per SM.
 template <int DIM, int K>
-__global__ void __launch_bounds__(PostCfg<DIM, K>::NT) post_kernel(DevMesh mesh, Tabs T, PostTabs P,
+__global__ void __launch_bounds__(PostCfg<DIM, K>::NT, PostCfg<DIM, K>::MINB) post_kernel(DevMesh mesh, Tabs T, PostTabs P,
                                                                    const double* __restrict__ u,
                                                                    const double* __restrict__ lam,
                                                                    double* __restrict__ pstar) {
   using D = Dims<DIM, K>;
   using C = PostCfg<DIM, K>;
-  constexpr int NP = C::NP, NF = D::NF, NFC = D::NFC, N = D::N, NP1 = C::NP1, NA = C::NA, NT = C::NT;
-  __shared__ double A[NA][NA + 1];
-  __shared__ double g[GEO_STRIDE], p[NP], lf[NFC * NF], q[DIM * NP], b[NA], gm[DIM * DIM];
-  const int tid = threadIdx.x;
-  for (int64_t e = blockIdx.x; e < mesh.ne; e += gridDim.x) {
-    if (tid < GEO_STRIDE) g[tid] = mesh.geo[e * GEO_STRIDE + tid];
-    for (int t = tid; t < NP; t += NT) p[t] = u[e * N + t];
-    for (int t = tid; t < NFC * NF; t += NT) {
+  constexpr int NP = C::NP, NF = D::NF, NFC = D::NFC, N = D::N, NP1 = C::NP1, NA = C::NA;
+  __shared__ double smem[C::WPB][C::SM_W];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double(*A)[NA + 1] = reinterpret_cast<double(*)[NA + 1]>(smem[w]);
+  double* g = smem[w] + NA * (NA + 1);
+  double* p = g + GEO_STRIDE;
+  double* lf = p + NP;
+  double* q = lf + NFC * NF;
+  double* b = q + DIM * NP;
+  double* gm = b + NA;
+  const int64_t nw = (int64_t)gridDim.x * C::WPB;
+  for (int64_t e = (int64_t)blockIdx.x * C::WPB + w; e < mesh.ne; e += nw) {
+    for (int t = lane; t < GEO_STRIDE; t += 32) g[t] = mesh.geo[e * GEO_STRIDE + t];
+    for (int t = lane; t < NP; t += 32) p[t] = u[e * N + t];
+    for (int t = lane; t < NFC * NF; t += 32) {
       const int f = mesh.elem_face[e * NFC + t / NF];
       lf[t] = lam[(int64_t)f * NF + t % NF];
     }
-    __syncthreads();
-    if (tid < DIM * DIM) {
-      const int r = tid / DIM, s = tid % DIM;
+    __syncwarp();
+    if (lane < DIM * DIM) {
+      const int r = lane / DIM, s = lane % DIM;
       double v = 0.0;
       for (int j = 0; j < DIM; ++j) v += g[1 + r * DIM + j] * g[1 + s * DIM + j];
-      gm[tid] = v;
+      gm[lane] = v;
     }
     // discrete gradient q_h
-    for (int t = tid; t < DIM * NP; t += NT) {
+    for (int t = lane; t < DIM * NP; t += 32) {
       const int j = t / NP, i = t % NP;
       double vol = 0.0;
       for (int r = 0; r < DIM; ++r) {
@@ -73,9 +87,9 @@ __global__ void __launch_bounds__(PostCfg<DIM, K>::NT) post_kernel(DevMesh mesh,
       }
       q[t] = fc / g[0] - vol;
     }
-    __syncthreads();
+    __syncwarp();
     // right-hand side and the lower triangle of A' (modes 1..NP1-1)
-    for (int t = tid; t < NA; t += NT) {
+    for (int t = lane; t < NA; t += 32) {
       double s = 0.0;
       for (int j = 0; j < DIM; ++j)
         for (int r = 0; r < DIM; ++r) {
@@ -85,48 +99,50 @@ __global__ void __launch_bounds__(PostCfg<DIM, K>::NT) post_kernel(DevMesh mesh,
         }
       b[t] = s;
     }
-    for (int t = tid; t < NA * NA; t += NT) {
-      const int i = t / NA, l = t % NA;
-      if (l > i) continue;
+    for (int t = lane; t < NA * (NA + 1) / 2; t += 32) {
+      // t -> (i, l), l <= i, row by row
+      int i = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+      while ((i + 1) * (i + 2) / 2 <= t) ++i;
+      while (i * (i + 1) / 2 > t) --i;
+      const int l = t - i * (i + 1) / 2;
       double s = 0.0;
 #pragma unroll
       for (int rs = 0; rs < DIM * DIM; ++rs) s += gm[rs] * P.K1[(rs * NP1 + i + 1) * NP1 + l + 1];
       A[i][l] = s;
     }
-    __syncthreads();
+    __syncwarp();
     // Cholesky A' = L L^T in place (lower triangle)
     for (int c = 0; c < NA; ++c) {
-      if (tid == 0) A[c][c] = sqrt(A[c][c]);
-      __syncthreads();
-      for (int i = c + 1 + tid; i < NA; i += NT) A[i][c] /= A[c][c];
-      __syncthreads();
-      const int nt = NA - c - 1;
-      for (int t = tid; t < nt * nt; t += NT) {
-        const int i = c + 1 + t / nt, l = c + 1 + t % nt;
-        if (l <= i) A[i][l] -= A[i][c] * A[l][c];
-      }
-      __syncthreads();
+      const double dc = sqrt(A[c][c]);
+      __syncwarp();
+      if (lane == 0) A[c][c] = dc;
+      for (int i = c + 1 + lane; i < NA; i += 32) A[i][c] /= dc;
+      __syncwarp();
+      for (int i = c + 1; i < NA; ++i)
+        for (int l = c + 1 + lane; l <= i; l += 32) A[i][l] -= A[i][c] * A[l][c];
+      __syncwarp();
     }
-    // L y = b, then L^T c' = y, by warp 0 (b is overwritten)
-    if (tid < 32) {
-      for (int i = 0; i < NA; ++i) {
-        double s = 0.0;
-        for (int l = tid; l < i; l += 32) s += A[i][l] * b[l];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (tid == 0) b[i] = (b[i] - s) / A[i][i];
-        __syncwarp();
-      }
-      for (int i = NA - 1; i >= 0; --i) {
-        double s = 0.0;
-        for (int l = i + 1 + tid; l < NA; l += 32) s += A[l][i] * b[l];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (tid == 0) b[i] = (b[i] - s) / A[i][i];
-        __syncwarp();
-      }
+    // L y = b, then L^T c' = y (b is overwritten)
+    for (int i = 0; i < NA; ++i) {
+      double s = 0.0;
+      for (int l = lane; l < i; l += 32) s += A[i][l] * b[l];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const double bi = (b[i] - s) / A[i][i];
+      __syncwarp();
+      if (lane == 0) b[i] = bi;
+      __syncwarp();
     }
-    __syncthreads();
-    for (int t = tid; t < NP1; t += NT) pstar[e * NP1 + t] = t == 0 ? p[0] : b[t - 1];
-    __syncthreads();
+    for (int i = NA - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int l = i + 1 + lane; l < NA; l += 32) s += A[l][i] * b[l];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const double bi = (b[i] - s) / A[i][i];
+      __syncwarp();
+      if (lane == 0) b[i] = bi;
+      __syncwarp();
+    }
+    for (int t = lane; t < NP1; t += 32) pstar[e * NP1 + t] = t == 0 ? p[0] : b[t - 1];
+    __syncwarp();
   }
 }
 

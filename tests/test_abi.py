@@ -102,3 +102,10 @@ def test_setup_rejects_unsupported_elastic_configurations_on_host(libpath):
     st = lib.hdg_setup(ctypes.byref(mesh), 2, 1.0, ctypes.byref(mat), None, None, ctypes.byref(ctx))
     assert st == -1 and b"Lame" in lib.hdg_last_error(ctx)
     lib.hdg_destroy(ctx)
+
+
+def test_entry_points_reject_null_arguments_without_gpu(libpath):
+    from paper_1807_00086_gb300 import hdg
+    lib = hdg.load()
+    assert lib.hdg_postprocess(None, None, None, None) == -1
+    assert lib.hdg_recover(None, None, None, None) == -1
