@@ -161,6 +161,17 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def max_over_ranks(dist, x, device):
+    """The largest x over all ranks (x itself without a process group): the replicas' job
+    time is that of the slowest rank."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------------- GPU leg
 def run_ours(args):
     import torch
@@ -241,10 +252,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     st = s.hdg_get_stats(reset=True)
     s.hdg_enable_stats(False)
-    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
+    ms_max = max_over_ranks(dist, ms, "cuda")
     value = world * dofs * args.steps / (ms_max / 1e3)
 
     # end to end through the public API with host buffers: the state (u^n, u^{n-1}) goes
@@ -275,10 +283,7 @@ def run_ours(args):
             l_h.copy_(l_d, non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
-    t_e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
-    e2e_value = world * dofs * e2e_steps / float(t_e.item())
+    e2e_value = world * dofs * e2e_steps / max_over_ranks(dist, e2e_s, "cuda")
     field_bytes = int(np.prod(s._fshape)) * 8
     trace_bytes = int(np.prod(s._tshape)) * 8
     nschur, nslot = s.sizes.schur_entries, s.sizes.slot_entries
