@@ -198,6 +198,29 @@ hdg_status hdg_recover(hdg_ctx* ctx, const double* F_dev, const double* lam_dev,
  * (one allocation, then a stream synchronisation). */
 hdg_status hdg_postprocess(hdg_ctx* ctx, const double* u_dev, const double* lam_dev, double* pstar_dev);
 
+/* Host-only views of what hdg_setup builds on the host, for tests and tools: no context, no
+ * CUDA call, all pointers host memory owned by the caller. HDG_EINVAL (nothing written
+ * beyond what was already copied) for invalid arguments.
+ * hdg_host_skeleton: the skeleton E_h and the affine geometry of a simplex mesh (Sec. 2.1),
+ * vert [n_vert][dim] and elem [n_elem][dim+1] as in hdg_mesh. Outputs:
+ *   n_faces                        number of faces (lexicographic order of sorted vertex ids)
+ *   elem_face [n_elem][dim+1]      face of local face j (opposite the j-th vertex, ascending ids)
+ *   face_slot [(dim+1) n_elem][2]  slots e*(dim+1)+j of each face, lower first, -1 if none
+ *                                  (the first 2 n_faces entries are written)
+ *   face_bnd  [(dim+1) n_elem]     boundary index or -1 (the first n_faces entries are written)
+ *   geo       [n_elem][32]         |det J|, J^{-1} row-major (d xi_r / d x_j), face Jacobians,
+ *                                  outward unit normals (face-major)
+ * hdg_host_tables: reference tables of degree k (1..4) in dimension dim (2, 3), orthonormal
+ * Dubiner bases phi (degree k), mu (faces, degree k), psi (degree k + 1); any pointer may be NULL:
+ *   Dr [dim][Np][Np]        Dr[r][i][l] = int d_r phi_l phi_i
+ *   Ff [dim+1][Np][Nf]      Ff[f][i][m] = int over reference face f of phi_i mu_m
+ *   K1 [dim][dim][Np1][Np1] K1[r][s][i][l] = int d_r psi_i d_s psi_l
+ *   E1 [dim][Np1][Np]       E1[r][i][l] = int d_r psi_i phi_l                              */
+hdg_status hdg_host_skeleton(int32_t dim, int64_t n_vert, int64_t n_elem, const double* vert, const int32_t* elem,
+                             int64_t* n_faces, int32_t* elem_face, int32_t* face_slot, int32_t* face_bnd,
+                             double* geo);
+hdg_status hdg_host_tables(int32_t dim, int32_t k, double* Dr, double* Ff, double* K1, double* E1);
+
 /* Data of the time-dependent problem. Point sources in the pressure equation at
  * positions pos_host [nsrc][dim], source i with amplitude amp_host[i] and the Ricker
  * wavelet r(t - d_i), r(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2), delayed

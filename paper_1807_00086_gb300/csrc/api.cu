@@ -946,6 +946,38 @@ void hdg_default_options(hdg_options* o) {
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+hdg_status hdg_host_skeleton(int32_t dim, int64_t n_vert, int64_t n_elem, const double* vert, const int32_t* elem,
+                             int64_t* n_faces, int32_t* elem_face, int32_t* face_slot, int32_t* face_bnd,
+                             double* geo) {
+  if (!vert || !elem || !n_faces || !elem_face || !face_slot || !face_bnd || !geo) return HDG_EINVAL;
+  Skeleton sk;
+  std::string err;
+  if (!build_skeleton(dim, n_vert, n_elem, vert, elem, sk, err)) return HDG_EINVAL;
+  *n_faces = sk.nf;
+  std::copy(sk.elem_face.begin(), sk.elem_face.end(), elem_face);
+  std::copy(sk.face_slot.begin(), sk.face_slot.end(), face_slot);
+  std::copy(sk.face_bnd.begin(), sk.face_bnd.end(), face_bnd);
+  std::copy(sk.geo.begin(), sk.geo.end(), geo);
+  return HDG_OK;
+}
+
+hdg_status hdg_host_tables(int32_t dim, int32_t k, double* Dr, double* Ff, double* K1, double* E1) {
+  if (dim < 2 || dim > 3 || k < 1 || k > 4) return HDG_EINVAL;
+  try {
+    const RefTables T = build_tables(dim, k);
+    if (Dr) std::copy(T.Dr.begin(), T.Dr.end(), Dr);
+    if (Ff) std::copy(T.Ff.begin(), T.Ff.end(), Ff);
+    if (K1 || E1) {
+      const PostTables P = build_post_tables(dim, k);
+      if (K1) std::copy(P.K1.begin(), P.K1.end(), K1);
+      if (E1) std::copy(P.E1.begin(), P.E1.end(), E1);
+    }
+  } catch (const std::exception&) {
+    return HDG_EINVAL;
+  }
+  return HDG_OK;
+}
+
 void hdg_destroy(hdg_ctx* c) {
   if (!c) return;
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
