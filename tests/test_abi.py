@@ -104,8 +104,22 @@ def test_setup_rejects_unsupported_elastic_configurations_on_host(libpath):
     lib.hdg_destroy(ctx)
 
 
-def test_entry_points_reject_null_arguments_without_gpu(libpath):
+def test_entry_points_reject_a_null_context_without_gpu(libpath):
+    """Every context entry point returns HDG_EINVAL for a null context, before any CUDA call."""
     from paper_1807_00086_gb300 import hdg
     lib = hdg.load()
-    assert lib.hdg_postprocess(None, None, None, None) == -1
-    assert lib.hdg_recover(None, None, None, None) == -1
+    names = ["hdg_get_sizes", "hdg_condense", "hdg_get_schur", "hdg_trace_apply", "hdg_condensed_rhs",
+             "hdg_trace_solve", "hdg_recover", "hdg_postprocess", "hdg_set_sources", "hdg_quadrature_points",
+             "hdg_project_volume", "hdg_set_dirichlet", "hdg_set_state", "hdg_get_state", "hdg_step",
+             "hdg_reset_column", "hdg_get_tuning", "hdg_enable_stats", "hdg_get_stats"]
+    for name in names:
+        args = []
+        for t in hdg.SIGNATURES[name][1]:
+            if t in (ctypes.c_int32, ctypes.c_int64):
+                args.append(0)
+            elif t is ctypes.c_double:
+                args.append(1.0)
+            else:
+                args.append(None)
+        assert getattr(lib, name)(*args) == -1, name
+    assert lib.hdg_last_error(None) == b"null context"
