@@ -412,8 +412,10 @@ def dirk3_tableau():
     return a, b, c
 
 
-def run_bdf(prob, u0, dt, nsteps, order, t0=0.0, u_prev=None, on_step=None):
-    """BDF(order) marching (Eq. ch5appendx1:eq9b); order 2 starts from u^{-1} = u_prev (default u0)."""
+def run_bdf(prob, u0, dt, nsteps, order, t0=0.0, u_prev=None, on_step=None, solve=None):
+    """BDF(order) marching (Eq. ch5appendx1:eq9b); order 2 starts from u^{-1} = u_prev (default u0).
+    solve(prob, cond, hist, t) -> (u, lam) is the stage solve (default: solve_stage, HDG traces)."""
+    solve = solve or solve_stage
     a, bs = BDF[order]
     alpha = a[-1] / (bs * dt)
     cond = condense(prob, alpha)
@@ -423,15 +425,17 @@ def run_bdf(prob, u0, dt, nsteps, order, t0=0.0, u_prev=None, on_step=None):
     for n in range(nsteps):
         t = t0 + (n + 1) * dt
         h = -sum(a[i] * hist_u[i] for i in range(order)) / a[-1]
-        u, lam = solve_stage(prob, cond, h, t)
+        u, lam = solve(prob, cond, h, t)
         hist_u = hist_u[1:] + [u]
         if on_step is not None:
             on_step(n, t, u, lam)
     return hist_u[-1], lam, t
 
 
-def run_dirk3(prob, u0, dt, nsteps, t0=0.0, on_step=None):
-    """DIRK(3,3) marching in the stage form of Eq. ch5appendx1:eq10_1 with update Eq. 10_2."""
+def run_dirk3(prob, u0, dt, nsteps, t0=0.0, on_step=None, solve=None):
+    """DIRK(3,3) marching in the stage form of Eq. ch5appendx1:eq10_1 with update Eq. 10_2.
+    solve(prob, cond, hist, t) -> (u, lam) is the stage solve (default: solve_stage, HDG traces)."""
+    solve = solve or solve_stage
     a, b, c = dirk3_tableau()
     d = np.linalg.inv(a)
     e = b @ d
@@ -447,7 +451,7 @@ def run_dirk3(prob, u0, dt, nsteps, t0=0.0, on_step=None):
                 cond = condense(prob, d[i, i] / dt)
             # sum_j d_ij (u^{n,j} - u^n) + dt f(u^{n,i}) = 0, j <= i (d lower triangular)
             h = (sum(d[i, j] for j in range(i + 1)) * u - sum(d[i, j] * stages[j] for j in range(i))) / d[i, i]
-            ui, lam = solve_stage(prob, cond, h, tn + c[i] * dt)
+            ui, lam = solve(prob, cond, h, tn + c[i] * dt)
             stages.append(ui)
         u = (1.0 - b @ d.sum(axis=1)) * u + sum(e[j] * stages[j] for j in range(s))
         if on_step is not None:
