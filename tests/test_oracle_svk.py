@@ -58,3 +58,31 @@ def test_small_strain_limit_is_linear_elasticity():
     for t in (1e-3, 1e-4):
         P = svk.first_pk(np.eye(3) + t * H, lam, mu)
         assert np.abs(P / t - lin).max() < 20 * t * np.abs(lin).max()
+
+
+def test_plate_solution_satisfies_the_equations():
+    """Central differences (not the symbolic derivatives) of the plate data: dF/dt = grad v,
+    rho dv/dt - div P = f, P = P_SVK(F), and v = 0 on the clamped sides."""
+    pytest.importorskip("sympy")
+    lam, mu, rho = 1.5, 1.0, 1.0
+    sol = svk.plate_solution(lam, mu, rho)
+    rng = np.random.default_rng(6)
+    x = np.column_stack([rng.uniform(0.1, 0.9, 5), rng.uniform(0.1, 0.9, 5), rng.uniform(0.0, 0.01, 5)])
+    t, h = 0.37, 1e-5
+    F = sol["F"](x, t).reshape(-1, 3, 3)
+    dFdt = (sol["F"](x, t + h) - sol["F"](x, t - h)).reshape(-1, 3, 3) / (2 * h)
+    dvdt = (sol["v"](x, t + h) - sol["v"](x, t - h)) / (2 * h)
+    gradv = np.zeros_like(dFdt)
+    divP = np.zeros((x.shape[0], 3))
+    for J in range(3):
+        e = np.zeros(3)
+        e[J] = h
+        gradv[:, :, J] = (sol["v"](x + e, t) - sol["v"](x - e, t)) / (2 * h)
+        dP = (sol["P"](x + e, t) - sol["P"](x - e, t)).reshape(-1, 3, 3) / (2 * h)
+        divP += dP[:, :, J]
+    assert np.abs(dFdt - gradv).max() < 1e-6
+    assert np.abs(rho * dvdt - divP - sol["f"](x, t)).max() < 1e-5
+    for q in range(x.shape[0]):
+        assert np.abs(sol["P"](x[q:q + 1], t).reshape(3, 3) - svk.first_pk(F[q], lam, mu)).max() < 1e-13
+    sides = np.array([[0.0, 0.3, 0.005], [1.0, 0.6, 0.0], [0.4, 0.0, 0.01], [0.2, 1.0, 0.003]])
+    assert np.abs(sol["v"](sides, t)).max() < 1e-15
