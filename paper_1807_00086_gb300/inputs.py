@@ -84,6 +84,27 @@ def random_traces(n_faces, n_face_dofs, seed=DEFAULT_SEED):
     return rng.standard_normal((n_faces, n_face_dofs))
 
 
+def plate_tet(n, thickness=0.01):
+    """The unit square plate [0, 1]^2 x [0, thickness] with n x n x 1 cubes of 6 Kuhn tets each
+    (one element layer through the thickness): (vert[(n+1)^2 2, 3], elem[6 n^2, 4])."""
+    gx = np.linspace(0.0, 1.0, n + 1)
+    vert, elem = [], []
+    Z, Y, X = np.meshgrid(np.array([0.0, thickness]), gx, gx, indexing="ij")
+    vert = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    n1 = n + 1
+    for j in range(n):
+        for i in range(n):
+            for perm in itertools.permutations(range(3)):
+                c = [i, j, 0]
+                path = [tuple(c)]
+                for ax in perm:
+                    c = list(c)
+                    c[ax] += 1
+                    path.append(tuple(c))
+                elem.append([p[0] + n1 * (p[1] + n1 * p[2]) for p in path])
+    return vert, np.array(elem, dtype=np.int32)
+
+
 def acoustic_3d_workload(N=32, k=3, seed=DEFAULT_SEED):
     """3D acoustic wave workload: unit cube, 6 N^3 tets, c ~ logU[1, 3] per element, rho = 1,
     one Ricker point source at the cube centre shifted by 0.3 h (1, 1, 1) (no vertex/face tie)."""
