@@ -6,9 +6,12 @@
     of the solutions shrinks linearly with the amplitude (the nonlinearity is quadratic);
   * on the clamped vibrating plate (Sec. 4.5, SVK material, one element through the
     thickness, traction data on the faces) the velocity converges at order k + 1, as the
-    paper reports for the nonlinear case.
+    paper reports for the nonlinear case. tests/golden/eoc_nonlinear_elastodyn.txt holds the
+    paper's printed finest-mesh rates; its meshes are finer and of unstated type, so the rate
+    is compared, not the error.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -92,4 +95,7 @@ def test_plate_velocity_converges_at_order_k_plus_1():
         u, _, _ = nl.run_dirk3(prob, u0, T / (2 * n), 2 * n)
         errs.append(nl.l2_error_velocity(prob, u, sol["v"], T))
     rate = math.log2(errs[0] / errs[1])
-    assert rate > k + 1 - 0.3, (errs, rate)
+    golden = os.path.join(os.path.dirname(__file__), "golden", "eoc_nonlinear_elastodyn.txt")
+    rows = [ln.split() for ln in open(golden) if ln.strip() and not ln.startswith("#")]
+    paper_rate = float([r for r in rows if int(r[0]) == k][0][3])
+    assert rate > k + 1 - 0.3 and abs(rate - paper_rate) < 0.3, (errs, rate, paper_rate)
