@@ -27,7 +27,7 @@ oracle/acoustic.py. Parity unpinned: the Gaussian-bump initial data of the bench
 workload is a convention.
 """
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 import scipy.linalg as sla

@@ -19,7 +19,7 @@ Quadrature: 2k + 2 points per direction in the volume (the term F S(F) phi has d
 and k + 2 on faces; faces, bases and orientations are those of oracle/acoustic.py.
 """
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 import scipy.linalg as sla

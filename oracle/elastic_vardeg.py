@@ -19,7 +19,6 @@ Every step follows oracle/elastic.py: per-element LU of alpha Mw + A0, S_K = D -
 assembly over interior faces, a sparse direct trace solve, local recovery. Dirichlet data
 are v_hat = v_D on boundary faces (L2 projection onto the face space), zero when absent.
 """
-import math
 from dataclasses import dataclass
 
 import numpy as np

@@ -5,7 +5,6 @@ import pytest
 
 from gpu_helpers import relerr
 from oracle import acoustic as ac
-from paper_1807_00086_gb300 import inputs
 from paper_1807_00086_gb300.serve import F0, T0, Request, Server, mesh_for
 
 pytestmark = pytest.mark.gpu
