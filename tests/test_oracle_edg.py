@@ -134,3 +134,34 @@ def test_pressure_converges_at_order_k_plus_1_on_the_standing_mode(variant):
         errs.append(ac.l2_error(prob, u, lambda x: ex(x, T)))
     rate = math.log2(errs[-2] / errs[-1])
     assert rate > k + 1 - 0.25, (errs, rate)
+
+
+def test_continuous_traces_need_no_more_jacobi_cg_iterations_than_hdg():
+    """At the benchmark's c dt / h (acoustic recipe, k = 3, 384 tets) the restricted systems
+    R^T (-K) R of EDG and IEDG converge in fewer Jacobi-CG iterations than HDG's -K (run with
+    -s to print the counts): fewer unknowns, and no more passes over the same S_K."""
+    import scipy.sparse.linalg as spla
+    N = 4
+    w = inputs.acoustic_3d_workload(N=N, k=3)
+    prob = ac.build_problem(w["vert"], w["elem"], 3, w["tau"], w["rho"], w["c"])
+    cond = ac.condense(prob, 1.5 / (2e-3 * 32.0 / N))
+    b0 = np.random.default_rng(1807).standard_normal(cond.K.shape[0])
+    counts = {}
+    for name in ("hdg", "iedg", "edg"):
+        if name == "hdg":
+            A, b = (-cond.K).tocsr(), b0
+        else:
+            tm = edg.trace_map(prob, name)
+            A, b = (tm.R.T @ (-cond.K) @ tm.R).tocsr(), tm.R.T @ b0
+        d, n = A.diagonal(), A.shape[0]
+        it = [0]
+
+        def cb(_):
+            it[0] += 1
+        x, info = spla.cg(A, b, rtol=1e-12, atol=0.0, maxiter=2000,
+                          M=spla.LinearOperator((n, n), matvec=lambda r: r / d), callback=cb)
+        assert info == 0
+        counts[name] = (n, it[0])
+    print("\nJacobi CG (unknowns, iterations):", counts)
+    assert counts["edg"][0] < counts["iedg"][0] < counts["hdg"][0]
+    assert counts["edg"][1] <= counts["hdg"][1] and counts["iedg"][1] <= counts["hdg"][1]
