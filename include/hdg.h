@@ -220,6 +220,18 @@ hdg_status hdg_host_skeleton(int32_t dim, int64_t n_vert, int64_t n_elem, const 
                              int64_t* n_faces, int32_t* elem_face, int32_t* face_slot, int32_t* face_bnd,
                              double* geo);
 hdg_status hdg_host_tables(int32_t dim, int32_t k, double* Dr, double* Ff, double* K1, double* E1);
+/* hdg_host_trace_nodes: the continuous trace spaces of Sec. 2.2 on the mesh of
+ * hdg_host_skeleton, all faces continuous (all_faces = 1: EDG) or the interior faces
+ * (all_faces = 0: IEDG). The unknowns are the degree-k equispaced face nodes, shared between
+ * faces; EDG fixes those on the boundary. Outputs:
+ *   n_free                       number of free nodes
+ *   face_node [(dim+1) n_elem][Nf] free node of each face node (the first n_faces * Nf entries
+ *                                are written; -1 for a fixed node or a face outside the set),
+ *                                face nodes in lexicographic order of their integer barycentric
+ *                                weights on the face's vertices (ascending global ids)
+ *   Vinv [Nf][Nf]                nodal values -> coefficients of the orthonormal face basis    */
+hdg_status hdg_host_trace_nodes(int32_t dim, int64_t n_vert, int64_t n_elem, const double* vert, const int32_t* elem,
+                                int32_t k, int32_t all_faces, int64_t* n_free, int32_t* face_node, double* Vinv);
 
 /* Data of the time-dependent problem. Point sources in the pressure equation at
  * positions pos_host [nsrc][dim], source i with amplitude amp_host[i] and the Ricker

@@ -961,6 +961,27 @@ hdg_status hdg_host_skeleton(int32_t dim, int64_t n_vert, int64_t n_elem, const 
   return HDG_OK;
 }
 
+hdg_status hdg_host_trace_nodes(int32_t dim, int64_t n_vert, int64_t n_elem, const double* vert, const int32_t* elem,
+                                int32_t k, int32_t all_faces, int64_t* n_free, int32_t* face_node, double* Vinv) {
+  if (!vert || !elem || !n_free || !face_node || !Vinv) return HDG_EINVAL;
+  Skeleton sk;
+  std::string err;
+  if (!build_skeleton(dim, n_vert, n_elem, vert, elem, sk, err)) return HDG_EINVAL;
+  std::vector<int32_t> fn;
+  int64_t nfree = 0;
+  if (!build_trace_nodes(sk, k, all_faces != 0, nfree, fn, err)) return HDG_EINVAL;
+  std::vector<double> T;
+  try {
+    T = face_nodal_to_modal(dim, k);
+  } catch (const std::exception&) {
+    return HDG_EINVAL;
+  }
+  *n_free = nfree;
+  std::copy(fn.begin(), fn.end(), face_node);
+  std::copy(T.begin(), T.end(), Vinv);
+  return HDG_OK;
+}
+
 hdg_status hdg_host_tables(int32_t dim, int32_t k, double* Dr, double* Ff, double* K1, double* E1) {
   if (dim < 2 || dim > 3 || k < 1 || k > 4) return HDG_EINVAL;
   try {

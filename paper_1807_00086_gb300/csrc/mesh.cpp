@@ -4,7 +4,10 @@
 
 #include <algorithm>
 #include <array>
+#include <climits>
 #include <cmath>
+#include <unordered_map>
+#include <unordered_set>
 
 namespace hdg {
 
@@ -110,6 +113,81 @@ bool build_skeleton(int dim, int64_t nv, int64_t ne, const double* vert, const i
       for (int q = 0; q < dim; ++q) g[geo_n(dim) + f * dim + q] = n[q];
     }
   }
+  return true;
+}
+
+namespace {
+struct Key3 {
+  std::array<int64_t, 3> v;
+  bool operator==(const Key3& o) const { return v == o.v; }
+};
+struct Key3Hash {
+  size_t operator()(const Key3& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t x : k.v) { h ^= (uint64_t)x + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2); }
+    return (size_t)h;
+  }
+};
+}  // namespace
+
+bool build_trace_nodes(const Skeleton& sk, int k, bool all_faces, int64_t& n_free, std::vector<int32_t>& face_node,
+                       std::string& err) {
+  const int dim = sk.dim, nc = dim + 1, fv = dim;   // a face has dim vertices
+  if (k < 1 || k > 4) { err = "trace degree must be 1..4"; return false; }
+  const int Nf = dim == 2 ? k + 1 : (k + 1) * (k + 2) / 2;
+  auto face_verts = [&](int64_t f, int64_t* out) {
+    const int32_t slot = sk.face_slot[2 * f];
+    const int64_t e = slot / nc;
+    const int j = slot % nc;
+    int c = 0;
+    for (int i = 0; i < nc; ++i) if (i != j) out[c++] = sk.elem[e * nc + i];
+  };
+  // node weights of a face in lexicographic order
+  std::vector<std::array<int, 3>> bs;
+  for (int b0 = 0; b0 <= k; ++b0)
+    if (fv == 2) bs.push_back({b0, k - b0, 0});
+    else for (int b1 = 0; b0 + b1 <= k; ++b1) bs.push_back({b0, b1, k - b0 - b1});
+  // sub-simplices of boundary faces (EDG: nodes supported there are fixed)
+  std::unordered_set<Key3, Key3Hash> bsub;
+  if (all_faces)
+    for (int64_t f = 0; f < sk.nf; ++f) {
+      if (sk.face_bnd[f] < 0) continue;
+      int64_t v[3];
+      face_verts(f, v);
+      for (int mask = 1; mask < (1 << fv); ++mask) {
+        Key3 key{{-1, -1, -1}};
+        int c = 0;
+        for (int i = 0; i < fv; ++i) if (mask & (1 << i)) key.v[c++] = v[i];
+        bsub.insert(key);
+      }
+    }
+  std::unordered_map<Key3, int64_t, Key3Hash> id;
+  std::vector<uint8_t> fixed;
+  std::vector<int64_t> node_of((size_t)sk.nf * Nf, -1);
+  for (int64_t f = 0; f < sk.nf; ++f) {
+    if (!all_faces && sk.face_bnd[f] >= 0) continue;
+    int64_t v[3];
+    face_verts(f, v);
+    for (int a = 0; a < Nf; ++a) {
+      Key3 key{{-1, -1, -1}}, support{{-1, -1, -1}};
+      int c = 0;
+      for (int i = 0; i < fv; ++i)
+        if (bs[a][i] > 0) { key.v[c] = v[i] * (k + 1) + bs[a][i]; support.v[c] = v[i]; ++c; }
+      auto it = id.find(key);
+      if (it == id.end()) {
+        it = id.emplace(key, (int64_t)fixed.size()).first;
+        fixed.push_back(all_faces && bsub.count(support) ? 1 : 0);
+      }
+      node_of[(size_t)f * Nf + a] = it->second;
+    }
+  }
+  std::vector<int64_t> free_pos(fixed.size(), -1);
+  n_free = 0;
+  for (size_t i = 0; i < fixed.size(); ++i) if (!fixed[i]) free_pos[i] = n_free++;
+  if (n_free > INT32_MAX) { err = "too many trace nodes"; return false; }
+  face_node.assign((size_t)sk.nf * Nf, -1);
+  for (size_t t = 0; t < node_of.size(); ++t)
+    if (node_of[t] >= 0) face_node[t] = (int32_t)free_pos[node_of[t]];
   return true;
 }
 

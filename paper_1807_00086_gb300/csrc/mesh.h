@@ -30,4 +30,13 @@ struct Skeleton {
 bool build_skeleton(int dim, int64_t nv, int64_t ne, const double* vert, const int32_t* ev, Skeleton& sk,
                     std::string& err);
 
+// Continuous traces on a face subset (Sec. 2.2): all faces (EDG) or the interior faces (IEDG).
+// The unknowns are the degree-k equispaced nodes of those faces, shared between faces by the
+// vertices of the smallest sub-simplex containing the node and its integer barycentric
+// weights there, and numbered by first appearance over the faces in face order, lexicographic
+// (b_0, ..) within a face. EDG fixes the nodes that lie on the boundary. face_node [nf][Nf]:
+// the free node of each face node, -1 for a fixed node or a face outside the subset.
+bool build_trace_nodes(const Skeleton& sk, int k, bool all_faces, int64_t& n_free, std::vector<int32_t>& face_node,
+                       std::string& err);
+
 }  // namespace hdg

@@ -3,6 +3,7 @@
 // lexicographically in (i, j[, l]). These realise the discrete spaces of Sec. 2.2.
 #include "reftab.h"
 
+#include <array>
 #include <cmath>
 #include <stdexcept>
 
@@ -283,6 +284,65 @@ PostTables build_post_tables(int dim, int k) {
         T.E1[((size_t)r * Np1 + i) * Np + l] = s;
       }
   return T;
+}
+
+std::vector<double> face_nodal_to_modal(int dim, int k) {
+  if (dim < 2 || dim > 3 || k < 1 || k > 4) throw std::invalid_argument("dim must be 2/3 and 1 <= k <= 4");
+  const int fd = dim - 1, nf = n_modes(fd, k);
+  // nodes and monomial exponents, both in lexicographic order
+  std::vector<std::array<int, 2>> nodes, expo;
+  for (int b0 = 0; b0 <= k; ++b0)
+    if (fd == 1) nodes.push_back({k - b0, 0});
+    else for (int b1 = 0; b0 + b1 <= k; ++b1) nodes.push_back({b1, k - b0 - b1});
+  for (int i = 0; i <= k; ++i)
+    for (int j = 0; (fd == 2 ? i + j : j) <= (fd == 2 ? k : 0); ++j) expo.push_back({i, j});
+  auto mono = [&](const double* x, int m) {
+    double v = std::pow(x[0], expo[m][0]);
+    if (fd == 2) v *= std::pow(x[1], expo[m][1]);
+    return v;
+  };
+  // W[a][m] = x_a^m at the nodes; invert by Gauss-Jordan with partial pivoting
+  std::vector<double> W((size_t)nf * nf), Wi((size_t)nf * nf, 0.0);
+  for (int a = 0; a < nf; ++a) {
+    const double x[2] = {nodes[a][0] / (double)k, nodes[a][1] / (double)k};
+    for (int m = 0; m < nf; ++m) W[(size_t)a * nf + m] = mono(x, m);
+    Wi[(size_t)a * nf + a] = 1.0;
+  }
+  for (int c = 0; c < nf; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < nf; ++r)
+      if (std::fabs(W[(size_t)r * nf + c]) > std::fabs(W[(size_t)piv * nf + c])) piv = r;
+    for (int j = 0; j < nf; ++j) {
+      std::swap(W[(size_t)c * nf + j], W[(size_t)piv * nf + j]);
+      std::swap(Wi[(size_t)c * nf + j], Wi[(size_t)piv * nf + j]);
+    }
+    const double d = W[(size_t)c * nf + c];
+    if (std::fabs(d) < 1e-14) throw std::logic_error("face nodes are not unisolvent");
+    for (int j = 0; j < nf; ++j) { W[(size_t)c * nf + j] /= d; Wi[(size_t)c * nf + j] /= d; }
+    for (int r = 0; r < nf; ++r) {
+      if (r == c) continue;
+      const double f = W[(size_t)r * nf + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < nf; ++j) { W[(size_t)r * nf + j] -= f * W[(size_t)c * nf + j]; Wi[(size_t)r * nf + j] -= f * Wi[(size_t)c * nf + j]; }
+    }
+  }
+  // Lagrange functions at a face rule, projected on the orthonormal basis
+  std::vector<double> pts, w;
+  simplex_rule(fd, k + 2, pts, w);
+  const int nq = (int)w.size();
+  std::vector<double> U((size_t)nq * nf);
+  dubiner(fd, k, pts.data(), nq, U.data(), nullptr);
+  std::vector<double> out((size_t)nf * nf, 0.0);
+  for (int q = 0; q < nq; ++q) {
+    std::vector<double> mq(nf);
+    for (int m = 0; m < nf; ++m) mq[m] = mono(&pts[(size_t)q * fd], m);
+    for (int a = 0; a < nf; ++a) {
+      double ell = 0.0;   // ell_a(x_q) = sum_m x_q^m (W^{-1})[m][a]
+      for (int m = 0; m < nf; ++m) ell += mq[m] * Wi[(size_t)m * nf + a];
+      for (int mm = 0; mm < nf; ++mm) out[(size_t)mm * nf + a] += w[q] * U[(size_t)q * nf + mm] * ell;
+    }
+  }
+  return out;
 }
 
 }  // namespace hdg

@@ -47,4 +47,11 @@ struct PostTables {
 };
 PostTables build_post_tables(int dim, int k);
 
+// Values at the degree-k equispaced nodes of the reference face of a dim-simplex (integer
+// barycentric weights (b_0, .., b_{dim-1}) summing to k, in lexicographic order; reference
+// coordinates (b_1, .., b_{dim-1}) / k) -> coefficients in the orthonormal face basis:
+// [Nf][Nf] row-major, the L2 projection of each nodal Lagrange function (built from monomials,
+// so the collapsed-coordinate basis is never evaluated at its singular vertex).
+std::vector<double> face_nodal_to_modal(int dim, int k);
+
 }  // namespace hdg

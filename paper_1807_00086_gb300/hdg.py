@@ -83,6 +83,8 @@ SIGNATURES = {
     "hdg_host_skeleton": (c_int32, [c_int32, c_int64, c_int64, P_double, P_int32, ctypes.POINTER(c_int64), P_int32,
                                     P_int32, P_int32, P_double]),
     "hdg_host_tables": (c_int32, [c_int32, c_int32, P_double, P_double, P_double, P_double]),
+    "hdg_host_trace_nodes": (c_int32, [c_int32, c_int64, c_int64, P_double, P_int32, c_int32, c_int32,
+                                       ctypes.POINTER(c_int64), P_int32, P_double]),
     "hdg_set_sources": (c_int32, [c_void_p, c_int32, P_double, P_double, P_int32, P_double, c_double, c_double]),
     "hdg_reset_column": (c_int32, [c_void_p, c_int32]),
     "hdg_stream_create": (c_int32, [ctypes.POINTER(c_void_p)]),

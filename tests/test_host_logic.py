@@ -120,3 +120,34 @@ def test_reference_tables_match_the_oracle_bases(lib, dim, k):
 def test_reference_tables_reject_unsupported_degrees(lib):
     assert lib.hdg_host_tables(3, 5, None, None, None, None) == -1
     assert lib.hdg_host_tables(1, 2, None, None, None, None) == -1
+
+
+@pytest.mark.parametrize("dim,N,k", [(2, 3, 2), (2, 2, 4), (3, 2, 2), (3, 1, 3)])
+@pytest.mark.parametrize("variant", ["edg", "iedg"])
+def test_trace_node_map_matches_the_oracle(lib, dim, N, k, variant):
+    """The C++ continuous-trace node map and nodal-to-modal table give the oracle's
+    restriction R (same node numbering convention, independent construction)."""
+    from oracle import edg
+    vert, elem = inputs.unit_square_tri(N) if dim == 2 else inputs.unit_cube_tet(N)
+    vert = np.ascontiguousarray(vert, dtype=np.float64)
+    elem = np.ascontiguousarray(elem, dtype=np.int32)
+    ne, nc = elem.shape
+    Nf = ref.n_modes(dim - 1, k)
+    nfree = ctypes.c_int64()
+    fn = np.zeros((nc * ne, Nf), dtype=np.int32)
+    Vinv = np.zeros((Nf, Nf))
+    st = lib.hdg_host_trace_nodes(dim, vert.shape[0], ne, _ptr(vert, ctypes.c_double), _ptr(elem, ctypes.c_int32), k,
+                                  1 if variant == "edg" else 0, ctypes.byref(nfree), _ptr(fn, ctypes.c_int32),
+                                  _ptr(Vinv, ctypes.c_double))
+    assert st == 0
+    prob = ac.build_problem(vert, elem, k, 1.0, 1.0, 1.0)
+    tm = edg.trace_map(prob, variant)
+    assert nfree.value == tm.n_free
+    assert np.abs(Vinv - tm.Vinv).max() < 1e-12
+    interior = np.nonzero(~prob.sk.boundary)[0]
+    R = np.zeros((interior.size * Nf, tm.n_free))
+    for r, f in enumerate(interior):
+        for a in range(Nf):
+            if fn[f, a] >= 0:
+                R[r * Nf:(r + 1) * Nf, fn[f, a]] += Vinv[:, a]
+    assert np.abs(R - tm.R.toarray()).max() < 1e-12
