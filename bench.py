@@ -341,6 +341,12 @@ def run_ours(args):
                          "kernel": "apply16_kernel<3,3> (FP16 packed-symmetric S_K, per-element scale)",
                          "bytes_per_elem": b16, "launch_ms": a16, "launches": st["apply16_launches"],
                          "fp32_apply": fp32_view})
+            if args.k == 3:
+                # dram__bytes_read + write of one apply16 launch captured at 82,944 tets
+                # (148.8 MB, 1,794 B per element; the FP16 copy streamed once, the gather partly
+                # from L2), scaled to this launch by the element count
+                roof["traffic"] = 148.8e6 / 82944 * ne
+                roof["traffic_source"] = "ncu capture at 82,944 tets scaled by elements"
         if st.get("applydf_launches"):
             adf = st["applydf_ms"] / st["applydf_launches"]
             roof["df_refinement_apply"] = {
