@@ -39,6 +39,13 @@ METRIC = "HDG DOF-steps/s on 1 GB300, mixed vs FP64 at <=1e-9 rel err; serve p50
 UNIT = "DOF-steps/s"
 DT = 2e-3
 SAMPLE_N = 4          # oracle sample: 4^3 x 6 = 384 tetrahedra, same k, same recipe
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of a kernel, from an
+# ncu capture of that kernel at that element count; keyed by (kernel, n_elem). An entry is
+# removed whenever the kernel changes.
+MEASURED_TRAFFIC = {
+    ("apply16_kernel<3,3>", 196608): (348950357, "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of 3 launches "
+                                                  "at this size (profiles/apply16_acoustic3d_k3_196608tets_dram.md)"),
+}
 
 
 def load_peaks():
@@ -140,7 +147,8 @@ def oracle_sample(steps=None, budget_s=None, warmup=0):
             break
     total = sum(times)
     dofs = ne * nloc
-    return {"value": dofs * len(times) / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": dofs * len(times) / total, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": "%d BDF2 steps of the same workload on a %d^3x6 = %d-tet mesh (k=3, %d field DOFs); "
                       "oracle = numpy/scipy FP64, per-element LU + sparse direct trace solve" % (len(times), SAMPLE_N,
                                                                                                 ne, dofs),
@@ -156,7 +164,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "acoustic3d_k3_32cube_bdf2 (bounded sample: %d^3x6 tets)" % SAMPLE_N},
-           "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+           "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "host_cores", "kind", "sample")},
            "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -226,18 +234,43 @@ def run_ours(args):
     s = make_solver(args.prec)
     dofs = int(np.prod(s._fshape))
     stream = s.stream
-    # warm-up (includes the condensation for alpha = 3/(2 dt))
-    for _ in range(args.warmup):
-        s.hdg_step(dt, scheme, 1)
+    total = args.total_steps if args.total_steps is not None else (100 if elastic else 200)
+    preroll = args.preroll if args.preroll is not None else (0 if elastic else 60)
+    run = {"iters": 0, "sweeps": 0, "steps": 0, "ms": 0.0}
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def advance(solver, n, tally=None):
+        """n untimed steps, device time and Krylov counts added to tally."""
+        if n <= 0:
+            return
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(n):
+            info = solver.hdg_step(dt, scheme, 1)
+            if tally is not None:
+                tally["iters"] += info["iterations"]
+                tally["sweeps"] += info["sweeps"]
+        b.record(stream)
+        b.synchronize()
+        if tally is not None:
+            tally["steps"] += n
+            tally["ms"] += a.elapsed_time(b)
+
+    # pre-roll to the source's peak (t0 = 0.12 at 60 steps of 2e-3), so that the timed window lies
+    # in the wave-propagation phase of the run rather than in the quiet start from rest; then the
+    # warm-up (the condensation for alpha = 3/(2 dt) happens in the first step)
+    advance(s, preroll, run)
+    advance(s, args.warmup, run)
     torch.cuda.synchronize()
-    s.hdg_enable_stats(True)
-    s.hdg_get_stats(reset=True)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.hdg_get_stats(reset=True)
+    ev0, ev1 = ev(), ev()
     ev0.record(stream)
     iters = 0
     sweeps = 0
@@ -250,10 +283,34 @@ def run_ours(args):
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    st = s.hdg_get_stats(reset=True)
-    s.hdg_enable_stats(False)
+    launches_timed = s.hdg_get_stats(reset=True)["kernel_launches"]
+    run["iters"] += iters
+    run["sweeps"] += sweeps
+    run["steps"] += args.steps
+    run["ms"] += ms
     ms_max = max_over_ranks(dist, ms, "cuda")
     value = world * dofs * args.steps / (ms_max / 1e3)
+    window = {"first_step": preroll + args.warmup + 1, "last_step": preroll + args.warmup + args.steps,
+              "t_start": (preroll + args.warmup) * dt, "t_end": (preroll + args.warmup + args.steps) * dt}
+
+    # per-launch kernel durations for the roofline: the same number of steps again, each launch of
+    # the trace applies bracketed by CUDA events on the context stream (the timed window above
+    # runs without these events)
+    s.hdg_enable_stats(True)
+    s.hdg_get_stats(reset=True)
+    a_i, b_i = ev(), ev()
+    a_i.record(stream)
+    for _ in range(args.steps):
+        info = s.hdg_step(dt, scheme, 1)
+        run["iters"] += info["iterations"]
+        run["sweeps"] += info["sweeps"]
+    b_i.record(stream)
+    b_i.synchronize()
+    run["steps"] += args.steps
+    run["ms"] += a_i.elapsed_time(b_i)
+    st = s.hdg_get_stats(reset=True)
+    s.hdg_enable_stats(False)
+    instrumented_ms_per_step = a_i.elapsed_time(b_i) / args.steps
 
     # end to end through the public API with host buffers: the state (u^n, u^{n-1}) goes
     # host -> device, one step, and u^{n+1}, u^n come back device -> host, every step.
@@ -275,7 +332,9 @@ def run_ours(args):
             up_d.copy_(up_h, non_blocking=True)
             l_d.copy_(l_h, non_blocking=True)
         s.hdg_set_state(u_d, t_now, uprev=up_d, lam=l_d)
-        s.hdg_step(dt, scheme, 1)
+        info = s.hdg_step(dt, scheme, 1)
+        run["iters"] += info["iterations"]
+        run["sweeps"] += info["sweeps"]
         _, _, _, t_now = s.hdg_get_state(u=u_d, uprev=up_d, lam=l_d, want_prev=True)
         with torch.cuda.stream(stream):
             u_h.copy_(u_d, non_blocking=True)
@@ -283,77 +342,84 @@ def run_ours(args):
             l_h.copy_(l_d, non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
+    run["steps"] += e2e_steps
     e2e_value = world * dofs * e2e_steps / max_over_ranks(dist, e2e_s, "cuda")
     field_bytes = int(np.prod(s._fshape)) * 8
     trace_bytes = int(np.prod(s._tshape)) * 8
     nschur, nslot = s.sizes.schur_entries, s.sizes.slot_entries
+    # the rest of the configured run (Krylov counts over every step of it); the e2e steps above
+    # restarted the guess history (hdg_set_state), as a resumed run would
+    advance(s, total - run["steps"], run)
+    full_run = {"steps": run["steps"], "krylov_iters_per_step": run["iters"] / max(1, run["steps"]),
+                "refinement_sweeps_per_step": run["sweeps"] / max(1, run["steps"]) if args.prec != "fp64" else None,
+                "device_ms_excluding_e2e_steps": run["ms"],
+                "dof_steps_per_s_excluding_e2e_steps": dofs * (run["steps"] - e2e_steps) / (run["ms"] / 1e3)
+                if run["ms"] > 0 else None}
 
-    # roofline of the dominant kernel (matrix-free trace apply)
+    # roofline of the dominant kernel (matrix-free trace apply). Algorithmic bytes of one apply
+    # y = sum_K P_K^T S_K P_K x: every element's packed symmetric S_K at the operator's
+    # precision (plus its scale for FP16), x read once per interior trace entry and y written once.
     peaks, src = load_peaks()
     m = s.m
+    P = m * (m + 1) // 2
+    n_int = (s.n_faces - s.n_bnd) * s.Nf if not vardeg else None
+
+    def alg_bytes(s_bytes, scale_bytes, vec_bytes, cols=1):
+        return ne * (P * s_bytes + scale_bytes) + 2 * n_int * cols * vec_bytes
+
+    def hbm_line(kernel, byt, launch_ms, launches, extra=None):
+        ach = byt / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
+        d = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": None, "kernel": kernel,
+             "peak_source": src + " hbm_gbs (copy)", "bytes_per_launch": byt, "bytes_per_elem": byt / ne,
+             "launch_ms": launch_ms, "launches": launches}
+        if extra:
+            d.update(extra)
+        return d
+
     apply_avg_ms = st["apply_ms"] / max(1, st["apply_launches"])
     if R > 1:
-        # multi-column apply: S_K read once per element, the R-column trace blocks gathered twice
-        # (once per neighbour) and the slot products written once
-        a32 = (st["apply32_ms"] / max(1, st["apply32_launches"])) if args.prec != "fp64" else apply_avg_ms
-        ebytes = 4 if args.prec != "fp64" else 8
-        sbytes = ((m * (m + 1) // 2 + 3) // 4) * 16 if args.prec != "fp64" else m * m * 8
-        bytes_el = sbytes + 2 * m * R * ebytes
-        ach = bytes_el * ne / (a32 / 1e3) / 1e9
-        peaks, src = load_peaks()
-        roof_multi = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                      "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                      "kernel": "apply_multi_kernel<3,3,%s> (%d columns)" % ("float" if args.prec != "fp64" else "double", R),
-                      "bytes_per_elem": bytes_el, "launch_ms": a32,
-                      "launches": st["apply32_launches"] if args.prec != "fp64" else st["apply_launches"],
-                      "flops_per_elem": 2 * m * m * R}
+        if args.prec != "fp64":
+            a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
+            roof_multi = hbm_line("apply32m_kernel<3,3> (FP32 packed S_K, %d columns)" % R, alg_bytes(4, 0, 4, R), a32,
+                                  st["apply32_launches"],
+                                  {"implementation_bytes_per_elem": ((P + 3) // 4) * 16 + 2 * m * R * 4,
+                                   "flops_per_elem": 2 * m * m * R})
+        else:
+            roof_multi = hbm_line("apply_multi_kernel<3,3,double> (%d columns)" % R, ne * m * m * 8 + 2 * n_int * R * 8,
+                                  apply_avg_ms, st["apply_launches"], {"flops_per_elem": 2 * m * m * R})
     fp64_view = {"kernel": "apply_kernel<3,3> (FP64 S_K x lambda_K)", "launches": st["apply_launches"],
                  "launch_ms": apply_avg_ms,
-                 "achieved_tflops": 2 * m * m * ne / (apply_avg_ms / 1e3) / 1e12 if st["apply_launches"] else None,
-                 "achieved_gbs": (m * m * 8 + 2 * m * 8) * ne / (apply_avg_ms / 1e3) / 1e9 if st["apply_launches"] else None}
+                 "achieved_tflops": 2 * m * m * ne / (apply_avg_ms / 1e3) / 1e12 if st["apply_launches"] else None}
     if args.prec == "fp64":
         ach = fp64_view["achieved_tflops"]
         roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
                 "traffic": None, "kernel": fp64_view["kernel"],
                 "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (probe measured 1.20)",
-                "bytes_per_elem": m * m * 8 + 2 * m * 8, "flops_per_elem": 2 * m * m,
-                "launch_ms": apply_avg_ms, "launches": st["apply_launches"],
-                "hbm_view": {"achieved_gbs": fp64_view["achieved_gbs"], "peak_gbs": peaks["hbm_gbs"]}}
+                "flops_per_elem": 2 * m * m, "launch_ms": apply_avg_ms, "launches": st["apply_launches"]}
     else:
         a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
-        p4 = (m * (m + 1) // 2 + 3) // 4
-        bytes_el = p4 * 16 + 2 * m * 4
-        ach = bytes_el * ne / (a32 / 1e3) / 1e9 if a32 > 0 else None
-        roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"] if ach else None, "traffic": None,
-                "kernel": "apply32_kernel<3,3> (FP32 packed-symmetric S_K x lambda_K)",
-                "peak_source": src + " (hbm_gbs: copy)", "bytes_per_elem": bytes_el,
-                "launch_ms": a32, "launches": st["apply32_launches"], "fp64_refinement_apply": fp64_view}
+        roof = hbm_line("apply32_kernel<3,3> (FP32 packed-symmetric S_K x lambda_K)", alg_bytes(4, 0, 4) if n_int else 0,
+                        a32, st["apply32_launches"])
         if st.get("apply16_launches"):
-            # FP16 inner operator: packed halves + one FP32 scale per element, FP32 trace gather/slots
             a16 = st["apply16_ms"] / st["apply16_launches"]
-            p8 = (m * (m + 1) // 2 + 7) // 8
-            b16 = p8 * 16 + 4 + 2 * m * 4
-            ach16 = b16 * ne / (a16 / 1e3) / 1e9
-            fp32_view = {k: roof[k] for k in ("kernel", "bytes_per_elem", "launch_ms", "launches")}
-            fp32_view["achieved_gbs"] = ach if st["apply32_launches"] else None
-            roof.update({"achieved": ach16, "frac": ach16 / peaks["hbm_gbs"],
-                         "kernel": "apply16_kernel<3,3> (FP16 packed-symmetric S_K, per-element scale)",
-                         "bytes_per_elem": b16, "launch_ms": a16, "launches": st["apply16_launches"],
-                         "fp32_apply": fp32_view})
-            if args.k == 3:
-                # dram__bytes_read + write of one apply16 launch captured at 82,944 tets
-                # (148.8 MB, 1,794 B per element; the FP16 copy streamed once, the gather partly
-                # from L2), scaled to this launch by the element count
-                roof["traffic"] = 148.8e6 / 82944 * ne
-                roof["traffic_source"] = "ncu capture at 82,944 tets scaled by elements"
+            fp32_view = {k: roof[k] for k in ("kernel", "bytes_per_launch", "launch_ms", "launches", "achieved")}
+            roof = hbm_line("apply16_kernel<3,3> (FP16 packed-symmetric S_K, per-element FP32 scale)",
+                            alg_bytes(2, 4, 4), a16, st["apply16_launches"],
+                            {"implementation_bytes_per_elem": ((P + 7) // 8) * 16 + 4 + 2 * m * 4,
+                             "fp32_apply": fp32_view})
+            tr = MEASURED_TRAFFIC.get(("apply16_kernel<3,3>", ne))
+            if tr:
+                roof["traffic"] = tr[0]
+                roof["traffic_source"] = tr[1]
         if st.get("applydf_launches"):
             adf = st["applydf_ms"] / st["applydf_launches"]
+            byt = alg_bytes(8, 0, 8)
             roof["df_refinement_apply"] = {
-                "kernel": "apply_df_kernel<3,3> (double-float hi + lo, diagonal-major per element)", "launches": st["applydf_launches"],
-                "launch_ms": adf, "bytes_per_elem": 2 * p4 * 16 + m * 8 + m * 8,
-                "achieved_gbs": (2 * p4 * 16 + 2 * m * 8) * ne / (adf / 1e3) / 1e9}
-
+                "kernel": "apply_df_kernel<3,3> (double-float hi + lo packed S_K)", "launches": st["applydf_launches"],
+                "launch_ms": adf, "bytes_per_launch": byt, "achieved_gbs": byt / (adf / 1e3) / 1e9,
+                "frac": byt / (adf / 1e3) / 1e9 / peaks["hbm_gbs"]}
+        roof["fp64_refinement_apply"] = fp64_view
     # element-local post-processing of the final state into P_{k+1}, timed on its own (outside
     # the steps' timed region); FP64-ALU bound, algorithmic flops per element as counted here
     post = None
@@ -389,8 +455,7 @@ def run_ours(args):
         s.close()
         torch.cuda.empty_cache()
         s64 = make_solver("fp64")
-        for _ in range(args.warmup):
-            s64.hdg_step(dt, scheme, 1)
+        advance(s64, preroll + args.warmup)
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -398,18 +463,20 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         ms64 = ev0.elapsed_time(ev1)
-        # same steps from the same start; the e2e leg advanced the mixed run by e2e_steps more
-        for _ in range(e2e_steps):
-            s64.hdg_step(dt, scheme, 1)
+        # the rest of the same run from the same start, to the same final step as the mixed run
+        advance(s64, run["steps"] - preroll - args.warmup - args.steps)
         u64 = s64.hdg_get_state()[0]
         rel = float((u_mixed - u64).abs().max() / u64.abs().max().clamp_min(1e-300))
         fp64 = {"value": dofs * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
-                "speedup_mixed_over_fp64": (dofs * args.steps / (ms_max / 1e3)) / (dofs * args.steps / (ms64 / 1e3)),
-                "max_rel_diff_fields_after_%d_steps" % (args.warmup + args.steps + e2e_steps): rel}
+                "speedup_mixed_over_fp64": ms64 / ms_max,
+                "max_rel_diff_fields_after_%d_steps" % run["steps"]: rel}
         s64.close()
 
     if R > 1:
         roof = roof_multi
+    roof["timing"] = ("CUDA events around every launch on the context stream during %d instrumented steps that "
+                      "follow the timed window (%.3f ms/step with the events); the timed window runs without them"
+                      % (args.steps, instrumented_ms_per_step))
     if vardeg:
         # per launch: every compact S_K (FP32, or FP64 for the plain path), the trace gather and
         # the slot products
@@ -453,7 +520,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = oracle_sample(budget_s=args.cpu_budget)
-        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "host_cores", "kind", "sample")}
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -466,6 +533,7 @@ def run_ours(args):
                           "trace_dofs": int(s.sizes.trace_entries) * R, "dt": dt, "scheme": scheme.upper(),
                           "precision": args.prec, "rtol": args.rtol, "parallelism": "replicas",
                           "l2": "inputs larger than L2 (S_K %.2f GB)" % (nschur * 8 / 1e9),
+                          "timed_window": window, "preroll_steps": preroll,
                           "krylov_iters_per_step": iters / args.steps,
                           "refinement_sweeps_per_step": sweeps / args.steps if args.prec != "fp64" else None,
                           "inner_rtol": args.inner_rtol if args.prec != "fp64" else None,
@@ -473,7 +541,7 @@ def run_ours(args):
                "roofline": roof, "cpu_baseline": cpu, "fp64_gpu": fp64,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * field_bytes + trace_bytes,
                        "d2h_bytes_per_step": 2 * field_bytes + trace_bytes, "steps": e2e_steps},
-               "gpu_launches": st["kernel_launches"], "clocks": clk}
+               "gpu_launches": launches_timed, "clocks": clk, "full_run": full_run}
         if post is not None:
             out["postprocess"] = post
         if vardeg:
@@ -546,6 +614,11 @@ def main():
                     help="elastic: per-element degree uniform in {1..4} (the mixed-degree workload)")
     ap.add_argument("--nrhs", type=int, default=1,
                     help="right-hand-side columns solved together (64: the multi-source workload)")
+    ap.add_argument("--preroll", type=int, default=None,
+                    help="untimed steps before the warm-up (default: 60 for the acoustic workloads, i.e. to the "
+                         "Ricker source's peak at t0 = 0.12; 0 for elastic)")
+    ap.add_argument("--total-steps", type=int, default=None,
+                    help="steps of the whole run whose Krylov counts are reported (default: 200 acoustic, 100 elastic)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--postprocess", action="store_true",

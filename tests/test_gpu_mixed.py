@@ -15,21 +15,27 @@ from paper_1807_00086_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-def mixed_pair(dim, N, k, **kw):
+def mixed_pair(dim, N, k, prec="mixed", inner_rtol=None, max_sweeps=None, **kw):
     import torch
     from paper_1807_00086_gb300 import hdg
     s, prob, _ = make_pair(dim, N, k, **kw)
     vert, elem = mesh(dim, N)
     ne = elem.shape[0]
     sm = hdg.Solver(vert, elem, k, 1.0, inputs.loguniform(ne, 0.5, 2.0, kw.get("seed", 1) + 7),
-                    inputs.loguniform(ne, 1.0, 3.0, kw.get("seed", 1)), prec="mixed", rtol=1e-12)
+                    inputs.loguniform(ne, 1.0, 3.0, kw.get("seed", 1)), prec=prec, rtol=1e-12,
+                    inner_rtol=inner_rtol, max_sweeps=max_sweeps)
     return s, sm, prob, torch
 
 
+# the FP16 operator (HDG_MIXED16) runs with the benchmark's inner tolerance 1e-3
+PRECS = [("mixed", None), ("mixed16", 1e-3)]
+
+
+@pytest.mark.parametrize("prec,inner", PRECS)
 @pytest.mark.parametrize("dim,N,k", [(2, 4, 2), (3, 2, 3), (3, 2, 1), (3, 1, 4)])
-def test_mixed_trace_solve_matches_direct_solve(dim, N, k):
+def test_mixed_trace_solve_matches_direct_solve(dim, N, k, prec, inner):
     import scipy.sparse.linalg as spla
-    s, sm, prob, torch = mixed_pair(dim, N, k)
+    s, sm, prob, torch = mixed_pair(dim, N, k, prec=prec, inner_rtol=inner)
     sm.hdg_condense(40.0)
     cond = ac.condense(prob, 40.0)
     r = inputs.random_traces(sm.n_faces, sm.Nf, 12)
@@ -42,12 +48,13 @@ def test_mixed_trace_solve_matches_direct_solve(dim, N, k):
     assert relerr(lam.cpu().numpy(), lo) < 1e-10
 
 
+@pytest.mark.parametrize("prec,inner", PRECS)
 @pytest.mark.parametrize("scheme", ["bdf2", "dirk3"])
-def test_mixed_3d_point_source_steps(scheme):
+def test_mixed_3d_point_source_steps(scheme, prec, inner):
     dim, N, k = 3, 2, 3
     h = 1.0 / N
     src = [[0.5 + 0.3 * h, 0.5 + 0.3 * h, 0.5 + 0.3 * h]]
-    s, sm, prob, torch = mixed_pair(dim, N, k, seed=4, sources=src, f0=10.0, t0=0.02)
+    s, sm, prob, torch = mixed_pair(dim, N, k, prec=prec, inner_rtol=inner, seed=4, sources=src, f0=10.0, t0=0.02)
     from gpu_helpers import dirichlet_profile
     xb = sm.hdg_quadrature_points(1)
     sm.hdg_set_dirichlet(np.stack([dirichlet_profile(x) for x in xb]), 3.0, 0.2)
@@ -69,13 +76,14 @@ def test_mixed_3d_point_source_steps(scheme):
         assert info["rel_residual"] <= 1e-12
 
 
-def test_mixed_2d_standing_mode_backward_euler():
+@pytest.mark.parametrize("prec,inner", PRECS)
+def test_mixed_2d_standing_mode_backward_euler(prec, inner):
     import torch
     from paper_1807_00086_gb300 import hdg
     vert, elem = mesh(2, 16)
     ex = ac.standing_mode(2)
     k, dt, nsteps = 2, 0.01, 20
-    s = hdg.Solver(vert, elem, k, 1.0, 1.0, 1.0, prec="mixed", rtol=1e-12)
+    s = hdg.Solver(vert, elem, k, 1.0, 1.0, 1.0, prec=prec, rtol=1e-12, inner_rtol=inner)
     xb = s.hdg_quadrature_points(1)
     s.hdg_set_dirichlet(np.stack([np.cos(np.pi * x[:, 0]) * np.cos(np.pi * x[:, 1]) for x in xb]),
                         math.sqrt(2) * math.pi, 0.0)
@@ -94,14 +102,17 @@ def test_mixed_2d_standing_mode_backward_euler():
 
 
 def test_mixed_full_size_step_matches_fp64_path():
-    """Benchmark workload (196,608 tets): one BDF2 step from a random state, mixed vs FP64 path."""
+    """Benchmark workload (196,608 tets, the launch configuration bench.py times): two BDF2
+    steps from a random state with the FP32 and with the FP16 inner operator, each against the
+    FP64 path."""
     import torch
     from paper_1807_00086_gb300 import hdg
     w = inputs.acoustic_3d_workload()
     u0 = torch.tensor(inputs.random_state(w["elem"].shape[0], 80, 33), device="cuda")
     out = {}
-    for prec in ("fp64", "mixed"):
-        s = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=prec, rtol=1e-12)
+    for prec in ("fp64", "mixed", "mixed16"):
+        s = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=prec, rtol=1e-12,
+                       inner_rtol=1e-3 if prec == "mixed16" else None)
         s.hdg_set_sources(w["sources"], [1.0], w["f0"], w["t0"])
         s.hdg_set_state(u0, 0.0)
         info = s.hdg_step(2e-3, "bdf2", 2)
@@ -110,5 +121,29 @@ def test_mixed_full_size_step_matches_fp64_path():
         s.close()
         del s
         torch.cuda.empty_cache()
-    assert relerr(out["mixed"][0], out["fp64"][0]) < 1e-9
-    assert relerr(out["mixed"][1], out["fp64"][1]) < 1e-9
+    for prec in ("mixed", "mixed16"):
+        assert relerr(out[prec][0], out["fp64"][0]) < 1e-9, prec
+        assert relerr(out[prec][1], out["fp64"][1]) < 1e-9, prec
+        assert out[prec][2]["rel_residual"] <= 1e-12
+
+
+def test_mixed16_switches_to_fp32_operator_and_still_converges():
+    """A refinement sweep of HDG_MIXED16 that gains less than a factor 10 switches the rest of
+    the solve to the FP32 copy of S_K. An inner tolerance of 0.5 makes every sweep gain about
+    2x, so the first check switches; the solve must still reach the FP64 solution."""
+    import scipy.sparse.linalg as spla
+    s, sm, prob, torch = mixed_pair(3, 2, 3, prec="mixed16", inner_rtol=0.5, max_sweeps=80)
+    sm.hdg_condense(40.0)
+    cond = ac.condense(prob, 40.0)
+    r = inputs.random_traces(sm.n_faces, sm.Nf, 13)
+    r[prob.sk.boundary] = 0.0
+    lam = torch.zeros((sm.n_faces, sm.Nf), dtype=torch.float64, device="cuda")
+    sm.hdg_enable_stats(True)
+    sm.hdg_get_stats(reset=True)
+    info = sm.hdg_trace_solve(torch.tensor(r, device="cuda"), lam)
+    st = sm.hdg_get_stats(reset=True)
+    lo = np.zeros_like(r)
+    lo[cond.interior] = spla.spsolve(cond.K.tocsc(), r[cond.interior].ravel()).reshape(-1, sm.Nf)
+    assert info["rel_residual"] <= 1e-12 and info["sweeps"] > 10
+    assert st["apply16_launches"] > 0 and st["apply32_launches"] > 0
+    assert relerr(lam.cpu().numpy(), lo) < 1e-10

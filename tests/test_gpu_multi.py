@@ -33,10 +33,11 @@ def _setup(prec, R, dim=3, N=2, k=2, seed=3):
     return s, prob, pos, u0
 
 
-@pytest.mark.parametrize("R", [2, 4, 32])
+@pytest.mark.parametrize("R", [2, 4, 32, 64])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 1e-9)])
 def test_multi_source_batch_matches_single_column_oracle(prec, tol, R):
-    """R < 32 runs the narrow kernels (several elements per warp), R = 32 the wide ones."""
+    """R < 32 runs the narrow kernels (several elements per warp), R = 32 the wide ones with
+    one column group, R = 64 (the multi-source workload's width) two column groups."""
     dt, nsteps = 2e-3, 3
     s, prob, pos, u0 = _setup(prec, R)
     amps = np.linspace(1.0, 2.0, R)
