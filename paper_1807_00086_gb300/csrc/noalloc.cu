@@ -42,7 +42,8 @@ struct NaDims {
   static constexpr int NT = EPB * M;
 };
 
-// slot[e][r] = sum_c S_K[r][c] x_K[c] (x gathered from faces, boundary faces read as 0).
+// slot[e][r] = sum_c S_K[r][c] x_K[c] (x gathered from faces, boundary faces read as 0). Thread r
+// of an element walks row r of S_K, so S_K need not be symmetric.
 template <int DIM, int K>
 __global__ void __launch_bounds__(NaDims<DIM, K>::NT)
     noalloc_elem_kernel(int64_t ne, const double* __restrict__ S, const int32_t* __restrict__ elem_face,
@@ -58,9 +59,9 @@ __global__ void __launch_bounds__(NaDims<DIM, K>::NT)
   }
   __syncthreads();
   if (e < ne) {
-    const double* Se = S + e * (int64_t)(M * M);
+    const double* Sr = S + e * (int64_t)(M * M) + (int64_t)r * M;
     double acc = 0.0;
-    for (int c = 0; c < M; ++c) acc += Se[c * M + r] * lx[el][c];
+    for (int c = 0; c < M; ++c) acc += Sr[c] * lx[el][c];
     slot[e * M + r] = acc;
   }
 }
@@ -123,12 +124,23 @@ extern "C" hdg_status hdg_trace_apply_noalloc(int32_t dim, int32_t k, int64_t n_
     put_err(err, err_len, "hdg_trace_apply_noalloc: no usable current device");
     return HDG_ECUDA;
   }
-  double* slot;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // The host-side name of the array is only a stand-in, so the kernels get its device address,
+  // looked up with the device current. The lookup allocates nothing. It is repeated on every
+  // call made while `st` is not being captured, so a context re-created after cudaDeviceReset
+  // never sees a stale address; while `st` is being captured no lookup is made and the address
+  // of the last call on this device is used, so the first call on a device must come before
+  // any stream capture.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) {
+    put_err(err, err_len, "hdg_trace_apply_noalloc: cudaStreamIsCapturing failed");
+    return HDG_ECUDA;
+  }
+  double* slot = nullptr;
   {
-    // one-time set-up per device, with that device current: the host-side name of the
-    // array is only a stand-in, so the kernels get its device address.
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_slot_scratch);
       if (e != cudaSuccess || !p) {
@@ -136,10 +148,13 @@ extern "C" hdg_status hdg_trace_apply_noalloc(int32_t dim, int32_t k, int64_t n_
         return HDG_ECUDA;
       }
       g_scratch_ptr[dev] = (double*)p;
+    } else if (!g_scratch_ptr[dev]) {
+      put_err(err, err_len,
+              "hdg_trace_apply_noalloc: the first call on a device must come before any stream capture");
+      return HDG_ESTATE;
     }
     slot = g_scratch_ptr[dev];
   }
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   switch (dim * 10 + k) {
     case 21: launch_noalloc<2, 1>(n_elem, n_faces, S_dev, elem_face_dev, face_slot_dev, face_bnd_dev, x_dev, y_dev, slot, st); break;
     case 22: launch_noalloc<2, 2>(n_elem, n_faces, S_dev, elem_face_dev, face_slot_dev, face_bnd_dev, x_dev, y_dev, slot, st); break;
