@@ -218,14 +218,15 @@ def run_ours(args):
         if elastic:
             sv = hdg.Solver(w["vert"], w["elem"], w["k"], 1.0, w["rho"], lam=w["lam"], mu=w["mu"], prec=prec,
                             rtol=args.rtol, inner_rtol=args.inner_rtol, elem_k=w.get("elem_k"),
-                            guess_history=args.guess_history)
+                            guess_history=args.guess_history, device_loops=not args.host_loops)
             if u_init is None:
                 xq = sv.hdg_quadrature_points(0)
                 u_init = sv.hdg_project_volume(inputs.gaussian_velocity_values(xq, w["center"], w["width"], 9))
             sv.hdg_set_state(u_init, 0.0)
             return sv
         sv = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=prec, rtol=args.rtol,
-                        inner_rtol=args.inner_rtol, nrhs=R, guess_history=args.guess_history)
+                        inner_rtol=args.inner_rtol, nrhs=R, guess_history=args.guess_history,
+                        device_loops=not args.host_loops, trace_space=args.trace_space)
         sv.hdg_set_sources(w["sources"], np.ones(len(w["sources"])), w["f0"], w["t0"], col=w.get("source_cols"))
         sv.hdg_set_dirichlet(None)
         sv.hdg_set_state(sv.empty_fields(), 0.0)
@@ -391,7 +392,9 @@ def run_ours(args):
     fp64_view = {"kernel": "apply_kernel<3,3> (FP64 S_K x lambda_K)", "launches": st["apply_launches"],
                  "launch_ms": apply_avg_ms,
                  "achieved_tflops": 2 * m * m * ne / (apply_avg_ms / 1e3) / 1e12 if st["apply_launches"] else None}
-    if args.prec == "fp64":
+    if vardeg:
+        roof = {}   # set below from the compact per-element-degree blocks
+    elif args.prec == "fp64":
         ach = fp64_view["achieved_tflops"]
         roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
                 "traffic": None, "kernel": fp64_view["kernel"],
@@ -474,9 +477,6 @@ def run_ours(args):
 
     if R > 1:
         roof = roof_multi
-    roof["timing"] = ("CUDA events around every launch on the context stream during %d instrumented steps that "
-                      "follow the timed window (%.3f ms/step with the events); the timed window runs without them"
-                      % (args.steps, instrumented_ms_per_step))
     if vardeg:
         # per launch: every compact S_K (FP32, or FP64 for the plain path), the trace gather and
         # the slot products
@@ -517,6 +517,9 @@ def run_ours(args):
                 "bytes_per_elem": bytes_el, "launch_ms": a32, "launches": st["apply32_launches"],
                 "fp64_refinement_apply": fp64_view}
 
+    roof["timing"] = ("CUDA events around every launch on the context stream during %d instrumented steps that "
+                      "follow the timed window (%.3f ms/step with the events); the timed window runs without them"
+                      % (args.steps, instrumented_ms_per_step))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = oracle_sample(budget_s=args.cpu_budget)
@@ -528,7 +531,8 @@ def run_ours(args):
                "data": "synthetic",
                "config": {"workload": ("elastic3d_k%s_%dcube_dirk3" % ("mix1to4" if vardeg else args.k,
                                                                     round((ne / 6) ** (1 / 3))) if elastic else
-                                       "acoustic3d_k3_32cube_bdf2" + ("_%dsrc" % R if R > 1 else "")), "n_elem": ne,
+                                       "acoustic3d_k3_32cube_bdf2" + ("_%dsrc" % R if R > 1 else "") +
+                                       ("_" + args.trace_space if args.trace_space != "hdg" else "")), "n_elem": ne,
                           "k": "U{1..4} per element" if vardeg else args.k, "dofs": dofs, "nrhs": R,
                           "trace_dofs": int(s.sizes.trace_entries) * R, "dt": dt, "scheme": scheme.upper(),
                           "precision": args.prec, "rtol": args.rtol, "parallelism": "replicas",
@@ -537,7 +541,11 @@ def run_ours(args):
                           "krylov_iters_per_step": iters / args.steps,
                           "refinement_sweeps_per_step": sweeps / args.steps if args.prec != "fp64" else None,
                           "inner_rtol": args.inner_rtol if args.prec != "fp64" else None,
-                          "guess_history": args.guess_history if R == 1 else None},
+                          "guess_history": args.guess_history if R == 1 else None,
+                          "trace_space": args.trace_space,
+                          "trace_unknowns": int(s.sizes.trace_unknowns) * R,
+                          "trace_solve": "host-driven loops" if (args.host_loops or R > 1) else
+                          "one CUDA-graph launch per trace solve (device-side loop conditions)"},
                "roofline": roof, "cpu_baseline": cpu, "fp64_gpu": fp64,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * field_bytes + trace_bytes,
                        "d2h_bytes_per_step": 2 * field_bytes + trace_bytes, "steps": e2e_steps},
@@ -619,6 +627,10 @@ def main():
                          "Ricker source's peak at t0 = 0.12; 0 for elastic)")
     ap.add_argument("--total-steps", type=int, default=None,
                     help="steps of the whole run whose Krylov counts are reported (default: 200 acoustic, 100 elastic)")
+    ap.add_argument("--trace-space", default="hdg", choices=["hdg", "iedg", "edg"],
+                    help="acoustic, one column: continuous traces on the interior (iedg) or all (edg) faces")
+    ap.add_argument("--host-loops", action="store_true",
+                    help="host-driven Krylov and refinement loops (polled) instead of one graph launch per trace solve")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--postprocess", action="store_true",

@@ -115,7 +115,26 @@ typedef struct {
                             /* columns each column has its own fit; hdg_reset_column  */
                             /* drops a column's pairs. 0: the polynomial extrapolation */
                             /* of the last traces (BDF only)                           */
+  int32_t device_loops;     /* nrhs = 1: each trace solve is one CUDA-graph launch whose */
+                            /* Krylov iterations and refinement sweeps are WHILE loops   */
+                            /* with conditions set on the device (no host polling; the   */
+                            /* graphs are built at the first solve per buffer pair and   */
+                            /* kept). 0: host-driven loops polled every check_every      */
+                            /* iterations. Statistics (hdg_enable_stats) use the host-   */
+                            /* driven loops, which time each apply with CUDA events      */
+  int32_t trace_space;      /* Sec. 2.2, Eq. e:spaces2: HDG_TRACE_HDG (default) traces   */
+                            /* discontinuous across face edges; HDG_TRACE_IEDG traces    */
+                            /* continuous on the interior faces (unknowns: the degree-k  */
+                            /* equispaced face nodes shared between interior faces;      */
+                            /* boundary faces keep the L2-projected Dirichlet data);     */
+                            /* HDG_TRACE_EDG continuous on all faces (nodes on the       */
+                            /* boundary fixed; homogeneous Dirichlet data only). The     */
+                            /* trace system is then R^T K R mu = R^T r, lam_F = V^{-1}   */
+                            /* mu(nodes of F). Acoustic, uniform k, nrhs = 1,            */
+                            /* device_loops = 1                                          */
 } hdg_options;
+
+enum { HDG_TRACE_HDG = 0, HDG_TRACE_IEDG = 1, HDG_TRACE_EDG = 2 };
 
 typedef struct {
   int32_t dim, k, Np, Nf, n_local, n_trace_local;  /* n_local = n, n_trace_local = m */
@@ -129,6 +148,8 @@ typedef struct {
                             /* degrees the sum of the faces' own sizes                */
   int64_t schur_entries;    /* stored S_K entries summed over the elements (m^2 each) */
   int64_t slot_entries;     /* element trace entries summed over the elements (m each) */
+  int64_t trace_unknowns;   /* unknowns of the global trace system: interior trace      */
+                            /* entries (HDG) or free shared face nodes (IEDG / EDG)     */
 } hdg_sizes;
 
 typedef struct {
@@ -138,7 +159,7 @@ typedef struct {
 } hdg_solve_info;
 
 /* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1,
- * use_graphs 0, guess_history 8. */
+ * use_graphs 0, guess_history 8, device_loops 1, trace_space HDG_TRACE_HDG. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face
@@ -175,7 +196,9 @@ hdg_status hdg_condensed_rhs(hdg_ctx* ctx, const double* F_dev, const double* la
 /* Krylov solve of K lam = r on interior faces (preconditioned CG on -K, which is SPD).
  * r_dev, lam_dev: [n_faces][Nf]; lam_dev on entry is the initial guess (interior
  * entries), on exit the solution; its boundary entries are left unchanged. Completes
- * before returning; fills info (may be NULL). HDG_ENOCONV if maxit was reached. */
+ * before returning; fills info (may be NULL). HDG_ENOCONV if maxit was reached.
+ * IEDG / EDG contexts solve R^T K R mu = R^T r from mu = 0 and return lam = R mu on the
+ * interior faces (the entry values of lam_dev are not used as a guess). */
 hdg_status hdg_trace_solve(hdg_ctx* ctx, const double* r_dev, double* lam_dev, hdg_solve_info* info);
 
 /* Local recovery: u_K = A_K^{-1} (F_K - B_K lam_K) for every element, lam_dev over all
@@ -292,9 +315,16 @@ hdg_status hdg_step(hdg_ctx* ctx, double dt, hdg_scheme scheme, int32_t nsteps, 
  * latency-bound loop, code confined to memory it was handed at start-up, or plug-ins
  * that may not touch the process's allocator. It computes the same y = K x as
  * hdg_trace_apply, with every input and output owned by the caller and no context:
- *   S_dev          [n_elem][m][m]   element Schur blocks (e.g. copied by hdg_get_schur)
- *   elem_face_dev  [n_elem][dim+1]  face id of local face j (faces in the library's
- *                                   lexicographic order, local face j opposite vertex j)
+ *   S_dev          [n_elem][m][m]   element Schur blocks, row-major (e.g. copied by
+ *                                   hdg_get_schur); y gathers S_K x_K, so S_K need not be
+ *                                   symmetric
+ *   elem_face_dev  [n_elem][dim+1]  face id of local face j, where the element's vertices are
+ *                                   taken in ascending global id and local face j is the face
+ *                                   opposite the j-th of them (faces numbered in the library's
+ *                                   lexicographic order of sorted vertex ids; a face's trace
+ *                                   modes are parametrised from its vertices in ascending
+ *                                   global id, as hdg_setup does; tables built from unsorted
+ *                                   connectivity give a wrong y without an error)
  *   face_slot_dev  [n_faces][2]     slots e*(dim+1)+j of the face's elements, lower element
  *                                   first, -1 for the missing side of a boundary face
  *   face_bnd_dev   [n_faces]        >= 0 on boundary faces, -1 on interior faces
@@ -303,12 +333,12 @@ hdg_status hdg_step(hdg_ctx* ctx, double dt, hdg_scheme scheme, int32_t nsteps, 
  * per-element products, lives in one fixed 8 MiB device array inside the library (held
  * by every GPU that loads it until the process exits), so n_elem * m may not exceed
  * 1,048,576 (26,214 tetrahedra at k = 3); larger sizes return HDG_EINVAL with a message
- * in err (err_len bytes, may be NULL). The first call on each device looks up the
- * array's device address with that device current; make that first call before any
- * stream capture. The call enqueues work and returns; it allocates and frees nothing.
- * Every call shares the one array and leaves its products there; each call writes every
- * entry it reads before reading it, so nothing has to be cleared, but calls whose work
- * overlaps on the GPU (e.g. on two streams at once) race on the array. */
+ * in err (err_len bytes, may be NULL). Each call looks up the array's device address with
+ * the current device (no allocation); the first call on each device must come before any
+ * stream capture (HDG_ESTATE otherwise). The call enqueues work and returns; it allocates
+ * and frees nothing. Every call shares the one array and leaves its products there; each
+ * call writes every entry it reads before reading it, so nothing has to be cleared, but
+ * calls whose work overlaps on the GPU (e.g. on two streams at once) race on the array. */
 hdg_status hdg_trace_apply_noalloc(int32_t dim, int32_t k, int64_t n_elem, int64_t n_faces, const double* S_dev,
                                    const int32_t* elem_face_dev, const int32_t* face_slot_dev,
                                    const int32_t* face_bnd_dev, const double* x_dev, double* y_dev,

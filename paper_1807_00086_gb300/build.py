@@ -23,9 +23,17 @@ def build(verbose=False):
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
 
+    # a unit is rebuilt when it, a header of the library or this script is newer than its object
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    deps += [os.path.join(HERE, "..", "include", "hdg.h"), os.path.abspath(__file__)]
+    newest_dep = max(os.path.getmtime(d) for d in deps if os.path.exists(d))
+
     def compile_unit(u):
         obj = os.path.join(objdir, u + ".o")
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", os.path.join(CSRC, u), "-o", obj]
+        src = os.path.join(CSRC, u)
+        if os.path.exists(obj) and os.path.getmtime(obj) > max(newest_dep, os.path.getmtime(src)):
+            return obj
+        cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (u, " ".join(cmd), r.stderr))

@@ -17,6 +17,7 @@
 #include "dflocal.cuh"
 #include "multi.cuh"
 #include "elastic.cuh"
+#include "edg.cuh"
 #include "mesh.h"
 #include "reftab.h"
 
@@ -171,10 +172,16 @@ void launch_apply_df(hdg_ctx* c, const double* x, double* zslot) {
   using C = ApplyDfCfg<DIM, K>;
   const unsigned grid = (unsigned)((c->sk.ne + C::EPB - 1) / C::EPB);
   c->n_launch += 1;
-  cudaFuncSetAttribute(apply_df_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
   cudaEvent_t stop = apply_begin(c, 2, -1);
   apply_df_kernel<DIM, K><<<grid, C::NT, C::SMEM, c->stream>>>(devmesh(c), c->d_Sdf, x, zslot);
   apply_end(c, stop);
+}
+
+// dynamic shared memory of the double-float apply (set outside any stream capture)
+template <int DIM, int K>
+void attr_apply_df(hdg_ctx* c) {
+  (void)c;
+  cudaFuncSetAttribute(apply_df_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ApplyDfCfg<DIM, K>::SMEM);
 }
 
 template <int DIM, int K>
@@ -201,8 +208,54 @@ void launch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, in
   apply_end(c, stop);
 }
 
+// ---- continuous traces (IEDG / EDG): expansion lam = R mu and restriction R^T (face weights)
+template <int DIM, int K>
+void edg_expand64(hdg_ctx* c, const double* mu, double* lam, int zero_bnd) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  c->n_launch += 1;
+  edg_expand_kernel<double, NF><<<grid_for(c, c->sk.nf * NF), 256, 0, c->stream>>>(c->sk.nf, c->d_face_bnd, c->d_face_node,
+                                                                                   c->d_vinv, mu, lam, zero_bnd);
+}
+
+template <int DIM, int K>
+void edg_expand32(hdg_ctx* c, const float* mu, float* lam) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  c->n_launch += 1;
+  edg_expand_kernel<float, NF><<<grid_for(c, c->sk.nf * NF), 256, 0, c->stream>>>(c->sk.nf, c->d_face_bnd, c->d_face_node,
+                                                                                  c->d_vinv, mu, lam, 1);
+}
+
+// face nodal weights from element slots (slot) or from a face array (yface)
+template <int DIM, int K>
+void edg_face_w64(hdg_ctx* c, const double* slot, const double* yface, double* w) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  c->n_launch += 1;
+  edg_face_w_kernel<double, NF><<<grid_for(c, c->sk.nf), 256, 0, c->stream>>>(c->sk.nf, c->d_face_slot, c->d_face_bnd,
+                                                                              c->d_vinv, slot, yface, w);
+}
+
+template <int DIM, int K>
+void edg_face_w32(hdg_ctx* c, const float* slot, float* w) {
+  constexpr int NF = Dims<DIM, K>::NF;
+  c->n_launch += 1;
+  edg_face_w_kernel<float, NF><<<grid_for(c, c->sk.nf), 256, 0, c->stream>>>(c->sk.nf, c->d_face_slot, c->d_face_bnd,
+                                                                             c->d_vinv, slot, nullptr, w);
+}
+
+// Jacobi diagonal of R^T K R (sgn convention of the Krylov operator), FP64 and FP32 copies
+template <int DIM, int K>
+void edg_diag(hdg_ctx* c) {
+  using D = Dims<DIM, K>;
+  c->n_launch += 2;
+  edg_diag_elem_kernel<DIM, D::NF><<<grid_for(c, c->sk.ne * D::M), 256, 0, c->stream>>>(
+      c->sk.ne, c->d_elem_face, c->d_face_node, c->d_vinv, c->d_S, c->d_slot);
+  edg_diag_node_kernel<<<grid_for(c, c->n_mu), 256, 0, c->stream>>>(c->n_mu, D::NF, c->d_node_ptr, c->d_node_inc,
+                                                                    c->d_face_slot, c->d_slot, c->sgn, c->d_dinv,
+                                                                    c->d_dinv32);
+}
+
 hdg_status do_condense(hdg_ctx* c, double alpha) {
-  c->g_n = c->g_next = 0;   // the stored stage solutions belong to the previous operator
+  guess_clear(c);   // the stored stage solutions belong to the previous operator
   if (c->vd) return vd_condense(c, alpha);
   if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(c, HDG_EINVAL, "alpha must be positive and finite");
   c->alpha = alpha;
@@ -230,6 +283,7 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
     } else {
       HDG_DISPATCH(c, launch_pack32, c);
       HDG_DISPATCH(c, launch_packdf, c);
+      HDG_DISPATCH(c, attr_apply_df, c);
       if (c->d_S16) HDG_DISPATCH(c, launch_pack16, c);
       const int64_t nH = c->sk.ne * (int64_t)c->nv * c->nv;
       c->n_launch += 1;
@@ -239,6 +293,13 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
     c->n_launch += 1;
     to32_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_dinv, c->d_dinv32);
     if ((s = check_launch(c, "pack32"))) return s;
+  }
+  if (c->tspace) {
+    // the nodal Jacobi diagonal replaces the face one; FP32 padding entries stay zero
+    HDG_DISPATCH(c, edg_diag, c);
+    if (c->d_dinv32 && c->n_mu4 > c->n_mu)
+      CUDA_TRY(c, cudaMemsetAsync(c->d_dinv32 + c->n_mu, 0, (size_t)(c->n_mu4 - c->n_mu) * 4, c->stream));
+    if ((s = check_launch(c, "edg_diag"))) return s;
   }
   int herr = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -264,7 +325,7 @@ hdg_status cg32_inner(hdg_ctx* c, int* iters, double tol, int* last, bool use16)
   c->n_launch += 2;
   cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32, (float4*)c->d_x32,
                                               (float4*)c->d_r32, (float4*)c->d_z32, (float4*)c->d_p32, c->d_part);
-  cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, tol, c->d_sc);
+  cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, tol, c->d_sc, nullptr);
   hdg_status s = check_launch(c, "cg32_init");
   if (s) return s;
   int it = 0;
@@ -294,7 +355,7 @@ hdg_status cg32_inner(hdg_ctx* c, int* iters, double tol, int* last, bool use16)
         HDG_DISPATCH(c, launch_update_f32, c, par);
       }
       cg32_direction_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, it, c->d_part + nb, (const float4*)c->d_z32,
-                                                       (float4*)c->d_p32, c->d_sc, maxit);
+                                                       (float4*)c->d_p32, c->d_sc, maxit, 0);
     }
     if ((s = check_launch(c, "cg32_iter"))) return s;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
@@ -364,8 +425,277 @@ hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
                                   " with relative residual " + std::to_string(rel));
 }
 
+// ---- device-driven solves (one graph launch per trace solve; loop conditions set on the device)
+// FP64 PCG on (sgn K) x = bvec: the initial residual, then a WHILE loop of two iterations per trip.
+hdg_status cg_solve_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int64_t nfe = c->sk.nf * c->Nf;
+  const int nb = c->nb_red, maxit = c->opt.maxit;
+  auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
+    std::vector<cudaGraphNode_t> deps, bd;
+    const int64_t n0 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr, -1);
+      c->n_launch += 2;
+      cg_init_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec,
+                                                c->d_dinv, c->d_r, c->d_z, c->d_p, c->d_part);
+      cg_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->opt.rtol, c->d_sc);
+    });
+    const cudaGraphConditionalHandle h = gb.handle(G, 1, true);
+    cudaGraph_t B = gb.loop(G, deps, h);
+    const int64_t n1 = c->n_launch;
+    gb.seq(B, bd, [&] {
+      for (int par = 0; par < 2; ++par) {
+        HDG_DISPATCH(c, launch_apply, c, c->d_p, c->d_slot, &c->d_sc->done, -1);
+        c->n_launch += 3;
+        HDG_DISPATCH(c, launch_face_q64, c);
+        cg_update_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, c->d_part, c->d_p, c->d_q, c->d_dinv, x, c->d_r, c->d_z,
+                                                    c->d_part + nb, c->d_sc);
+        cg_direction_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, -1, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit, h);
+      }
+    });
+    const int64_t n2 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 2;
+      cg_ctl_finish_kernel<<<1, 32, 0, c->stream>>>(c->d_sc, c->d_lc);
+      zero_masked_if_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_intmask, c->d_lc, x);
+    });
+    dg.n_static = (n1 - n0) + (c->n_launch - n2);
+    dg.n_body = 0;
+    dg.n_trip = n2 - n1;
+  };
+  return devgraph_solve(c, 0, bvec, x, build, info);
+}
+
+// Mixed precision: FP64 iterative refinement as a WHILE loop over sweeps; each sweep forms the
+// FP64-accurate residual, lets the control kernel decide (stop, operator, inner tolerance), and
+// runs the inner FP32 PCG with the FP16 or the FP32 copy of S_K as a nested WHILE loop.
+hdg_status solve_mixed_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int64_t nfe = c->sk.nf * c->Nf;
+  const int nb = c->nb_red, maxit = c->opt.maxit;
+  const int64_t n4 = c->nfe4 / 4;
+  const bool has16 = c->d_S16 != nullptr;
+  auto inner = [&](bool use16, cudaGraphConditionalHandle h) {
+    for (int par = 0; par < 2; ++par) {
+      if (use16) {
+        HDG_DISPATCH(c, launch_apply16, c, c->d_p32, c->d_slot32, &c->d_sc->done, -1);
+      } else {
+        HDG_DISPATCH(c, launch_apply32, c, c->d_p32, c->d_slot32, &c->d_sc->done, -1);
+      }
+      if (c->phys == HDG_ELASTIC) {
+        c->n_launch += 3;
+        HDG_DISPATCH(c, launch_face_q32, c);
+        cg32_update_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, c->d_part, (const float4*)c->d_p32,
+                                                      (const float4*)c->d_q32, (const float4*)c->d_dinv32,
+                                                      (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
+                                                      c->d_part + nb, c->d_sc);
+      } else {
+        c->n_launch += 2;
+        HDG_DISPATCH(c, launch_update_f32, c, par);
+      }
+      cg32_direction_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, -1, c->d_part + nb, (const float4*)c->d_z32,
+                                                       (float4*)c->d_p32, c->d_sc, maxit, h);
+    }
+  };
+  auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
+    std::vector<cudaGraphNode_t> deps, bd, d16, d32;
+    const int64_t n0 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 1;
+      loopctl_init_kernel<<<1, 32, 0, c->stream>>>(c->d_lc, has16 ? 1 : 0);
+    });
+    const cudaGraphConditionalHandle h_sweep = gb.handle(G, 1, true);
+    cudaGraph_t B = gb.loop(G, deps, h_sweep);
+    const cudaGraphConditionalHandle h16 = has16 ? gb.handle(B, 0, false) : 0;
+    const cudaGraphConditionalHandle h32 = gb.handle(B, 0, false);
+    const int64_t n1 = c->n_launch;
+    gb.seq(B, bd, [&] {
+      if (c->d_Sdf) {
+        HDG_DISPATCH(c, launch_apply_df, c, x, c->d_slot);
+      } else {
+        HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr, -1);
+      }
+      c->n_launch += 6;
+      refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot,
+                                                        bvec, c->d_res, c->d_part);
+      refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
+      sweep_ctl_kernel<<<1, 32, 0, c->stream>>>(c->d_rs, c->d_sc, c->d_lc, c->opt.rtol, c->opt.inner_rtol,
+                                                c->opt.max_sweeps, h_sweep, has16 ? 1 : 0, h16, h32);
+      to32_scaled_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_res, c->d_rs, c->d_b32);
+      cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32,
+                                                  (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
+                                                  (float4*)c->d_p32, c->d_part);
+      cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, 0.5, c->d_sc, &c->d_lc->tol);
+    });
+    const int64_t n2 = c->n_launch;
+    if (has16) {
+      cudaGraph_t B16 = gb.loop(B, bd, h16);
+      gb.seq(B16, d16, [&] { inner(true, h16); });
+    }
+    const int64_t n3 = c->n_launch;
+    cudaGraph_t B32 = gb.loop(B, bd, h32);
+    gb.seq(B32, d32, [&] { inner(false, h32); });
+    const int64_t n4_ = c->n_launch;
+    gb.seq(B, bd, [&] {
+      c->n_launch += 1;
+      refine_update_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_bnd, c->d_x32, c->d_rs, x);
+    });
+    const int64_t n5 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 1;
+      zero_masked_if_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_intmask, c->d_lc, x);
+    });
+    dg.n_static = (n1 - n0) + (c->n_launch - n5);
+    dg.n_body = (n2 - n1) + (n5 - n4_);
+    dg.n_trip = n4_ - n3;
+  };
+  return devgraph_solve(c, 1, bvec, x, build, info);
+}
+
+// ---- continuous traces: device-driven solves of (sgn R^T K R) mu = b_mu on the free nodes
+// FP64 PCG: every apply expands the nodal vector to face traces, applies the element blocks and
+// gathers the face nodal weights back to the nodes in a fixed order.
+hdg_status edg_cg_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int64_t n = c->n_mu;
+  const int nb = c->nb_red, maxit = c->opt.maxit;
+  auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
+    std::vector<cudaGraphNode_t> deps, bd;
+    const int64_t n0 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      HDG_DISPATCH(c, edg_expand64, c, x, c->d_ew64, 1);
+      HDG_DISPATCH(c, launch_apply, c, c->d_ew64, c->d_slot, (const int*)nullptr, -1);
+      HDG_DISPATCH(c, edg_face_w64, c, c->d_slot, (const double*)nullptr, c->d_w64);
+      c->n_launch += 2;
+      edg_cg_init_kernel<<<nb, 256, 0, c->stream>>>(n, c->sgn, c->d_node_ptr, c->d_node_inc, c->d_w64, bvec, c->d_dinv,
+                                                    c->d_r, c->d_z, c->d_p, c->d_part);
+      cg_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->opt.rtol, c->d_sc);
+    });
+    const cudaGraphConditionalHandle h = gb.handle(G, 1, true);
+    cudaGraph_t B = gb.loop(G, deps, h);
+    const int64_t n1 = c->n_launch;
+    gb.seq(B, bd, [&] {
+      for (int par = 0; par < 2; ++par) {
+        HDG_DISPATCH(c, edg_expand64, c, c->d_p, c->d_ew64, 1);
+        HDG_DISPATCH(c, launch_apply, c, c->d_ew64, c->d_slot, &c->d_sc->done, -1);
+        HDG_DISPATCH(c, edg_face_w64, c, c->d_slot, (const double*)nullptr, c->d_w64);
+        c->n_launch += 3;
+        edg_q64_kernel<<<nb, 256, 0, c->stream>>>(n, c->sgn, c->d_node_ptr, c->d_node_inc, c->d_w64, c->d_p, c->d_q,
+                                                  c->d_part, c->d_sc);
+        cg_update_kernel<<<nb, 256, 0, c->stream>>>(n, nb, par, c->d_part, c->d_p, c->d_q, c->d_dinv, x, c->d_r, c->d_z,
+                                                    c->d_part + nb, c->d_sc);
+        cg_direction_kernel<<<nb, 256, 0, c->stream>>>(n, nb, par, -1, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit, h);
+      }
+    });
+    const int64_t n2 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 2;
+      cg_ctl_finish_kernel<<<1, 32, 0, c->stream>>>(c->d_sc, c->d_lc);
+      zero_masked_if_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, nullptr, c->d_lc, x);
+    });
+    dg.n_static = (n1 - n0) + (c->n_launch - n2);
+    dg.n_body = 0;
+    dg.n_trip = n2 - n1;
+  };
+  return devgraph_solve(c, 4, bvec, x, build, info);
+}
+
+// Mixed precision: FP64-accurate residual through the double-float apply of the expanded face
+// traces, inner FP32 PCG on the nodes with the FP16 or FP32 element blocks.
+hdg_status edg_mixed_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int64_t n = c->n_mu;
+  const int nb = c->nb_red, maxit = c->opt.maxit;
+  const int64_t n4 = c->n_mu4 / 4;
+  const bool has16 = c->d_S16 != nullptr;
+  auto inner = [&](bool use16, cudaGraphConditionalHandle h) {
+    for (int par = 0; par < 2; ++par) {
+      HDG_DISPATCH(c, edg_expand32, c, c->d_p32, c->d_ew32);
+      if (use16) {
+        HDG_DISPATCH(c, launch_apply16, c, c->d_ew32, c->d_slot32, &c->d_sc->done, -1);
+      } else {
+        HDG_DISPATCH(c, launch_apply32, c, c->d_ew32, c->d_slot32, &c->d_sc->done, -1);
+      }
+      HDG_DISPATCH(c, edg_face_w32, c, c->d_slot32, c->d_w32);
+      c->n_launch += 2;
+      edg_update32_kernel<<<nb, 256, 0, c->stream>>>(n, (float)c->sgn, c->d_node_ptr, c->d_node_inc, c->d_w32, c->d_p32,
+                                                     c->d_dinv32, c->d_x32, c->d_r32, c->d_z32, par, c->d_pq, c->d_part,
+                                                     c->d_sc);
+      cg32_direction_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, -1, c->d_part, (const float4*)c->d_z32,
+                                                       (float4*)c->d_p32, c->d_sc, maxit, h);
+    }
+  };
+  auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
+    std::vector<cudaGraphNode_t> deps, bd, d16, d32;
+    const int64_t n0 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 1;
+      loopctl_init_kernel<<<1, 32, 0, c->stream>>>(c->d_lc, has16 ? 1 : 0);
+    });
+    const cudaGraphConditionalHandle h_sweep = gb.handle(G, 1, true);
+    cudaGraph_t B = gb.loop(G, deps, h_sweep);
+    const cudaGraphConditionalHandle h16 = has16 ? gb.handle(B, 0, false) : 0;
+    const cudaGraphConditionalHandle h32 = gb.handle(B, 0, false);
+    const int64_t n1 = c->n_launch;
+    gb.seq(B, bd, [&] {
+      HDG_DISPATCH(c, edg_expand64, c, x, c->d_ew64, 1);
+      if (c->d_Sdf) {
+        HDG_DISPATCH(c, launch_apply_df, c, c->d_ew64, c->d_slot);
+      } else {
+        HDG_DISPATCH(c, launch_apply, c, c->d_ew64, c->d_slot, (const int*)nullptr, -1);
+      }
+      HDG_DISPATCH(c, edg_face_w64, c, c->d_slot, (const double*)nullptr, c->d_w64);
+      c->n_launch += 6;
+      edg_residual_kernel<<<nb, 256, 0, c->stream>>>(n, c->sgn, c->d_node_ptr, c->d_node_inc, c->d_w64, bvec, c->d_res,
+                                                     c->d_part);
+      refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
+      sweep_ctl_kernel<<<1, 32, 0, c->stream>>>(c->d_rs, c->d_sc, c->d_lc, c->opt.rtol, c->opt.inner_rtol,
+                                                c->opt.max_sweeps, h_sweep, has16 ? 1 : 0, h16, h32);
+      to32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_res, c->d_rs, c->d_b32);
+      cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32,
+                                                  (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
+                                                  (float4*)c->d_p32, c->d_part);
+      cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, 0.5, c->d_sc, &c->d_lc->tol);
+    });
+    const int64_t n2 = c->n_launch;
+    if (has16) {
+      cudaGraph_t B16 = gb.loop(B, bd, h16);
+      gb.seq(B16, d16, [&] { inner(true, h16); });
+    }
+    const int64_t n3 = c->n_launch;
+    cudaGraph_t B32 = gb.loop(B, bd, h32);
+    gb.seq(B32, d32, [&] { inner(false, h32); });
+    const int64_t n4_ = c->n_launch;
+    gb.seq(B, bd, [&] {
+      c->n_launch += 1;
+      flat_refine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_x32, c->d_rs, x);
+    });
+    const int64_t n5 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 1;
+      zero_masked_if_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, nullptr, c->d_lc, x);
+    });
+    dg.n_static = (n1 - n0) + (c->n_launch - n5);
+    dg.n_body = (n2 - n1) + (n5 - n4_);
+    dg.n_trip = n4_ - n3;
+  };
+  return devgraph_solve(c, 5, bvec, x, build, info);
+}
+
+// b_mu = R^T b for a face array b (interior faces)
+hdg_status edg_restrict(hdg_ctx* c, const double* b, double* bmu) {
+  HDG_DISPATCH(c, edg_face_w64, c, (const double*)nullptr, b, c->d_w64);
+  c->n_launch += 1;
+  edg_node_gather_kernel<<<grid_for(c, c->n_mu), 256, 0, c->stream>>>(c->n_mu, c->d_node_ptr, c->d_node_inc, c->d_w64, 1.0,
+                                                                      bmu);
+  return check_launch(c, "edg_restrict");
+}
+
+// solve (sgn R^T K R) mu = bmu from the initial guess in mu
+hdg_status edg_solve(hdg_ctx* c, const double* bmu, double* mu, hdg_solve_info* info) {
+  return c->opt.prec != HDG_FP64 ? edg_mixed_graph(c, bmu, mu, info) : edg_cg_graph(c, bmu, mu, info);
+}
+
 // PCG on (-K) x = bvec over interior faces; x holds the initial guess (interior entries).
 hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  if (use_devgraph(c)) return c->opt.prec != HDG_FP64 ? solve_mixed_graph(c, bvec, x, info) : cg_solve_graph(c, bvec, x, info);
   if (c->opt.prec != HDG_FP64) return solve_mixed(c, bvec, x, info);
   const int64_t nfe = c->sk.nf * c->Nf;
   const int nb = c->nb_red;
@@ -397,7 +727,7 @@ hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* i
       HDG_DISPATCH(c, launch_face_q64, c);
       cg_update_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, c->d_part, c->d_p, c->d_q, c->d_dinv, x, c->d_r, c->d_z,
                                                   c->d_part + nb, c->d_sc);
-      cg_direction_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, it, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit);
+      cg_direction_kernel<<<nb, 256, 0, c->stream>>>(nfe, nb, par, it, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit, 0);
     }
     s = check_launch(c, "cg_iter");
     if (s) return s;
@@ -522,6 +852,7 @@ void mlaunch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, i
                                                          (const float4*)c->d_S32, x, slot, done);
   apply_end(c, stop);
 }
+
 
 template <int DIM, int K, typename TV>
 void mlaunch_face_q(hdg_ctx* c, const TV* slot, const TV* p, TV* q) {
@@ -738,6 +1069,16 @@ hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, 
   if (s) return s;
   // Krylov right-hand side b = sgn r = -sgn sum_K C_K A_K^{-1} F~_K
   if ((s = faces_from_slots(c, -c->sgn, c->d_b))) return s;
+  if (c->tspace) {
+    // continuous traces: b_mu = R^T b, solve on the free nodes, lam = R mu on interior faces
+    if ((s = edg_restrict(c, c->d_b, c->d_bmu))) return s;
+    if ((s = guess_before_v(c, c->n_mu, c->d_bmu, c->d_mu, nullptr))) return s;
+    if ((s = edg_solve(c, c->d_bmu, c->d_mu, info))) return s;
+    if ((s = guess_after_v(c, c->n_mu, c->d_bmu, c->d_mu))) return s;
+    HDG_DISPATCH(c, edg_expand64, c, c->d_mu, c->d_lam, 0);
+    HDG_DISPATCH(c, launch_local, c, 1, (const double*)nullptr, hist, tt, c->d_lam, uout);
+    return check_launch(c, "recover");
+  }
   if ((s = guess_before(c))) return s;
   if ((s = cg_solve(c, c->d_b, c->d_lam, info))) return s;
   if ((s = guess_after(c))) return s;
@@ -781,28 +1122,45 @@ void dirk3(double a[3][3], double b[3], double cc[3]) {
 // per column when there are several right-hand sides.
 hdg_status guess_setup(hdg_ctx* c, const uint8_t* host_mask) {
   c->g_q = 0;
-  if (c->opt.guess_history <= 0) return HDG_OK;
+  hdg_status s;
+  // the interior-entry mask and the control block of the device-driven solves exist always
+  if ((s = dalloc(c, &c->d_intmask, (size_t)c->ntr))) return s;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_intmask, host_mask, (size_t)c->ntr, cudaMemcpyHostToDevice, c->stream));
+  if ((s = dalloc(c, &c->d_lc, 1))) return s;
+  CUDA_TRY(c, cudaMallocHost((void**)&c->h_lc, sizeof(LoopCtl)));
+  if (c->opt.guess_history <= 0) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // host_mask is released at return
+    return HDG_OK;
+  }
   const int q = std::min(c->opt.guess_history, 8), R = c->R;
   const size_t n = (size_t)c->ntr * R;
-  hdg_status s;
   if ((s = dalloc(c, &c->d_gb, q * n))) return s;
   if ((s = dalloc(c, &c->d_gl, q * n))) return s;
   if ((s = dalloc(c, &c->d_gdots, (size_t)9 * R))) return s;
   if ((s = dalloc(c, &c->d_gpart, (size_t)c->nb_red * 9 * R))) return s;
-  if ((s = dalloc(c, &c->d_intmask, (size_t)c->ntr))) return s;
   if (R > 1) {
     if ((s = dalloc(c, &c->d_gcoef, (size_t)8 * R))) return s;
     c->gm_gram.assign((size_t)R * 64, 0.0);
     c->gm_dots.assign((size_t)9 * R, 0.0);
     c->gm_coef.assign((size_t)8 * R, 0.0);
+  } else {
+    if ((s = dalloc(c, &c->d_gd, 1))) return s;
   }
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_intmask, host_mask, (size_t)c->ntr, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_gb, 0, q * n * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_gl, 0, q * n * 8, c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->g_q = q;
+  guess_clear(c);
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return check_launch(c, "guess_setup");
+}
+
+// forget the stored pairs (new operator or new state)
+void guess_clear(hdg_ctx* c) {
   c->g_n = c->g_next = 0;
-  return HDG_OK;
+  if (c->d_gd) {
+    c->n_launch += 1;
+    guess_reset_kernel<<<1, 32, 0, c->stream>>>(c->d_gd, c->g_q);
+  }
 }
 
 namespace {
@@ -837,25 +1195,35 @@ bool ls_solve(int m, const double* G, const double* g, double* x) {
 }
 }  // namespace
 
+// one column, on the device: dots of the new right-hand side b (n entries) with the stored
+// b_i, the damped normal equations, and the combination written into x (entries with mask != 0;
+// null mask: every entry)
+hdg_status guess_before_v(hdg_ctx* c, int64_t n, const double* b, double* x, const uint8_t* mask) {
+  if (!c->g_q) return HDG_OK;
+  const int nb = c->nb_red;
+  c->n_launch += 3;
+  gdots_kernel<<<nb, 256, 0, c->stream>>>(n, c->d_gd, c->d_gb, b, c->d_gpart);
+  gsolve_kernel<<<1, 256, 0, c->stream>>>(nb, c->d_gpart, c->d_gd);
+  glincomb_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_gd, c->d_gl, mask, x);
+  return check_launch(c, "guess");
+}
+
+// one column: store (b, x) of the solve just finished and update the Gram matrix
+hdg_status guess_after_v(hdg_ctx* c, int64_t n, const double* b, const double* x) {
+  if (!c->g_q) return HDG_OK;
+  c->n_launch += 2;
+  gstore_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_gd, b, x, c->d_gb, c->d_gl);
+  gupdate_kernel<<<1, 32, 0, c->stream>>>(c->d_gd);
+  c->g_next = (c->g_next + 1) % c->g_q;
+  c->g_n = std::min(c->g_n + 1, c->g_q);
+  return check_launch(c, "guess_store");
+}
+
 hdg_status guess_before(hdg_ctx* c) {
   if (!c->g_q) return HDG_OK;
   const int R = c->R, m = c->g_n, nb = c->nb_red;
   const int64_t n = c->ntr * (int64_t)R;
-  if (R == 1) {
-    c->n_launch += 2;
-    dots_ring_kernel<<<nb, 256, 0, c->stream>>>(n, m, n, c->d_gb, c->d_b, c->d_gpart);
-    dots_final_kernel<<<1, 256, 0, c->stream>>>(nb, m, c->d_gpart, c->d_gdots);
-    CUDA_TRY(c, cudaMemcpyAsync(c->g_dots, c->d_gdots, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    if (m == 0) return HDG_OK;
-    double x[8];
-    if (!ls_solve(m, &c->g_gram[0][0], c->g_dots, x)) return HDG_OK;
-    Coef8 cf{};
-    for (int i = 0; i < m; ++i) cf.c[i] = x[i];
-    c->n_launch += 1;
-    lincomb_ring_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, m, n, c->d_gl, cf, c->d_intmask, c->d_lam);
-    return check_launch(c, "guess");
-  }
+  if (R == 1) return guess_before_v(c, n, c->d_b, c->d_lam, c->d_intmask);
   c->n_launch += 2;
   mdots_ring_kernel<<<nb, 256, 0, c->stream>>>(n, R, m, n, c->d_gb, c->d_b, c->d_gpart);
   mdots_final_kernel<<<1, 256, 0, c->stream>>>(nb, R, m, c->d_gpart, c->d_gdots);
@@ -887,19 +1255,14 @@ hdg_status guess_after(hdg_ctx* c) {
   const int R = c->R;
   const int64_t n = c->ntr * (int64_t)R;
   const int s = c->g_next;
+  if (R == 1) return guess_after_v(c, n, c->d_b, c->d_lam);
   CUDA_TRY(c, cudaMemcpyAsync(c->d_gb + (int64_t)s * n, c->d_b, n * 8, cudaMemcpyDeviceToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_gl + (int64_t)s * n, c->d_lam, n * 8, cudaMemcpyDeviceToDevice, c->stream));
-  if (R == 1) {
+  for (int j = 0; j < R; ++j) {
+    double* G = &c->gm_gram[(size_t)j * 64];
     for (int i = 0; i < c->g_n; ++i)
-      if (i != s) c->g_gram[s][i] = c->g_gram[i][s] = c->g_dots[i];
-    c->g_gram[s][s] = c->g_dots[c->g_n];
-  } else {
-    for (int j = 0; j < R; ++j) {
-      double* G = &c->gm_gram[(size_t)j * 64];
-      for (int i = 0; i < c->g_n; ++i)
-        if (i != s) G[s * 8 + i] = G[i * 8 + s] = c->gm_dots[(size_t)i * R + j];
-      G[s * 8 + s] = c->gm_dots[(size_t)c->g_n * R + j];
-    }
+      if (i != s) G[s * 8 + i] = G[i * 8 + s] = c->gm_dots[(size_t)i * R + j];
+    G[s * 8 + s] = c->gm_dots[(size_t)c->g_n * R + j];
   }
   c->g_next = (s + 1) % c->g_q;
   c->g_n = std::min(c->g_n + 1, c->g_q);
@@ -942,6 +1305,7 @@ void hdg_default_options(hdg_options* o) {
   o->nrhs = 1;
   o->use_graphs = 0;
   o->guess_history = 8;
+  o->device_loops = 1;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -1002,6 +1366,9 @@ hdg_status hdg_host_tables(int32_t dim, int32_t k, double* Dr, double* Ff, doubl
 void hdg_destroy(hdg_ctx* c) {
   if (!c) return;
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+  for (auto& g : c->dgraphs) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->h_lc) cudaFreeHost(c->h_lc);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
@@ -1031,6 +1398,11 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if (c->opt.nrhs < 1 || c->opt.nrhs > 256 || (c->opt.nrhs & (c->opt.nrhs - 1)))
     return fail(c, HDG_EINVAL, "nrhs must be a power of two in 1..256");
   c->R = c->opt.nrhs;
+  c->tspace = c->opt.trace_space;
+  if (c->tspace < HDG_TRACE_HDG || c->tspace > HDG_TRACE_EDG) return fail(c, HDG_EINVAL, "unknown trace space");
+  if (c->tspace != HDG_TRACE_HDG &&
+      (mat->phys != HDG_ACOUSTIC || c->R != 1 || mesh->elem_k || !c->opt.device_loops))
+    return fail(c, HDG_EINVAL, "IEDG / EDG traces: acoustic, uniform degree, nrhs = 1 and device_loops = 1 only");
   std::string err;
   if (mat->phys != HDG_ACOUSTIC && mat->phys != HDG_ELASTIC) return fail(c, HDG_EINVAL, "unknown physics");
   c->phys = mat->phys;
@@ -1238,6 +1610,48 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
     if ((s = dalloc(c, &c->d_rs, 1))) return s;
     CUDA_TRY(c, cudaMallocHost((void**)&c->h_rs, sizeof(RefScal)));
   }
+  std::vector<int32_t> fnode, node_ptr, node_inc;
+  std::vector<double> vinv;
+  if (c->tspace) {
+    // continuous traces: free face nodes, their incidence lists (face entries in increasing
+    // order, so node sums run in a fixed order) and the nodal-to-modal table
+    int64_t nfree = 0;
+    if (!build_trace_nodes(c->sk, k, c->tspace == HDG_TRACE_EDG, nfree, fnode, err)) return fail(c, HDG_EINVAL, err);
+    try {
+      vinv = face_nodal_to_modal(c->dim, k);
+    } catch (const std::exception& ex) {
+      return fail(c, HDG_EINVAL, ex.what());
+    }
+    node_ptr.assign((size_t)nfree + 1, 0);
+    for (int32_t v : fnode)
+      if (v >= 0) node_ptr[(size_t)v + 1] += 1;
+    for (int64_t i = 0; i < nfree; ++i) node_ptr[i + 1] += node_ptr[i];
+    node_inc.assign((size_t)node_ptr[nfree], 0);
+    std::vector<int32_t> fill(node_ptr.begin(), node_ptr.end() - 1);
+    for (size_t t = 0; t < fnode.size(); ++t)
+      if (fnode[t] >= 0) node_inc[fill[fnode[t]]++] = (int32_t)t;
+    c->n_mu = nfree;
+    c->n_mu4 = (nfree + 3) / 4 * 4;
+    if ((s = dalloc(c, &c->d_face_node, fnode.size()))) return s;
+    if ((s = dalloc(c, &c->d_node_ptr, node_ptr.size()))) return s;
+    if ((s = dalloc(c, &c->d_node_inc, node_inc.size()))) return s;
+    if ((s = dalloc(c, &c->d_vinv, vinv.size()))) return s;
+    if ((s = dalloc(c, &c->d_mu, (size_t)nfree))) return s;
+    if ((s = dalloc(c, &c->d_bmu, (size_t)nfree))) return s;
+    if ((s = dalloc(c, &c->d_ew64, nfe))) return s;
+    if ((s = dalloc(c, &c->d_w64, nfe))) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_face_node, fnode.data(), fnode.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_node_ptr, node_ptr.data(), node_ptr.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    if (!node_inc.empty())
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_node_inc, node_inc.data(), node_inc.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_vinv, vinv.data(), vinv.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, (size_t)nfree * 8, c->stream));
+    if (c->opt.prec != HDG_FP64) {
+      if ((s = dalloc(c, &c->d_ew32, (size_t)c->nfe4))) return s;
+      if ((s = dalloc(c, &c->d_w32, nfe))) return s;
+      CUDA_TRY(c, cudaMemsetAsync(c->d_ew32, 0, (size_t)c->nfe4 * 4, c->stream));
+    }
+  }
   CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, nfe * R * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_u, 0, (size_t)ne * c->n * R * 8, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_uprev, 0, (size_t)ne * c->n * R * 8, c->stream));
@@ -1262,6 +1676,12 @@ hdg_status hdg_get_sizes(const hdg_ctx* c, hdg_sizes* o) {
   o->trace_entries = c->ntr;
   o->schur_entries = c->nschur;
   o->slot_entries = c->nslot;
+  int64_t nint = 0;
+  if (!c->vd)
+    for (int64_t f = 0; f < c->sk.nf; ++f) nint += c->sk.face_bnd[f] < 0 ? c->Nf : 0;
+  else
+    nint = c->ntr;
+  o->trace_unknowns = c->tspace ? c->n_mu : nint;
   return HDG_OK;
 }
 
@@ -1320,6 +1740,16 @@ hdg_status hdg_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_i
   if (s) return s;
   if (c->R > 1) {
     if ((s = msolve(c, c->d_b, lam, info))) return s;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return HDG_OK;
+  }
+  if (c->tspace) {
+    // continuous traces: R^T K R mu = R^T r from mu = 0, lam = R mu on interior faces
+    if ((s = edg_restrict(c, c->d_b, c->d_bmu))) return s;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, (size_t)c->n_mu * 8, c->stream));
+    if ((s = edg_solve(c, c->d_bmu, c->d_mu, info))) return s;
+    HDG_DISPATCH(c, edg_expand64, c, c->d_mu, lam, 0);
+    if ((s = check_launch(c, "edg_expand"))) return s;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return HDG_OK;
   }
@@ -1497,6 +1927,7 @@ hdg_status hdg_set_dirichlet(hdg_ctx* c, const double* vals, double omega, doubl
   c->omega = omega; c->phase = phase;
   if (!vals || c->sk.nb == 0) return HDG_OK;
   if (c->phys == HDG_ELASTIC) return fail(c, HDG_EINVAL, "elastic path supports clamped boundaries (NULL data) only");
+  if (c->tspace == HDG_TRACE_EDG) return fail(c, HDG_EINVAL, "EDG traces: homogeneous Dirichlet data (NULL) only");
   // lam_f[m] = sum_q w_q g(x_q) mu_m(eta_q)   (face mass J_F I cancels J_F)
   const int nq = c->T.nqf, Nf = c->Nf;
   std::vector<double> coef((size_t)c->sk.nb * Nf, 0.0);
@@ -1527,8 +1958,9 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
   c->t = t;
   c->have_state = true;
   c->n_lam_hist = 0;
-  c->g_n = c->g_next = 0;
-  return HDG_OK;
+  if (c->d_mu) CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, (size_t)c->n_mu * 8, c->stream));
+  guess_clear(c);
+  return check_launch(c, "set_state");
 }
 
 hdg_status hdg_get_state(hdg_ctx* c, double* u, double* uprev, double* lam, double* t) {

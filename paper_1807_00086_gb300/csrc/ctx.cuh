@@ -12,6 +12,7 @@
 
 #include "../../include/hdg.h"
 #include "kernels.cuh"
+#include "devloop.cuh"
 #include "dflocal.cuh"
 #include "mesh.h"
 #include "reftab.h"
@@ -122,6 +123,27 @@ struct hdg_ctx {
   // the same per column (nrhs > 1): Gram matrices [R][8][8], dots [9][R], coefficients [8][R]
   std::vector<double> gm_gram, gm_dots, gm_coef;
   double* d_gcoef = nullptr;
+  GuessDev* d_gd = nullptr;   // the same on the device (one column): Gram matrix, ring counters
+  // device-driven trace solves: control block, capture stream and the cached graphs (one per
+  // solver kind and right-hand-side / solution buffers), with the kernel launches they hold
+  LoopCtl* d_lc = nullptr;
+  LoopCtl* h_lc = nullptr;   // pinned
+  cudaStream_t cap_stream = nullptr;
+  struct DevGraph {
+    int kind;
+    const void* b;
+    const void* x;
+    cudaGraphExec_t exec;
+    int64_t n_static, n_body, n_trip;   // launches outside the loops, per sweep body, per inner trip
+  };
+  std::vector<DevGraph> dgraphs;
+  // continuous traces (IEDG / EDG): free face nodes, the node map and its incidence lists, the
+  // nodal-to-modal table, the nodal unknowns and right-hand side, face work arrays
+  int tspace = 0;                 // HDG_TRACE_HDG / IEDG / EDG
+  int64_t n_mu = 0, n_mu4 = 0;    // free nodes; FP32 node vectors padded to a multiple of 4
+  int32_t *d_face_node = nullptr, *d_node_ptr = nullptr, *d_node_inc = nullptr;
+  double *d_vinv = nullptr, *d_mu = nullptr, *d_bmu = nullptr, *d_ew64 = nullptr, *d_w64 = nullptr;
+  float *d_ew32 = nullptr, *d_w32 = nullptr;
   VarDeg* vd = nullptr;
 };
 
@@ -227,6 +249,65 @@ void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
   c->ev_used = 0;
 }
 
+// ---- device-driven trace solves
+// Runs the solve graph of this kind for the buffers (b, x), building it at the first use:
+// build(gb, G, dg) adds the solve to G (while it runs, c->stream is the capture stream) and
+// records in dg the kernel launches outside the loops, per sweep body and per inner trip of two
+// Krylov iterations. The graph ends with the control block written; the call waits for it and
+// maps the stop code to a status. At most kMaxDevGraphs graphs are kept (oldest dropped).
+constexpr size_t kMaxDevGraphs = 12;
+
+template <class BUILD>
+hdg_status devgraph_solve(hdg_ctx* c, int kind, const void* b, const void* x, BUILD build, hdg_solve_info* info) {
+  hdg_ctx::DevGraph* dg = nullptr;
+  for (auto& g : c->dgraphs)
+    if (g.kind == kind && g.b == b && g.x == x) dg = &g;
+  if (!dg) {
+    if (!c->cap_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (c->dgraphs.size() >= kMaxDevGraphs) {
+      cudaGraphExecDestroy(c->dgraphs.front().exec);
+      c->dgraphs.erase(c->dgraphs.begin());
+    }
+    cudaGraph_t G = nullptr;
+    CUDA_TRY(c, cudaGraphCreate(&G, 0));
+    GraphBuild gb;
+    gb.st = c->cap_stream;
+    hdg_ctx::DevGraph ng{kind, b, x, nullptr, 0, 0, 0};
+    const cudaStream_t keep = c->stream;
+    const int64_t keep_launch = c->n_launch;
+    c->stream = c->cap_stream;
+    build(gb, G, ng);
+    c->stream = keep;
+    c->n_launch = keep_launch;
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = gb.err;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, G, 0);
+    cudaGraphDestroy(G);
+    if (e != cudaSuccess) return fail(c, HDG_ECUDA, std::string("device-driven solve graph: ") + cudaGetErrorString(e));
+    ng.exec = ex;
+    c->dgraphs.push_back(ng);
+    dg = &c->dgraphs.back();
+  }
+  CUDA_TRY(c, cudaGraphLaunch(dg->exec, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_lc, c->d_lc, sizeof(LoopCtl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const LoopCtl L = *c->h_lc;
+  c->n_launch += dg->n_static + (int64_t)(L.sweep + 1) * dg->n_body + (int64_t)((L.total_it + 1) / 2 + L.sweep) * dg->n_trip;
+  if (info) {
+    info->iterations += L.total_it;
+    info->sweeps += L.sweep;
+    info->rel_residual = L.rel;
+  }
+  if (L.stop == 1 || L.stop == 2) return HDG_OK;
+  if (L.stop == 3)
+    return fail(c, HDG_ENOCONV, "mixed-precision refinement reached max_sweeps=" + std::to_string(c->opt.max_sweeps) +
+                                    " with relative residual " + std::to_string(L.rel));
+  return fail(c, HDG_ENOCONV, "trace solve reached maxit=" + std::to_string(c->opt.maxit) + " with relative residual " +
+                                  std::to_string(L.rel));
+}
+
+inline bool use_devgraph(const hdg_ctx* c) { return c->opt.device_loops && !c->stats_on && c->R == 1 && c->d_lc; }
+
 // ---- dispatch on (dim, k)
 #define HDG_DISPATCH(c, FN, ...)                     \
   switch ((c)->dim * 10 + (c)->k) {                  \
@@ -247,8 +328,11 @@ void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
 hdg_status vd_setup(hdg_ctx* c, const int32_t* elem_k);
 // least-squares initial guess around a stage solve (api.cu); both are no-ops when disabled
 hdg_status guess_setup(hdg_ctx* c, const uint8_t* host_mask);
+void guess_clear(hdg_ctx* c);
 hdg_status guess_before(hdg_ctx* c);
 hdg_status guess_after(hdg_ctx* c);
+hdg_status guess_before_v(hdg_ctx* c, int64_t n, const double* b, double* x, const uint8_t* mask);
+hdg_status guess_after_v(hdg_ctx* c, int64_t n, const double* b, const double* x);
 void guess_reset_column(hdg_ctx* c, int j);
 hdg_status vd_condense(hdg_ctx* c, double alpha);
 hdg_status vd_stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info);

@@ -526,7 +526,8 @@ static __global__ void cg_init_scalars(int nb, const double* __restrict__ part, 
     sc->rho[0] = rz; sc->rho[1] = 0; sc->bb = bb; sc->rr = rr;
     sc->tol2 = rtol * rtol * bb;
     sc->iters = 0;
-    sc->done = (rr <= sc->tol2) ? 1 : 0;
+    // a zero right-hand side ends the solve here (its solution is zero on interior faces)
+    sc->done = (bb == 0.0 || rr <= sc->tol2) ? 1 : 0;
   }
 }
 
@@ -603,16 +604,23 @@ static __global__ void cg_update_kernel(int64_t n, int nb, int parity, const dou
   s = block_sum256(rr, red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
 }
 
-// beta = rz_new / rho; p = z + beta p; convergence test.
+// beta = rz_new / rho; p = z + beta p; convergence test. iter >= 0: the iteration index from the
+// host, h unused. iter < 0 (device-driven loop): block 0 counts the iterations in sc->iters and
+// sets the loop condition h (continue while not done), also when the solve had already finished.
 static __global__ void cg_direction_kernel(int64_t n, int nb, int parity, int iter, const double* __restrict__ part,
-                                    const double* __restrict__ z, double* __restrict__ p, CgScal* sc, int maxit) {
-  if (sc->done) return;
+                                    const double* __restrict__ z, double* __restrict__ p, CgScal* sc, int maxit,
+                                    cudaGraphConditionalHandle h) {
+  if (sc->done) {
+    if (iter < 0 && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   __shared__ double red[8];
   const double rz = reduce_partials(part + 0, nb, 2, red);
   const double rr = reduce_partials(part + 1, nb, 2, red);
   const bool conv = rr <= sc->tol2;
-  const int it = iter + 1;  // iteration index from the host: no block reads what block 0 writes
-  if (!conv && it < maxit) {
+  // with a host index no block reads what block 0 writes; on the device only block 0 uses it
+  const int it = iter >= 0 ? iter + 1 : sc->iters + 1;
+  if (!conv && (iter < 0 || it < maxit)) {
     const double be = rz / sc->rho[parity];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -630,7 +638,9 @@ static __global__ void cg_direction_kernel(int64_t n, int nb, int parity, int it
     sc->rho[parity ^ 1] = rz;
     sc->rr = rr;
     sc->iters = it;
-    if (conv || it >= maxit) sc->done = conv ? 1 : 2;
+    const int done = conv ? 1 : (it >= maxit ? 2 : 0);
+    if (done) sc->done = done;
+    if (iter < 0) cudaGraphSetConditional(h, done ? 0u : 1u);
   }
 }
 
@@ -1038,13 +1048,16 @@ static __global__ void cg32_init_kernel(int64_t n4, const float4* __restrict__ b
   s = block_sum256(rr.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
 }
 
-static __global__ void cg32_init_scalars(int nb, const double* __restrict__ part, double rtol, CgScal* sc) {
+// rtol_dev (may be null): the relative tolerance read on the device instead of rtol
+static __global__ void cg32_init_scalars(int nb, const double* __restrict__ part, double rtol, CgScal* sc,
+                                         const double* __restrict__ rtol_dev) {
   __shared__ double red[8];
   const double rz = reduce_partials(part + 0, nb, 2, red);
   const double rr = reduce_partials(part + 1, nb, 2, red);
   if (threadIdx.x == 0) {
+    const double tol = rtol_dev ? *rtol_dev : rtol;
     sc->rho[0] = rz; sc->rho[1] = 0; sc->bb = rr; sc->rr = rr;
-    sc->tol2 = rtol * rtol * rr;
+    sc->tol2 = tol * tol * rr;
     sc->iters = 0;
     sc->done = (rr == 0.0) ? 1 : 0;
   }
@@ -1140,15 +1153,20 @@ __global__ void __launch_bounds__(256) cg32_update_f_kernel(int64_t n4, int64_t 
   s = block_sum256(rr.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
 }
 
+// as cg_direction_kernel, FP32 vectors (float4)
 static __global__ void cg32_direction_kernel(int64_t n4, int nb, int parity, int iter, const double* __restrict__ part,
-                                      const float4* __restrict__ z, float4* __restrict__ p, CgScal* sc, int maxit) {
-  if (sc->done) return;
+                                      const float4* __restrict__ z, float4* __restrict__ p, CgScal* sc, int maxit,
+                                      cudaGraphConditionalHandle h) {
+  if (sc->done) {
+    if (iter < 0 && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   __shared__ double red[8];
   const double rz = reduce_partials(part + 0, nb, 2, red);
   const double rr = reduce_partials(part + 1, nb, 2, red);
   const bool conv = rr <= sc->tol2;
-  const int it = iter + 1;
-  if (!conv && it < maxit) {
+  const int it = iter >= 0 ? iter + 1 : sc->iters + 1;
+  if (!conv && (iter < 0 || it < maxit)) {
     const float be = (float)(rz / sc->rho[parity]);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1165,7 +1183,9 @@ static __global__ void cg32_direction_kernel(int64_t n4, int nb, int parity, int
     sc->rho[parity ^ 1] = rz;
     sc->rr = rr;
     sc->iters = it;
-    if (conv || it >= maxit) sc->done = conv ? 1 : 2;
+    const int done = conv ? 1 : (it >= maxit ? 2 : 0);
+    if (done) sc->done = done;
+    if (iter < 0) cudaGraphSetConditional(h, done ? 0u : 1u);
   }
 }
 

@@ -288,7 +288,7 @@ hdg_status vd_cg(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info
                                                           c->d_part, c->d_sc);
       cg_update_kernel<<<nb, 256, 0, c->stream>>>(n, nb, par, c->d_part, c->d_p, c->d_q, c->d_dinv, x, c->d_r, c->d_z,
                                                   c->d_part + nb, c->d_sc);
-      cg_direction_kernel<<<nb, 256, 0, c->stream>>>(n, nb, par, it, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit);
+      cg_direction_kernel<<<nb, 256, 0, c->stream>>>(n, nb, par, it, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit, 0);
     }
     if ((s = check_launch(c, "vd_cg_iter"))) return s;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
@@ -310,7 +310,7 @@ hdg_status vd_cg32(hdg_ctx* c, double tol, int* iters, bool use16) {
   c->n_launch += 2;
   cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32, (float4*)c->d_x32,
                                               (float4*)c->d_r32, (float4*)c->d_z32, (float4*)c->d_p32, c->d_part);
-  cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, tol, c->d_sc);
+  cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, tol, c->d_sc, nullptr);
   hdg_status s = check_launch(c, "vd_cg32_init");
   if (s) return s;
   int it = 0;
@@ -331,7 +331,7 @@ hdg_status vd_cg32(hdg_ctx* c, double tol, int* iters, bool use16) {
                                                     (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
                                                     c->d_part + nb, c->d_sc);
       cg32_direction_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, it, c->d_part + nb, (const float4*)c->d_z32,
-                                                       (float4*)c->d_p32, c->d_sc, maxit);
+                                                       (float4*)c->d_p32, c->d_sc, maxit, 0);
     }
     if ((s = check_launch(c, "vd_cg32_iter"))) return s;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScal), cudaMemcpyDeviceToHost, c->stream));
@@ -391,7 +391,120 @@ hdg_status vd_refine(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* 
                                   " with relative residual " + std::to_string(rel));
 }
 
+// ---- device-driven solves (one graph launch per trace solve; see devloop.cuh)
+hdg_status vd_cg_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int64_t n = c->ntr;
+  const int nb = c->nb_red, maxit = c->opt.maxit;
+  auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
+    std::vector<cudaGraphNode_t> deps, bd;
+    const int64_t n0 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      vd_apply64(c, x, c->d_slot, nullptr, -1);
+      c->n_launch += 2;
+      vd_cg_init_kernel<<<nb, 256, 0, c->stream>>>(n, c->sgn, c->vd->d_dslot, c->d_slot, bvec, c->d_dinv, c->d_r, c->d_z,
+                                                   c->d_p, c->d_part);
+      cg_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->opt.rtol, c->d_sc);
+    });
+    const cudaGraphConditionalHandle h = gb.handle(G, 1, true);
+    cudaGraph_t B = gb.loop(G, deps, h);
+    const int64_t n1 = c->n_launch;
+    gb.seq(B, bd, [&] {
+      for (int par = 0; par < 2; ++par) {
+        vd_apply64(c, c->d_p, c->d_slot, &c->d_sc->done, -1);
+        c->n_launch += 3;
+        vd_face_q_kernel<double><<<nb, 256, 0, c->stream>>>(n, c->sgn, c->vd->d_dslot, c->d_slot, c->d_p, c->d_q,
+                                                            c->d_part, c->d_sc);
+        cg_update_kernel<<<nb, 256, 0, c->stream>>>(n, nb, par, c->d_part, c->d_p, c->d_q, c->d_dinv, x, c->d_r, c->d_z,
+                                                    c->d_part + nb, c->d_sc);
+        cg_direction_kernel<<<nb, 256, 0, c->stream>>>(n, nb, par, -1, c->d_part + nb, c->d_z, c->d_p, c->d_sc, maxit, h);
+      }
+    });
+    const int64_t n2 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 2;
+      cg_ctl_finish_kernel<<<1, 32, 0, c->stream>>>(c->d_sc, c->d_lc);
+      zero_masked_if_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_intmask, c->d_lc, x);
+    });
+    dg.n_static = (n1 - n0) + (c->n_launch - n2);
+    dg.n_body = 0;
+    dg.n_trip = n2 - n1;
+  };
+  return devgraph_solve(c, 2, bvec, x, build, info);
+}
+
+hdg_status vd_refine_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int64_t n = c->ntr;
+  const int nb = c->nb_red, maxit = c->opt.maxit;
+  const int64_t n4 = c->nfe4 / 4;
+  const bool has16 = c->vd->d_S16 != nullptr;
+  auto inner = [&](bool use16, cudaGraphConditionalHandle h) {
+    for (int par = 0; par < 2; ++par) {
+      if (use16) vd_apply16(c, c->d_p32, c->d_slot32, &c->d_sc->done, -1);
+      else vd_apply32(c, c->d_p32, c->d_slot32, &c->d_sc->done, -1);
+      c->n_launch += 3;
+      vd_face_q_kernel<float><<<nb, 256, 0, c->stream>>>(n, (float)c->sgn, c->vd->d_dslot, c->d_slot32, c->d_p32,
+                                                         c->d_q32, c->d_part, c->d_sc);
+      cg32_update_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, c->d_part, (const float4*)c->d_p32,
+                                                    (const float4*)c->d_q32, (const float4*)c->d_dinv32,
+                                                    (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
+                                                    c->d_part + nb, c->d_sc);
+      cg32_direction_kernel<<<nb, 256, 0, c->stream>>>(n4, nb, par, -1, c->d_part + nb, (const float4*)c->d_z32,
+                                                       (float4*)c->d_p32, c->d_sc, maxit, h);
+    }
+  };
+  auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
+    std::vector<cudaGraphNode_t> deps, bd, d16, d32;
+    const int64_t n0 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 1;
+      loopctl_init_kernel<<<1, 32, 0, c->stream>>>(c->d_lc, has16 ? 1 : 0);
+    });
+    const cudaGraphConditionalHandle h_sweep = gb.handle(G, 1, true);
+    cudaGraph_t B = gb.loop(G, deps, h_sweep);
+    const cudaGraphConditionalHandle h16 = has16 ? gb.handle(B, 0, false) : 0;
+    const cudaGraphConditionalHandle h32 = gb.handle(B, 0, false);
+    const int64_t n1 = c->n_launch;
+    gb.seq(B, bd, [&] {
+      vd_apply_df(c, x, c->d_slot);
+      c->n_launch += 6;
+      vd_refine_residual_kernel<<<nb, 256, 0, c->stream>>>(n, c->sgn, c->vd->d_dslot, c->d_slot, bvec, c->d_res,
+                                                           c->d_part);
+      refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
+      sweep_ctl_kernel<<<1, 32, 0, c->stream>>>(c->d_rs, c->d_sc, c->d_lc, c->opt.rtol, c->opt.inner_rtol,
+                                                c->opt.max_sweeps, h_sweep, has16 ? 1 : 0, h16, h32);
+      to32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_res, c->d_rs, c->d_b32);
+      cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32,
+                                                  (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
+                                                  (float4*)c->d_p32, c->d_part);
+      cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, 0.5, c->d_sc, &c->d_lc->tol);
+    });
+    const int64_t n2 = c->n_launch;
+    if (has16) {
+      cudaGraph_t B16 = gb.loop(B, bd, h16);
+      gb.seq(B16, d16, [&] { inner(true, h16); });
+    }
+    const int64_t n3 = c->n_launch;
+    cudaGraph_t B32 = gb.loop(B, bd, h32);
+    gb.seq(B32, d32, [&] { inner(false, h32); });
+    const int64_t n4_ = c->n_launch;
+    gb.seq(B, bd, [&] {
+      c->n_launch += 1;
+      vd_refine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->vd->d_dslot, c->d_x32, c->d_rs, x);
+    });
+    const int64_t n5 = c->n_launch;
+    gb.seq(G, deps, [&] {
+      c->n_launch += 1;
+      zero_masked_if_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_intmask, c->d_lc, x);
+    });
+    dg.n_static = (n1 - n0) + (c->n_launch - n5);
+    dg.n_body = (n2 - n1) + (n5 - n4_);
+    dg.n_trip = n4_ - n3;
+  };
+  return devgraph_solve(c, 3, bvec, x, build, info);
+}
+
 hdg_status vd_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  if (use_devgraph(c)) return c->opt.prec == HDG_FP64 ? vd_cg_graph(c, bvec, x, info) : vd_refine_graph(c, bvec, x, info);
   return c->opt.prec == HDG_FP64 ? vd_cg(c, bvec, x, info) : vd_refine(c, bvec, x, info);
 }
 

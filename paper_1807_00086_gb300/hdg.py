@@ -37,14 +37,15 @@ class Material(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32),
                 ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32), ("use_graphs", c_int32),
-                ("guess_history", c_int32)]
+                ("guess_history", c_int32), ("device_loops", c_int32), ("trace_space", c_int32)]
 
 
 class Sizes(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("k", c_int32), ("Np", c_int32), ("Nf", c_int32), ("n_local", c_int32),
                 ("n_trace_local", c_int32), ("n_elem", c_int64), ("n_faces", c_int64), ("n_bnd_faces", c_int64),
                 ("nq_vol", c_int32), ("nq_face", c_int32), ("device_bytes", c_int64), ("field_entries", c_int64),
-                ("trace_entries", c_int64), ("schur_entries", c_int64), ("slot_entries", c_int64)]
+                ("trace_entries", c_int64), ("schur_entries", c_int64), ("slot_entries", c_int64),
+                ("trace_unknowns", c_int64)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -156,9 +157,10 @@ class Solver:
 
     def __init__(self, vert, elem, k, tau, rho, c=None, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
                  inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None, lam=None, mu=None,
-                 elem_k=None, guess_history=None):
+                 elem_k=None, guess_history=None, device_loops=None, trace_space="hdg"):
         """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu).
-        elem_k: per-element degrees (3D elastic); fields and traces are then flat vectors."""
+        elem_k: per-element degrees (3D elastic); fields and traces are then flat vectors.
+        trace_space: "hdg", "iedg" or "edg" (continuous traces on the interior / all faces)."""
         import torch
         self.lib = load()
         self.torch = torch
@@ -191,6 +193,9 @@ class Solver:
         opt.use_graphs = 1 if use_graphs else 0
         if guess_history is not None:
             opt.guess_history = guess_history
+        if device_loops is not None:
+            opt.device_loops = 1 if device_loops else 0
+        opt.trace_space = {"hdg": 0, "iedg": 1, "edg": 2}[trace_space]
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream()
