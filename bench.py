@@ -520,6 +520,28 @@ def run_ours(args):
     roof["timing"] = ("CUDA events around every launch on the context stream during %d instrumented steps that "
                       "follow the timed window (%.3f ms/step with the events); the timed window runs without them"
                       % (args.steps, instrumented_ms_per_step))
+    # bounded serving leg (the serve p50/p99 half of the metric): the first requests of the
+    # Poisson(20/s) serving workload through the continuous-batching server, after the solver
+    # above has released its memory
+    serve = None
+    if args.serve_leg > 0 and not elastic and R == 1:
+        from paper_1807_00086_gb300.serve import Server, serving_workload
+        try:
+            s.close()
+        except Exception:
+            pass
+        torch.cuda.empty_cache()
+        reqs = serving_workload(n_req=args.serve_leg, rate=args.serve_rate)
+        srv = Server(budget_bytes=int(args.serve_budget_gb * (1 << 30)), R=args.serve_slots, prec="mixed")
+        st_srv = srv.run(reqs)
+        srv.close()
+        serve = {"requests": st_srv["requests"], "arrival_rate_per_s": args.serve_rate, "p50_ms": st_srv["p50_ms"],
+                 "p99_ms": st_srv["p99_ms"], "mean_ms": st_srv["mean_ms"], "dof_steps_per_s": st_srv["dof_steps_per_s"],
+                 "wall_s": st_srv["wall_s"], "slots_per_context": args.serve_slots,
+                 "contexts": st_srv["contexts_created"],
+                 "workload": "first %d requests of the seeded serving workload (2D/3D acoustic, 1e3-1e5 elements, "
+                             "k in 1..4, 20-200 BDF2 steps)" % args.serve_leg}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = oracle_sample(budget_s=args.cpu_budget)
@@ -552,6 +574,8 @@ def run_ours(args):
                "gpu_launches": launches_timed, "clocks": clk, "full_run": full_run}
         if post is not None:
             out["postprocess"] = post
+        if serve is not None:
+            out["serve"] = serve
         if vardeg:
             out["config"]["autotuned_tiles"] = tiles
         print(json.dumps(out), flush=True)
@@ -640,6 +664,8 @@ def main():
                     help="apply: profiling driver that only condenses and applies K (no JSON bench line)")
     ap.add_argument("--serve", action="store_true", help="run the continuous-batching serving workload")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-leg", type=int, default=100,
+                    help="requests of the serving workload run after the step benchmark (0: none)")
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)

@@ -132,7 +132,15 @@ typedef struct {
                             /* trace system is then R^T K R mu = R^T r, lam_F = V^{-1}   */
                             /* mu(nodes of F). Acoustic, uniform k, nrhs = 1,            */
                             /* device_loops = 1                                          */
+  int32_t solver;           /* HDG_SOLVER_CG (default): preconditioned CG on sgn K (SPD).  */
+                            /* HDG_SOLVER_GMRES: restarted GMRES(gmres_restart) with      */
+                            /* iterated classical Gram-Schmidt (two passes) and right      */
+                            /* Jacobi preconditioning, the paper's Krylov method (Sec.     */
+                            /* 2.4); FP64, HDG traces, nrhs = 1, host-driven iterations    */
+  int32_t gmres_restart;    /* Krylov basis size before a restart (2..64)                */
 } hdg_options;
+
+enum { HDG_SOLVER_CG = 0, HDG_SOLVER_GMRES = 1 };
 
 enum { HDG_TRACE_HDG = 0, HDG_TRACE_IEDG = 1, HDG_TRACE_EDG = 2 };
 
@@ -159,7 +167,8 @@ typedef struct {
 } hdg_solve_info;
 
 /* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1,
- * use_graphs 0, guess_history 8, device_loops 1, trace_space HDG_TRACE_HDG. */
+ * use_graphs 0, guess_history 8, device_loops 1, trace_space HDG_TRACE_HDG, solver HDG_SOLVER_CG,
+ * gmres_restart 40. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face
@@ -300,6 +309,20 @@ hdg_status hdg_set_dirichlet(hdg_ctx* ctx, const double* vals_host, double omega
 hdg_status hdg_set_state(hdg_ctx* ctx, const double* u_dev, const double* uprev_dev, const double* lam_dev,
                          double t);
 hdg_status hdg_get_state(hdg_ctx* ctx, double* u_dev, double* uprev_dev, double* lam_dev, double* t);
+
+/* Complete solver checkpoint for a bitwise resume: the time, the fields and the previous level,
+ * the traces and their history, the stored stage solutions of the least-squares initial guess
+ * (and its Gram matrices), the nodal unknowns of IEDG / EDG contexts, and the mass shift of the
+ * last condensation. A context with the same mesh, degree, material and options that loads the
+ * checkpoint (condensing first if its operators are for another alpha) continues exactly as the
+ * saved one would (given the same sources and boundary data): the same steps give the same
+ * bits. hdg_checkpoint_size gives the bytes of
+ * host memory the caller provides; hdg_save_checkpoint writes them (completes before returning),
+ * hdg_load_checkpoint reads them (HDG_EINVAL if the checkpoint was written by a context of
+ * other sizes or options). */
+hdg_status hdg_checkpoint_size(const hdg_ctx* ctx, int64_t* bytes);
+hdg_status hdg_save_checkpoint(hdg_ctx* ctx, void* host_buf);
+hdg_status hdg_load_checkpoint(hdg_ctx* ctx, const void* host_buf);
 
 /* Advances nsteps implicit steps of size dt with BE or BDF2 (Eq. ch5appendx1:eq9b) or
  * Alexander's DIRK(3,3) in the stage form of Eq. ch5appendx1:eq10_1 with the update of

@@ -18,6 +18,7 @@
 #include "multi.cuh"
 #include "elastic.cuh"
 #include "edg.cuh"
+#include "gmres.cuh"
 #include "mesh.h"
 #include "reftab.h"
 
@@ -184,6 +185,14 @@ void attr_apply_df(hdg_ctx* c) {
   cudaFuncSetAttribute(apply_df_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ApplyDfCfg<DIM, K>::SMEM);
 }
 
+// dynamic shared memory of the tensor-core column-block apply (set outside any stream capture)
+template <int DIM, int K>
+void attr_apply_tc(hdg_ctx* c) {
+  (void)c;
+  cudaFuncSetAttribute(apply_tc_kernel<DIM, K, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ApplyTcCfg<DIM, K>::SMEM);
+  cudaFuncSetAttribute(apply_tc_kernel<DIM, K, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ApplyTcCfg<DIM, K>::SMEM);
+}
+
 template <int DIM, int K>
 void launch_pack32m(hdg_ctx* c) {
   using PK = Packed<DIM, K>;
@@ -271,6 +280,7 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
     } else if (c->R > 1) {
       if (c->R >= 32) {
         HDG_DISPATCH(c, launch_pack32m, c);
+        HDG_DISPATCH(c, attr_apply_tc, c);
       } else {
         HDG_DISPATCH(c, launch_pack32, c);   // group layout, read by the narrow multi-column apply
       }
@@ -693,8 +703,136 @@ hdg_status edg_solve(hdg_ctx* c, const double* bmu, double* mu, hdg_solve_info* 
   return c->opt.prec != HDG_FP64 ? edg_mixed_graph(c, bmu, mu, info) : edg_cg_graph(c, bmu, mu, info);
 }
 
+// Restarted GMRES(m) on (sgn K) x = bvec with right Jacobi preconditioning and iterated
+// classical Gram-Schmidt (two passes per Arnoldi step), FP64 (Sec. 2.4's Krylov method). The
+// vector work runs in the kernels of gmres.cuh; the small Hessenberg least-squares problem
+// (Givens rotations) and the restart / convergence decisions are on the host.
+hdg_status gmres_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  const int m = c->opt.gmres_restart, nb = c->nb_red;
+  const int64_t n = c->sk.nf * c->Nf;
+  hdg_status s;
+  if (!c->d_gmV) {
+    // the FP64 residual vector and its scalars exist only in mixed-precision contexts
+    if (!c->d_res && (s = dalloc(c, &c->d_res, (size_t)n))) return s;
+    if (!c->d_rs && (s = dalloc(c, &c->d_rs, 1))) return s;
+    if (!c->h_rs) CUDA_TRY(c, cudaMallocHost((void**)&c->h_rs, sizeof(RefScal)));
+    if ((s = dalloc(c, &c->d_gmV, (size_t)(m + 1) * n))) return s;
+    if ((s = dalloc(c, &c->d_gmpart, (size_t)(m + 2) * nb))) return s;
+    if ((s = dalloc(c, &c->d_gmh, (size_t)m + 2))) return s;
+    if ((s = dalloc(c, &c->d_gmy, (size_t)m + 1))) return s;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_gmV, 0, (size_t)(m + 1) * n * 8, c->stream));
+  }
+  double* V = c->d_gmV;
+  std::vector<double> hv((size_t)m + 2);
+  // dots of the first q basis vectors with w, then (w, w), into d_gmh and hv
+  auto dots = [&](int q, const double* w) -> hdg_status {
+    c->n_launch += 2;
+    gm_dots_kernel<<<dim3((unsigned)nb, (unsigned)(q + 1)), 256, 0, c->stream>>>(n, q, V, w, c->d_gmpart);
+    gm_dots_final_kernel<<<q + 1, 256, 0, c->stream>>>(nb, c->d_gmpart, c->d_gmh);
+    CUDA_TRY(c, cudaMemcpyAsync(hv.data(), c->d_gmh, (size_t)(q + 1) * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return check_launch(c, "gmres_dots");
+  };
+  // w = sgn K Dinv v (interior entries; zero on boundary faces)
+  auto opK = [&](const double* v, double* w) -> hdg_status {
+    c->n_launch += 2;
+    vmul_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_dinv, v, c->d_z);
+    HDG_DISPATCH(c, launch_apply, c, (const double*)c->d_z, c->d_slot, (const int*)nullptr, -1);
+    face_gather_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd, c->d_slot,
+                                                              c->sgn, w);
+    return check_launch(c, "gmres_op");
+  };
+  if ((s = dots(0, bvec))) return s;
+  const double bb = hv[0];
+  if (bb == 0.0) {
+    c->n_launch += 1;
+    zero_interior_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_bnd, x);
+    if (info) { info->rel_residual = 0.0; info->sweeps += 1; }
+    return check_launch(c, "zero_interior");
+  }
+  const double bn = std::sqrt(bb);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g((size_t)m + 1), y(m);
+  int total = 0, cycles = 0;
+  double rel = 0.0;
+  for (;;) {
+    // true residual r = b - sgn K x
+    HDG_DISPATCH(c, launch_apply, c, (const double*)x, c->d_slot, (const int*)nullptr, -1);
+    c->n_launch += 2;
+    refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec,
+                                                      c->d_res, c->d_part);
+    refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_rs, c->d_rs, sizeof(RefScal), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const RefScal rs = *c->h_rs;
+    const double beta = std::sqrt(rs.rr);
+    rel = beta / bn;
+    if (rel <= c->opt.rtol) break;
+    if (total >= c->opt.maxit) {
+      if (info) { info->iterations += total; info->sweeps += cycles; info->rel_residual = rel; }
+      return fail(c, HDG_ENOCONV, "GMRES reached maxit=" + std::to_string(c->opt.maxit) + " with relative residual " +
+                                      std::to_string(rel));
+    }
+    ++cycles;
+    c->n_launch += 1;
+    combine_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, 1.0 / beta, c->d_res, 0, nullptr, 0, nullptr, 0, nullptr, V);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m && total < c->opt.maxit; ++j) {
+      double* w = V + (int64_t)(j + 1) * n;
+      if ((s = opK(V + (int64_t)j * n, w))) return s;
+      // two classical Gram-Schmidt passes against V_0..V_j
+      double hcol[66];
+      if ((s = dots(j + 1, w))) return s;
+      for (int i = 0; i <= j; ++i) hcol[i] = hv[i];
+      c->n_launch += 1;
+      gm_orth_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, j + 1, V, c->d_gmh, w);
+      if ((s = dots(j + 1, w))) return s;
+      for (int i = 0; i <= j; ++i) hcol[i] += hv[i];
+      c->n_launch += 1;
+      gm_orth_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, j + 1, V, c->d_gmh, w);
+      if ((s = dots(0, w))) return s;
+      const double hn = std::sqrt(std::max(0.0, hv[0]));
+      hcol[j + 1] = hn;
+      // previous rotations, then the one that zeroes the subdiagonal entry
+      for (int i = 0; i < j; ++i) {
+        const double a = hcol[i], b2 = hcol[i + 1];
+        hcol[i] = cs[i] * a + sn[i] * b2;
+        hcol[i + 1] = -sn[i] * a + cs[i] * b2;
+      }
+      const double r = std::hypot(hcol[j], hcol[j + 1]);
+      cs[j] = r > 0.0 ? hcol[j] / r : 1.0;
+      sn[j] = r > 0.0 ? hcol[j + 1] / r : 0.0;
+      hcol[j] = r;
+      hcol[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+      ++total;
+      k = j + 1;
+      if (std::fabs(g[j + 1]) <= c->opt.rtol * bn || hn == 0.0) break;
+      c->n_launch += 1;
+      combine_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, 1.0 / hn, w, 0, nullptr, 0, nullptr, 0, nullptr, w);
+    }
+    // y = H^{-1} g (upper triangular k x k), x += Dinv V y
+    for (int i = k - 1; i >= 0; --i) {
+      double v = g[i];
+      for (int jj = i + 1; jj < k; ++jj) v -= H[(size_t)i * m + jj] * y[jj];
+      y[i] = v / H[(size_t)i * m + i];
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_gmy, y.data(), (size_t)k * 8, cudaMemcpyHostToDevice, c->stream));
+    c->n_launch += 1;
+    gm_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, k, V, c->d_gmy, c->d_dinv, c->d_intmask, x);
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // y is released by the next cycle
+    if ((s = check_launch(c, "gmres_update"))) return s;
+  }
+  if (info) { info->iterations += total; info->sweeps += std::max(1, cycles); info->rel_residual = rel; }
+  return HDG_OK;
+}
+
 // PCG on (-K) x = bvec over interior faces; x holds the initial guess (interior entries).
 hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+  if (c->opt.solver == HDG_SOLVER_GMRES) return gmres_solve(c, bvec, x, info);
   if (use_devgraph(c)) return c->opt.prec != HDG_FP64 ? solve_mixed_graph(c, bvec, x, info) : cg_solve_graph(c, bvec, x, info);
   if (c->opt.prec != HDG_FP64) return solve_mixed(c, bvec, x, info);
   const int64_t nfe = c->sk.nf * c->Nf;
@@ -844,12 +982,17 @@ void mlaunch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, i
     mlaunch_apply<DIM, K, float>(c, x, slot, done, iter);
     return;
   }
-  using AC = Apply32mCfg<DIM, K>;
-  const unsigned grid = (unsigned)((c->sk.ne + AC::EPB - 1) / AC::EPB);
+  // 32 columns or more: S_K times the column block on the tensor cores
+  using AC = ApplyTcCfg<DIM, K>;
+  const unsigned grid = (unsigned)((c->sk.ne + AC::WPB - 1) / AC::WPB);
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 1, iter);
-  apply32m_kernel<DIM, K><<<grid, 256, 0, c->stream>>>(c->sk.ne, c->R, c->d_elem_face, c->d_face_bnd,
-                                                         (const float4*)c->d_S32, x, slot, done);
+  if (c->R == 32)
+    apply_tc_kernel<DIM, K, 32><<<grid, 32 * AC::WPB, AC::SMEM, c->stream>>>(c->sk.ne, c->R, c->d_elem_face, c->d_face_bnd,
+                                                                             (const float4*)c->d_S32, x, slot, done);
+  else
+    apply_tc_kernel<DIM, K, 64><<<grid, 32 * AC::WPB, AC::SMEM, c->stream>>>(c->sk.ne, c->R, c->d_elem_face, c->d_face_bnd,
+                                                                             (const float4*)c->d_S32, x, slot, done);
   apply_end(c, stop);
 }
 
@@ -943,7 +1086,7 @@ hdg_status mcg(hdg_ctx* c, const TV* b, TV* x, TV* r, TV* z, TV* p, TV* q, TV* s
       }
       mcols_alpha<<<1, 256, 0, c->stream>>>(nb, c->R, par, c->d_part, mscal(c));
       mupdate_kernel<TV><<<nb, 256, 0, c->stream>>>(n, c->R, p, q, dinv, x, r, z, c->d_part, mscal(c));
-      mcols_beta<<<1, 256, 0, c->stream>>>(nb, c->R, par, maxit, c->d_part, mscal(c), c->d_mbeta);
+      mcols_beta<<<1, 256, 0, c->stream>>>(nb, c->R, par, maxit, c->d_part, mscal(c), c->d_mbeta, 0, 0);
       mdirection_kernel<TV><<<nb, 256, 0, c->stream>>>(n, c->R, z, p, c->d_mbeta, c->d_mdone);
     }
   };
@@ -994,7 +1137,107 @@ hdg_status mcg(hdg_ctx* c, const TV* b, TV* x, TV* r, TV* z, TV* p, TV* q, TV* s
   return HDG_OK;
 }
 
+// Device-driven multi-column solve (one graph launch): the per-column Krylov iterations run as
+// a WHILE loop whose condition the single-block beta kernel sets, and the mixed-precision sweeps
+// as an outer WHILE loop with a one-thread control kernel (all columns converged / max_sweeps).
+hdg_status msolve_graph(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) {
+  const int64_t n = c->sk.nf * c->Nf * (int64_t)c->R;
+  const int nb = c->nb_red, maxit = c->opt.maxit, R = c->R;
+  const bool mixed = c->opt.prec != HDG_FP64;
+  auto iters = [&](bool f32, cudaGraphConditionalHandle h) {
+    for (int par = 0; par < 2; ++par) {
+      c->n_launch += 5;
+      if (f32) {
+        HDG_DISPATCH(c, mlaunch_apply32, c, (const float*)c->d_p32, c->d_mslot32, c->d_mdone, -1);
+        HDG_DISPATCH(c, mlaunch_face_q32, c, (const float*)c->d_mslot32, (const float*)c->d_p32, c->d_q32);
+        mcols_alpha<<<1, 256, 0, c->stream>>>(nb, R, par, c->d_part, mscal(c));
+        mupdate_kernel<float><<<nb, 256, 0, c->stream>>>(n, R, c->d_p32, c->d_q32, c->d_dinv32, c->d_x32, c->d_r32,
+                                                         c->d_z32, c->d_part, mscal(c));
+        mcols_beta<<<1, 256, 0, c->stream>>>(nb, R, par, maxit, c->d_part, mscal(c), c->d_mbeta, 1, h);
+        mdirection_kernel<float><<<nb, 256, 0, c->stream>>>(n, R, c->d_z32, c->d_p32, c->d_mbeta, c->d_mdone);
+      } else {
+        HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)c->d_p, c->d_mslot, c->d_mdone, -1);
+        HDG_DISPATCH(c, mlaunch_face_q64, c, (const double*)c->d_mslot, (const double*)c->d_p, c->d_q);
+        mcols_alpha<<<1, 256, 0, c->stream>>>(nb, R, par, c->d_part, mscal(c));
+        mupdate_kernel<double><<<nb, 256, 0, c->stream>>>(n, R, c->d_p, c->d_q, c->d_dinv, x, c->d_r, c->d_z, c->d_part,
+                                                          mscal(c));
+        mcols_beta<<<1, 256, 0, c->stream>>>(nb, R, par, maxit, c->d_part, mscal(c), c->d_mbeta, 1, h);
+        mdirection_kernel<double><<<nb, 256, 0, c->stream>>>(n, R, c->d_z, c->d_p, c->d_mbeta, c->d_mdone);
+      }
+    }
+  };
+  auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
+    std::vector<cudaGraphNode_t> deps, bd, di;
+    const int64_t n0 = c->n_launch;
+    if (!mixed) {
+      gb.seq(G, deps, [&] {
+        HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)x, c->d_mslot, (const int*)nullptr, -1);
+        c->n_launch += 2;
+        HDG_DISPATCH(c, mlaunch_init64, c, (const double*)c->d_mslot, b, (const double*)c->d_dinv, c->d_r, c->d_z, c->d_p);
+        mcols_init<<<1, 256, 0, c->stream>>>(nb, R, c->opt.rtol, 0, c->d_part, mscal(c));
+      });
+      const cudaGraphConditionalHandle h = gb.handle(G, 1, true);
+      cudaGraph_t B = gb.loop(G, deps, h);
+      const int64_t n1 = c->n_launch;
+      gb.seq(B, bd, [&] { iters(false, h); });
+      const int64_t n2 = c->n_launch;
+      gb.seq(G, deps, [&] {
+        c->n_launch += 1;
+        mcg_finish_kernel<<<1, 32, 0, c->stream>>>(c->d_mdone, c->d_miters, c->d_lc);
+      });
+      dg.n_static = (n1 - n0) + (c->n_launch - n2);
+      dg.n_body = 0;
+      dg.n_trip = n2 - n1;
+      return;
+    }
+    gb.seq(G, deps, [&] {
+      c->n_launch += 1;
+      loopctl_init_kernel<<<1, 32, 0, c->stream>>>(c->d_lc, 0);
+    });
+    const cudaGraphConditionalHandle h_sweep = gb.handle(G, 1, true);
+    cudaGraph_t B = gb.loop(G, deps, h_sweep);
+    const cudaGraphConditionalHandle h_in = gb.handle(B, 0, false);
+    const int64_t n1 = c->n_launch;
+    gb.seq(B, bd, [&] {
+      HDG_DISPATCH(c, mlaunch_apply_df, c, (const double*)x, c->d_mslot);
+      HDG_DISPATCH(c, mlaunch_refres, c, b);
+      c->n_launch += 4;
+      msweep_ctl_kernel<<<1, 32, 0, c->stream>>>(c->d_mnconv, c->d_miters, c->d_lc, c->opt.max_sweeps, h_sweep, h_in);
+      mto32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, R, c->d_res, c->d_mscale, c->d_b32);
+      cudaMemsetAsync(c->d_x32, 0, (size_t)n * sizeof(float), c->stream);
+      HDG_DISPATCH(c, mlaunch_init32, c, (const float*)nullptr, (const float*)c->d_b32, (const float*)c->d_dinv32,
+                   c->d_r32, c->d_z32, c->d_p32);
+      mcols_init<<<1, 256, 0, c->stream>>>(nb, R, c->opt.inner_rtol, 1, c->d_part, mscal(c), c->d_mrr2, c->d_mbb2,
+                                           c->opt.rtol);
+    });
+    const int64_t n2 = c->n_launch;
+    cudaGraph_t BI = gb.loop(B, bd, h_in);
+    gb.seq(BI, di, [&] { iters(true, h_in); });
+    const int64_t n3 = c->n_launch;
+    gb.seq(B, bd, [&] {
+      c->n_launch += 1;
+      mrefine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, R, c->Nf, c->d_face_bnd, c->d_x32, c->d_mscale, x);
+    });
+    const int64_t n4 = c->n_launch;
+    dg.n_static = n1 - n0;
+    dg.n_body = (n2 - n1) + (n4 - n3);
+    dg.n_trip = n3 - n2;
+  };
+  hdg_status s = devgraph_solve(c, 6, b, x, build, info);
+  if (s != HDG_OK) return s;
+  // the worst column's relative residual (FP64 path: the CG recurrence's; mixed: the last sweep's)
+  std::vector<double> rr(R), bb(R);
+  CUDA_TRY(c, cudaMemcpyAsync(rr.data(), mixed ? c->d_mrr2 : c->d_mrr, R * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(bb.data(), mixed ? c->d_mbb2 : c->d_mbb, R * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  double worst = 0.0;
+  for (int j = 0; j < R; ++j) worst = std::max(worst, bb[j] > 0 ? std::sqrt(rr[j] / bb[j]) : 0.0);
+  if (info) info->rel_residual = std::max(info->rel_residual, worst);
+  return HDG_OK;
+}
+
 hdg_status msolve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) {
+  if (c->opt.device_loops && !c->stats_on && c->d_lc) return msolve_graph(c, b, x, info);
   const int64_t n = c->sk.nf * c->Nf * (int64_t)c->R;
   hdg_status s;
   if (c->opt.prec == HDG_FP64) {
@@ -1306,6 +1549,9 @@ void hdg_default_options(hdg_options* o) {
   o->use_graphs = 0;
   o->guess_history = 8;
   o->device_loops = 1;
+  o->trace_space = HDG_TRACE_HDG;
+  o->solver = HDG_SOLVER_CG;
+  o->gmres_restart = 40;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -1403,6 +1649,11 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if (c->tspace != HDG_TRACE_HDG &&
       (mat->phys != HDG_ACOUSTIC || c->R != 1 || mesh->elem_k || !c->opt.device_loops))
     return fail(c, HDG_EINVAL, "IEDG / EDG traces: acoustic, uniform degree, nrhs = 1 and device_loops = 1 only");
+  if (c->opt.solver != HDG_SOLVER_CG && c->opt.solver != HDG_SOLVER_GMRES) return fail(c, HDG_EINVAL, "unknown solver");
+  if (c->opt.solver == HDG_SOLVER_GMRES &&
+      (c->opt.prec != HDG_FP64 || c->R != 1 || mesh->elem_k || c->tspace != HDG_TRACE_HDG ||
+       c->opt.gmres_restart < 2 || c->opt.gmres_restart > 64))
+    return fail(c, HDG_EINVAL, "GMRES: FP64, HDG traces, uniform degree, nrhs = 1 and 2 <= gmres_restart <= 64 only");
   std::string err;
   if (mat->phys != HDG_ACOUSTIC && mat->phys != HDG_ELASTIC) return fail(c, HDG_EINVAL, "unknown physics");
   c->phys = mat->phys;
@@ -1971,6 +2222,98 @@ hdg_status hdg_get_state(hdg_ctx* c, double* u, double* uprev, double* lam, doub
   if (lam) CUDA_TRY(c, cudaMemcpyAsync(lam, c->d_lam, (size_t)c->ntr * c->R * 8, cudaMemcpyDeviceToDevice, c->stream));
   if (t) *t = c->t;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return HDG_OK;
+}
+
+// ---- checkpoint: a header, then the device arrays in a fixed order
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version, dim, k, R, phys, prec, tspace, n_lam_hist, g_q, g_n, g_next, condensed;
+  int64_t nfld, ntr, n_mu;
+  double t, alpha;
+};
+
+// (device pointer, bytes) of every array the checkpoint holds, in order
+std::vector<std::pair<void*, size_t>> ckpt_arrays(hdg_ctx* c) {
+  std::vector<std::pair<void*, size_t>> a;
+  const size_t fb = (size_t)c->nfld * c->R * 8, tb = (size_t)c->ntr * c->R * 8;
+  a.push_back({c->d_u, fb});
+  a.push_back({c->d_uprev, fb});
+  for (double* p : {c->d_lam, c->d_lam_prev, c->d_lam_prev2})
+    if (p) a.push_back({p, tb});
+  if (c->g_q) {
+    a.push_back({c->d_gb, (size_t)c->g_q * tb});
+    a.push_back({c->d_gl, (size_t)c->g_q * tb});
+  }
+  if (c->d_gd) a.push_back({c->d_gd, sizeof(GuessDev)});
+  if (c->d_mu) a.push_back({c->d_mu, (size_t)c->n_mu * 8});
+  return a;
+}
+
+size_t ckpt_bytes(hdg_ctx* c) {
+  size_t n = sizeof(CkptHeader) + c->gm_gram.size() * 8;
+  for (auto& p : ckpt_arrays(c)) n += p.second;
+  return n;
+}
+}  // namespace
+
+hdg_status hdg_checkpoint_size(const hdg_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return HDG_EINVAL;
+  *bytes = (int64_t)ckpt_bytes(const_cast<hdg_ctx*>(c));
+  return HDG_OK;
+}
+
+hdg_status hdg_save_checkpoint(hdg_ctx* c, void* buf) {
+  if (!c || !buf) return fail(c, HDG_EINVAL, "null argument");
+  CkptHeader h{};
+  std::memcpy(h.magic, "HDGCKPT", 8);
+  h.version = 1; h.dim = c->dim; h.k = c->k; h.R = c->R; h.phys = c->phys; h.prec = c->opt.prec; h.tspace = c->tspace;
+  h.n_lam_hist = c->n_lam_hist; h.g_q = c->g_q; h.g_n = c->g_n; h.g_next = c->g_next; h.condensed = c->condensed ? 1 : 0;
+  h.nfld = c->nfld; h.ntr = c->ntr; h.n_mu = c->n_mu; h.t = c->t; h.alpha = c->alpha;
+  char* out = static_cast<char*>(buf);
+  std::memcpy(out, &h, sizeof h);
+  size_t off = sizeof h;
+  if (!c->gm_gram.empty()) {
+    std::memcpy(out + off, c->gm_gram.data(), c->gm_gram.size() * 8);
+    off += c->gm_gram.size() * 8;
+  }
+  for (auto& p : ckpt_arrays(c)) {
+    CUDA_TRY(c, cudaMemcpyAsync(out + off, p.first, p.second, cudaMemcpyDeviceToHost, c->stream));
+    off += p.second;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return HDG_OK;
+}
+
+hdg_status hdg_load_checkpoint(hdg_ctx* c, const void* buf) {
+  if (!c || !buf) return fail(c, HDG_EINVAL, "null argument");
+  CkptHeader h;
+  const char* in = static_cast<const char*>(buf);
+  std::memcpy(&h, in, sizeof h);
+  if (std::memcmp(h.magic, "HDGCKPT", 8) != 0 || h.version != 1)
+    return fail(c, HDG_EINVAL, "not a checkpoint of this library version");
+  if (h.dim != c->dim || h.k != c->k || h.R != c->R || h.phys != c->phys || h.prec != c->opt.prec ||
+      h.tspace != c->tspace || h.g_q != c->g_q || h.nfld != c->nfld || h.ntr != c->ntr || h.n_mu != c->n_mu)
+    return fail(c, HDG_EINVAL, "checkpoint of a context with other sizes or options");
+  hdg_status s;
+  // operators for the saved alpha first: a condensation clears the stored stage solutions
+  if (h.condensed && (s = ensure_alpha(c, h.alpha))) return s;
+  size_t off = sizeof h;
+  if (!c->gm_gram.empty()) {
+    std::memcpy(c->gm_gram.data(), in + off, c->gm_gram.size() * 8);
+    off += c->gm_gram.size() * 8;
+  }
+  for (auto& p : ckpt_arrays(c)) {
+    CUDA_TRY(c, cudaMemcpyAsync(p.first, in + off, p.second, cudaMemcpyHostToDevice, c->stream));
+    off += p.second;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->t = h.t;
+  c->n_lam_hist = h.n_lam_hist;
+  c->g_n = h.g_n;
+  c->g_next = h.g_next;
+  c->have_state = true;
   return HDG_OK;
 }
 

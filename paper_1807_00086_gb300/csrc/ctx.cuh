@@ -144,6 +144,9 @@ struct hdg_ctx {
   int32_t *d_face_node = nullptr, *d_node_ptr = nullptr, *d_node_inc = nullptr;
   double *d_vinv = nullptr, *d_mu = nullptr, *d_bmu = nullptr, *d_ew64 = nullptr, *d_w64 = nullptr;
   float *d_ew32 = nullptr, *d_w32 = nullptr;
+  // restarted GMRES (allocated at the first GMRES solve): basis [m + 1][n], dot partials, the
+  // dots of the last pass and the coefficients of the update
+  double *d_gmV = nullptr, *d_gmpart = nullptr, *d_gmh = nullptr, *d_gmy = nullptr;
   VarDeg* vd = nullptr;
 };
 

@@ -18,14 +18,44 @@
 
 namespace hdg {
 
+// The 10-term sums below are FP32 on the FP32 path and double-float (FP64-class accuracy on the
+// FP32 pipe; GB300 issues FP64 at 1/58 of the FP32 rate) on the FP64 path.
+template <typename T>
+struct VTab;
+template <>
+struct VTab<float> {
+  float v;
+  __device__ static VTab from(double x) { return VTab{(float)x}; }
+};
+template <>
+struct VTab<double> {
+  df2 v;
+  __device__ static VTab from(double x) { return VTab{df_from(x)}; }
+};
+
+template <typename T>
+struct VSum;
+template <>
+struct VSum<float> {
+  float s = 0.f;
+  __device__ __forceinline__ void add(const VTab<float>& a, float x) { s = fmaf(a.v, x, s); }
+  __device__ __forceinline__ float value() const { return s; }
+};
+template <>
+struct VSum<double> {
+  DfAcc acc;
+  __device__ __forceinline__ void add(const VTab<double>& a, double x) { acc.fma(a.v, df_from(x)); }
+  __device__ __forceinline__ double value() const { return acc.value(); }
+};
+
 // lam[f][m] = sum_a vinv[m][a] mu[face_node[f][a]] on interior faces. Boundary faces: 0 when
 // zero_bnd (Krylov work vectors), left as they are otherwise (the step's Dirichlet traces).
 template <typename T, int NF>
 __global__ void edg_expand_kernel(int64_t nf, const int32_t* __restrict__ face_bnd, const int32_t* __restrict__ face_node,
                                   const double* __restrict__ vinv, const T* __restrict__ mu, T* __restrict__ lam,
                                   int zero_bnd) {
-  __shared__ double V[NF * NF];
-  for (int i = threadIdx.x; i < NF * NF; i += blockDim.x) V[i] = vinv[i];
+  __shared__ VTab<T> V[NF * NF];
+  for (int i = threadIdx.x; i < NF * NF; i += blockDim.x) V[i] = VTab<T>::from(vinv[i]);
   __syncthreads();
   const int64_t n = nf * NF;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
@@ -35,13 +65,13 @@ __global__ void edg_expand_kernel(int64_t nf, const int32_t* __restrict__ face_b
       if (zero_bnd) lam[t] = T(0);
       continue;
     }
-    double v = 0.0;
+    VSum<T> v;
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
       const int32_t node = face_node[f * NF + a];
-      if (node >= 0) v += V[m * NF + a] * (double)mu[node];
+      if (node >= 0) v.add(V[m * NF + a], mu[node]);
     }
-    lam[t] = (T)v;
+    lam[t] = v.value();
   }
 }
 
@@ -52,8 +82,8 @@ template <typename T, int NF>
 __global__ void edg_face_w_kernel(int64_t nf, const int32_t* __restrict__ face_slot, const int32_t* __restrict__ face_bnd,
                                   const double* __restrict__ vinv, const T* __restrict__ slot, const T* __restrict__ yface,
                                   T* __restrict__ w) {
-  __shared__ double V[NF * NF];
-  for (int i = threadIdx.x; i < NF * NF; i += blockDim.x) V[i] = vinv[i];
+  __shared__ VTab<T> V[NF * NF];
+  for (int i = threadIdx.x; i < NF * NF; i += blockDim.x) V[i] = VTab<T>::from(vinv[i]);
   __syncthreads();
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     if (face_bnd[f] >= 0) {
@@ -61,22 +91,22 @@ __global__ void edg_face_w_kernel(int64_t nf, const int32_t* __restrict__ face_s
       for (int a = 0; a < NF; ++a) w[f * NF + a] = T(0);
       continue;
     }
-    double y[NF];
+    T y[NF];
     if (slot) {
       const T* s0 = slot + (int64_t)face_slot[2 * f] * NF;
       const T* s1 = slot + (int64_t)face_slot[2 * f + 1] * NF;
 #pragma unroll
-      for (int m = 0; m < NF; ++m) y[m] = (double)s0[m] + (double)s1[m];
+      for (int m = 0; m < NF; ++m) y[m] = s0[m] + s1[m];
     } else {
 #pragma unroll
-      for (int m = 0; m < NF; ++m) y[m] = (double)yface[f * NF + m];
+      for (int m = 0; m < NF; ++m) y[m] = yface[f * NF + m];
     }
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
-      double v = 0.0;
+      VSum<T> v;
 #pragma unroll
-      for (int m = 0; m < NF; ++m) v += V[m * NF + a] * y[m];
-      w[f * NF + a] = (T)v;
+      for (int m = 0; m < NF; ++m) v.add(V[m * NF + a], y[m]);
+      w[f * NF + a] = v.value();
     }
   }
 }

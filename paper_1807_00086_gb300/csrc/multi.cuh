@@ -5,6 +5,7 @@
 // operators are the same as in the single-column kernels of kernels.cuh.
 #pragma once
 #include "kernels.cuh"
+#include "devloop.cuh"
 
 namespace hdg {
 
@@ -359,6 +360,136 @@ __global__ void __launch_bounds__(256) apply32m_kernel(int64_t ne, int R, const 
   }
 }
 
+// Tensor-core apply of S_K to the R-column trace block of every element, Y_K = S_K X_K (m x R),
+// R a multiple of 8: the GEMM-shaped contraction of the multi-source batch, as warp-level
+// mma.sync m16n8k8 with TF32 operands and FP32 accumulation. Each CTA stages WPB elements'
+// packed S_K and gathered X_K (boundary faces read as 0) in shared memory; warp w multiplies
+// element w: the A fragments (S_K rounded to TF32, rows and columns padded to the tile sizes with
+// zeros) are loaded once per element, X is split into X_hi + X_lo (both TF32), so the product
+// carries only the TF32 rounding of S_K (relative 2^-11, the accuracy class of the FP16 inner
+// operator) and not that of the Krylov vector. Output slots [e][m][R] as apply32m_kernel.
+template <int DIM, int K>
+struct ApplyTcCfg {
+  static constexpr int M = Dims<DIM, K>::M;
+  static constexpr int P4 = Packed<DIM, K>::P4;
+  static constexpr int MT = (M + 15) / 16;   // 16-row tiles of S_K
+  static constexpr int KS = (M + 7) / 8;     // 8-wide k steps
+  static constexpr int WPB = 4;              // warps (= elements in flight) per CTA
+  static constexpr int XS = 64 + 8;          // padded row of the staged X (64 columns per pass; conflict-free B reads)
+  static constexpr size_t SMEM = (size_t)WPB * (P4 * 16 + (size_t)KS * 8 * XS * 4);
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// NC columns per pass (32 for R = 32, else 64; R a multiple of NC)
+template <int DIM, int K, int NC>
+__global__ void __launch_bounds__(32 * ApplyTcCfg<DIM, K>::WPB) apply_tc_kernel(
+    int64_t ne, int R, const int32_t* __restrict__ elem_face, const int32_t* __restrict__ face_bnd,
+    const float4* __restrict__ S32m, const float* __restrict__ x, float* __restrict__ slot, const int* __restrict__ done) {
+  using C = ApplyTcCfg<DIM, K>;
+  using Dm = Dims<DIM, K>;
+  constexpr int M = C::M, NF = Dm::NF, NFC = Dm::NFC, P4 = C::P4, MT = C::MT, KS = C::KS, WPB = C::WPB, XS = C::XS;
+  constexpr int Q = NC / 4, NLD = KS * 8 * Q, LPL = (NLD + 31) / 32;   // float4 loads of X: total, per lane
+  if (done && *done) return;
+  extern __shared__ float4 smem4[];
+  float* sS = reinterpret_cast<float*>(smem4);                 // [WPB][P4 * 4] packed S_K
+  float* sX = sS + WPB * P4 * 4;                               // [WPB][KS * 8][XS] X_K, NC columns per pass
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int64_t e0 = (int64_t)blockIdx.x * WPB;
+  const int nel = (int)((ne - e0) < WPB ? (ne - e0) : WPB);
+  // packed S_K of the CTA's elements (contiguous in the element-major packed layout)
+  for (int t = threadIdx.x; t < nel * P4; t += blockDim.x) smem4[t] = __ldcs(S32m + e0 * P4 + t);
+  const int el = w;
+  const bool act = el < nel;
+  const int64_t e = e0 + (act ? el : 0);
+  const float* Se = sS + el * P4 * 4;
+  float* Xe = sX + (size_t)el * KS * 8 * XS;
+  // the element's faces: lane f < NFC holds face f's trace offset (-1: boundary, read as zero)
+  int64_t fo = -1;
+  if (act && lane < NFC) {
+    const int f = elem_face[e * NFC + lane];
+    fo = face_bnd[f] < 0 ? (int64_t)f * NF * R : -1;
+  }
+  // A fragments of this warp's element, once: rows mt*16 + g (+8), columns ks*8 + tq (+4)
+  uint32_t a[MT][KS][4];
+  for (int c0 = 0; c0 < R; c0 += NC) {
+    __syncthreads();   // S staged (first pass) / previous pass done with X
+    // stage X_K (rows k < M from the element's faces, rows M..KS*8 and boundary faces zero) with
+    // 16-byte asynchronous copies: every copy of the pass is in flight before the first is used;
+    // a zero-filled chunk reads no global memory (source size 0, a valid address is passed)
+    const unsigned xs = (unsigned)__cvta_generic_to_shared(Xe);
+#pragma unroll 4
+    for (int i = 0; i < LPL; ++i) {
+      const int t = lane + 32 * i;
+      const int r = (t < NLD ? t : 0) / Q, q = t % Q;
+      const int64_t off = __shfl_sync(0xffffffffu, fo, (r < M ? r : 0) / NF);
+      if (t < NLD) {
+        const bool rd = act && r < M && off >= 0;
+        const float* src = rd ? x + off + (int64_t)(r % NF) * R + c0 + 4 * q : x;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(xs + 4u * (unsigned)(r * XS + 4 * q)),
+                     "l"(src), "r"(rd ? 16 : 0)
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
+    if (!act) continue;
+    if (c0 == 0) {
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int r = mt * 16 + g + (h & 1) * 8, cc = ks * 8 + tq + (h >> 1) * 4;
+            float sv = 0.f;
+            if (r < M && cc < M) sv = Se[r <= cc ? packed_index(M, r, cc) : packed_index(M, cc, r)];
+            a[mt][ks][h] = to_tf32(sv);
+          }
+    }
+#pragma unroll 2
+    for (int nt = 0; nt < NC / 8; ++nt) {
+      float acc[MT][4];
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const float x0 = Xe[(ks * 8 + tq) * XS + nt * 8 + g];
+        const float x1 = Xe[(ks * 8 + tq + 4) * XS + nt * 8 + g];
+        const uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1);
+        const uint32_t l0 = to_tf32(x0 - __uint_as_float(h0)), l1 = to_tf32(x1 - __uint_as_float(h1));
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          mma_tf32(acc[mt], a[mt][ks], h0, h1);
+          mma_tf32(acc[mt], a[mt][ks], l0, l1);
+        }
+      }
+      // D fragment: (row g, cols 2 tq, 2 tq + 1) and (row g + 8, same cols) of each 16 x 8 tile
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int col = c0 + nt * 8 + 2 * tq;
+        const int r0 = mt * 16 + g, r1 = r0 + 8;
+        if (r0 < M) *reinterpret_cast<float2*>(slot + (e * M + r0) * R + col) = make_float2(acc[mt][0], acc[mt][1]);
+        if (r1 < M) *reinterpret_cast<float2*>(slot + (e * M + r1) * R + col) = make_float2(acc[mt][2], acc[mt][3]);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ per-column Krylov kernels
 // Vector entries t = entry * R + column; with a grid stride that is a multiple of R (256
 // threads per block, R | 256) every thread keeps one column, so per-thread accumulators
@@ -520,12 +651,17 @@ __global__ void __launch_bounds__(256) mupdate_kernel(int64_t n, int R, const TV
 
 // rho_new, rr per column; convergence; beta. Single block: the iteration counter lives on the
 // device (read by every thread before thread 0 advances it), so launches carry no host index.
+// dev != 0 (device-driven loop): thread 0 also sets the loop condition h (continue while not
+// done), including when the solve had already finished.
 static __global__ void mcols_beta(int nb, int R, int parity, int maxit, const double* __restrict__ part, MScal sc,
-                           double* __restrict__ beta) {
+                           double* __restrict__ beta, int dev, cudaGraphConditionalHandle h) {
   __shared__ int notconv;
   if (threadIdx.x == 0) notconv = 0;
   __syncthreads();
-  if (*sc.done) return;
+  if (*sc.done) {
+    if (dev && threadIdx.x == 0) cudaGraphSetConditional(h, 0u);
+    return;
+  }
   const int iter = *sc.iters;
   __shared__ double red[256], rzs[256];
   col_partials(part, nb, R, 0, red);
@@ -544,8 +680,34 @@ static __global__ void mcols_beta(int nb, int R, int parity, int maxit, const do
   __syncthreads();
   if (threadIdx.x == 0) {
     *sc.iters = iter + 1;
-    if (notconv == 0 || iter + 1 >= maxit) *sc.done = notconv == 0 ? 1 : 2;
+    const int done = (notconv == 0 || iter + 1 >= maxit) ? (notconv == 0 ? 1 : 2) : 0;
+    if (done) *sc.done = done;
+    if (dev) cudaGraphSetConditional(h, done ? 0u : 1u);
   }
+}
+
+// Sweep control of the device-driven multi-column refinement, one thread: records the last
+// inner solve's iterations, stops when every column has converged (nconv == 0) or after
+// max_sweeps, and sets the sweep and inner-loop conditions.
+static __global__ void msweep_ctl_kernel(const int* __restrict__ nconv, const int* __restrict__ iters, LoopCtl* L,
+                                         int max_sweeps, cudaGraphConditionalHandle h_sweep,
+                                         cudaGraphConditionalHandle h_in) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (L->sweep > 0) L->total_it += *iters;
+  const int stop = *nconv == 0 ? 1 : (L->sweep >= max_sweeps ? 3 : 0);
+  if (!stop) L->sweep += 1;
+  L->stop = stop;
+  cudaGraphSetConditional(h_sweep, stop ? 0u : 1u);
+  cudaGraphSetConditional(h_in, stop ? 0u : 1u);
+}
+
+// End of a device-driven multi-column FP64 solve, one thread: iterations and stop code.
+static __global__ void mcg_finish_kernel(const int* __restrict__ done, const int* __restrict__ iters, LoopCtl* L) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  L->total_it = *iters;
+  L->sweep = 1;
+  L->rel = 0.0;
+  L->stop = *done == 1 ? 1 : 4;
 }
 
 template <typename TV>

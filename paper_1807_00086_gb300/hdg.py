@@ -37,7 +37,8 @@ class Material(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32),
                 ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32), ("use_graphs", c_int32),
-                ("guess_history", c_int32), ("device_loops", c_int32), ("trace_space", c_int32)]
+                ("guess_history", c_int32), ("device_loops", c_int32), ("trace_space", c_int32),
+                ("solver", c_int32), ("gmres_restart", c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -96,6 +97,9 @@ SIGNATURES = {
     "hdg_set_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_double]),
     "hdg_get_state": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
     "hdg_step": (c_int32, [c_void_p, c_double, c_int32, c_int32, ctypes.POINTER(SolveInfo)]),
+    "hdg_checkpoint_size": (c_int32, [c_void_p, ctypes.POINTER(c_int64)]),
+    "hdg_save_checkpoint": (c_int32, [c_void_p, c_void_p]),
+    "hdg_load_checkpoint": (c_int32, [c_void_p, c_void_p]),
     "hdg_trace_apply_noalloc": (c_int32, [c_int32, c_int32, c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
                                           c_void_p, c_void_p, c_void_p, ctypes.c_char_p, c_int32]),
     "hdg_enable_stats": (c_int32, [c_void_p, c_int32]),
@@ -157,10 +161,12 @@ class Solver:
 
     def __init__(self, vert, elem, k, tau, rho, c=None, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
                  inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None, lam=None, mu=None,
-                 elem_k=None, guess_history=None, device_loops=None, trace_space="hdg"):
+                 elem_k=None, guess_history=None, device_loops=None, trace_space="hdg", solver="cg",
+                 gmres_restart=None):
         """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu).
         elem_k: per-element degrees (3D elastic); fields and traces are then flat vectors.
-        trace_space: "hdg", "iedg" or "edg" (continuous traces on the interior / all faces)."""
+        trace_space: "hdg", "iedg" or "edg" (continuous traces on the interior / all faces).
+        solver: "cg" (default) or "gmres" (restarted GMRES with two-pass classical Gram-Schmidt)."""
         import torch
         self.lib = load()
         self.torch = torch
@@ -196,6 +202,9 @@ class Solver:
         if device_loops is not None:
             opt.device_loops = 1 if device_loops else 0
         opt.trace_space = {"hdg": 0, "iedg": 1, "edg": 2}[trace_space]
+        opt.solver = {"cg": 0, "gmres": 1}[solver]
+        if gmres_restart is not None:
+            opt.gmres_restart = gmres_restart
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -377,6 +386,18 @@ class Solver:
         self._check(self.lib.hdg_get_tuning(self.ctx, ctypes.byref(t)))
         return {"tuned": t.tuned, "apply32_tile": (t.apply32_warps, t.apply32_unroll),
                 "apply64_tile": (t.apply64_warps, t.apply64_unroll), "local_threads": tuple(t.local_threads)}
+
+    def hdg_save_checkpoint(self):
+        """The complete solver state as a host byte array (bitwise resume with hdg_load_checkpoint)."""
+        n = c_int64()
+        self._check(self.lib.hdg_checkpoint_size(self.ctx, ctypes.byref(n)))
+        buf = np.zeros(n.value, dtype=np.uint8)
+        self._check(self.lib.hdg_save_checkpoint(self.ctx, buf.ctypes.data_as(c_void_p)))
+        return buf
+
+    def hdg_load_checkpoint(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(self.lib.hdg_load_checkpoint(self.ctx, buf.ctypes.data_as(c_void_p)))
 
     def hdg_step(self, dt, scheme, nsteps=1):
         info = SolveInfo()

@@ -135,3 +135,43 @@ def test_device_loops_zero_right_hand_side():
         info = s.hdg_trace_solve(r, lam)
         assert info["rel_residual"] == 0.0
         assert torch.all(lam[~bnd] == 0) and torch.equal(lam[bnd], lam0[bnd])
+
+
+@pytest.mark.parametrize("R", [4, 64])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 1e-9)])
+def test_device_loops_multi_column_match_host_loops_and_oracle(prec, tol, R):
+    """R columns: one graph launch per trace solve (per-column Krylov loop inside the sweep
+    loop) against the host-driven loops and, for two columns, against the oracle."""
+    import torch
+    from paper_1807_00086_gb300 import hdg
+    from gpu_helpers import dirichlet_profile
+    vert, elem = mesh(3, 2)
+    ne = elem.shape[0]
+    k, seed = 2, 3
+    rho = inputs.loguniform(ne, 0.5, 2.0, seed + 7)
+    c = inputs.loguniform(ne, 1.0, 3.0, seed)
+    pos = inputs.uniform_points(R, 3, 0.1, 0.9, seed + 1)
+    amps = np.linspace(1.0, 2.0, R)
+    dt, nsteps = 2e-3, 3
+    out = {}
+    for dl in (True, False):
+        s = hdg.Solver(vert, elem, k, 1.0, rho, c, prec=prec, rtol=1e-12, nrhs=R, device_loops=dl)
+        xb = s.hdg_quadrature_points(1)
+        s.hdg_set_dirichlet(np.stack([dirichlet_profile(x) for x in xb]), 3.0, 0.2)
+        s.hdg_set_sources(pos, amps, 10.0, 0.02, col=np.arange(R))
+        u0 = inputs.random_state(ne, s.n * R, seed + 2).reshape(ne, s.n, R)
+        s.hdg_set_state(torch.tensor(u0, device="cuda"), 0.0)
+        for _ in range(nsteps):
+            info = s.hdg_step(dt, "bdf2", 1)
+            assert info["rel_residual"] <= 1e-12 and info["iterations"] > 0
+        u, lam, t = s.hdg_get_state()
+        out[dl] = (u.cpu().numpy(), lam.cpu().numpy())
+    assert relerr(out[True][0], out[False][0]) < tol and relerr(out[True][1], out[False][1]) < tol
+    prob = ac.build_problem(vert, elem, k, 1.0, rho, c)
+    prob.dirichlet = lambda x, t: dirichlet_profile(x) * np.cos(3.0 * t + 0.2)
+    for j in (0, R - 1):
+        prob.sources = []
+        ac.add_point_source(prob, pos[j], 10.0, 0.02, amp=amps[j])
+        uo, lo, to = ac.run_bdf(prob, u0[:, :, j], dt, nsteps, 2)
+        assert relerr(out[True][0][:, :, j], uo) < tol, j
+        assert relerr(out[True][1][:, :, j], lo) < tol, j
