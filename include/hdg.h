@@ -54,7 +54,8 @@ typedef enum {
   HDG_ENOMEM = -2,   /* device allocation failed                               */
   HDG_ECUDA = -3,    /* a CUDA runtime call failed                             */
   HDG_ENOCONV = -4,  /* Krylov solve hit maxit before rtol                     */
-  HDG_ETIMEOUT = -5, /* a device wait gave up (reserved)                       */
+  HDG_ETIMEOUT = -5, /* reserved: no kernel of the library spins on a flag; every device  */
+                     /* loop ends by its own iteration bound (maxit, max_sweeps)          */
   HDG_ESTATE = -6    /* call out of order (e.g. solve before condense)         */
 } hdg_status;
 
@@ -279,6 +280,13 @@ hdg_status hdg_set_sources(hdg_ctx* ctx, int32_t nsrc, const double* pos_host, c
 hdg_status hdg_stream_create(void** stream_out);
 hdg_status hdg_stream_destroy(void* stream);
 
+/* Rebinds the context to another caller-owned stream (cudaStream_t, may be NULL for the
+ * legacy stream). The call first waits for all work enqueued on the previous stream; every
+ * later call enqueues on the new one. The context's cached CUDA graphs do not depend on
+ * the stream they are launched on and stay valid. The library never creates or destroys
+ * the bound stream. HDG_ECUDA if the wait fails (the binding is then left unchanged). */
+hdg_status hdg_set_stream(hdg_ctx* ctx, void* cuda_stream);
+
 /* Zeroes column j of the fields, the previous level and the traces (a column restarted
  * from rest; used to recycle a finished request's slot). Enqueued on the stream. */
 hdg_status hdg_reset_column(hdg_ctx* ctx, int32_t j);
@@ -398,6 +406,15 @@ typedef struct {
   double applydf_ms;        /* summed device time of those launches                    */
   int64_t apply16_launches; /* launches of the FP16 apply (HDG_MIXED16 Krylov iterations) */
   double apply16_ms;        /* summed device time of those launches                    */
+  /* Device-side timing of the single-column FP32 and FP16 applies, taken by the kernels
+   * themselves from %globaltimer (first CTA start to the end of the last CTA) and therefore
+   * also inside the CUDA graphs of the device-driven loops. It runs whether or not stats are
+   * enabled; launches that return at once (solve already converged) are not counted. The
+   * timer ticks at about 1 us on some parts, so use the mean over many launches. */
+  int64_t dev_apply32_launches;
+  double dev_apply32_ms;
+  int64_t dev_apply16_launches;
+  double dev_apply16_ms;
 } hdg_stats;
 hdg_status hdg_enable_stats(hdg_ctx* ctx, int32_t enable);
 hdg_status hdg_get_stats(hdg_ctx* ctx, hdg_stats* out, int32_t reset);

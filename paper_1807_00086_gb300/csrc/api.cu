@@ -116,8 +116,15 @@ void launch_face_q64(hdg_ctx* c) {
                                                                      c->d_slot, c->d_p, c->d_q, c->d_part, c->d_sc);
 }
 
-// p.q reduction target of the single-column FP32/FP16 applies
-PqOut pq_out(hdg_ctx* c) { return PqOut{c->d_pqpart, c->d_ticket, c->d_pq, (float)c->sgn}; }
+// zero the device-side launch timers (start stamps to the maximum, so the first CTA lowers them)
+hdg_status reset_dev_timing(hdg_ctx* c) {
+  const DevTiming z[2] = {{~0ull, 0, 0.0}, {~0ull, 0, 0.0}};
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_dtime, z, sizeof(z), cudaMemcpyHostToDevice, c->stream));
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? HDG_OK : HDG_ECUDA;
+}
+
+// p.q reduction target of the single-column FP32/FP16 applies, with the launch-timing slot
+PqOut pq_out(hdg_ctx* c, DevTiming* timing) { return PqOut{c->d_pqpart, c->d_ticket, c->d_pq, (float)c->sgn, timing}; }
 
 template <int DIM, int K>
 void launch_update_f32(hdg_ctx* c, int par) {
@@ -162,9 +169,8 @@ void launch_apply16(hdg_ctx* c, const float* x, float* slot, const int* done, in
   const int64_t ngroups = (c->sk.ne + 31) / 32;
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 3, iter);
-  apply16_kernel<DIM, K><<<(unsigned)((ngroups + 3) / 4), 128, 0, c->stream>>>(c->sk.ne, c->d_elem_face, c->d_face_bnd,
-                                                                              c->d_S16, c->d_sc16, x, slot, done,
-                                                                              pq_out(c));
+  apply16_kernel<DIM, K><<<(unsigned)((ngroups + 3) / 4), 128, 0, c->stream>>>(
+      c->sk.ne, c->d_elem_face, c->d_face_bnd, c->d_S16, c->d_sc16, x, slot, done, pq_out(c, c->d_dtime + 1));
   apply_end(c, stop);
 }
 
@@ -213,7 +219,8 @@ void launch_apply32(hdg_ctx* c, const float* x, float* slot, const int* done, in
     return;
   }
   apply32_kernel<DIM, K><<<(unsigned)((ngroups + 3) / 4), 128, 0, c->stream>>>(c->sk.ne, c->d_elem_face, c->d_face_bnd,
-                                                                              c->d_S32, x, slot, done, pq_out(c));
+                                                                              c->d_S32, x, slot, done,
+                                                                              pq_out(c, c->d_dtime));
   apply_end(c, stop);
 }
 
@@ -222,16 +229,16 @@ template <int DIM, int K>
 void edg_expand64(hdg_ctx* c, const double* mu, double* lam, int zero_bnd) {
   constexpr int NF = Dims<DIM, K>::NF;
   c->n_launch += 1;
-  edg_expand_kernel<double, NF><<<grid_for(c, c->sk.nf * NF), 256, 0, c->stream>>>(c->sk.nf, c->d_face_bnd, c->d_face_node,
-                                                                                   c->d_vinv, mu, lam, zero_bnd);
+  edg_expand_kernel<double, NF><<<grid_for(c, c->sk.nf), 256, 0, c->stream>>>(c->sk.nf, c->d_face_bnd, c->d_face_node,
+                                                                              c->d_vinv, mu, lam, zero_bnd);
 }
 
 template <int DIM, int K>
 void edg_expand32(hdg_ctx* c, const float* mu, float* lam) {
   constexpr int NF = Dims<DIM, K>::NF;
   c->n_launch += 1;
-  edg_expand_kernel<float, NF><<<grid_for(c, c->sk.nf * NF), 256, 0, c->stream>>>(c->sk.nf, c->d_face_bnd, c->d_face_node,
-                                                                                  c->d_vinv, mu, lam, 1);
+  edg_expand_kernel<float, NF><<<grid_for(c, c->sk.nf), 256, 0, c->stream>>>(c->sk.nf, c->d_face_bnd, c->d_face_node,
+                                                                             c->d_vinv, mu, lam, 1);
 }
 
 // face nodal weights from element slots (slot) or from a face array (yface)
@@ -344,7 +351,9 @@ hdg_status cg32_inner(hdg_ctx* c, int* iters, double tol, int* last, bool use16)
   c->h_sc->done = 0;
   const int first = std::max(2, std::min(chk, *last - 1));   // first poll near the last solve's count
   while (!c->h_sc->done && it < maxit) {
-    const int upto = std::min(maxit, it + (it == 0 ? first : std::min(chk, 3)));
+    // with statistics on, poll at check_every: a poll idles the GPU until the host enqueues the
+    // next apply, and that gap would land inside the apply's event pair
+    const int upto = std::min(maxit, it + (it == 0 ? first : (c->stats_on ? chk : std::min(chk, 3))));
     for (; it < upto; ++it) {
       const int par = it & 1;
       if (use16) {
@@ -857,7 +866,7 @@ hdg_status cg_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* i
   const int chk = std::max(1, c->opt.check_every);
   int first = std::max(2, std::min(chk, c->last_it64 - 1));   // first poll near the last solve's count
   while (!c->h_sc->done && it < maxit) {
-    const int upto = std::min(maxit, it + (it == 0 ? first : std::min(chk, 4)));
+    const int upto = std::min(maxit, it + (it == 0 ? first : (c->stats_on ? chk : std::min(chk, 4))));
     for (; it < upto; ++it) {
       const int par = it & 1;
       HDG_DISPATCH(c, launch_apply, c, c->d_p, c->d_slot, &c->d_sc->done, it);
@@ -1615,6 +1624,7 @@ void hdg_destroy(hdg_ctx* c) {
   for (auto& g : c->dgraphs) cudaGraphExecDestroy(g.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_lc) cudaFreeHost(c->h_lc);
+  if (c->h_sacc) cudaFreeHost(c->h_sacc);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_sc) cudaFreeHost(c->h_sc);
@@ -1813,6 +1823,8 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
     if ((s = dalloc(c, &c->d_pq, 1))) return s;
     if ((s = dalloc(c, &c->d_ticket, 1))) return s;
     CUDA_TRY(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream));
+    if ((s = dalloc(c, &c->d_dtime, 2))) return s;
+    if ((s = reset_dev_timing(c))) return s;
     if (c->R == 1 && c->phys == HDG_ACOUSTIC) {
       // whole 32-element groups, so the per-CTA staging copy never runs past the end
       const size_t nSdf = (size_t)ngroups * 32 * 2 * P4 * 4;
@@ -2378,6 +2390,29 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
       }
       const double alpha = d[0][0] / dt;
       if ((s = ensure_alpha(c, alpha))) return s;
+      // Eq. 10_2 weights: u^{n+1} = (1 - sum_i b_i sum_j d_ij) u^n + sum_j e_j U_j, e_j = sum_i b_i d_ij
+      double e[3] = {0, 0, 0}, w0 = 1.0;
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) e[j] += b[i] * d[i][j];
+      for (int j = 0; j < 3; ++j) w0 -= e[j];
+      if (c->vd) {
+        // the whole step as one graph launch once the per-element-degree path is tuned
+        double hc[3][3] = {}, uc[4] = {w0, e[0], e[1], e[2]};
+        for (int i = 0; i < 3; ++i) {
+          double cu = 0.0;
+          for (int j = 0; j <= i; ++j) cu += d[i][j];
+          hc[i][0] = cu / d[i][i];
+          for (int j = 0; j < i; ++j) hc[i][1 + j] = -d[i][j] / d[i][i];
+        }
+        bool done = false;
+        if ((s = vd_dirk3_step_graph(c, hc, uc, &si, &done))) return s;
+        if (done) {
+          std::swap(c->d_uprev, c->d_u);
+          std::swap(c->d_u, c->d_unew);
+          c->t = tn + dt;
+          continue;
+        }
+      }
       for (int i = 0; i < 3; ++i) {
         // Eq. 10_1, stage i: d_ii Mw U_i + dt f(U_i) = Mw [ (sum_{j<=i} d_ij) u^n - sum_{j<i} d_ij U_j ]
         double cu = 0.0;
@@ -2388,11 +2423,7 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
         combine(c, c->d_h, cu / d[i][i], c->d_u, co[0], in[0], co[1], in[1], co[2], in[2]);
         if ((s = stage_solve(c, c->d_h, tn + cc[i] * dt, c->d_stage[i], &si))) return s;
       }
-      // Eq. 10_2: u^{n+1} = (1 - sum_i b_i sum_j d_ij) u^n + sum_j e_j U_j, e_j = sum_i b_i d_ij
-      double e[3] = {0, 0, 0}, w0 = 1.0;
-      for (int j = 0; j < 3; ++j)
-        for (int i = 0; i < 3; ++i) e[j] += b[i] * d[i][j];
-      for (int j = 0; j < 3; ++j) w0 -= e[j];
+      // Eq. 10_2 update
       combine(c, c->d_unew, w0, c->d_u, e[0], c->d_stage[0], e[1], c->d_stage[1], e[2], c->d_stage[2]);
       std::swap(c->d_uprev, c->d_u);
       std::swap(c->d_u, c->d_unew);
@@ -2409,6 +2440,13 @@ hdg_status hdg_stream_create(void** out) {
   cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return HDG_ECUDA;
   *out = (void*)st;
+  return HDG_OK;
+}
+
+hdg_status hdg_set_stream(hdg_ctx* c, void* cuda_stream) {
+  if (!c) return HDG_EINVAL;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->stream = (cudaStream_t)cuda_stream;
   return HDG_OK;
 }
 
@@ -2451,6 +2489,19 @@ hdg_status hdg_get_stats(hdg_ctx* c, hdg_stats* o, int32_t reset) {
   if (!c || !o) return HDG_EINVAL;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   harvest(c);
+  DevTiming dt[2] = {{~0ull, 0, 0.0}, {~0ull, 0, 0.0}};
+  if (c->d_dtime) {
+    CUDA_TRY(c, cudaMemcpy(dt, c->d_dtime, sizeof(dt), cudaMemcpyDeviceToHost));
+    if (reset) {
+      hdg_status s = reset_dev_timing(c);
+      if (s) return s;
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  o->dev_apply32_launches = (int64_t)dt[0].count;
+  o->dev_apply32_ms = dt[0].ms;
+  o->dev_apply16_launches = (int64_t)dt[1].count;
+  o->dev_apply16_ms = dt[1].ms;
   o->kernel_launches = c->n_launch;
   o->apply_launches = c->n_apply;
   o->apply_ms = c->apply_ms;

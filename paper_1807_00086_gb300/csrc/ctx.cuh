@@ -64,6 +64,7 @@ struct hdg_ctx {
   float* d_sc16 = nullptr;      // its per-element scales
   double *d_pqpart = nullptr, *d_pq = nullptr;   // p.q block partials and result of the FP32/FP16 apply
   unsigned* d_ticket = nullptr;                   // last-block counter of that reduction
+  DevTiming* d_dtime = nullptr;   // device-side launch timing: [0] FP32 apply, [1] FP16 apply
   float *d_r32 = nullptr, *d_z32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_x32 = nullptr, *d_b32 = nullptr;
   double* d_res = nullptr;   // FP64 refinement residual
   int64_t nfe4 = 0;          // FP32 face vectors padded to a multiple of 4 entries
@@ -135,8 +136,11 @@ struct hdg_ctx {
     const void* x;
     cudaGraphExec_t exec;
     int64_t n_static, n_body, n_trip;   // launches outside the loops, per sweep body, per inner trip
+    double alpha;                       // mass shift baked into a whole-step graph (0 for a solve)
   };
   std::vector<DevGraph> dgraphs;
+  StepAcc* d_sacc = nullptr;   // totals of a graph-launched step, and their pinned host copy
+  StepAcc* h_sacc = nullptr;
   // continuous traces (IEDG / EDG): free face nodes, the node map and its incidence lists, the
   // nodal-to-modal table, the nodal unknowns and right-hand side, face work arrays
   int tspace = 0;                 // HDG_TRACE_HDG / IEDG / EDG
@@ -275,7 +279,7 @@ hdg_status devgraph_solve(hdg_ctx* c, int kind, const void* b, const void* x, BU
     CUDA_TRY(c, cudaGraphCreate(&G, 0));
     GraphBuild gb;
     gb.st = c->cap_stream;
-    hdg_ctx::DevGraph ng{kind, b, x, nullptr, 0, 0, 0};
+    hdg_ctx::DevGraph ng{kind, b, x, nullptr, 0, 0, 0, 0.0};
     const cudaStream_t keep = c->stream;
     const int64_t keep_launch = c->n_launch;
     c->stream = c->cap_stream;
@@ -339,6 +343,11 @@ hdg_status guess_after_v(hdg_ctx* c, int64_t n, const double* b, const double* x
 void guess_reset_column(hdg_ctx* c, int j);
 hdg_status vd_condense(hdg_ctx* c, double alpha);
 hdg_status vd_stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, hdg_solve_info* info);
+// one DIRK(3,3) step of a per-element-degree context as one graph launch (nullptr: not possible
+// yet, the caller steps through the launches); hc[i] = history weights of stage i on (u, U_0,
+// U_1), uc = update weights on (u, U_0, U_1, U_2)
+hdg_status vd_dirk3_step_graph(hdg_ctx* c, const double hc[3][3], const double uc[4], hdg_solve_info* info,
+                               bool* done);
 hdg_status vd_trace_apply(hdg_ctx* c, const double* x, double* y);
 hdg_status vd_condensed_rhs(hdg_ctx* c, const double* F, const double* lamD, double* r);
 hdg_status vd_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_info* info);

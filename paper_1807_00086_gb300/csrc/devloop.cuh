@@ -81,6 +81,29 @@ static __global__ void loopctl_init_kernel(LoopCtl* L, int use16) {
   L->sweep = 0; L->use16 = use16; L->stop = 0; L->total_it = 0;
 }
 
+// Totals of the trace solves inside one graph-launched time step.
+struct StepAcc {
+  double rel;       // relative residual of the last solve
+  int iters;        // Krylov iterations summed over the stage solves
+  int sweeps;       // refinement sweeps (or solves) summed
+  int bad;          // stop code of a solve that did not converge (3 max_sweeps, 4 maxit), else 0
+  int pad;
+};
+
+static __global__ void step_acc_reset_kernel(StepAcc* A) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  A->rel = 0.0; A->iters = 0; A->sweeps = 0; A->bad = 0;
+}
+
+// after a stage solve: add its counts, keep the first failure
+static __global__ void step_acc_kernel(const LoopCtl* __restrict__ L, StepAcc* A) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  A->iters += L->total_it;
+  A->sweeps += L->sweep;
+  A->rel = L->rel;
+  if (!A->bad && L->stop != 1 && L->stop != 2) A->bad = L->stop;
+}
+
 // ---------------------------------------------------------------- least-squares initial guess
 // Ring of the last q stage right-hand sides b_i and solutions lam_i of the same operator
 // (K lam_i = b_i to the solver tolerance). With the Gram matrix G_ij = (b_i, b_j) kept on the

@@ -50,6 +50,7 @@ struct VSum<double> {
 
 // lam[f][m] = sum_a vinv[m][a] mu[face_node[f][a]] on interior faces. Boundary faces: 0 when
 // zero_bnd (Krylov work vectors), left as they are otherwise (the step's Dirichlet traces).
+// One thread per face: its NF nodal values are gathered once.
 template <typename T, int NF>
 __global__ void edg_expand_kernel(int64_t nf, const int32_t* __restrict__ face_bnd, const int32_t* __restrict__ face_node,
                                   const double* __restrict__ vinv, const T* __restrict__ mu, T* __restrict__ lam,
@@ -57,21 +58,27 @@ __global__ void edg_expand_kernel(int64_t nf, const int32_t* __restrict__ face_b
   __shared__ VTab<T> V[NF * NF];
   for (int i = threadIdx.x; i < NF * NF; i += blockDim.x) V[i] = VTab<T>::from(vinv[i]);
   __syncthreads();
-  const int64_t n = nf * NF;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t f = t / NF;
-    const int m = (int)(t - f * NF);
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
     if (face_bnd[f] >= 0) {
-      if (zero_bnd) lam[t] = T(0);
+      if (zero_bnd) {
+#pragma unroll
+        for (int m = 0; m < NF; ++m) lam[f * NF + m] = T(0);
+      }
       continue;
     }
-    VSum<T> v;
+    T mv[NF];
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
       const int32_t node = face_node[f * NF + a];
-      if (node >= 0) v.add(V[m * NF + a], mu[node]);
+      mv[a] = node >= 0 ? mu[node] : T(0);
     }
-    lam[t] = v.value();
+#pragma unroll
+    for (int m = 0; m < NF; ++m) {
+      VSum<T> v;
+#pragma unroll
+      for (int a = 0; a < NF; ++a) v.add(V[m * NF + a], mv[a]);
+      lam[f * NF + m] = v.value();
+    }
   }
 }
 

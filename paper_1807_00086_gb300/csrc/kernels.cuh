@@ -775,12 +775,33 @@ __global__ void pack32_kernel(int64_t ne, const double* __restrict__ S, float* _
 // sum of the element blocks, p.q = sgn sum_K p_K . (S_K p_K) (boundary entries of p are zero
 // on both sides). Each 4-warp block writes its partial; the last block to finish (ticket
 // counter, no waiting) sums the partials in index order and resets the counter.
+// Launch timing on the device (also inside CUDA graphs): the first CTA to start lowers
+// start_ns, the last CTA to finish (the one that sums the partials) adds the elapsed
+// %globaltimer time to ms and counts the launch. Launches that return early (solve converged)
+// are not counted.
+struct DevTiming {
+  unsigned long long start_ns;   // ULLONG_MAX between launches
+  unsigned long long count;
+  double ms;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 struct PqOut {
   double* part;       // [gridDim.x] block partials
   unsigned* ticket;   // zero between launches
   double* pq;         // result
   float sgn;
+  DevTiming* timing;  // may be null
 };
+
+__device__ __forceinline__ void timing_start(const PqOut& o) {
+  if (o.timing && o.part && threadIdx.x == 0) atomicMin(&o.timing->start_ns, global_ns());
+}
 
 __device__ __forceinline__ void pq_epilogue(const PqOut& o, double v) {
   __shared__ double wsum[4];
@@ -805,6 +826,15 @@ __device__ __forceinline__ void pq_epilogue(const PqOut& o, double v) {
   if (threadIdx.x == 0) {
     *o.pq = (double)o.sgn * ((wsum[0] + wsum[1]) + (wsum[2] + wsum[3]));
     *o.ticket = 0u;
+    if (o.timing) {
+      const unsigned long long t1 = global_ns();
+      const unsigned long long t0 = *(volatile unsigned long long*)&o.timing->start_ns;
+      if (t1 > t0) {
+        o.timing->ms += 1e-6 * (double)(t1 - t0);
+        o.timing->count += 1;
+      }
+      o.timing->start_ns = ~0ull;
+    }
   }
 }
 
@@ -821,6 +851,7 @@ __global__ void __launch_bounds__(128, 4) apply32_kernel(int64_t ne, const int32
   constexpr int MP = M + 1;   // padded row: conflict-free transposed writes
   __shared__ float tr[4][32 * MP];
   if (done && *done) return;
+  timing_start(pqo);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t g0 = (int64_t)blockIdx.x * 4 + wid;
   const bool wact = g0 * 32 < ne;                 // the last block may hold idle warps
@@ -932,6 +963,7 @@ __global__ void __launch_bounds__(128, 4) apply16_kernel(int64_t ne, const int32
   constexpr int MP = M + 1;
   __shared__ float tr[4][32 * MP];
   if (done && *done) return;
+  timing_start(pqo);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t g0 = (int64_t)blockIdx.x * 4 + wid;
   const bool wact = g0 * 32 < ne;

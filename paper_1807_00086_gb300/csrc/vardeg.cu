@@ -392,11 +392,14 @@ hdg_status vd_refine(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* 
 }
 
 // ---- device-driven solves (one graph launch per trace solve; see devloop.cuh)
-hdg_status vd_cg_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
+// Appends the solve of (sgn K) x = bvec to G after deps (deps: the solve's last nodes on return);
+// dg, if given, receives the launch counts (outside the loops, per sweep body, per inner trip).
+void vd_build_solve(hdg_ctx* c, GraphBuild& gb, cudaGraph_t G, std::vector<cudaGraphNode_t>& deps, const double* bvec,
+                    double* x, hdg_ctx::DevGraph* dg) {
   const int64_t n = c->ntr;
   const int nb = c->nb_red, maxit = c->opt.maxit;
-  auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
-    std::vector<cudaGraphNode_t> deps, bd;
+  std::vector<cudaGraphNode_t> bd, d16, d32;
+  if (c->opt.prec == HDG_FP64) {
     const int64_t n0 = c->n_launch;
     gb.seq(G, deps, [&] {
       vd_apply64(c, x, c->d_slot, nullptr, -1);
@@ -425,16 +428,13 @@ hdg_status vd_cg_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
       cg_ctl_finish_kernel<<<1, 32, 0, c->stream>>>(c->d_sc, c->d_lc);
       zero_masked_if_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_intmask, c->d_lc, x);
     });
-    dg.n_static = (n1 - n0) + (c->n_launch - n2);
-    dg.n_body = 0;
-    dg.n_trip = n2 - n1;
-  };
-  return devgraph_solve(c, 2, bvec, x, build, info);
-}
-
-hdg_status vd_refine_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
-  const int64_t n = c->ntr;
-  const int nb = c->nb_red, maxit = c->opt.maxit;
+    if (dg) {
+      dg->n_static = (n1 - n0) + (c->n_launch - n2);
+      dg->n_body = 0;
+      dg->n_trip = n2 - n1;
+    }
+    return;
+  }
   const int64_t n4 = c->nfe4 / 4;
   const bool has16 = c->vd->d_S16 != nullptr;
   auto inner = [&](bool use16, cudaGraphConditionalHandle h) {
@@ -452,59 +452,65 @@ hdg_status vd_refine_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_
                                                        (float4*)c->d_p32, c->d_sc, maxit, h);
     }
   };
+  const int64_t n0 = c->n_launch;
+  gb.seq(G, deps, [&] {
+    c->n_launch += 1;
+    loopctl_init_kernel<<<1, 32, 0, c->stream>>>(c->d_lc, has16 ? 1 : 0);
+  });
+  const cudaGraphConditionalHandle h_sweep = gb.handle(G, 1, true);
+  cudaGraph_t B = gb.loop(G, deps, h_sweep);
+  const cudaGraphConditionalHandle h16 = has16 ? gb.handle(B, 0, false) : 0;
+  const cudaGraphConditionalHandle h32 = gb.handle(B, 0, false);
+  const int64_t n1 = c->n_launch;
+  gb.seq(B, bd, [&] {
+    vd_apply_df(c, x, c->d_slot);
+    c->n_launch += 6;
+    vd_refine_residual_kernel<<<nb, 256, 0, c->stream>>>(n, c->sgn, c->vd->d_dslot, c->d_slot, bvec, c->d_res,
+                                                         c->d_part);
+    refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
+    sweep_ctl_kernel<<<1, 32, 0, c->stream>>>(c->d_rs, c->d_sc, c->d_lc, c->opt.rtol, c->opt.inner_rtol,
+                                              c->opt.max_sweeps, h_sweep, has16 ? 1 : 0, h16, h32);
+    to32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_res, c->d_rs, c->d_b32);
+    cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32,
+                                                (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
+                                                (float4*)c->d_p32, c->d_part);
+    cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, 0.5, c->d_sc, &c->d_lc->tol);
+  });
+  const int64_t n2 = c->n_launch;
+  if (has16) {
+    cudaGraph_t B16 = gb.loop(B, bd, h16);
+    gb.seq(B16, d16, [&] { inner(true, h16); });
+  }
+  const int64_t n3 = c->n_launch;
+  cudaGraph_t B32 = gb.loop(B, bd, h32);
+  gb.seq(B32, d32, [&] { inner(false, h32); });
+  const int64_t n4_ = c->n_launch;
+  gb.seq(B, bd, [&] {
+    c->n_launch += 1;
+    vd_refine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->vd->d_dslot, c->d_x32, c->d_rs, x);
+  });
+  const int64_t n5 = c->n_launch;
+  gb.seq(G, deps, [&] {
+    c->n_launch += 1;
+    zero_masked_if_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_intmask, c->d_lc, x);
+  });
+  if (dg) {
+    dg->n_static = (n1 - n0) + (c->n_launch - n5);
+    dg->n_body = (n2 - n1) + (n5 - n4_);
+    dg->n_trip = n4_ - n3;
+  }
+}
+
+hdg_status vd_solve_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
   auto build = [&](GraphBuild& gb, cudaGraph_t G, hdg_ctx::DevGraph& dg) {
-    std::vector<cudaGraphNode_t> deps, bd, d16, d32;
-    const int64_t n0 = c->n_launch;
-    gb.seq(G, deps, [&] {
-      c->n_launch += 1;
-      loopctl_init_kernel<<<1, 32, 0, c->stream>>>(c->d_lc, has16 ? 1 : 0);
-    });
-    const cudaGraphConditionalHandle h_sweep = gb.handle(G, 1, true);
-    cudaGraph_t B = gb.loop(G, deps, h_sweep);
-    const cudaGraphConditionalHandle h16 = has16 ? gb.handle(B, 0, false) : 0;
-    const cudaGraphConditionalHandle h32 = gb.handle(B, 0, false);
-    const int64_t n1 = c->n_launch;
-    gb.seq(B, bd, [&] {
-      vd_apply_df(c, x, c->d_slot);
-      c->n_launch += 6;
-      vd_refine_residual_kernel<<<nb, 256, 0, c->stream>>>(n, c->sgn, c->vd->d_dslot, c->d_slot, bvec, c->d_res,
-                                                           c->d_part);
-      refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
-      sweep_ctl_kernel<<<1, 32, 0, c->stream>>>(c->d_rs, c->d_sc, c->d_lc, c->opt.rtol, c->opt.inner_rtol,
-                                                c->opt.max_sweeps, h_sweep, has16 ? 1 : 0, h16, h32);
-      to32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_res, c->d_rs, c->d_b32);
-      cg32_init_kernel<<<nb, 256, 0, c->stream>>>(n4, (const float4*)c->d_b32, (const float4*)c->d_dinv32,
-                                                  (float4*)c->d_x32, (float4*)c->d_r32, (float4*)c->d_z32,
-                                                  (float4*)c->d_p32, c->d_part);
-      cg32_init_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, 0.5, c->d_sc, &c->d_lc->tol);
-    });
-    const int64_t n2 = c->n_launch;
-    if (has16) {
-      cudaGraph_t B16 = gb.loop(B, bd, h16);
-      gb.seq(B16, d16, [&] { inner(true, h16); });
-    }
-    const int64_t n3 = c->n_launch;
-    cudaGraph_t B32 = gb.loop(B, bd, h32);
-    gb.seq(B32, d32, [&] { inner(false, h32); });
-    const int64_t n4_ = c->n_launch;
-    gb.seq(B, bd, [&] {
-      c->n_launch += 1;
-      vd_refine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->vd->d_dslot, c->d_x32, c->d_rs, x);
-    });
-    const int64_t n5 = c->n_launch;
-    gb.seq(G, deps, [&] {
-      c->n_launch += 1;
-      zero_masked_if_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_intmask, c->d_lc, x);
-    });
-    dg.n_static = (n1 - n0) + (c->n_launch - n5);
-    dg.n_body = (n2 - n1) + (n5 - n4_);
-    dg.n_trip = n4_ - n3;
+    std::vector<cudaGraphNode_t> deps;
+    vd_build_solve(c, gb, G, deps, bvec, x, &dg);
   };
-  return devgraph_solve(c, 3, bvec, x, build, info);
+  return devgraph_solve(c, c->opt.prec == HDG_FP64 ? 2 : 3, bvec, x, build, info);
 }
 
 hdg_status vd_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info* info) {
-  if (use_devgraph(c)) return c->opt.prec == HDG_FP64 ? vd_cg_graph(c, bvec, x, info) : vd_refine_graph(c, bvec, x, info);
+  if (use_devgraph(c)) return vd_solve_graph(c, bvec, x, info);
   return c->opt.prec == HDG_FP64 ? vd_cg(c, bvec, x, info) : vd_refine(c, bvec, x, info);
 }
 
@@ -785,6 +791,88 @@ hdg_status vd_stage_solve(hdg_ctx* c, const double* hist, double tt, double* uou
   if ((s = guess_after(c))) return s;
   vd_local(c, 1, nullptr, hist, c->d_lam, uout);
   return check_launch(c, "vd_recover");
+}
+
+// One DIRK(3,3) step (Eqs. 10_1-2) of the per-element-degree path as ONE graph launch: for each
+// stage the history combination, the element right-hand sides of every degree class, the face
+// gather, the least-squares guess, the device-driven trace solve and the recovery, then the
+// update. Built once per (u, u_new) buffer pair and mass shift; the local-solve block sizes must
+// have been tuned (the first step runs through individual launches).
+hdg_status vd_dirk3_step_graph(hdg_ctx* c, const double hc[3][3], const double uc[4], hdg_solve_info* info, bool* done) {
+  *done = false;
+  VarDeg* v = c->vd;
+  if (!use_devgraph(c) || v->local_nth[0] == 0 || v->local_nth[1] == 0 || !c->condensed) return HDG_OK;
+  hdg_status s;
+  if (!c->d_sacc) {
+    if ((s = dalloc(c, &c->d_sacc, 1))) return s;
+    CUDA_TRY(c, cudaMallocHost((void**)&c->h_sacc, sizeof(StepAcc)));
+  }
+  hdg_ctx::DevGraph* dg = nullptr;
+  for (auto& g : c->dgraphs)
+    if (g.kind == 10 && g.b == c->d_u && g.x == c->d_unew && g.alpha == c->alpha) dg = &g;
+  if (!dg) {
+    if (!c->cap_stream) CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    if (c->dgraphs.size() >= kMaxDevGraphs) {
+      cudaGraphExecDestroy(c->dgraphs.front().exec);
+      c->dgraphs.erase(c->dgraphs.begin());
+    }
+    cudaGraph_t G = nullptr;
+    CUDA_TRY(c, cudaGraphCreate(&G, 0));
+    GraphBuild gb;
+    gb.st = c->cap_stream;
+    const cudaStream_t keep = c->stream;
+    const int64_t keep_launch = c->n_launch;
+    c->stream = c->cap_stream;
+    const int64_t n = c->nfld;
+    std::vector<cudaGraphNode_t> deps;
+    gb.seq(G, deps, [&] { step_acc_reset_kernel<<<1, 32, 0, c->stream>>>(c->d_sacc); });
+    for (int i = 0; i < 3; ++i) {
+      gb.seq(G, deps, [&] {
+        combine_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, hc[i][0], c->d_u, hc[i][1],
+                                                              i > 0 ? c->d_stage[0] : nullptr, hc[i][2],
+                                                              i > 1 ? c->d_stage[1] : nullptr, 0, nullptr, c->d_h);
+        vd_local(c, 0, nullptr, c->d_h, c->d_lam, c->d_slot);
+        vd_gather(c, c->d_slot, -c->sgn, c->d_b);
+        guess_before(c);
+      });
+      vd_build_solve(c, gb, G, deps, c->d_b, c->d_lam, nullptr);
+      gb.seq(G, deps, [&] {
+        step_acc_kernel<<<1, 32, 0, c->stream>>>(c->d_lc, c->d_sacc);
+        guess_after(c);
+        vd_local(c, 1, nullptr, c->d_h, c->d_lam, c->d_stage[i]);
+      });
+    }
+    gb.seq(G, deps, [&] {
+      combine_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, uc[0], c->d_u, uc[1], c->d_stage[0], uc[2], c->d_stage[1],
+                                                            uc[3], c->d_stage[2], c->d_unew);
+    });
+    hdg_ctx::DevGraph ng{10, c->d_u, c->d_unew, nullptr, c->n_launch - keep_launch, 0, 0, c->alpha};
+    c->stream = keep;
+    c->n_launch = keep_launch;
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = gb.err;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, G, 0);
+    cudaGraphDestroy(G);
+    if (e != cudaSuccess) return fail(c, HDG_ECUDA, std::string("step graph: ") + cudaGetErrorString(e));
+    ng.exec = ex;
+    c->dgraphs.push_back(ng);
+    dg = &c->dgraphs.back();
+  }
+  CUDA_TRY(c, cudaGraphLaunch(dg->exec, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_sacc, c->d_sacc, sizeof(StepAcc), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const StepAcc A = *c->h_sacc;
+  c->n_launch += dg->n_static + (int64_t)A.iters * 3;
+  if (info) {
+    info->iterations += A.iters;
+    info->sweeps += A.sweeps;
+    info->rel_residual = A.rel;
+  }
+  *done = true;
+  if (A.bad == 3)
+    return fail(c, HDG_ENOCONV, "mixed-precision refinement reached max_sweeps=" + std::to_string(c->opt.max_sweeps));
+  if (A.bad) return fail(c, HDG_ENOCONV, "trace solve reached maxit=" + std::to_string(c->opt.maxit));
+  return HDG_OK;
 }
 
 hdg_status vd_trace_apply(hdg_ctx* c, const double* x, double* y) {

@@ -59,7 +59,9 @@ class SolveInfo(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("kernel_launches", c_int64), ("apply_launches", c_int64), ("apply_ms", c_double),
                 ("apply32_launches", c_int64), ("apply32_ms", c_double), ("applydf_launches", c_int64),
-                ("applydf_ms", c_double), ("apply16_launches", c_int64), ("apply16_ms", c_double)]
+                ("applydf_ms", c_double), ("apply16_launches", c_int64), ("apply16_ms", c_double),
+                ("dev_apply32_launches", c_int64), ("dev_apply32_ms", c_double),
+                ("dev_apply16_launches", c_int64), ("dev_apply16_ms", c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -91,6 +93,7 @@ SIGNATURES = {
     "hdg_reset_column": (c_int32, [c_void_p, c_int32]),
     "hdg_stream_create": (c_int32, [ctypes.POINTER(c_void_p)]),
     "hdg_stream_destroy": (c_int32, [c_void_p]),
+    "hdg_set_stream": (c_int32, [c_void_p, c_void_p]),
     "hdg_quadrature_points": (c_int32, [c_void_p, c_int32, P_double]),
     "hdg_project_volume": (c_int32, [c_void_p, P_double, c_void_p]),
     "hdg_set_dirichlet": (c_int32, [c_void_p, P_double, c_double, c_double]),
@@ -257,6 +260,11 @@ class Solver:
         return _ptr(t)
 
     # entry points --------------------------------------------------------------------------
+    def hdg_set_stream(self, stream):
+        """Rebind the context to `stream` (a torch.cuda.Stream or ExternalStream)."""
+        self._check(self.lib.hdg_set_stream(self.ctx, ctypes.c_void_p(stream.cuda_stream)))
+        self.stream = stream
+
     def hdg_condense(self, alpha):
         self._check(self.lib.hdg_condense(self.ctx, alpha))
 
@@ -378,7 +386,9 @@ class Solver:
         return {"kernel_launches": st.kernel_launches, "apply_launches": st.apply_launches, "apply_ms": st.apply_ms,
                 "apply32_launches": st.apply32_launches, "apply32_ms": st.apply32_ms,
                 "applydf_launches": st.applydf_launches, "applydf_ms": st.applydf_ms,
-                "apply16_launches": st.apply16_launches, "apply16_ms": st.apply16_ms}
+                "apply16_launches": st.apply16_launches, "apply16_ms": st.apply16_ms,
+                "dev_apply32_launches": st.dev_apply32_launches, "dev_apply32_ms": st.dev_apply32_ms,
+                "dev_apply16_launches": st.dev_apply16_launches, "dev_apply16_ms": st.dev_apply16_ms}
 
     def hdg_get_tuning(self):
         """Autotuned tiles of a per-element-degree context (see hdg_tuning in include/hdg.h)."""

@@ -70,3 +70,28 @@ def test_resume_from_checkpoint_is_bitwise(name, make, scheme, dt):
     other = _acoustic(2, 2, 1, "fp64")
     with pytest.raises(hdg.HDGError):
         other.hdg_load_checkpoint(ck)
+
+
+@pytest.mark.parametrize("prec,nrhs", [("mixed16", 1), ("fp64", 1), ("mixed", 4)])
+def test_rebinding_the_stream_mid_run_is_bitwise_neutral(prec, nrhs):
+    """hdg_set_stream: 2 steps on the creation stream, rebind to a library-created stream,
+    2 more steps (device-loop graphs captured before the switch are launched on the new
+    stream) gives bitwise the fields and traces of 4 steps on one stream."""
+    import torch
+    from paper_1807_00086_gb300 import hdg
+    a = _acoustic(3, 2, 3, prec, nrhs)
+    b = _acoustic(3, 2, 3, prec, nrhs)
+    a.hdg_step(2e-3, "bdf2", 4)
+    b.hdg_step(2e-3, "bdf2", 2)
+    st = hdg.own_stream()
+    try:
+        b.hdg_set_stream(st)
+        b.hdg_step(2e-3, "bdf2", 2)
+        ua, la, ta = a.hdg_get_state()
+        ub, lb, tb = b.hdg_get_state()
+        torch.cuda.synchronize()
+        assert ta == tb
+        assert torch.equal(ua, ub) and torch.equal(la, lb)
+    finally:
+        b.close()
+        hdg.release_stream(st)

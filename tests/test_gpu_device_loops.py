@@ -175,3 +175,4 @@ def test_device_loops_multi_column_match_host_loops_and_oracle(prec, tol, R):
         uo, lo, to = ac.run_bdf(prob, u0[:, :, j], dt, nsteps, 2)
         assert relerr(out[True][0][:, :, j], uo) < tol, j
         assert relerr(out[True][1][:, :, j], lo) < tol, j
+
