@@ -60,7 +60,7 @@ typedef enum {
 } hdg_status;
 
 typedef enum { HDG_BE = 1, HDG_BDF2 = 2, HDG_DIRK3 = 3 } hdg_scheme;
-typedef enum { HDG_ACOUSTIC = 0, HDG_ELASTIC = 1 } hdg_physics;
+typedef enum { HDG_ACOUSTIC = 0, HDG_ELASTIC = 1, HDG_SVK = 2 } hdg_physics;
 typedef enum { HDG_FP64 = 0, HDG_MIXED = 1, HDG_MIXED16 = 2 } hdg_precision;
 
 typedef struct {
@@ -80,7 +80,8 @@ typedef struct {
 } hdg_mesh;
 
 typedef struct {
-  hdg_physics phys;         /* HDG_ACOUSTIC (uses rho, c) or HDG_ELASTIC (rho, lam, mu) */
+  hdg_physics phys;         /* HDG_ACOUSTIC (uses rho, c), HDG_ELASTIC (rho, lam, mu) or  */
+                            /* HDG_SVK (rho, lam, mu: nonlinear elastodynamics below)   */
   const double* rho;        /* _host [n_elem] density, > 0                           */
   const double* c;          /* _host [n_elem] sound speed, > 0 (acoustic)            */
   const double* lam;        /* _host [n_elem] Lame lambda (elastic), d lam + 2 mu > 0 */
@@ -139,6 +140,10 @@ typedef struct {
                             /* Jacobi preconditioning, the paper's Krylov method (Sec.     */
                             /* 2.4); FP64, HDG traces, nrhs = 1, host-driven iterations    */
   int32_t gmres_restart;    /* Krylov basis size before a restart (2..64)                */
+  double newton_tol;        /* HDG_SVK: a stage's Newton iteration stops when the largest */
+                            /* increment (fields and traces) is <= newton_tol *         */
+                            /* max(1, max |u|)                                          */
+  int32_t newton_maxit;     /* HDG_SVK: Newton iteration cap per stage (HDG_ENOCONV)     */
 } hdg_options;
 
 enum { HDG_SOLVER_CG = 0, HDG_SOLVER_GMRES = 1 };
@@ -169,7 +174,7 @@ typedef struct {
 
 /* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1,
  * use_graphs 0, guess_history 8, device_loops 1, trace_space HDG_TRACE_HDG, solver HDG_SOLVER_CG,
- * gmres_restart 40. */
+ * gmres_restart 40, newton_tol 1e-11, newton_maxit 25. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face
@@ -393,6 +398,44 @@ typedef struct {
 } hdg_tuning;
 hdg_status hdg_get_tuning(const hdg_ctx* ctx, hdg_tuning* out);
 
+/* ---- Nonlinear elastodynamics (Sec. 4.4, Eqs. UNEL, eq:HDG_nelas1-5): HDG_SVK contexts.
+ * Saint Venant-Kirchhoff material, P = F S(F), S = lam tr(E) I + 2 mu E, E = (F^T F - I) / 2,
+ * in the velocity / deformation-gradient / stress form
+ *   (alpha rho (v - h_v), w) + (P, grad w) - <P n - s (v - v_hat), w> = (f, w)
+ *   (alpha (H - h_H), G) + (v, div G) - <v_hat, G n> = 0,   H = F - I
+ *   (P, Q) - (F S(F), Q) = 0
+ * with s = 2 sqrt(rho mu) per element and conservation of P n - s (v - v_hat) on the faces.
+ * 3D tetrahedra, uniform k in 1..3, nrhs = 1, HDG traces, CG, FP64. Fields [n_elem][21][Np]:
+ * v_1..3, H_iJ (row-major (i, J)), P_iJ; traces [n_faces][3 Nf] (v_hat, component-major).
+ * Boundary faces are clamped (v_hat = 0) unless marked as traction faces. The volume rule of
+ * hdg_quadrature_points / hdg_project_volume has (2k + 2)^3 points (nq_vol of hdg_get_sizes).
+ * Every implicit stage is solved by Newton's method: each iteration forms, per element, the
+ * residual and its Jacobian at quadrature points, condenses it (Eq. LS: H and P eliminated
+ * through their diagonal mass blocks, then the velocity block by Cholesky), solves the trace
+ * system (CG to rtol; 1e-10 is enough, Newton corrects the rest) and recovers the element
+ * increments. hdg_step runs HDG_DIRK3 (the stages start Newton from the previous stage);
+ * info->sweeps returns the Newton iterations, info->iterations the CG iterations.
+ * hdg_condense / hdg_condensed_rhs / hdg_recover / hdg_postprocess / hdg_set_dirichlet with
+ * data return HDG_EINVAL; HDG_EINVAL also when an element's velocity block is not positive
+ * definite (the tangent lost ellipticity). */
+
+/* Marks boundary faces as traction faces (mask_host [n_bnd] in the order of
+ * hdg_quadrature_points(which = 1), 1 = traction; NULL clears): their traces become
+ * unknowns, loaded by the traction data of the forcing callback. */
+hdg_status hdg_svk_set_traction_faces(hdg_ctx* ctx, const uint8_t* mask_host);
+
+/* Forcing of the stage equations, called by hdg_step on the host before each stage with the
+ * stage time t: fill f_host [n_elem][nq_vol][3] with the body force f at the volume points and
+ * g_host [n_bnd][nq_face][3] with the traction P n at the boundary-face points (only traction
+ * faces are read). Both arrive zero-filled; return 0 on success (otherwise hdg_step fails with
+ * HDG_EINVAL). NULL fn: no forcing. */
+typedef int32_t (*hdg_svk_forcing)(void* user, double t, double* f_host, double* g_host);
+hdg_status hdg_svk_set_forcing(hdg_ctx* ctx, hdg_svk_forcing fn, void* user);
+
+/* Newton iterations of each stage of the last hdg_step (count = 3 x steps); writes at most
+ * cap entries into out_host (may be NULL to query the count). */
+hdg_status hdg_svk_newton_counts(const hdg_ctx* ctx, int32_t* out_host, int32_t cap, int32_t* count);
+
 /* Instrumentation (not part of the method). When enabled, the context counts its kernel
  * launches and times every launch of the matrix-free trace apply with CUDA events on the
  * context stream; hdg_get_stats returns the totals since the last reset. */
@@ -415,6 +458,10 @@ typedef struct {
   double dev_apply32_ms;
   int64_t dev_apply16_launches;
   double dev_apply16_ms;
+  int64_t svk_condense_launches; /* HDG_SVK: per-Newton-iteration condensation kernel   */
+  double svk_condense_ms;        /* (CUDA events while stats are enabled)               */
+  int64_t svk_recover_launches;  /* HDG_SVK: per-Newton-iteration recovery kernel       */
+  double svk_recover_ms;
 } hdg_stats;
 hdg_status hdg_enable_stats(hdg_ctx* ctx, int32_t enable);
 hdg_status hdg_get_stats(hdg_ctx* ctx, hdg_stats* out, int32_t reset);

@@ -1367,6 +1367,10 @@ void dirk3(double a[3][3], double b[3], double cc[3]) {
 
 }  // namespace
 
+// entry points of this unit used by the other translation units
+hdg_status trace_cg_solve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) { return cg_solve(c, b, x, info); }
+void dirk3_tableau(double a[3][3], double b[3], double cc[3]) { dirk3(a, b, cc); }
+
 // ---- least-squares initial guess over earlier stage solutions (same alpha)
 // The stored pairs satisfy K lam_i = b_i to the solver tolerance, so minimising
 // |b - K sum c_i lam_i| over the span needs only the Gram matrix of the stored b_i and their
@@ -1561,6 +1565,8 @@ void hdg_default_options(hdg_options* o) {
   o->trace_space = HDG_TRACE_HDG;
   o->solver = HDG_SOLVER_CG;
   o->gmres_restart = 40;
+  o->newton_tol = 1e-11;
+  o->newton_maxit = 25;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -1631,6 +1637,7 @@ void hdg_destroy(hdg_ctx* c) {
   if (c->h_rs) cudaFreeHost(c->h_rs);
   if (c->h_mint) cudaFreeHost(c->h_mint);
   vd_destroy(c);
+  svk_destroy(c);
   delete c;
 }
 
@@ -1665,8 +1672,16 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
        c->opt.gmres_restart < 2 || c->opt.gmres_restart > 64))
     return fail(c, HDG_EINVAL, "GMRES: FP64, HDG traces, uniform degree, nrhs = 1 and 2 <= gmres_restart <= 64 only");
   std::string err;
-  if (mat->phys != HDG_ACOUSTIC && mat->phys != HDG_ELASTIC) return fail(c, HDG_EINVAL, "unknown physics");
-  c->phys = mat->phys;
+  const bool svk = mat->phys == HDG_SVK;
+  if (mat->phys != HDG_ACOUSTIC && mat->phys != HDG_ELASTIC && !svk) return fail(c, HDG_EINVAL, "unknown physics");
+  if (svk && (mesh->dim != 3 || k > 3 || mesh->elem_k || c->R != 1 || c->tspace != HDG_TRACE_HDG ||
+              c->opt.solver != HDG_SOLVER_CG || c->opt.prec != HDG_FP64))
+    return fail(c, HDG_EINVAL, "SVK: 3D, uniform k in 1..3, nrhs = 1, HDG traces, CG and FP64 only");
+  if (svk && (!(c->opt.newton_tol > 0.0) || c->opt.newton_maxit < 1))
+    return fail(c, HDG_EINVAL, "SVK: newton_tol must be > 0 and newton_maxit >= 1");
+  // SVK contexts share the elastic trace layout (3 N_f velocity traces per face)
+  c->phys = svk ? HDG_ELASTIC : mat->phys;
+  if (svk) c->opt.guess_history = 0;
   if (c->phys == HDG_ELASTIC && (!mat->lam || !mat->mu)) return fail(c, HDG_EINVAL, "elastic material needs lam and mu");
   if (c->phys == HDG_ELASTIC && c->opt.nrhs != 1) return fail(c, HDG_EINVAL, "elastic path supports nrhs = 1 only");
   // uniform degree 4 in 3D elastic runs through the per-element-degree path (its local
@@ -1696,10 +1711,17 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   } catch (const std::exception& ex) {
     return fail(c, HDG_EINVAL, ex.what());
   }
+  if (svk) {
+    // the SVK stress term F S(F) phi has degree 4k: volume rule of 2k + 2 points per direction
+    simplex_rule(3, 2 * k + 2, c->T.qv_pts, c->T.qv_w);
+    c->T.nqv = (int)c->T.qv_w.size();
+    c->T.qv_phi.assign((size_t)c->T.nqv * c->T.Np, 0.0);
+    dubiner(3, k, c->T.qv_pts.data(), c->T.nqv, c->T.qv_phi.data(), nullptr);
+  }
   c->Np = c->T.Np; c->nfc = c->dim + 1;
   if (c->phys == HDG_ELASTIC) {
     const int nt = c->dim * (c->dim + 1) / 2;
-    c->ncomp = c->dim + nt;
+    c->ncomp = svk ? 21 : c->dim + nt;
     c->Nf = c->dim * c->T.Nf;          // trace DOFs per face: d velocity components
     c->nv = c->dim * c->Np;
     c->sgn = 1.0;
@@ -1779,12 +1801,14 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   const size_t nfe = (size_t)nf * c->Nf;
   const size_t R = (size_t)c->R;
   if ((s = dalloc(c, &c->d_S, (size_t)ne * c->m * c->m))) return s;
-  if ((s = dalloc(c, &c->d_Hinv, (size_t)ne * c->nv * c->nv))) return s;
+  if ((s = dalloc(c, &c->d_Hinv, svk ? (size_t)1 : (size_t)ne * c->nv * c->nv))) return s;
   if ((s = dalloc(c, &c->d_dinv, nfe))) return s;
   if ((s = dalloc(c, &c->d_err, 1))) return s;
   for (double** p : {&c->d_r, &c->d_z, &c->d_p, &c->d_q, &c->d_b, &c->d_lam, &c->d_lam_prev, &c->d_lam_prev2, &c->d_lam_x})
     if ((s = dalloc(c, p, nfe * R))) return s;
-  if ((s = dalloc(c, &c->d_slot, (size_t)ne * std::max(c->m, 1)))) return s;
+  // element slots plus one zero slot past the last (the missing neighbour of an SVK traction face)
+  if ((s = dalloc(c, &c->d_slot, (size_t)ne * std::max(c->m, 1) + c->Nf))) return s;
+  CUDA_TRY(c, cudaMemsetAsync(c->d_slot, 0, ((size_t)ne * std::max(c->m, 1) + c->Nf) * 8, c->stream));
   if ((s = dalloc(c, &c->d_part, (size_t)c->nb_red * 3 * R))) return s;
   if (c->R > 1) {
     if ((s = dalloc(c, &c->d_mslot, (size_t)ne * c->m * R))) return s;
@@ -1925,6 +1949,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
       for (int mm = 0; mm < c->Nf; ++mm) mask[(size_t)f * c->Nf + mm] = c->sk.face_bnd[f] < 0 ? 1 : 0;
     if ((s = guess_setup(c, mask.data()))) return s;
   }
+  if (svk && (s = svk_setup(c))) return s;
   c->have_state = true;
   return HDG_OK;
 }
@@ -1950,6 +1975,7 @@ hdg_status hdg_get_sizes(const hdg_ctx* c, hdg_sizes* o) {
 
 hdg_status hdg_condense(hdg_ctx* c, double alpha) {
   if (!c) return HDG_EINVAL;
+  if (c->svk) return fail(c, HDG_EINVAL, "SVK: every Newton iteration of hdg_step condenses; no hdg_condense");
   return do_condense(c, alpha);
 }
 
@@ -1978,6 +2004,7 @@ hdg_status hdg_trace_apply(hdg_ctx* c, const double* x, double* y) {
 
 hdg_status hdg_condensed_rhs(hdg_ctx* c, const double* F, const double* lamD, double* r) {
   if (!c || !F || !r) return fail(c, HDG_EINVAL, "null argument");
+  if (c->svk) return fail(c, HDG_EINVAL, "SVK: the Newton stages of hdg_step condense and recover");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
   if (c->vd) return vd_condensed_rhs(c, F, lamD, r);
   if (c->R > 1) {
@@ -2021,6 +2048,7 @@ hdg_status hdg_trace_solve(hdg_ctx* c, const double* r, double* lam, hdg_solve_i
 
 hdg_status hdg_recover(hdg_ctx* c, const double* F, const double* lam, double* u) {
   if (!c || !F || !lam || !u) return fail(c, HDG_EINVAL, "null argument");
+  if (c->svk) return fail(c, HDG_EINVAL, "SVK: the Newton stages of hdg_step condense and recover");
   if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
   if (c->vd) return vd_recover(c, F, lam, u);
   if (c->R > 1) {
@@ -2333,6 +2361,7 @@ hdg_status hdg_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hd
   if (!c) return HDG_EINVAL;
   if (!(dt > 0.0) || nsteps < 0) return fail(c, HDG_EINVAL, "dt must be positive and nsteps >= 0");
   if (scheme != HDG_BE && scheme != HDG_BDF2 && scheme != HDG_DIRK3) return fail(c, HDG_EINVAL, "unknown scheme");
+  if (c->svk) return svk_step(c, dt, scheme, nsteps, info);
   if (info) { info->iterations = 0; info->sweeps = 0; info->rel_residual = 0; }
   hdg_solve_info si{};
   hdg_status s;
@@ -2511,9 +2540,14 @@ hdg_status hdg_get_stats(hdg_ctx* c, hdg_stats* o, int32_t reset) {
   o->applydf_ms = c->applydf_ms;
   o->apply16_launches = c->n_apply16;
   o->apply16_ms = c->apply16_ms;
+  o->svk_condense_launches = c->n_svkc;
+  o->svk_condense_ms = c->svkc_ms;
+  o->svk_recover_launches = c->n_svkr;
+  o->svk_recover_ms = c->svkr_ms;
   if (reset) {
     c->n_launch = 0; c->n_apply = 0; c->apply_ms = 0.0; c->n_apply32 = 0; c->apply32_ms = 0.0;
     c->n_applydf = 0; c->applydf_ms = 0.0; c->n_apply16 = 0; c->apply16_ms = 0.0;
+    c->n_svkc = 0; c->svkc_ms = 0.0; c->n_svkr = 0; c->svkr_ms = 0.0;
   }
   return HDG_OK;
 }

@@ -20,6 +20,7 @@
 using namespace hdg;
 
 struct VarDeg;   // variable-degree (per-element k) data of an elastic context
+struct Svk;      // nonlinear (Saint Venant-Kirchhoff) elastodynamics data
 
 struct hdg_ctx {
   std::string err;
@@ -104,10 +105,11 @@ struct hdg_ctx {
   std::vector<void*> allocs;
   // instrumentation
   bool stats_on = false;
-  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0, n_applydf = 0, n_apply16 = 0;
-  double apply_ms = 0.0, apply32_ms = 0.0, applydf_ms = 0.0, apply16_ms = 0.0;
+  int64_t n_launch = 0, n_apply = 0, n_apply32 = 0, n_applydf = 0, n_apply16 = 0, n_svkc = 0, n_svkr = 0;
+  double apply_ms = 0.0, apply32_ms = 0.0, applydf_ms = 0.0, apply16_ms = 0.0, svkc_ms = 0.0, svkr_ms = 0.0;
   std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
-  std::vector<char> ev_kind;          // per pair: 0 FP64, 1 FP32, 2 double-float, 3 FP16 apply
+  std::vector<char> ev_kind;          // per pair: 0 FP64, 1 FP32, 2 double-float, 3 FP16 apply,
+                                      // 4 SVK condensation, 5 SVK recovery
   std::vector<int> ev_iter;           // per pair: Krylov iteration index (-1: always live)
   size_t ev_used = 0;
   // entries of one field / trace column (n N_e and N_f N_faces for one degree; sums of the
@@ -152,6 +154,7 @@ struct hdg_ctx {
   // dots of the last pass and the coefficients of the update
   double *d_gmV = nullptr, *d_gmpart = nullptr, *d_gmh = nullptr, *d_gmy = nullptr;
   VarDeg* vd = nullptr;
+  Svk* svk = nullptr;   // set for HDG_SVK contexts (elastic trace layout, 21 N_p fields)
 };
 
 namespace {
@@ -250,6 +253,8 @@ void harvest(hdg_ctx* c, int live_iters = 1 << 30) {
       if (c->ev_kind[i / 2] == 1) { c->apply32_ms += ms; c->n_apply32 += 1; }
       else if (c->ev_kind[i / 2] == 2) { c->applydf_ms += ms; c->n_applydf += 1; }
       else if (c->ev_kind[i / 2] == 3) { c->apply16_ms += ms; c->n_apply16 += 1; }
+      else if (c->ev_kind[i / 2] == 4) { c->svkc_ms += ms; c->n_svkc += 1; }
+      else if (c->ev_kind[i / 2] == 5) { c->svkr_ms += ms; c->n_svkr += 1; }
       else { c->apply_ms += ms; c->n_apply += 1; }
     }
   }
@@ -356,3 +361,11 @@ hdg_status vd_quadrature_points(hdg_ctx* c, int32_t which, double* xyz);
 hdg_status vd_project_volume(hdg_ctx* c, const double* vals, double* u);
 hdg_status vd_get_tuning(const hdg_ctx* c, hdg_tuning* out);
 void vd_destroy(hdg_ctx* c);
+// nonlinear elastodynamics (svk.cu)
+hdg_status svk_setup(hdg_ctx* c);
+hdg_status svk_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hdg_solve_info* info);
+void svk_destroy(hdg_ctx* c);
+// api.cu: the context's trace solve (CG on the assembled S_K, device- or host-driven) and the
+// DIRK(3,3) tableau
+hdg_status trace_cg_solve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info);
+void dirk3_tableau(double a[3][3], double b[3], double cc[3]);

@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32),
                 ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32), ("use_graphs", c_int32),
                 ("guess_history", c_int32), ("device_loops", c_int32), ("trace_space", c_int32),
-                ("solver", c_int32), ("gmres_restart", c_int32)]
+                ("solver", c_int32), ("gmres_restart", c_int32), ("newton_tol", c_double), ("newton_maxit", c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -61,12 +61,18 @@ class Stats(ctypes.Structure):
                 ("apply32_launches", c_int64), ("apply32_ms", c_double), ("applydf_launches", c_int64),
                 ("applydf_ms", c_double), ("apply16_launches", c_int64), ("apply16_ms", c_double),
                 ("dev_apply32_launches", c_int64), ("dev_apply32_ms", c_double),
-                ("dev_apply16_launches", c_int64), ("dev_apply16_ms", c_double)]
+                ("dev_apply16_launches", c_int64), ("dev_apply16_ms", c_double),
+                ("svk_condense_launches", c_int64), ("svk_condense_ms", c_double),
+                ("svk_recover_launches", c_int64), ("svk_recover_ms", c_double)]
 
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tuned", c_int32), ("apply32_warps", c_int32), ("apply32_unroll", c_int32),
                 ("apply64_warps", c_int32), ("apply64_unroll", c_int32), ("local_threads", c_int32 * 2)]
+
+
+# hdg_svk_forcing: int32 (*)(void* user, double t, double* f_host, double* g_host)
+FORCING = ctypes.CFUNCTYPE(c_int32, c_void_p, c_double, ctypes.POINTER(c_double), ctypes.POINTER(c_double))
 
 
 # exported entry points: name -> (restype, argtypes)
@@ -94,6 +100,9 @@ SIGNATURES = {
     "hdg_stream_create": (c_int32, [ctypes.POINTER(c_void_p)]),
     "hdg_stream_destroy": (c_int32, [c_void_p]),
     "hdg_set_stream": (c_int32, [c_void_p, c_void_p]),
+    "hdg_svk_set_traction_faces": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_uint8)]),
+    "hdg_svk_set_forcing": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "hdg_svk_newton_counts": (c_int32, [c_void_p, P_int32, c_int32, P_int32]),
     "hdg_quadrature_points": (c_int32, [c_void_p, c_int32, P_double]),
     "hdg_project_volume": (c_int32, [c_void_p, P_double, c_void_p]),
     "hdg_set_dirichlet": (c_int32, [c_void_p, P_double, c_double, c_double]),
@@ -165,8 +174,9 @@ class Solver:
     def __init__(self, vert, elem, k, tau, rho, c=None, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
                  inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None, lam=None, mu=None,
                  elem_k=None, guess_history=None, device_loops=None, trace_space="hdg", solver="cg",
-                 gmres_restart=None):
-        """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu).
+                 gmres_restart=None, svk=False, newton_tol=None, newton_maxit=None):
+        """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu);
+        svk=True with lam, mu: nonlinear Saint Venant-Kirchhoff elastodynamics (Newton per stage).
         elem_k: per-element degrees (3D elastic); fields and traces are then flat vectors.
         trace_space: "hdg", "iedg" or "edg" (continuous traces on the interior / all faces).
         solver: "cg" (default) or "gmres" (restarted GMRES with two-pass classical Gram-Schmidt)."""
@@ -182,8 +192,8 @@ class Solver:
         if self.elastic:
             self._lam, self._mu = arr(lam), arr(mu)
             self._c = arr(1.0)
-            mat = Material(1, _np_ptr(self._rho, c_double), _np_ptr(self._c, c_double), _np_ptr(self._lam, c_double),
-                           _np_ptr(self._mu, c_double))
+            mat = Material(2 if svk else 1, _np_ptr(self._rho, c_double), _np_ptr(self._c, c_double),
+                           _np_ptr(self._lam, c_double), _np_ptr(self._mu, c_double))
         else:
             self._c = arr(c)
             mat = Material(0, _np_ptr(self._rho, c_double), _np_ptr(self._c, c_double), None, None)
@@ -208,6 +218,12 @@ class Solver:
         opt.solver = {"cg": 0, "gmres": 1}[solver]
         if gmres_restart is not None:
             opt.gmres_restart = gmres_restart
+        if newton_tol is not None:
+            opt.newton_tol = newton_tol
+        if newton_maxit is not None:
+            opt.newton_maxit = newton_maxit
+        self.svk = bool(svk)
+        self._forcing_cb = None
         self.device = torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -264,6 +280,45 @@ class Solver:
         """Rebind the context to `stream` (a torch.cuda.Stream or ExternalStream)."""
         self._check(self.lib.hdg_set_stream(self.ctx, ctypes.c_void_p(stream.cuda_stream)))
         self.stream = stream
+
+    # nonlinear elastodynamics ---------------------------------------------------------------
+    def hdg_svk_set_traction_faces(self, mask):
+        """mask [n_bnd] (order of hdg_quadrature_points(1)): 1 = traction face, None clears."""
+        if mask is None:
+            self._check(self.lib.hdg_svk_set_traction_faces(self.ctx, None))
+            return
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        assert m.shape == (self.n_bnd,)
+        self._check(self.lib.hdg_svk_set_traction_faces(self.ctx, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+    def hdg_svk_set_forcing(self, fn):
+        """fn(t, f, g) fills f [n_elem, nq_vol, 3] (body force at the volume points) and
+        g [n_bnd, nq_face, 3] (traction P n at the boundary-face points) in place; None removes it."""
+        if fn is None:
+            self._forcing_cb = None
+            self._check(self.lib.hdg_svk_set_forcing(self.ctx, None, None))
+            return
+        sz = self.sizes
+        fshape = (self.n_elem, sz.nq_vol, 3)
+        gshape = (max(self.n_bnd, 1), sz.nq_face, 3)
+
+        def cb(user, t, fptr, gptr):
+            try:
+                f = np.ctypeslib.as_array(fptr, shape=fshape)
+                g = np.ctypeslib.as_array(gptr, shape=gshape)
+                fn(t, f, g[:self.n_bnd])
+                return 0
+            except Exception:   # reported to the library as a failed callback
+                return 1
+        self._forcing_cb = FORCING(cb)
+        self._check(self.lib.hdg_svk_set_forcing(self.ctx, ctypes.cast(self._forcing_cb, c_void_p), None))
+
+    def hdg_svk_newton_counts(self):
+        n = c_int32()
+        self._check(self.lib.hdg_svk_newton_counts(self.ctx, None, 0, ctypes.byref(n)))
+        out = np.zeros(max(n.value, 1), dtype=np.int32)
+        self._check(self.lib.hdg_svk_newton_counts(self.ctx, _np_ptr(out, c_int32), n.value, ctypes.byref(n)))
+        return out[:n.value].tolist()
 
     def hdg_condense(self, alpha):
         self._check(self.lib.hdg_condense(self.ctx, alpha))
@@ -344,7 +399,7 @@ class Solver:
 
     def hdg_project_volume(self, vals, u=None):
         vals = np.ascontiguousarray(vals, dtype=np.float64)
-        ncomp = (self.dim + self.dim * (self.dim + 1) // 2) if self.elastic else self.dim + 1
+        ncomp = 21 if self.svk else (self.dim + self.dim * (self.dim + 1) // 2) if self.elastic else self.dim + 1
         if self.vardeg:
             assert vals.shape == (int(self.vol_points_per_element().sum()), ncomp)
         else:
@@ -388,7 +443,9 @@ class Solver:
                 "applydf_launches": st.applydf_launches, "applydf_ms": st.applydf_ms,
                 "apply16_launches": st.apply16_launches, "apply16_ms": st.apply16_ms,
                 "dev_apply32_launches": st.dev_apply32_launches, "dev_apply32_ms": st.dev_apply32_ms,
-                "dev_apply16_launches": st.dev_apply16_launches, "dev_apply16_ms": st.dev_apply16_ms}
+                "dev_apply16_launches": st.dev_apply16_launches, "dev_apply16_ms": st.dev_apply16_ms,
+                "svk_condense_launches": st.svk_condense_launches, "svk_condense_ms": st.svk_condense_ms,
+                "svk_recover_launches": st.svk_recover_launches, "svk_recover_ms": st.svk_recover_ms}
 
     def hdg_get_tuning(self):
         """Autotuned tiles of a per-element-degree context (see hdg_tuning in include/hdg.h)."""
