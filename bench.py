@@ -607,6 +607,176 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def svk_condense_flops(k):
+    """FP64 flops of one element of svk_condense_kernel<k> (an FMA counts 2): the residual on the
+    (2k+2)^3 rule, the deformation gradient on the (2k+1)^3 rule, per Jacobian point the tangent
+    and the three outer-product accumulations (Dx T Dx^T upper triangle, Dx T BH, BH^T T BH
+    upper triangle) with their per-point precomputes, the Cholesky of S_v, Z = L^{-1} W, Z^T Z
+    and the two tangent applies."""
+    NP = (k + 1) * (k + 2) * (k + 3) // 6
+    NFP = (k + 1) * (k + 2) // 2
+    NV, M, N = 3 * NP, 12 * NFP, 21 * NP
+    NQR, NQJ = (2 * k + 2) ** 3, (2 * k + 1) ** 3
+    ea, eb, ec = NV * (NV + 1) // 2, NV * M, M * (M + 1) // 2
+    per_point = 3 * (60 + 81 * 8 + 3 * NP * 6 + 4 * NFP)           # stress, tangent, g_J, psi per pass
+    per_point += 27 * NP * 6 + ea * 8                                  # (a)
+    per_point += 108 * 6 + 36 * NP * 6 + eb * 4                        # (b)
+    per_point += 144 * 18 + ec * 5                                     # (c)
+    f = NQJ * per_point
+    f += NQR * (18 * NP + 80) + 9 * NP * NQR * 2 + NQJ * 9 * NP * 2    # residual, F at the Jacobian points
+    f += NV ** 3 // 3 + NV * NV * M + ec * NV * 2                      # Cholesky, Z, Z^T Z
+    f += 2 * NQJ * (9 * NP * 4 + 81 * 2 + 700)                         # two tangent applies
+    f += N * (4 * (NP + NFP) * 2 + 6 * NP)                             # volume / face terms of R
+    return f
+
+
+def run_svk(args):
+    """Nonlinear SVK elastodynamics (Sec. 4.4-4.5): free large-amplitude vibration of the clamped
+    plate (n x n x 1 cubes of 6 tets, one element through the 0.01 thickness, traction-free top
+    and bottom, clamped sides), DIRK3 with a Newton solve per stage, each Newton iteration
+    condensing every element with its tangent at the quadrature points. Initial state: the
+    plate solution's velocity 0.4 pi sin(pi x) sin(pi y) e_z, F = I, P = 0."""
+    import torch
+    from paper_1807_00086_gb300 import hdg, inputs
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.N
+    k = args.k
+    dt = 2e-3
+    vert, elem = inputs.plate_tet(n)
+    ne = elem.shape[0]
+
+    def make():
+        sv = hdg.Solver(vert, elem, k, 1.0, np.ones(ne), lam=np.full(ne, 1.5), mu=np.ones(ne), svk=True, rtol=1e-10)
+        zb = sv.hdg_quadrature_points(1)[:, :, 2]
+        sv.hdg_svk_set_traction_faces(np.all(np.abs(zb - 0.01) < 1e-13, axis=1) | np.all(np.abs(zb) < 1e-13, axis=1))
+        xv = sv.hdg_quadrature_points(0)
+        vals = np.zeros(xv.shape[:2] + (21,))
+        vals[:, :, 2] = 0.4 * np.pi * np.sin(np.pi * xv[:, :, 0]) * np.sin(np.pi * xv[:, :, 1])
+        sv.hdg_set_state(sv.hdg_project_volume(vals), 0.0)
+        return sv
+
+    s = make()
+    dofs = ne * s.n
+    stream = s.stream
+    for _ in range(args.warmup):
+        s.hdg_step(dt, "dirk3", 1)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.hdg_get_stats(reset=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    newton, cg = 0, 0
+    a.record(stream)
+    for _ in range(args.steps):
+        info = s.hdg_step(dt, "dirk3", 1)
+        newton += info["sweeps"]
+        cg += info["iterations"]
+    b.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b)
+    launches = s.hdg_get_stats(reset=True)["kernel_launches"]
+    ms_max = max_over_ranks(dist, ms, "cuda")
+    value = world * dofs * args.steps / (ms_max / 1e3)
+    # kernel times: one more step with CUDA events around every condensation and recovery
+    s.hdg_enable_stats(True)
+    s.hdg_get_stats(reset=True)
+    s.hdg_step(dt, "dirk3", 1)
+    st = s.hdg_get_stats(reset=True)
+    s.hdg_enable_stats(False)
+    cms = st["svk_condense_ms"] / max(1, st["svk_condense_launches"])
+    rms = st["svk_recover_ms"] / max(1, st["svk_recover_launches"])
+    fl = svk_condense_flops(k) * ne
+    ach = fl / (cms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25, "traffic": None,
+            "kernel": "svk_condense_kernel<%d> (FP64: residual, tangent at (2k+1)^3 points, condensation)" % k,
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (the FP64 pipe; no FP64 tensor path is used)",
+            "flops_per_elem": svk_condense_flops(k), "launch_ms": cms, "launches": st["svk_condense_launches"],
+            "timing": "CUDA events around every launch during one instrumented step after the timed window",
+            "recover_kernel": {"kernel": "svk_recover_kernel<%d>" % k, "launch_ms": rms,
+                               "launches": st["svk_recover_launches"]}}
+    # end to end through the public API with host buffers: fields and traces in, one step, out
+    u_h = torch.empty(s._fshape, dtype=torch.float64).pin_memory()
+    l_h = torch.empty(s._tshape, dtype=torch.float64).pin_memory()
+    u_d, l_d = s.empty_fields(), s.empty_traces()
+    _, _, t_now = s.hdg_get_state(u=u_d, lam=l_d)
+    u_h.copy_(u_d)
+    l_h.copy_(l_d)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            u_d.copy_(u_h, non_blocking=True)
+            l_d.copy_(l_h, non_blocking=True)
+        s.hdg_set_state(u_d, t_now, lam=l_d)
+        s.hdg_step(dt, "dirk3", 1)
+        _, _, t_now = s.hdg_get_state(u=u_d, lam=l_d)
+        with torch.cuda.stream(stream):
+            u_h.copy_(u_d, non_blocking=True)
+            l_h.copy_(l_d, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * dofs * e2e_steps / max_over_ranks(dist, e2e_s, "cuda")
+    fb, tb = int(np.prod(s._fshape)) * 8, int(np.prod(s._tshape)) * 8
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import elastic_svk as nl
+        vs, es = inputs.plate_tet(2)
+
+        def tb_face(Y):
+            z = Y[:, 2]
+            return bool(np.all(np.abs(z - z[0]) < 1e-14) and (abs(z[0]) < 1e-14 or abs(z[0] - 0.01) < 1e-14))
+        prob = nl.build_problem(vs, es, k, 1.0, 1.5, 1.0, neumann_face=tb_face)
+
+        def v0(x, t):
+            v = np.zeros((x.shape[0], 3))
+            v[:, 2] = 0.4 * np.pi * np.sin(np.pi * x[:, 0]) * np.sin(np.pi * x[:, 1])
+            return v
+        u0 = nl.project(prob, v0, lambda x, t: np.zeros((x.shape[0], 9)), lambda x, t: np.zeros((x.shape[0], 9)), 0.0)
+        t0 = time.perf_counter()
+        nst = 0
+        while nst < 1 or time.perf_counter() - t0 < min(args.cpu_budget, 20.0):
+            u0, _, _ = nl.run_dirk3(prob, u0 + 0.0, dt, 1)
+            nst += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": es.shape[0] * 21 * prob.Np * nst / el, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": "%d DIRK3 steps of the SVK plate on a 2x2x1 = %d-tet plate (k=%d, %d field DOFs); oracle = "
+                         "numpy/scipy FP64, per-element LU of the 21 N_p Newton system + sparse direct trace solve"
+                         % (nst, es.shape[0], k, es.shape[0] * 21 * prob.Np)}
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "svk3d_plate_k%d_%dx%dx1_dirk3" % (k, n, n), "n_elem": ne, "k": k, "dofs": dofs,
+                          "trace_dofs": int(s.sizes.trace_entries), "dt": dt, "scheme": "DIRK3", "precision": "fp64",
+                          "newton_tol": 1e-11, "cg_rtol": 1e-10, "parallelism": "replicas",
+                          "newton_iters_per_stage": newton / (3 * args.steps),
+                          "cg_iters_per_newton": cg / max(1, newton),
+                          "l2": "inputs larger than L2 (S_K %.2f GB)" % (s.sizes.schur_entries * 8 / 1e9)},
+               "roofline": roof, "cpu_baseline": cpu,
+               "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": fb + tb, "d2h_bytes_per_step": fb + tb,
+                       "steps": e2e_steps},
+               "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_apply_only(args):
     """Profiling driver: condense the workload at size N and run `steps` trace applies."""
     import torch
@@ -662,8 +832,9 @@ def main():
                          "3e-6 (FP32 operator, one right-hand side), 1e-4 (FP32, many)")
     ap.add_argument("--N", type=int, default=32)
     ap.add_argument("--k", type=int, default=3)
-    ap.add_argument("--physics", default="acoustic", choices=["acoustic", "elastic"],
-                    help="elastic: the 3D linear elastodynamics workload (24^3 x 6 tets, DIRK3)")
+    ap.add_argument("--physics", default="acoustic", choices=["acoustic", "elastic", "svk"],
+                    help="elastic: the 3D linear elastodynamics workload (24^3 x 6 tets, DIRK3); svk: nonlinear "
+                         "elastodynamics, free vibration of the clamped plate (--N x --N x 1 cubes, k = --k)")
     ap.add_argument("--guess-history", type=int, default=8,
                     help="earlier stage solutions spanning the least-squares initial guess (0: extrapolation)")
     ap.add_argument("--mixed-degree", action="store_true",
@@ -701,7 +872,13 @@ def main():
                                   (args.physics == "elastic" and args.mixed_degree)) else "mixed"
     if args.inner_rtol is None:
         args.inner_rtol = 1e-3 if args.prec == "mixed16" else (1e-4 if args.nrhs > 1 else 3e-6)
-    if args.serve:
+    if args.physics == "svk":
+        if args.N == 32 and "--N" not in sys.argv:
+            args.N = 16
+        if args.k == 3 and "--k" not in sys.argv:
+            args.k = 2
+        run_svk(args)
+    elif args.serve:
         run_serve(args)
     elif args.mode == "apply":
         run_apply_only(args)

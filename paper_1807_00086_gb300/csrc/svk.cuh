@@ -47,8 +47,8 @@ struct SvkDims {
   static constexpr int QC = 8;                        // Jacobian points per chunk
   static constexpr int NT = 256;
   // chunk area: per-point S and F F^T (18), tangent (81), g_J (3 N_p), psi_f (4 N_fp), weight,
-  // and the largest per-pass precompute (27 N_p, 36 N_p or 144 per point)
-  static constexpr int PRE = 36 * NP > 144 ? 36 * NP : 144;
+  // and the largest per-pass precompute (27 N_p, 36 N_p + 108 or 144 per point)
+  static constexpr int PRE = 36 * NP + 108;
   static constexpr int CHJ = QC * (18 + 81 + 3 * NP + 4 * NFP + 1 + PRE);
   static constexpr int CHR = 9 * NQR;                 // P(F) at every residual point
   static constexpr int CHT = 9 * NQJ;                 // T-apply: values at the Jacobian points
@@ -405,19 +405,20 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
     for (int q0 = 0; q0 < NQJ; q0 += QC) {
       const int nq = NQJ - q0 < QC ? NQJ - q0 : QC;
       load_chunk(q0, nq);
+      // c_J[i][i2][f] = sum_L A[iJ][i2 L] n_fL, then u = sum_J g_J c_J
+      double* ccj = cpre + QC * 36 * NP;
+      for (int t = tid; t < nq * 108; t += NT) {
+        const int qq = t / 108, r = t % 108;
+        const int i = r / 36, i2 = (r / 12) % 3, f = (r / 3) % 4, J = r % 3;
+        const double* A = cA + qq * 81 + (i * 3 + J) * 9 + i2 * 3;
+        ccj[t] = A[0] * nrm[f * 3] + A[1] * nrm[f * 3 + 1] + A[2] * nrm[f * 3 + 2];
+      }
+      __syncthreads();
       for (int t = tid; t < nq * 36 * NP; t += NT) {
         const int qq = t / (36 * NP), c36 = (t / NP) % 36, aa = t % NP;
-        const int i = c36 / 12, i2 = (c36 / 4) % 3, f = c36 % 4;
-        const double* A = cA + qq * 81;
-        const double* gg = cg + qq * 3 * NP;
-        double v = 0.0;
-#pragma unroll
-        for (int J = 0; J < 3; ++J) {
-          const double cj = A[(i * 3 + J) * 9 + i2 * 3] * nrm[f * 3] + A[(i * 3 + J) * 9 + i2 * 3 + 1] * nrm[f * 3 + 1] +
-                            A[(i * 3 + J) * 9 + i2 * 3 + 2] * nrm[f * 3 + 2];
-          v += gg[J * NP + aa] * cj;
-        }
-        cpre[t] = v;
+        const double* cj = ccj + qq * 108 + c36 * 3;
+        const double* gg = cg + qq * 3 * NP + aa;
+        cpre[t] = gg[0] * cj[0] + gg[NP] * cj[1] + gg[2 * NP] * cj[2];
       }
       __syncthreads();
 #pragma unroll
