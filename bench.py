@@ -652,8 +652,11 @@ def run_svk(args):
     vert, elem = inputs.plate_tet(n)
     ne = elem.shape[0]
 
-    def make():
-        sv = hdg.Solver(vert, elem, k, 1.0, np.ones(ne), lam=np.full(ne, 1.5), mu=np.ones(ne), svk=True, rtol=1e-10)
+    prec = args.prec if args.prec in ("fp64", "mixed") else "mixed"
+
+    def make(prec=prec):
+        sv = hdg.Solver(vert, elem, k, 1.0, np.ones(ne), lam=np.full(ne, 1.5), mu=np.ones(ne), svk=True, rtol=1e-10,
+                        prec=prec)
         zb = sv.hdg_quadrature_points(1)[:, :, 2]
         sv.hdg_svk_set_traction_faces(np.all(np.abs(zb - 0.01) < 1e-13, axis=1) | np.all(np.abs(zb) < 1e-13, axis=1))
         xv = sv.hdg_quadrature_points(0)
@@ -701,9 +704,14 @@ def run_svk(args):
     rms = st["svk_recover_ms"] / max(1, st["svk_recover_launches"])
     fl = svk_condense_flops(k) * ne
     ach = fl / (cms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25, "traffic": None,
-            "kernel": "svk_condense_kernel<%d> (FP64: residual, tangent at (2k+1)^3 points, condensation)" % k,
-            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (the FP64 pipe; no FP64 tensor path is used)",
+    peak, psrc = ((1.25, "nominal GB300 FP64 1.25 TFLOP/s (the FP64 pipe; no FP64 tensor path is used)")
+                  if prec == "fp64" else
+                  (80.5, "GB300 FP32 CUDA cores: 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s (the "
+                         "Jacobian arithmetic; the FP64 residual is a few percent of the flops)"))
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "kernel": "svk_condense_kernel<%d, %s> (FP64 residual; tangent at (2k+1)^3 points and condensation in %s)"
+                      % (k, "double" if prec == "fp64" else "float", "FP64" if prec == "fp64" else "FP32"),
+            "peak_source": psrc,
             "flops_per_elem": svk_condense_flops(k), "launch_ms": cms, "launches": st["svk_condense_launches"],
             "timing": "CUDA events around every launch during one instrumented step after the timed window",
             "recover_kernel": {"kernel": "svk_recover_kernel<%d>" % k, "launch_ms": rms,
@@ -732,6 +740,33 @@ def run_svk(args):
     e2e_s = time.perf_counter() - t0
     e2e_value = world * dofs * e2e_steps / max_over_ranks(dist, e2e_s, "cuda")
     fb, tb = int(np.prod(s._fshape)) * 8, int(np.prod(s._tshape)) * 8
+    trace_dofs, schur_entries = s.sizes.trace_entries, s.sizes.schur_entries
+    # the FP64 form on the same trajectory: warm-up + timed steps from the same initial state,
+    # its rate and the largest field difference after them
+    fp64 = None
+    if prec != "fp64" and not args.no_fp64_compare:
+        u_m, _, _ = s.hdg_get_state()
+        s.close()
+        torch.cuda.empty_cache()
+        ref = make("fp64")
+        mix = make(prec)
+        nst = args.warmup + args.steps
+        mix.hdg_step(dt, "dirk3", nst)
+        ref.hdg_step(dt, "dirk3", args.warmup)
+        torch.cuda.synchronize()
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(ref.stream)
+        ref.hdg_step(dt, "dirk3", args.steps)
+        b2.record(ref.stream)
+        torch.cuda.synchronize()
+        ms64 = a2.elapsed_time(b2)
+        u64, _, _ = ref.hdg_get_state()
+        um, _, _ = mix.hdg_get_state()
+        fp64 = {"value": dofs * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
+                "speedup_mixed_over_fp64": ms64 / ms,
+                "max_rel_diff_fields_after_%d_steps" % nst: float((um - u64).abs().max() / u64.abs().max())}
+        ref.close()
+        mix.close()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import elastic_svk as nl
@@ -761,14 +796,16 @@ def run_svk(args):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
+               "data": "synthetic",
                "config": {"workload": "svk3d_plate_k%d_%dx%dx1_dirk3" % (k, n, n), "n_elem": ne, "k": k, "dofs": dofs,
-                          "trace_dofs": int(s.sizes.trace_entries), "dt": dt, "scheme": "DIRK3", "precision": "fp64",
+                          "trace_dofs": int(trace_dofs), "dt": dt, "scheme": "DIRK3",
+                          "precision": prec + (" (FP32 Jacobian, FP64 residual)" if prec != "fp64" else ""),
                           "newton_tol": 1e-11, "cg_rtol": 1e-10, "parallelism": "replicas",
                           "newton_iters_per_stage": newton / (3 * args.steps),
                           "cg_iters_per_newton": cg / max(1, newton),
-                          "l2": "inputs larger than L2 (S_K %.2f GB)" % (s.sizes.schur_entries * 8 / 1e9)},
-               "roofline": roof, "cpu_baseline": cpu,
+                          "l2": "inputs larger than L2 (S_K %.2f GB)" % (schur_entries * 8 / 1e9)},
+               "roofline": roof, "cpu_baseline": cpu, "fp64_gpu": fp64,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": fb + tb, "d2h_bytes_per_step": fb + tb,
                        "steps": e2e_steps},
                "gpu_launches": launches, "clocks": clk}

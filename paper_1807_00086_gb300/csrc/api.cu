@@ -1675,8 +1675,14 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   const bool svk = mat->phys == HDG_SVK;
   if (mat->phys != HDG_ACOUSTIC && mat->phys != HDG_ELASTIC && !svk) return fail(c, HDG_EINVAL, "unknown physics");
   if (svk && (mesh->dim != 3 || k > 3 || mesh->elem_k || c->R != 1 || c->tspace != HDG_TRACE_HDG ||
-              c->opt.solver != HDG_SOLVER_CG || c->opt.prec != HDG_FP64))
-    return fail(c, HDG_EINVAL, "SVK: 3D, uniform k in 1..3, nrhs = 1, HDG traces, CG and FP64 only");
+              c->opt.solver != HDG_SOLVER_CG || c->opt.prec == HDG_MIXED16))
+    return fail(c, HDG_EINVAL, "SVK: 3D, uniform k in 1..3, nrhs = 1, HDG traces, CG, FP64 or MIXED only");
+  if (svk) {
+    // HDG_MIXED: FP32 Jacobian (tangent, condensation, factor) around the FP64 residual; the
+    // trace system of each Newton iteration is solved in FP64
+    c->svk_mixed = c->opt.prec == HDG_MIXED;
+    c->opt.prec = HDG_FP64;
+  }
   if (svk && (!(c->opt.newton_tol > 0.0) || c->opt.newton_maxit < 1))
     return fail(c, HDG_EINVAL, "SVK: newton_tol must be > 0 and newton_maxit >= 1");
   // SVK contexts share the elastic trace layout (3 N_f velocity traces per face)

@@ -155,6 +155,7 @@ struct hdg_ctx {
   double *d_gmV = nullptr, *d_gmpart = nullptr, *d_gmh = nullptr, *d_gmy = nullptr;
   VarDeg* vd = nullptr;
   Svk* svk = nullptr;   // set for HDG_SVK contexts (elastic trace layout, 21 N_p fields)
+  bool svk_mixed = false; // HDG_SVK with HDG_MIXED: FP32 Jacobian, FP64 residual
 };
 
 namespace {

@@ -13,7 +13,11 @@ using namespace hdg;
 
 struct Svk {
   double* d_tab = nullptr;
+  float* d_tabf = nullptr;
   SvkTabs tabs{};
+  SvkJT<double> tjd{};     // Jacobian-rule tables, FP64 and FP32 copies
+  SvkJT<float> tjf{};
+  bool fp32_jacobian = false;
   int nqr = 0, nqj = 0;
   double *d_L = nullptr, *d_zR = nullptr, *d_dl = nullptr, *d_b = nullptr;
   unsigned long long* d_umax = nullptr;   // [0] max |du|, [1] max |u|, [2] max |dlam|
@@ -61,39 +65,60 @@ hdg_status svk_tables(hdg_ctx* c, Svk* v) {
   }
   std::vector<double> tab;
   size_t off[11];
-  const std::vector<double>* parts[11] = {&T.Dr, &T.Ff, &T.Ef, &phiR, &wr, &phiJ, &wj, &GJ, &PSJ, &T.qf_mu, &T.qf_w};
+  const std::vector<double>* parts[11] = {&T.Dr, &T.Ff, &T.Ef, &phiR, &wr, &T.qf_mu, &T.qf_w, &phiJ, &wj, &GJ, &PSJ};
   for (int i = 0; i < 11; ++i) { off[i] = tab.size(); tab.insert(tab.end(), parts[i]->begin(), parts[i]->end()); }
+  std::vector<float> tabf(tab.begin() + off[7], tab.end());
   hdg_status s;
   if ((s = dalloc(c, &v->d_tab, tab.size()))) return s;
+  if ((s = dalloc(c, &v->d_tabf, tabf.size()))) return s;
   CUDA_TRY(c, cudaMemcpyAsync(v->d_tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(v->d_tabf, tabf.data(), tabf.size() * 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   const double* b = v->d_tab;
-  v->tabs = SvkTabs{b + off[0], b + off[1], b + off[2], b + off[3], b + off[4], b + off[5],
-                    b + off[6], b + off[7], b + off[8], b + off[9], b + off[10], T.nqf};
+  const float* bf = v->d_tabf - off[7];   // same offsets as the FP64 buffer
+  v->tabs = SvkTabs{b + off[0], b + off[1], b + off[2], b + off[3], b + off[4], b + off[5], b + off[6], T.nqf};
+  v->tjd = SvkJT<double>{b + off[7], b + off[8], b + off[9], b + off[10]};
+  v->tjf = SvkJT<float>{bf + off[7], bf + off[8], bf + off[9], bf + off[10]};
   v->nqr = D::NQR;
   v->nqj = D::NQJ;
-  CUDA_TRY(c, cudaFuncSetAttribute(svk_condense_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(double) * D::SM_COND)));
-  CUDA_TRY(c, cudaFuncSetAttribute(svk_recover_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(double) * D::SM_REC)));
+  CUDA_TRY(c, cudaFuncSetAttribute(svk_condense_kernel<K, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)D::template cond_bytes<double>()));
+  CUDA_TRY(c, cudaFuncSetAttribute(svk_recover_kernel<K, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)D::template rec_bytes<double>()));
+  CUDA_TRY(c, cudaFuncSetAttribute(svk_condense_kernel<K, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)D::template cond_bytes<float>()));
+  CUDA_TRY(c, cudaFuncSetAttribute(svk_recover_kernel<K, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)D::template rec_bytes<float>()));
   return HDG_OK;
 }
 
 template <int K>
 void svk_launch_condense(hdg_ctx* c, const SvkArgs& a) {
+  using D = SvkDims<K>;
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 4);
-  svk_condense_kernel<K><<<(unsigned)c->sk.ne, SvkDims<K>::NT, sizeof(double) * SvkDims<K>::SM_COND, c->stream>>>(
-      a, c->svk->tabs);
+  const Svk* v = c->svk;
+  if (v->fp32_jacobian)
+    svk_condense_kernel<K, float><<<(unsigned)c->sk.ne, D::NT, D::template cond_bytes<float>(), c->stream>>>(
+        a, v->tabs, v->tjf);
+  else
+    svk_condense_kernel<K, double><<<(unsigned)c->sk.ne, D::NT, D::template cond_bytes<double>(), c->stream>>>(
+        a, v->tabs, v->tjd);
   apply_end(c, stop);
 }
 
 template <int K>
 void svk_launch_recover(hdg_ctx* c, const SvkRecArgs& a) {
+  using D = SvkDims<K>;
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 5);
-  svk_recover_kernel<K><<<(unsigned)c->sk.ne, SvkDims<K>::NT, sizeof(double) * SvkDims<K>::SM_REC, c->stream>>>(
-      a, c->svk->tabs);
+  const Svk* v = c->svk;
+  if (v->fp32_jacobian)
+    svk_recover_kernel<K, float><<<(unsigned)c->sk.ne, D::NT, D::template rec_bytes<float>(), c->stream>>>(
+        a, v->tabs, v->tjf);
+  else
+    svk_recover_kernel<K, double><<<(unsigned)c->sk.ne, D::NT, D::template rec_bytes<double>(), c->stream>>>(
+        a, v->tabs, v->tjd);
   apply_end(c, stop);
 }
 
@@ -203,6 +228,7 @@ hdg_status svk_setup(hdg_ctx* c) {
   Svk* v = new (std::nothrow) Svk();
   if (!v) return fail(c, HDG_ENOMEM, "out of host memory");
   c->svk = v;
+  v->fp32_jacobian = c->svk_mixed;
   hdg_status s;
   switch (c->k) {
     case 1: s = svk_tables<1>(c, v); break;

@@ -32,6 +32,10 @@
 
 namespace hdg {
 
+// Precision: the residual R, Rh (and so the solution Newton converges to) is FP64. The
+// Jacobian pipeline (tangent, the three accumulations, the Cholesky of S_v, S_K, and the
+// tangent applies of A^{-1} R and of the recovery) runs in TJ: double, or float for the
+// mixed mode, where Newton converges to the same stage solution with an approximate Jacobian.
 template <int K>
 struct SvkDims {
   static constexpr int NP = (K + 1) * (K + 2) * (K + 3) / 6;
@@ -50,13 +54,25 @@ struct SvkDims {
   // and the largest per-pass precompute (27 N_p, 36 N_p + 108 or 144 per point)
   static constexpr int PRE = 36 * NP + 108;
   static constexpr int CHJ = QC * (18 + 81 + 3 * NP + 4 * NFP + 1 + PRE);
-  static constexpr int CHR = 9 * NQR;                 // P(F) at every residual point
+  static constexpr int CHR = 9 * NQR;                 // P(F) at every residual point (double)
   static constexpr int CHT = 9 * NQJ;                 // T-apply: values at the Jacobian points
-  static constexpr int CH = CHJ > CHR ? (CHJ > CHT ? CHJ : CHT) : (CHR > CHT ? CHR : CHT);
-  // shared memory of the condensation kernel, in doubles
-  static constexpr int SM_COND = 32 + N + M + 3 * NP * NP + N + M + NV * NV + NV * M + 9 * NQJ + 4 * 9 * NP + 3 * NV + CH;
-  // and of the recovery kernel
-  static constexpr int SM_REC = 32 + N + M + 3 * NP * NP + NV * NV + 9 * NQJ + 4 * 9 * NP + 3 * NV + CHT;
+  // condensation kernel: double arena | scratch (double CHR or TJ chunk / T-apply) | TJ arena
+  static constexpr int SMD = 32 + N + M + 3 * NP * NP + N + M + 4 * 9 * NP + 3 * NV;
+  template <typename TJ>
+  __host__ __device__ static constexpr size_t scr_bytes() {
+    const size_t a = sizeof(double) * CHR, b = sizeof(TJ) * (CHJ > CHT ? CHJ : CHT);
+    return ((a > b ? a : b) + 15) / 16 * 16;
+  }
+  template <typename TJ>
+  __host__ __device__ static constexpr size_t cond_bytes() {
+    return sizeof(double) * SMD + scr_bytes<TJ>() + sizeof(TJ) * (NV * NV + NV * M + 9 * NQJ);
+  }
+  // recovery kernel: double arena | TJ arena (L, F at the points, T-apply scratch)
+  static constexpr int SMD_REC = 32 + N + M + 3 * NP * NP + 4 * 9 * NP + 3 * NV;
+  template <typename TJ>
+  __host__ __device__ static constexpr size_t rec_bytes() {
+    return sizeof(double) * SMD_REC + sizeof(TJ) * (NV * NV + 9 * NQJ + CHT);
+  }
 };
 
 // reference tables of one degree (device pointers into one buffer)
@@ -66,13 +82,18 @@ struct SvkTabs {
   const double* Ef;    // [4][Np][Np]   Ff Ff^T
   const double* phiR;  // [NQR][Np]     residual rule
   const double* wR;    // [NQR]
-  const double* phiJ;  // [NQJ][Np]     Jacobian rule
-  const double* wJ;    // [NQJ]
-  const double* GJ;    // [NQJ][3][Np]  sum_b Dr[r][a][b] phi_b(x_q)
-  const double* PSJ;   // [NQJ][4][Nfp] sum_a Ff[f][a][m] phi_a(x_q)
   const double* muF;   // [NQF][Nfp]    face rule: face basis values
   const double* wF;    // [NQF]
   int nqf;
+};
+
+// Jacobian-rule tables in the Jacobian precision
+template <typename T>
+struct SvkJT {
+  const T* phiJ;   // [NQJ][Np]
+  const T* wJ;     // [NQJ]
+  const T* GJ;     // [NQJ][3][Np]  sum_b Dr[r][a][b] phi_b(x_q)
+  const T* PSJ;    // [NQJ][4][Nfp] sum_a Ff[f][a][m] phi_a(x_q)
 };
 
 struct SvkArgs {
@@ -95,20 +116,24 @@ struct SvkArgs {
   int* err;                  // set when S_v is not positive definite
 };
 
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+
 // ------------------------------------------------------------------ pointwise material law
 // P = F S(F) and the tangent A[iJ][kL] = dP_iJ / dF_kL
 //   = delta_ik S_LJ + lam F_iJ F_kL + mu F_iL F_kJ + mu (F F^T)_ik delta_JL.
-__device__ __forceinline__ void svk_stress(const double* F, double lam, double mu, double* Sout, double* FFt) {
-  double C[9];
+template <typename T>
+__device__ __forceinline__ void svk_stress(const T* F, T lam, T mu, T* Sout, T* FFt) {
+  T C[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) C[a * 3 + b] = F[a] * F[b] + F[3 + a] * F[3 + b] + F[6 + a] * F[6 + b];
-  const double trE = 0.5 * (C[0] + C[4] + C[8] - 3.0);
+  const T trE = T(0.5) * (C[0] + C[4] + C[8] - T(3));
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) Sout[a * 3 + b] = mu * (C[a * 3 + b] - (a == b ? 1.0 : 0.0)) + (a == b ? lam * trE : 0.0);
+    for (int b = 0; b < 3; ++b) Sout[a * 3 + b] = mu * (C[a * 3 + b] - (a == b ? T(1) : T(0))) + (a == b ? lam * trE : T(0));
   if (FFt) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -117,71 +142,75 @@ __device__ __forceinline__ void svk_stress(const double* F, double lam, double m
   }
 }
 
-__device__ __forceinline__ double svk_tangent_entry(const double* F, const double* S, const double* FFt, double lam,
-                                                    double mu, int iJ, int kL) {
+template <typename T>
+__device__ __forceinline__ T svk_tangent_entry(const T* F, const T* S, const T* FFt, T lam, T mu, int iJ, int kL) {
   const int i = iJ / 3, J = iJ % 3, k = kL / 3, L = kL % 3;
-  double v = lam * F[iJ] * F[kL] + mu * F[i * 3 + L] * F[k * 3 + J];
+  T v = lam * F[iJ] * F[kL] + mu * F[i * 3 + L] * F[k * 3 + J];
   if (i == k) v += S[L * 3 + J];
   if (J == L) v += mu * FFt[i * 3 + k];
   return v;
 }
 
-// F = I + H at point q of a rule with basis values phi [Np]
-template <int NP>
-__device__ __forceinline__ void svk_deformation(const double* __restrict__ phi, const double* H, double* F) {
+// F = I + H at a point with basis values phi [Np] (H: [9][Np] FP64 coefficients)
+template <int NP, typename PT>
+__device__ __forceinline__ void svk_deformation(const PT* __restrict__ phi, const double* H, double* F) {
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
     double v = (c == 0 || c == 4 || c == 8) ? 1.0 : 0.0;
-    for (int a = 0; a < NP; ++a) v += H[c * NP + a] * phi[a];
+    for (int a = 0; a < NP; ++a) v += H[c * NP + a] * (double)phi[a];
     F[c] = v;
   }
 }
 
-// y = T x (x, y: [9][Np] in shared memory) on the Jacobian rule, FJ [NQJ][9] the deformation
-// gradient at its points; scratch CHT doubles. Ends with a block barrier.
-template <int K>
-__device__ void svk_T_apply(const SvkTabs& tb, const double* FJ, double lam, double mu, double dJ, const double* x,
-                            double* y, double* scr) {
+// y = T x (x, y: [9][Np] FP64 in shared memory) on the Jacobian rule in precision TJ; FJ
+// [NQJ][9] the deformation gradient at its points; scratch CHT entries. Ends with a barrier.
+template <int K, typename TJ>
+__device__ void svk_T_apply(const SvkJT<TJ>& tj, const TJ* FJ, TJ lam, TJ mu, TJ dJ, const double* x, double* y,
+                            TJ* scr) {
   using D = SvkDims<K>;
   constexpr int NP = D::NP, NQJ = D::NQJ, NT = D::NT;
   const int tid = threadIdx.x;
-  // values of x at the points, then the tangent times them, weighted
   for (int q = tid; q < NQJ; q += NT) {
-    const double* ph = tb.phiJ + (int64_t)q * NP;
-    double xv[9];
+    const TJ* ph = tj.phiJ + (int64_t)q * NP;
+    TJ xv[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      double v = 0.0;
-      for (int a = 0; a < NP; ++a) v += x[c * NP + a] * ph[a];
+      TJ v = TJ(0);
+      for (int a = 0; a < NP; ++a) v += (TJ)x[c * NP + a] * ph[a];
       xv[c] = v;
     }
-    const double* F = FJ + q * 9;
-    double S[9], FFt[9];
-    svk_stress(F, lam, mu, S, FFt);
-    const double w = tb.wJ[q] * dJ;
+    const TJ* F = FJ + q * 9;
+    TJ S[9], FFt[9];
+    svk_stress<TJ>(F, lam, mu, S, FFt);
+    const TJ w = tj.wJ[q] * dJ;
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
-      double v = 0.0;
+      TJ v = TJ(0);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) v += svk_tangent_entry(F, S, FFt, lam, mu, r, c) * xv[c];
+      for (int c = 0; c < 9; ++c) v += svk_tangent_entry<TJ>(F, S, FFt, lam, mu, r, c) * xv[c];
       scr[q * 9 + r] = w * v;
     }
   }
   __syncthreads();
   for (int idx = tid; idx < 9 * NP; idx += NT) {
     const int c = idx / NP, a = idx % NP;
-    double v = 0.0;
-    for (int q = 0; q < NQJ; ++q) v += tb.phiJ[(int64_t)q * NP + a] * scr[q * 9 + c];
-    y[idx] = v;
+    TJ v = TJ(0);
+    for (int q = 0; q < NQJ; ++q) v += tj.phiJ[(int64_t)q * NP + a] * scr[q * 9 + c];
+    y[idx] = (double)v;
   }
   __syncthreads();
 }
 
-// deformation gradient at every Jacobian-rule point from H (shared [9][Np])
-template <int K>
-__device__ void svk_F_at_jac(const SvkTabs& tb, const double* H, double* FJ) {
+// deformation gradient at every Jacobian-rule point from H (shared [9][Np], FP64)
+template <int K, typename TJ>
+__device__ void svk_F_at_jac(const SvkJT<TJ>& tj, const double* H, TJ* FJ) {
   using D = SvkDims<K>;
-  for (int q = threadIdx.x; q < D::NQJ; q += D::NT) svk_deformation<D::NP>(tb.phiJ + (int64_t)q * D::NP, H, FJ + q * 9);
+  for (int q = threadIdx.x; q < D::NQJ; q += D::NT) {
+    double F[9];
+    svk_deformation<D::NP, TJ>(tj.phiJ + (int64_t)q * D::NP, H, F);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) FJ[q * 9 + c] = (TJ)F[c];
+  }
   __syncthreads();
 }
 
@@ -192,31 +221,37 @@ __device__ __forceinline__ void tri_decode(int t, int n, int& r, int& c) {
   c = r + t;
 }
 
+// CTAs per SM the register budget is cut for: two for the FP32 Jacobian up to k = 2
+template <int K, typename TJ>
+struct SvkMinBlocks { static constexpr int value = sizeof(TJ) == 4 && K <= 2 ? 2 : 1; };
+
 // One Newton iteration's condensation of one element: residual, S_K, the factor of S_v,
 // A^{-1} R and the element part g_K = -Rh + C A^{-1} R of the condensed right-hand side.
-template <int K>
-__global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs tb) {
+template <int K, typename TJ>
+__global__ void __launch_bounds__(256, SvkMinBlocks<K, TJ>::value) svk_condense_kernel(SvkArgs a, SvkTabs tb, SvkJT<TJ> tj) {
   using D = SvkDims<K>;
   constexpr int NP = D::NP, NFP = D::NFP, NF = D::NF, NV = D::NV, N = D::N, M = D::M, NT = D::NT;
   constexpr int NQR = D::NQR, NQJ = D::NQJ, QC = D::QC;
-  extern __shared__ double sm[];
-  double* g = sm;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* g = reinterpret_cast<double*>(smraw);
   double* ue = g + 32;
   double* lk = ue + N;
   double* Dx = lk + M;       // [3][Np][Np]
   double* R = Dx + 3 * NP * NP;
   double* Rh = R + N;
-  double* Sv = Rh + M;       // [NV][NV] -> L
-  double* W = Sv + NV * NV;  // [NV][M] -> Z = L^{-1} W
-  double* FJ = W + NV * M;   // [NQJ][9]
-  double* y = FJ + 9 * NQJ;  // [9][Np]
+  double* y = Rh + M;        // [9][Np]
   double* zH = y + 9 * NP;
   double* t1 = zH + 9 * NP;  // [9][Np] T-apply results
   double* t2 = t1 + 9 * NP;  // [9][Np]
   double* rv = t2 + 9 * NP;  // [NV]
   double* w1 = rv + NV;
   double* zv = w1 + NV;
-  double* CH = zv + NV;
+  unsigned char* scr = smraw + sizeof(double) * D::SMD;
+  double* CHR = reinterpret_cast<double*>(scr);   // residual phase
+  TJ* CH = reinterpret_cast<TJ*>(scr);             // Jacobian phase
+  TJ* Sv = reinterpret_cast<TJ*>(scr + D::template scr_bytes<TJ>());   // [NV][NV] -> L
+  TJ* W = Sv + NV * NV;      // [NV][M] -> Z = L^{-1} W
+  TJ* FJ = W + NV * M;       // [NQJ][9]
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x;
   if (tid < 32) g[tid] = a.geo[e * 32 + tid];
@@ -232,6 +267,7 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   const double s = 2.0 * sqrt(rho * mu);
   const double alpha = a.alpha;
   const double iad2 = 1.0 / (alpha * dJ * dJ);
+  const TJ lamj = (TJ)lam, muj = (TJ)mu, dJj = (TJ)dJ;
   const double* Ji = g + 1;          // Jinv[r][j]
   const double* JF = g + 10;         // face Jacobians
   const double* nrm = g + 14;        // outward normals [4][3]
@@ -244,16 +280,16 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   }
   const double* Hc = ue + 3 * NP;
   const double* Pc = ue + 12 * NP;
-  // ---- residual: P(F) at the residual points, then the volume and face terms
+  // ---- residual (FP64): P(F) at the residual points, then the volume and face terms
   for (int q = tid; q < NQR; q += NT) {
     double F[9], S[9];
-    svk_deformation<NP>(tb.phiR + (int64_t)q * NP, Hc, F);
-    svk_stress(F, lam, mu, S, nullptr);
+    svk_deformation<NP, double>(tb.phiR + (int64_t)q * NP, Hc, F);
+    svk_stress<double>(F, lam, mu, S, nullptr);
     const double w = tb.wR[q];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int J = 0; J < 3; ++J) CH[q * 9 + i * 3 + J] = w * (F[i * 3] * S[J] + F[i * 3 + 1] * S[3 + J] + F[i * 3 + 2] * S[6 + J]);
+      for (int J = 0; J < 3; ++J) CHR[q * 9 + i * 3 + J] = w * (F[i * 3] * S[J] + F[i * 3 + 1] * S[3 + J] + F[i * 3 + 2] * S[6 + J]);
   }
   __syncthreads();
   const double* hv = a.h + e * N;
@@ -292,7 +328,7 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
     } else {
       const int c = idx / NP - 12, aa = idx % NP;
       double sq = 0.0;
-      for (int q = 0; q < NQR; ++q) sq += CH[q * 9 + c] * tb.phiR[(int64_t)q * NP + aa];
+      for (int q = 0; q < NQR; ++q) sq += CHR[q * 9 + c] * tb.phiR[(int64_t)q * NP + aa];
       v = dJ * (ue[idx] - sq);
     }
     R[idx] = v;
@@ -309,34 +345,39 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
     }
     Rh[idx] = v;
   }
-  svk_F_at_jac<K>(tb, Hc, FJ);   // barrier inside
+  __syncthreads();   // the residual scratch is reused below
+  svk_F_at_jac<K, TJ>(tj, Hc, FJ);   // barrier inside
   // chunk layout
-  double* cS = CH;                         // [QC][9]  S
-  double* cFF = cS + QC * 9;               // [QC][9]  F F^T
-  double* cA = cFF + QC * 9;               // [QC][81] tangent
-  double* cg = cA + QC * 81;               // [QC][3][Np] g_J
-  double* cps = cg + QC * 3 * NP;          // [QC][4][Nfp] psi_f
-  double* cw = cps + QC * 4 * NFP;         // [QC] physical weights
-  double* cpre = cw + QC;                  // per-pass precompute
+  TJ* cS = CH;                         // [QC][9]  S
+  TJ* cFF = cS + QC * 9;               // [QC][9]  F F^T
+  TJ* cA = cFF + QC * 9;               // [QC][81] tangent
+  TJ* cg = cA + QC * 81;               // [QC][3][Np] g_J
+  TJ* cps = cg + QC * 3 * NP;          // [QC][4][Nfp] psi_f
+  TJ* cw = cps + QC * 4 * NFP;         // [QC] physical weights
+  TJ* cpre = cw + QC;                  // per-pass precompute
+  __shared__ TJ Jij[9], nj[12];   // J^{-1} and the normals in the Jacobian precision
+  if (tid < 9) Jij[tid] = (TJ)Ji[tid];
+  else if (tid < 21) nj[tid - 9] = (TJ)nrm[tid - 9];
+  __syncthreads();
   // per chunk: S, F F^T, tangent, g_J, psi_f, weights of points q0 .. q0 + nq
   auto load_chunk = [&](int q0, int nq) {
     for (int t = tid; t < nq; t += NT) {
-      svk_stress(FJ + (q0 + t) * 9, lam, mu, cS + t * 9, cFF + t * 9);
-      cw[t] = tb.wJ[q0 + t] * dJ;
+      svk_stress<TJ>(FJ + (q0 + t) * 9, lamj, muj, cS + t * 9, cFF + t * 9);
+      cw[t] = tj.wJ[q0 + t] * dJj;
     }
     __syncthreads();
     for (int t = tid; t < nq * 81; t += NT) {
       const int qq = t / 81, r = t % 81;
-      cA[t] = svk_tangent_entry(FJ + (q0 + qq) * 9, cS + qq * 9, cFF + qq * 9, lam, mu, r / 9, r % 9);
+      cA[t] = svk_tangent_entry<TJ>(FJ + (q0 + qq) * 9, cS + qq * 9, cFF + qq * 9, lamj, muj, r / 9, r % 9);
     }
     for (int t = tid; t < nq * 3 * NP; t += NT) {
       const int qq = t / (3 * NP), J = (t / NP) % 3, aa = t % NP;
-      const double* G = tb.GJ + (int64_t)(q0 + qq) * 3 * NP;
-      cg[t] = dJ * (Ji[J] * G[aa] + Ji[3 + J] * G[NP + aa] + Ji[6 + J] * G[2 * NP + aa]);
+      const TJ* G = tj.GJ + (int64_t)(q0 + qq) * 3 * NP;
+      cg[t] = dJj * (Jij[J] * G[aa] + Jij[3 + J] * G[NP + aa] + Jij[6 + J] * G[2 * NP + aa]);
     }
     for (int t = tid; t < nq * 4 * NFP; t += NT) {
       const int qq = t / (4 * NFP), f = (t / NFP) % 4;
-      cps[t] = JF[f] * tb.PSJ[(int64_t)(q0 + qq) * 4 * NFP + t % (4 * NFP)];
+      cps[t] = (TJ)JF[f] * tj.PSJ[(int64_t)(q0 + qq) * 4 * NFP + t % (4 * NFP)];
     }
     __syncthreads();
   };
@@ -344,13 +385,15 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   //      t[i][k][L][a] = sum_J g_J(q)_a A[iJ][kL]
   {
     constexpr int NE = NV * (NV + 1) / 2, NS = (NE + NT - 1) / NT;
-    double acc[NS];
-    int rr[NS], cc[NS];
+    TJ acc[NS];
+    int rc[NS];
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
-      acc[u] = 0.0;
+      acc[u] = TJ(0);
       const int t = tid + u * NT;
-      if (t < NE) tri_decode(t, NV, rr[u], cc[u]); else { rr[u] = 0; cc[u] = 0; }
+      int r = 0, c = 0;
+      if (t < NE) tri_decode(t, NV, r, c);
+      rc[u] = (r << 16) | c;
     }
     for (int q0 = 0; q0 < NQJ; q0 += QC) {
       const int nq = NQJ - q0 < QC ? NQJ - q0 : QC;
@@ -358,8 +401,8 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
       for (int t = tid; t < nq * 27 * NP; t += NT) {
         const int qq = t / (27 * NP), ikL = (t / NP) % 27, aa = t % NP;
         const int i = ikL / 9, k = (ikL / 3) % 3, L = ikL % 3;
-        const double* A = cA + qq * 81;
-        const double* gg = cg + qq * 3 * NP;
+        const TJ* A = cA + qq * 81;
+        const TJ* gg = cg + qq * 3 * NP;
         cpre[t] = gg[aa] * A[(i * 3) * 9 + k * 3 + L] + gg[NP + aa] * A[(i * 3 + 1) * 9 + k * 3 + L] +
                   gg[2 * NP + aa] * A[(i * 3 + 2) * 9 + k * 3 + L];
       }
@@ -367,11 +410,12 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
 #pragma unroll
       for (int u = 0; u < NS; ++u) {
         if (tid + u * NT < NE) {
-          const int i = rr[u] / NP, aa = rr[u] % NP, k = cc[u] / NP, b = cc[u] % NP;
-          double v = acc[u];
+          const int r = rc[u] >> 16, c = rc[u] & 0xffff;
+          const int i = r / NP, aa = r % NP, k = c / NP, b = c % NP;
+          TJ v = acc[u];
           for (int qq = 0; qq < nq; ++qq) {
-            const double* tt = cpre + ((qq * 27) + i * 9 + k * 3) * NP + aa;
-            const double* gg = cg + qq * 3 * NP + b;
+            const TJ* tt = cpre + ((qq * 27) + i * 9 + k * 3) * NP + aa;
+            const TJ* gg = cg + qq * 3 * NP + b;
             v += cw[qq] * (tt[0] * gg[0] + tt[NP] * gg[NP] + tt[2 * NP] * gg[2 * NP]);
           }
           acc[u] = v;
@@ -382,16 +426,16 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
       if (tid + u * NT < NE) {
-        const int r = rr[u], c = cc[u];
+        const int r = rc[u] >> 16, c = rc[u] & 0xffff;
         const int i = r / NP, aa = r % NP, k = c / NP, b = c % NP;
-        double v = iad2 * acc[u];
+        double v = iad2 * (double)acc[u];
         if (i == k) {
           double ev = 0.0;
           for (int f = 0; f < 4; ++f) ev += JF[f] * tb.Ef[(f * NP + aa) * NP + b];
           v += s * ev + (aa == b ? alpha * rho * dJ : 0.0);
         }
-        Sv[r * NV + c] = v;
-        Sv[c * NV + r] = v;
+        Sv[r * NV + c] = (TJ)v;
+        Sv[c * NV + r] = (TJ)v;
       }
     }
   }
@@ -399,25 +443,25 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   //      u[i][i2][f][a] = sum_J g_J(q)_a sum_L A[iJ][i2 L] n_fL;   W = Bv + Dx T BH / (alpha d^2)
   {
     constexpr int NE = NV * M, NS = (NE + NT - 1) / NT;
-    double acc[NS];
+    TJ acc[NS];
 #pragma unroll
-    for (int u = 0; u < NS; ++u) acc[u] = 0.0;
+    for (int u = 0; u < NS; ++u) acc[u] = TJ(0);
     for (int q0 = 0; q0 < NQJ; q0 += QC) {
       const int nq = NQJ - q0 < QC ? NQJ - q0 : QC;
       load_chunk(q0, nq);
       // c_J[i][i2][f] = sum_L A[iJ][i2 L] n_fL, then u = sum_J g_J c_J
-      double* ccj = cpre + QC * 36 * NP;
+      TJ* ccj = cpre + QC * 36 * NP;
       for (int t = tid; t < nq * 108; t += NT) {
         const int qq = t / 108, r = t % 108;
         const int i = r / 36, i2 = (r / 12) % 3, f = (r / 3) % 4, J = r % 3;
-        const double* A = cA + qq * 81 + (i * 3 + J) * 9 + i2 * 3;
-        ccj[t] = A[0] * nrm[f * 3] + A[1] * nrm[f * 3 + 1] + A[2] * nrm[f * 3 + 2];
+        const TJ* A = cA + qq * 81 + (i * 3 + J) * 9 + i2 * 3;
+        ccj[t] = A[0] * nj[f * 3] + A[1] * nj[f * 3 + 1] + A[2] * nj[f * 3 + 2];
       }
       __syncthreads();
       for (int t = tid; t < nq * 36 * NP; t += NT) {
         const int qq = t / (36 * NP), c36 = (t / NP) % 36, aa = t % NP;
-        const double* cj = ccj + qq * 108 + c36 * 3;
-        const double* gg = cg + qq * 3 * NP + aa;
+        const TJ* cj = ccj + qq * 108 + c36 * 3;
+        const TJ* gg = cg + qq * 3 * NP + aa;
         cpre[t] = gg[0] * cj[0] + gg[NP] * cj[1] + gg[2 * NP] * cj[2];
       }
       __syncthreads();
@@ -427,7 +471,7 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
         if (t < NE) {
           const int r = t / M, col = t % M;
           const int i = r / NP, aa = r % NP, f = col / NF, i2 = (col % NF) / NFP, m = col % NFP;
-          double v = acc[u];
+          TJ v = acc[u];
           for (int qq = 0; qq < nq; ++qq)
             v += cw[qq] * cpre[((qq * 36) + i * 12 + i2 * 4 + f) * NP + aa] * cps[(qq * 4 + f) * NFP + m];
           acc[u] = v;
@@ -441,9 +485,9 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
       if (t < NE) {
         const int r = t / M, col = t % M;
         const int i = r / NP, aa = r % NP, f = col / NF, i2 = (col % NF) / NFP, m = col % NFP;
-        double v = -iad2 * acc[u];
+        double v = -iad2 * (double)acc[u];
         if (i == i2) v -= s * JF[f] * tb.Ff[(f * NP + aa) * NFP + m];
-        W[t] = v;
+        W[t] = (TJ)v;
       }
     }
   }
@@ -451,9 +495,9 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   // ---- Cholesky S_v = L L^T (in place, lower), then Z = L^{-1} W
   for (int j = 0; j < NV; ++j) {
     if (tid == 0) {
-      double dd = Sv[j * NV + j];
-      if (!(dd > 0.0)) { atomicExch(a.err, 1); dd = 1.0; }
-      Sv[j * NV + j] = sqrt(dd);
+      TJ dd = Sv[j * NV + j];
+      if (!(dd > TJ(0))) { atomicExch(a.err, 1); dd = TJ(1); }
+      Sv[j * NV + j] = tsqrt(dd);
     }
     __syncthreads();
     for (int i = j + 1 + tid; i < NV; i += NT) Sv[i * NV + j] /= Sv[j * NV + j];
@@ -467,7 +511,7 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   }
   for (int col = tid; col < M; col += NT) {
     for (int i = 0; i < NV; ++i) {
-      double v = W[i * M + col];
+      TJ v = W[i * M + col];
       for (int l = 0; l < i; ++l) v -= Sv[i * NV + l] * W[l * M + col];
       W[i * M + col] = v / Sv[i * NV + i];
     }
@@ -477,13 +521,15 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   //      c = n_f^T A^{(i,i2)} n_f2;   S_K = D - Z^T Z + BH^T T BH / (alpha d^2)
   {
     constexpr int NE = M * (M + 1) / 2, NS = (NE + NT - 1) / NT;
-    double acc[NS];
-    int rr[NS], cc[NS];
+    TJ acc[NS];
+    int rc[NS];
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
-      acc[u] = 0.0;
+      acc[u] = TJ(0);
       const int t = tid + u * NT;
-      if (t < NE) tri_decode(t, M, rr[u], cc[u]); else { rr[u] = 0; cc[u] = 0; }
+      int r = 0, c = 0;
+      if (t < NE) tri_decode(t, M, r, c);
+      rc[u] = (r << 16) | c;
     }
     for (int q0 = 0; q0 < NQJ; q0 += QC) {
       const int nq = NQJ - q0 < QC ? NQJ - q0 : QC;
@@ -491,22 +537,22 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
       for (int t = tid; t < nq * 144; t += NT) {
         const int qq = t / 144, c144 = t % 144;
         const int f = c144 / 36, i = (c144 / 12) % 3, f2 = (c144 / 3) % 4, i2 = c144 % 3;
-        const double* A = cA + qq * 81;
-        double v = 0.0;
+        const TJ* A = cA + qq * 81;
+        TJ v = TJ(0);
 #pragma unroll
         for (int J = 0; J < 3; ++J)
 #pragma unroll
-          for (int L = 0; L < 3; ++L) v += nrm[f * 3 + J] * A[(i * 3 + J) * 9 + i2 * 3 + L] * nrm[f2 * 3 + L];
+          for (int L = 0; L < 3; ++L) v += nj[f * 3 + J] * A[(i * 3 + J) * 9 + i2 * 3 + L] * nj[f2 * 3 + L];
         cpre[t] = cw[qq] * v;
       }
       __syncthreads();
 #pragma unroll
       for (int u = 0; u < NS; ++u) {
         if (tid + u * NT < NE) {
-          const int c1 = rr[u], c2 = cc[u];
+          const int c1 = rc[u] >> 16, c2 = rc[u] & 0xffff;
           const int f = c1 / NF, i = (c1 % NF) / NFP, m = c1 % NFP;
           const int f2 = c2 / NF, i2 = (c2 % NF) / NFP, m2 = c2 % NFP;
-          double v = acc[u];
+          TJ v = acc[u];
           for (int qq = 0; qq < nq; ++qq)
             v += cpre[qq * 144 + f * 36 + i * 12 + f2 * 3 + i2] * cps[(qq * 4 + f) * NFP + m] * cps[(qq * 4 + f2) * NFP + m2];
           acc[u] = v;
@@ -518,17 +564,18 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
 #pragma unroll
     for (int u = 0; u < NS; ++u) {
       if (tid + u * NT < NE) {
-        const int c1 = rr[u], c2 = cc[u];
-        double v = iad2 * acc[u];
-        for (int r = 0; r < NV; ++r) v -= W[r * M + c1] * W[r * M + c2];
+        const int c1 = rc[u] >> 16, c2 = rc[u] & 0xffff;
+        TJ zz = TJ(0);
+        for (int r = 0; r < NV; ++r) zz += W[r * M + c1] * W[r * M + c2];
+        double v = iad2 * (double)acc[u] - (double)zz;
         if (c1 == c2) v += s * JF[c1 / NF];
         Se[c1 * M + c2] = v;
         Se[c2 * M + c1] = v;
       }
     }
   }
-  // ---- condensed right-hand side and A^{-1} R
-  svk_T_apply<K>(tb, FJ, lam, mu, dJ, R + 3 * NP, t1, CH);           // T R_H
+  // ---- condensed right-hand side and A^{-1} R (FP64 vectors; the Jacobian factors in TJ)
+  svk_T_apply<K, TJ>(tj, FJ, lamj, muj, dJj, R + 3 * NP, t1, CH);           // T R_H
   for (int idx = tid; idx < 9 * NP; idx += NT) y[idx] = R[12 * NP + idx] / dJ + iad2 * t1[idx];
   __syncthreads();
   for (int idx = tid; idx < NV; idx += NT) {
@@ -542,13 +589,13 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   if (tid == 0) {
     for (int i = 0; i < NV; ++i) {
       double v = rv[i];
-      for (int l = 0; l < i; ++l) v -= Sv[i * NV + l] * w1[l];
-      w1[i] = v / Sv[i * NV + i];
+      for (int l = 0; l < i; ++l) v -= (double)Sv[i * NV + l] * w1[l];
+      w1[i] = v / (double)Sv[i * NV + i];
     }
     for (int i = NV - 1; i >= 0; --i) {
       double v = w1[i];
-      for (int l = i + 1; l < NV; ++l) v -= Sv[l * NV + i] * zv[l];
-      zv[i] = v / Sv[i * NV + i];
+      for (int l = i + 1; l < NV; ++l) v -= (double)Sv[l * NV + i] * zv[l];
+      zv[i] = v / (double)Sv[i * NV + i];
     }
   }
   __syncthreads();
@@ -556,7 +603,7 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
   for (int idx = tid; idx < M; idx += NT) {
     const int f = idx / NF, i = (idx % NF) / NFP, m = idx % NFP;
     double v = -Rh[idx];
-    for (int r = 0; r < NV; ++r) v += W[r * M + idx] * w1[r];
+    for (int r = 0; r < NV; ++r) v += (double)W[r * M + idx] * w1[r];
     for (int J = 0; J < 3; ++J) {
       double fy = 0.0;
       for (int b = 0; b < NP; ++b) fy += tb.Ff[(f * NP + b) * NFP + m] * y[(i * 3 + J) * NP + b];
@@ -571,7 +618,7 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
     zH[idx] = v / (alpha * dJ);
   }
   __syncthreads();
-  svk_T_apply<K>(tb, FJ, lam, mu, dJ, zH, t2, CH);                    // T z_H
+  svk_T_apply<K, TJ>(tj, FJ, lamj, muj, dJj, zH, t2, CH);                    // T z_H
   double* zr = a.zR + e * (int64_t)N;
   for (int idx = tid; idx < N; idx += NT) {
     double v;
@@ -581,7 +628,7 @@ __global__ void __launch_bounds__(256, 1) svk_condense_kernel(SvkArgs a, SvkTabs
     zr[idx] = v;
   }
   double* Le = a.L + e * (int64_t)(NV * NV);
-  for (int idx = tid; idx < NV * NV; idx += NT) Le[idx] = Sv[idx];
+  for (int idx = tid; idx < NV * NV; idx += NT) Le[idx] = (double)Sv[idx];
 }
 
 struct SvkRecArgs {
@@ -601,31 +648,31 @@ struct SvkRecArgs {
 };
 
 // Local recovery of the Newton increment (Eq. LS): du = -A^{-1} R - A^{-1} B dlam, u += du.
-template <int K>
-__global__ void __launch_bounds__(256, 1) svk_recover_kernel(SvkRecArgs a, SvkTabs tb) {
+template <int K, typename TJ>
+__global__ void __launch_bounds__(256, SvkMinBlocks<K, TJ>::value) svk_recover_kernel(SvkRecArgs a, SvkTabs tb, SvkJT<TJ> tj) {
   using D = SvkDims<K>;
   constexpr int NP = D::NP, NFP = D::NFP, NF = D::NF, NV = D::NV, N = D::N, M = D::M, NT = D::NT, NQJ = D::NQJ;
-  extern __shared__ double sm[];
-  double* g = sm;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* g = reinterpret_cast<double*>(smraw);
   double* ue = g + 32;
   double* dk = ue + N;
   double* Dx = dk + M;
-  double* Ls = Dx + 3 * NP * NP;
-  double* FJ = Ls + NV * NV;
-  double* rH = FJ + 9 * NQJ;   // [9][Np]
+  double* rH = Dx + 3 * NP * NP;   // [9][Np]
   double* t1 = rH + 9 * NP;
   double* zH = t1 + 9 * NP;
   double* t2 = zH + 9 * NP;
   double* rv = t2 + 9 * NP;
   double* w1 = rv + NV;
   double* zv = w1 + NV;
-  double* CH = zv + NV;
+  TJ* Ls = reinterpret_cast<TJ*>(smraw + sizeof(double) * D::SMD_REC);
+  TJ* FJ = Ls + NV * NV;
+  TJ* CH = FJ + 9 * NQJ;
   __shared__ double red[2][8];
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x;
   if (tid < 32) g[tid] = a.geo[e * 32 + tid];
   for (int i = tid; i < N; i += NT) ue[i] = a.u[e * N + i];
-  for (int i = tid; i < NV * NV; i += NT) Ls[i] = a.L[e * (int64_t)(NV * NV) + i];
+  for (int i = tid; i < NV * NV; i += NT) Ls[i] = (TJ)a.L[e * (int64_t)(NV * NV) + i];
   for (int i = tid; i < M; i += NT) {
     const int fid = a.elem_face[e * 4 + i / NF];
     dk[i] = a.face_bnd[fid] < 0 ? a.dl[(int64_t)fid * NF + i % NF] : 0.0;
@@ -669,8 +716,9 @@ __global__ void __launch_bounds__(256, 1) svk_recover_kernel(SvkRecArgs a, SvkTa
     }
   }
   __syncthreads();
-  svk_F_at_jac<K>(tb, ue + 3 * NP, FJ);
-  svk_T_apply<K>(tb, FJ, lam, mu, dJ, rH, t1, CH);   // T (BH dlam)
+  const TJ lamj = (TJ)lam, muj = (TJ)mu, dJj = (TJ)dJ;
+  svk_F_at_jac<K, TJ>(tj, ue + 3 * NP, FJ);
+  svk_T_apply<K, TJ>(tj, FJ, lamj, muj, dJj, rH, t1, CH);   // T (BH dlam)
   // z_v = S_v^{-1} (Bv dlam + Dx T BH dlam / (alpha d^2))
   for (int idx = tid; idx < NV; idx += NT) {
     const int i = idx / NP, aa = idx % NP;
@@ -683,13 +731,13 @@ __global__ void __launch_bounds__(256, 1) svk_recover_kernel(SvkRecArgs a, SvkTa
   if (tid == 0) {
     for (int i = 0; i < NV; ++i) {
       double v = w1[i];
-      for (int l = 0; l < i; ++l) v -= Ls[i * NV + l] * w1[l];
-      w1[i] = v / Ls[i * NV + i];
+      for (int l = 0; l < i; ++l) v -= (double)Ls[i * NV + l] * w1[l];
+      w1[i] = v / (double)Ls[i * NV + i];
     }
     for (int i = NV - 1; i >= 0; --i) {
       double v = w1[i];
-      for (int l = i + 1; l < NV; ++l) v -= Ls[l * NV + i] * zv[l];
-      zv[i] = v / Ls[i * NV + i];
+      for (int l = i + 1; l < NV; ++l) v -= (double)Ls[l * NV + i] * zv[l];
+      zv[i] = v / (double)Ls[i * NV + i];
     }
   }
   __syncthreads();
@@ -700,7 +748,7 @@ __global__ void __launch_bounds__(256, 1) svk_recover_kernel(SvkRecArgs a, SvkTa
     zH[idx] = v / (alpha * dJ);
   }
   __syncthreads();
-  svk_T_apply<K>(tb, FJ, lam, mu, dJ, zH, t2, CH);   // T z_H
+  svk_T_apply<K, TJ>(tj, FJ, lamj, muj, dJj, zH, t2, CH);   // T z_H
   const double* zr = a.zR + e * (int64_t)N;
   double mdu = 0.0, mu_ = 0.0;
   double* uo = a.u + e * (int64_t)N;
