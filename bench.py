@@ -226,7 +226,8 @@ def run_ours(args):
             return sv
         sv = hdg.Solver(w["vert"], w["elem"], w["k"], w["tau"], w["rho"], w["c"], prec=prec, rtol=args.rtol,
                         inner_rtol=args.inner_rtol, nrhs=R, guess_history=args.guess_history,
-                        device_loops=not args.host_loops, trace_space=args.trace_space, solver=args.solver)
+                        device_loops=not args.host_loops, trace_space=args.trace_space, solver=args.solver,
+                        precond=args.precond if args.solver == "gmres" else "jacobi")
         sv.hdg_set_sources(w["sources"], np.ones(len(w["sources"])), w["f0"], w["t0"], col=w.get("source_cols"))
         sv.hdg_set_dirichlet(None)
         sv.hdg_set_state(sv.empty_fields(), 0.0)
@@ -589,6 +590,7 @@ def run_ours(args):
                           "inner_rtol": args.inner_rtol if args.prec != "fp64" else None,
                           "guess_history": args.guess_history if R == 1 else None,
                           "trace_space": args.trace_space, "solver": args.solver,
+                          "precond": args.precond if args.solver == "gmres" else "jacobi",
                           "trace_unknowns": int(s.sizes.trace_unknowns) * R,
                           "trace_solve": "host-driven loops" if (args.host_loops or R > 1) else
                           "one CUDA-graph launch per trace solve (device-side loop conditions)"},
@@ -885,6 +887,8 @@ def main():
                     help="steps of the whole run whose Krylov counts are reported (default: 200 acoustic, 100 elastic)")
     ap.add_argument("--solver", default="cg", choices=["cg", "gmres"],
                     help="gmres: restarted GMRES with two-pass classical Gram-Schmidt (FP64, the paper's Krylov method)")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "bilu0"],
+                    help="with --solver gmres: right preconditioner, Jacobi or block ILU(0) (the paper's)")
     ap.add_argument("--trace-space", default="hdg", choices=["hdg", "iedg", "edg"],
                     help="acoustic, one column: continuous traces on the interior (iedg) or all (edg) faces")
     ap.add_argument("--host-loops", action="store_true",

@@ -144,7 +144,15 @@ typedef struct {
                             /* increment (fields and traces) is <= newton_tol *         */
                             /* max(1, max |u|)                                          */
   int32_t newton_maxit;     /* HDG_SVK: Newton iteration cap per stage (HDG_ENOCONV)     */
+  int32_t precond;          /* HDG_SOLVER_GMRES right preconditioner: HDG_PRECOND_JACOBI */
+                            /* (default, the inverse diagonal) or HDG_PRECOND_BILU0: block */
+                            /* ILU(0) of the assembled trace system (Sec. 2.4), one N_f x  */
+                            /* N_f block per pair of faces sharing an element, rows in     */
+                            /* face order; factored after every condensation, applied by   */
+                            /* level-scheduled block substitutions (N_f <= 32)             */
 } hdg_options;
+
+enum { HDG_PRECOND_JACOBI = 0, HDG_PRECOND_BILU0 = 1 };
 
 enum { HDG_SOLVER_CG = 0, HDG_SOLVER_GMRES = 1 };
 
@@ -174,7 +182,7 @@ typedef struct {
 
 /* Defaults: FP64, rtol 1e-13, maxit 2000, check_every 16, inner_rtol 1e-4, max_sweeps 20, nrhs 1,
  * use_graphs 0, guess_history 8, device_loops 1, trace_space HDG_TRACE_HDG, solver HDG_SOLVER_CG,
- * gmres_restart 40, newton_tol 1e-11, newton_maxit 25. */
+ * gmres_restart 40, newton_tol 1e-11, newton_maxit 25, precond HDG_PRECOND_JACOBI. */
 void hdg_default_options(hdg_options* opt);
 
 /* Sec. 2.1 mesh and skeleton + Sec. 2.2 spaces. Validates the mesh, builds the face
@@ -284,6 +292,12 @@ hdg_status hdg_set_sources(hdg_ctx* ctx, int32_t nsrc, const double* pos_host, c
  * contexts stepping concurrently from different threads; destroy it after the context. */
 hdg_status hdg_stream_create(void** stream_out);
 hdg_status hdg_stream_destroy(void* stream);
+
+/* z = M^{-1} r with the right preconditioner of the GMRES trace solve (Jacobi or block
+ * ILU(0), Sec. 2.4) for sgn K, on face vectors r_dev, z_dev [n_faces][Nf] (boundary entries
+ * of r ignored, of z zero). Solver HDG_SOLVER_GMRES after hdg_condense; returns after the
+ * work completes. */
+hdg_status hdg_precond_apply(hdg_ctx* ctx, const double* r_dev, double* z_dev);
 
 /* Rebinds the context to another caller-owned stream (cudaStream_t, may be NULL for the
  * legacy stream). The call first waits for all work enqueued on the previous stream; every

@@ -8,7 +8,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhdg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-UNITS = ["api.cu", "vardeg.cu", "svk.cu", "noalloc.cu", "reftab.cpp", "mesh.cpp"]
+UNITS = ["api.cu", "vardeg.cu", "svk.cu", "bilu.cu", "noalloc.cu", "reftab.cpp", "mesh.cpp"]
 
 
 def _nvcc():

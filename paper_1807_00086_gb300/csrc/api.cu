@@ -19,6 +19,7 @@
 #include "elastic.cuh"
 #include "edg.cuh"
 #include "gmres.cuh"
+#include "bilu.cuh"
 #include "mesh.h"
 #include "reftab.h"
 
@@ -323,6 +324,7 @@ hdg_status do_condense(hdg_ctx* c, double alpha) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (herr) { c->condensed = false; return fail(c, HDG_EINVAL, "local pressure block not positive definite"); }
   c->condensed = true;
+  if (c->bilu && (s = bilu_factor(c))) return s;
   return HDG_OK;
 }
 
@@ -742,10 +744,16 @@ hdg_status gmres_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return check_launch(c, "gmres_dots");
   };
-  // w = sgn K Dinv v (interior entries; zero on boundary faces)
+  // w = sgn K M^{-1} v (interior entries; zero on boundary faces); M^{-1} = Jacobi or block ILU(0)
   auto opK = [&](const double* v, double* w) -> hdg_status {
-    c->n_launch += 2;
-    vmul_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_dinv, v, c->d_z);
+    c->n_launch += 1;
+    if (c->bilu) {
+      hdg_status s2 = bilu_apply(c, v, c->d_z);
+      if (s2) return s2;
+    } else {
+      c->n_launch += 1;
+      vmul_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_dinv, v, c->d_z);
+    }
     HDG_DISPATCH(c, launch_apply, c, (const double*)c->d_z, c->d_slot, (const int*)nullptr, -1);
     face_gather_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_slot, c->d_face_bnd, c->d_slot,
                                                               c->sgn, w);
@@ -830,8 +838,16 @@ hdg_status gmres_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
       y[i] = v / H[(size_t)i * m + i];
     }
     CUDA_TRY(c, cudaMemcpyAsync(c->d_gmy, y.data(), (size_t)k * 8, cudaMemcpyHostToDevice, c->stream));
-    c->n_launch += 1;
-    gm_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, k, V, c->d_gmy, c->d_dinv, c->d_intmask, x);
+    if (c->bilu) {
+      // x += M^{-1} (V y)
+      c->n_launch += 2;
+      bilu_vcombine_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, k, V, c->d_gmy, c->d_p);
+      if ((s = bilu_apply(c, c->d_p, c->d_z))) return s;
+      bilu_add_masked_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_intmask, c->d_z, x);
+    } else {
+      c->n_launch += 1;
+      gm_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, k, V, c->d_gmy, c->d_dinv, c->d_intmask, x);
+    }
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));   // y is released by the next cycle
     if ((s = check_launch(c, "gmres_update"))) return s;
   }
@@ -1567,6 +1583,7 @@ void hdg_default_options(hdg_options* o) {
   o->gmres_restart = 40;
   o->newton_tol = 1e-11;
   o->newton_maxit = 25;
+  o->precond = HDG_PRECOND_JACOBI;
 }
 
 const char* hdg_last_error(const hdg_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -1638,6 +1655,7 @@ void hdg_destroy(hdg_ctx* c) {
   if (c->h_mint) cudaFreeHost(c->h_mint);
   vd_destroy(c);
   svk_destroy(c);
+  bilu_destroy(c);
   delete c;
 }
 
@@ -1671,6 +1689,10 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
       (c->opt.prec != HDG_FP64 || c->R != 1 || mesh->elem_k || c->tspace != HDG_TRACE_HDG ||
        c->opt.gmres_restart < 2 || c->opt.gmres_restart > 64))
     return fail(c, HDG_EINVAL, "GMRES: FP64, HDG traces, uniform degree, nrhs = 1 and 2 <= gmres_restart <= 64 only");
+  if (c->opt.precond != HDG_PRECOND_JACOBI && c->opt.precond != HDG_PRECOND_BILU0)
+    return fail(c, HDG_EINVAL, "unknown preconditioner");
+  if (c->opt.precond == HDG_PRECOND_BILU0 && c->opt.solver != HDG_SOLVER_GMRES)
+    return fail(c, HDG_EINVAL, "block ILU(0) preconditions the GMRES solver only");
   std::string err;
   const bool svk = mat->phys == HDG_SVK;
   if (mat->phys != HDG_ACOUSTIC && mat->phys != HDG_ELASTIC && !svk) return fail(c, HDG_EINVAL, "unknown physics");
@@ -1956,6 +1978,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
     if ((s = guess_setup(c, mask.data()))) return s;
   }
   if (svk && (s = svk_setup(c))) return s;
+  if (c->opt.precond == HDG_PRECOND_BILU0 && (s = bilu_setup(c))) return s;
   c->have_state = true;
   return HDG_OK;
 }
@@ -2475,6 +2498,23 @@ hdg_status hdg_stream_create(void** out) {
   cudaStream_t st = nullptr;
   if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return HDG_ECUDA;
   *out = (void*)st;
+  return HDG_OK;
+}
+
+hdg_status hdg_precond_apply(hdg_ctx* c, const double* r, double* z) {
+  if (!c || !r || !z) return fail(c, HDG_EINVAL, "null argument");
+  if (c->opt.solver != HDG_SOLVER_GMRES) return fail(c, HDG_EINVAL, "the preconditioner of the GMRES solver only");
+  if (!c->condensed) return fail(c, HDG_ESTATE, "hdg_condense has not run");
+  const int64_t n = c->sk.nf * c->Nf;
+  hdg_status s;
+  if (c->bilu) {
+    if ((s = bilu_apply(c, r, z))) return s;
+  } else {
+    c->n_launch += 1;
+    vmul_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->d_dinv, r, z);
+  }
+  if ((s = check_launch(c, "precond_apply"))) return s;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return HDG_OK;
 }
 

@@ -21,6 +21,7 @@ using namespace hdg;
 
 struct VarDeg;   // variable-degree (per-element k) data of an elastic context
 struct Svk;      // nonlinear (Saint Venant-Kirchhoff) elastodynamics data
+struct Bilu;     // block ILU(0) preconditioner of the GMRES trace solve
 
 struct hdg_ctx {
   std::string err;
@@ -156,6 +157,7 @@ struct hdg_ctx {
   VarDeg* vd = nullptr;
   Svk* svk = nullptr;   // set for HDG_SVK contexts (elastic trace layout, 21 N_p fields)
   bool svk_mixed = false; // HDG_SVK with HDG_MIXED: FP32 Jacobian, FP64 residual
+  Bilu* bilu = nullptr;   // set when opt.precond == HDG_PRECOND_BILU0
 };
 
 namespace {
@@ -366,6 +368,12 @@ void vd_destroy(hdg_ctx* c);
 hdg_status svk_setup(hdg_ctx* c);
 hdg_status svk_step(hdg_ctx* c, double dt, hdg_scheme scheme, int32_t nsteps, hdg_solve_info* info);
 void svk_destroy(hdg_ctx* c);
+// block ILU(0) (bilu.cu)
+hdg_status bilu_setup(hdg_ctx* c);
+hdg_status bilu_factor(hdg_ctx* c);
+hdg_status bilu_apply(hdg_ctx* c, const double* in, double* out);
+int bilu_levels(const hdg_ctx* c, int backward);
+void bilu_destroy(hdg_ctx* c);
 // api.cu: the context's trace solve (CG on the assembled S_K, device- or host-driven) and the
 // DIRK(3,3) tableau
 hdg_status trace_cg_solve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info);

@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
     _fields_ = [("prec", c_int32), ("rtol", c_double), ("maxit", c_int32), ("check_every", c_int32),
                 ("inner_rtol", c_double), ("max_sweeps", c_int32), ("nrhs", c_int32), ("use_graphs", c_int32),
                 ("guess_history", c_int32), ("device_loops", c_int32), ("trace_space", c_int32),
-                ("solver", c_int32), ("gmres_restart", c_int32), ("newton_tol", c_double), ("newton_maxit", c_int32)]
+                ("solver", c_int32), ("gmres_restart", c_int32), ("newton_tol", c_double), ("newton_maxit", c_int32),
+                ("precond", c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -100,6 +101,7 @@ SIGNATURES = {
     "hdg_stream_create": (c_int32, [ctypes.POINTER(c_void_p)]),
     "hdg_stream_destroy": (c_int32, [c_void_p]),
     "hdg_set_stream": (c_int32, [c_void_p, c_void_p]),
+    "hdg_precond_apply": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "hdg_svk_set_traction_faces": (c_int32, [c_void_p, ctypes.POINTER(ctypes.c_uint8)]),
     "hdg_svk_set_forcing": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "hdg_svk_newton_counts": (c_int32, [c_void_p, P_int32, c_int32, P_int32]),
@@ -174,12 +176,13 @@ class Solver:
     def __init__(self, vert, elem, k, tau, rho, c=None, prec="fp64", rtol=1e-13, maxit=2000, check_every=16,
                  inner_rtol=None, max_sweeps=None, nrhs=1, use_graphs=False, stream=None, lam=None, mu=None,
                  elem_k=None, guess_history=None, device_loops=None, trace_space="hdg", solver="cg",
-                 gmres_restart=None, svk=False, newton_tol=None, newton_maxit=None):
+                 gmres_restart=None, svk=False, newton_tol=None, newton_maxit=None, precond="jacobi"):
         """Acoustic when `c` is given (rho, c); elastic when `lam` and `mu` are given (rho, lam, mu);
         svk=True with lam, mu: nonlinear Saint Venant-Kirchhoff elastodynamics (Newton per stage).
         elem_k: per-element degrees (3D elastic); fields and traces are then flat vectors.
         trace_space: "hdg", "iedg" or "edg" (continuous traces on the interior / all faces).
-        solver: "cg" (default) or "gmres" (restarted GMRES with two-pass classical Gram-Schmidt)."""
+        solver: "cg" (default) or "gmres" (restarted GMRES with two-pass classical Gram-Schmidt).
+        precond: the GMRES right preconditioner, "jacobi" (default) or "bilu0" (block ILU(0))."""
         import torch
         self.lib = load()
         self.torch = torch
@@ -218,6 +221,7 @@ class Solver:
         opt.solver = {"cg": 0, "gmres": 1}[solver]
         if gmres_restart is not None:
             opt.gmres_restart = gmres_restart
+        opt.precond = {"jacobi": 0, "bilu0": 1}[precond]
         if newton_tol is not None:
             opt.newton_tol = newton_tol
         if newton_maxit is not None:
@@ -280,6 +284,12 @@ class Solver:
         """Rebind the context to `stream` (a torch.cuda.Stream or ExternalStream)."""
         self._check(self.lib.hdg_set_stream(self.ctx, ctypes.c_void_p(stream.cuda_stream)))
         self.stream = stream
+
+    def hdg_precond_apply(self, r, z=None):
+        """z = M^{-1} r with the GMRES preconditioner (Jacobi or block ILU(0)) for sgn K."""
+        z = self.empty_traces() if z is None else z
+        self._check(self.lib.hdg_precond_apply(self.ctx, self._dev(r, self._tshape), self._dev(z, self._tshape)))
+        return z
 
     # nonlinear elastodynamics ---------------------------------------------------------------
     def hdg_svk_set_traction_faces(self, mask):
