@@ -178,18 +178,25 @@ void launch_apply16(hdg_ctx* c, const float* x, float* slot, const int* done, in
 template <int DIM, int K>
 void launch_apply_df(hdg_ctx* c, const double* x, double* zslot) {
   using C = ApplyDfCfg<DIM, K>;
-  const unsigned grid = (unsigned)((c->sk.ne + C::EPB - 1) / C::EPB);
+  const int64_t ngroups = (c->sk.ne + C::EPB - 1) / C::EPB;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)c->sms * std::max(1, c->df_per_sm)));
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 2, -1);
-  apply_df_kernel<DIM, K><<<grid, C::NT, C::SMEM, c->stream>>>(devmesh(c), c->d_Sdf, x, zslot);
+  apply_df_kernel<DIM, K><<<grid, C::NT, C::SMEM, c->stream>>>(devmesh(c), c->d_Sdf, x, zslot, ngroups);
   apply_end(c, stop);
 }
 
-// dynamic shared memory of the double-float apply (set outside any stream capture)
+// dynamic shared memory and resident CTAs per SM of the double-float apply (set outside any
+// stream capture; the persistent grid is one resident wave)
 template <int DIM, int K>
 void attr_apply_df(hdg_ctx* c) {
-  (void)c;
-  cudaFuncSetAttribute(apply_df_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ApplyDfCfg<DIM, K>::SMEM);
+  using C = ApplyDfCfg<DIM, K>;
+  cudaFuncSetAttribute(apply_df_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_df_kernel<DIM, K>, C::NT, C::SMEM) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  c->df_per_sm = per_sm;
 }
 
 // dynamic shared memory of the tensor-core column-block apply (set outside any stream capture)
@@ -272,6 +279,7 @@ void edg_diag(hdg_ctx* c) {
 }
 
 hdg_status do_condense(hdg_ctx* c, double alpha) {
+  if (c->svk) return fail(c, HDG_EINVAL, "SVK: the Newton iterations of hdg_step condense; there is no linear condensation");
   guess_clear(c);   // the stored stage solutions belong to the previous operator
   if (c->vd) return vd_condense(c, alpha);
   if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(c, HDG_EINVAL, "alpha must be positive and finite");
@@ -2367,7 +2375,7 @@ hdg_status hdg_load_checkpoint(hdg_ctx* c, const void* buf) {
     return fail(c, HDG_EINVAL, "checkpoint of a context with other sizes or options");
   hdg_status s;
   // operators for the saved alpha first: a condensation clears the stored stage solutions
-  if (h.condensed && (s = ensure_alpha(c, h.alpha))) return s;
+  if (h.condensed && !c->svk && (s = ensure_alpha(c, h.alpha))) return s;
   size_t off = sizeof h;
   if (!c->gm_gram.empty()) {
     std::memcpy(c->gm_gram.data(), in + off, c->gm_gram.size() * 8);

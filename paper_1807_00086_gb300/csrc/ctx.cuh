@@ -55,6 +55,7 @@ struct hdg_ctx {
   CgScal* d_sc = nullptr;
   CgScal* h_sc = nullptr;   // pinned
   int nb_red = 0;
+  int df_per_sm = 1;            // resident CTAs per SM of the persistent double-float apply
   // mixed precision
   float *d_S32 = nullptr, *d_dinv32 = nullptr, *d_slot32 = nullptr;
   float* d_Sdf = nullptr;       // double-float diagonal-major copy of S_K (refinement apply)

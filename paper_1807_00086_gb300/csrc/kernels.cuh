@@ -1346,8 +1346,9 @@ __global__ void packdf_kernel(int64_t ne, const double* __restrict__ S, float* _
 
 // FP64-accurate refinement apply on the FP32 pipe: zslot[e][r] = sum_c S_K[r][c] x_K[c] with
 // S_K = hi + lo from the diagonal-major copy and x split into double-floats. CTA = EPB
-// elements, one thread per (element, row); the elements' copies are staged in shared memory
-// with 16-byte asynchronous copies. At step s thread r takes column c = (r + s) mod M: the
+// elements, one thread per (element, row); persistent over groups of EPB elements, the
+// copies of the next group staged in shared memory with 16-byte asynchronous copies while the
+// current one is computed (two stages). At step s thread r takes column c = (r + s) mod M: the
 // superdiagonal s at row r when c >= r, else the superdiagonal M - s at row c, so the threads
 // of an element read two runs of consecutive words.
 template <int DIM, int K>
@@ -1356,53 +1357,70 @@ struct ApplyDfCfg {
   static constexpr int EPB = 4;
   static constexpr int NT = EPB * M;
   static constexpr int PD = Packed<DIM, K>::P4 * 4;
-  static constexpr int CH = EPB * 2 * PD / 4;                   // 16-byte chunks per CTA
-  static constexpr size_t SMEM = sizeof(float) * EPB * 2 * PD + sizeof(df2) * EPB * M;
+  static constexpr int CH = EPB * 2 * PD / 4;                   // 16-byte chunks per group
+  static constexpr int STAGE = EPB * 2 * PD;                     // floats per stage
+  static constexpr size_t SMEM = sizeof(float) * 2 * STAGE + sizeof(df2) * EPB * M;
 };
 
 template <int DIM, int K>
 __global__ void __launch_bounds__(ApplyDfCfg<DIM, K>::NT) apply_df_kernel(DevMesh mesh, const float* __restrict__ Sdf,
                                                                          const double* __restrict__ x,
-                                                                         double* __restrict__ zslot) {
+                                                                         double* __restrict__ zslot, int64_t ngroups) {
   using D = Dims<DIM, K>;
   using C = ApplyDfCfg<DIM, K>;
   constexpr int NF = D::NF, M = D::M, NFC = D::NFC, EPB = C::EPB, PD = C::PD;
   extern __shared__ __align__(16) float dsm[];
-  df2* lx = reinterpret_cast<df2*>(dsm + EPB * 2 * PD);   // [EPB][M]
-  const int64_t e0 = (int64_t)blockIdx.x * EPB;
-  {
-    // the copy is padded to a whole number of CTAs, so every chunk is in bounds
-    const char* src = reinterpret_cast<const char*>(Sdf + e0 * 2 * PD);
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(dsm);
+  df2* lx = reinterpret_cast<df2*>(dsm + 2 * C::STAGE);   // [EPB][M]
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(dsm);
+  // the copy is padded to whole 32-element groups, so every chunk of a group is in bounds
+  auto issue = [&](int64_t g, int stage) {
+    const char* src = reinterpret_cast<const char*>(Sdf + g * EPB * 2 * PD);
+    const unsigned dst = sbase + (unsigned)(stage * C::STAGE * sizeof(float));
     for (int i = threadIdx.x; i < C::CH; i += C::NT)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16 * i), "l"(src + 16 * i) : "memory");
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  }
+  };
+  int64_t g = blockIdx.x;
+  if (g >= ngroups) return;
+  issue(g, 0);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   const int el = threadIdx.x / M, r = threadIdx.x % M;
-  const int64_t e = e0 + el;
-  {
+  // this thread's trace entry of group gg (gathered one group ahead, off the compute path)
+  auto gather = [&](int64_t gg) {
     double v = 0.0;
-    if (e < mesh.ne) {
-      const int f = mesh.elem_face[e * NFC + r / NF];
+    const int64_t ee = gg * EPB + el;
+    if (gg < ngroups && ee < mesh.ne) {
+      const int f = mesh.elem_face[ee * NFC + r / NF];
       if (mesh.face_bnd[f] < 0) v = x[(int64_t)f * NF + r % NF];
     }
-    lx[el * M + r] = df_from(v);
+    return v;
+  };
+  double vnext = gather(g);
+  for (int it = 0; g < ngroups; ++it, g += gridDim.x) {
+    const int cur = it & 1;
+    if (g + gridDim.x < ngroups) issue(g + gridDim.x, cur ^ 1);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const int64_t e = g * EPB + el;
+    lx[el * M + r] = df_from(vnext);
+    vnext = gather(g + gridDim.x);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    if (e < mesh.ne) {
+      const float* hi = dsm + cur * C::STAGE + el * 2 * PD;
+      const float* lo = hi + PD;
+      const df2* ex = lx + el * M;
+      DfAcc acc;
+#pragma unroll
+      for (int s = 0; s < M; ++s) {
+        const int c = r + s;
+        const bool up = c < M;
+        const int pos = up ? diag_off(M, s) + r : diag_off(M, M - s) + (c - M);
+        acc.fma(df2{hi[pos], lo[pos]}, ex[up ? c : c - M]);
+      }
+      zslot[e * M + r] = acc.value();
+    }
+    __syncthreads();   // the stage just read is the next prefetch target
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
-  if (e >= mesh.ne) return;
-  const float* hi = dsm + el * 2 * PD;
-  const float* lo = hi + PD;
-  const df2* ex = lx + el * M;
-  DfAcc acc;
-#pragma unroll
-  for (int s = 0; s < M; ++s) {
-    const int c = r + s;
-    const bool up = c < M;
-    const int pos = up ? diag_off(M, s) + r : diag_off(M, M - s) + (c - M);
-    acc.fma(df2{hi[pos], lo[pos]}, ex[up ? c : c - M]);
-  }
-  zslot[e * M + r] = acc.value();
 }
 
 }  // namespace hdg

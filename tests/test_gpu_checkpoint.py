@@ -40,12 +40,28 @@ def _elastic_vardeg(prec):
     return s
 
 
+def _svk(prec):
+    import torch
+    from paper_1807_00086_gb300 import hdg
+    vert, elem = inputs.unit_cube_tet(1)
+    ne = elem.shape[0]
+    s = hdg.Solver(vert, elem, 2, 1.0, np.ones(ne), lam=np.full(ne, 1.5), mu=np.ones(ne), svk=True, rtol=1e-12,
+                   prec=prec)
+    rng = np.random.default_rng(6)
+    u = np.zeros((ne, s.n))
+    u[:, :3 * s.Np] = 0.5 * rng.standard_normal((ne, 3 * s.Np))
+    u[:, 3 * s.Np:12 * s.Np] = 0.03 * rng.standard_normal((ne, 9 * s.Np))
+    s.hdg_set_state(torch.tensor(u, device="cuda"), 0.0)
+    return s
+
+
 CASES = [
     ("acoustic 3D k=3 mixed16 BDF2", lambda: _acoustic(3, 2, 3, "mixed16"), "bdf2", 2e-3),
     ("acoustic 2D k=2 FP64 DIRK3", lambda: _acoustic(2, 4, 2, "fp64"), "dirk3", 1e-2),
     ("acoustic 3D k=2 mixed, 4 columns, BDF2", lambda: _acoustic(3, 2, 2, "mixed", nrhs=4), "bdf2", 2e-3),
     ("acoustic 3D k=3 IEDG mixed16 BDF2", lambda: _acoustic(3, 2, 3, "mixed16", trace_space="iedg"), "bdf2", 2e-3),
     ("elastic per-element degree mixed16 DIRK3", lambda: _elastic_vardeg("mixed16"), "dirk3", 1e-2),
+    ("SVK k=2 FP32 Jacobian DIRK3", lambda: _svk("mixed"), "dirk3", 2e-2),
 ]
 
 
