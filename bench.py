@@ -580,6 +580,8 @@ def run_ours(args):
         srv.close()
         serve = {"requests": st_srv["requests"], "arrival_rate_per_s": args.serve_rate, "p50_ms": st_srv["p50_ms"],
                  "p99_ms": st_srv["p99_ms"], "mean_ms": st_srv["mean_ms"], "dof_steps_per_s": st_srv["dof_steps_per_s"],
+                 "wait_p50_ms": st_srv["wait_p50_ms"], "wait_p99_ms": st_srv["wait_p99_ms"],
+                 "service_p50_ms": st_srv["service_p50_ms"], "service_p99_ms": st_srv["service_p99_ms"],
                  "wall_s": st_srv["wall_s"], "slots_per_context": args.serve_slots,
                  "contexts": st_srv["contexts_created"],
                  "workload": "first %d requests of the seeded serving workload (2D/3D acoustic, 1e3-1e5 elements, "
@@ -865,6 +867,8 @@ def run_serve(args):
     srv.close()
     out = {"metric": METRIC, "mode": "serve", "value": stats["dof_steps_per_s"], "unit": UNIT,
            "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "mean_ms": stats["mean_ms"],
+           "wait_p50_ms": stats["wait_p50_ms"], "wait_p99_ms": stats["wait_p99_ms"],
+           "service_p50_ms": stats["service_p50_ms"], "service_p99_ms": stats["service_p99_ms"],
            "higher_is_better": True, "dtype": {"fp64": "f64", "mixed": "f32+f64", "mixed16": "f16+f32+f64"}[args.prec], "data": "synthetic",
            "config": {"workload": "serve_acoustic_2d3d_poisson%g" % args.serve_rate, "requests": stats["requests"],
                       "slots_per_context": args.serve_slots, "budget_gb": args.serve_budget_gb,

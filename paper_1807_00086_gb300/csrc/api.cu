@@ -1707,12 +1707,9 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
   if (svk && (mesh->dim != 3 || k > 3 || mesh->elem_k || c->R != 1 || c->tspace != HDG_TRACE_HDG ||
               c->opt.solver != HDG_SOLVER_CG || c->opt.prec == HDG_MIXED16))
     return fail(c, HDG_EINVAL, "SVK: 3D, uniform k in 1..3, nrhs = 1, HDG traces, CG, FP64 or MIXED only");
-  if (svk) {
-    // HDG_MIXED: FP32 Jacobian (tangent, condensation, factor) around the FP64 residual; the
-    // trace system of each Newton iteration is solved in FP64
-    c->svk_mixed = c->opt.prec == HDG_MIXED;
-    c->opt.prec = HDG_FP64;
-  }
+  // HDG_MIXED: FP32 Jacobian (tangent, condensation, factor) around the FP64 residual, and
+  // the trace system of each Newton iteration solved by FP32 CG inside FP64 refinement
+  if (svk) c->svk_mixed = c->opt.prec == HDG_MIXED;
   if (svk && (!(c->opt.newton_tol > 0.0) || c->opt.newton_maxit < 1))
     return fail(c, HDG_EINVAL, "SVK: newton_tol must be > 0 and newton_maxit >= 1");
   // SVK contexts share the elastic trace layout (3 N_f velocity traces per face)
@@ -1868,7 +1865,10 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
     const int P4 = (c->m * (c->m + 1) / 2 + 3) / 4;
     const size_t nS32 = c->phys == HDG_ELASTIC ? (size_t)ne * c->m * c->m : (size_t)ngroups * P4 * 128;
     if ((s = dalloc(c, &c->d_S32, nS32))) return s;
-    if ((s = dalloc(c, &c->d_slot32, (size_t)ngroups * c->m * 32))) return s;
+    // element slots (whole 32-element groups) plus one zero slot past the last element (the
+    // missing neighbour of an SVK traction face)
+    if ((s = dalloc(c, &c->d_slot32, (size_t)ngroups * c->m * 32 + c->Nf))) return s;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_slot32, 0, ((size_t)ngroups * c->m * 32 + c->Nf) * 4, c->stream));
     c->nfe4 = (int64_t)((nfe + 3) / 4) * 4;
     const size_t n32 = c->R > 1 ? nfe * R : (size_t)c->nfe4;
     for (float** p : {&c->d_dinv32, &c->d_r32, &c->d_z32, &c->d_p32, &c->d_q32, &c->d_x32, &c->d_b32}) {

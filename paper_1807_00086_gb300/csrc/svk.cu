@@ -7,6 +7,7 @@
 #include <cstring>
 
 #include "ctx.cuh"
+#include "elastic.cuh"
 #include "svk.cuh"
 
 using namespace hdg;
@@ -190,6 +191,13 @@ hdg_status svk_newton(hdg_ctx* c, double* u, const double* h, double alpha, doub
     }
     svk_diag_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nf, c->Nf, c->m, ne * 4, c->d_face_slot, c->d_face_bnd,
                                                             c->d_S, c->d_dinv);
+    if (c->opt.prec != HDG_FP64) {
+      // FP32 copies of S_K and of the Jacobi diagonal for the inner CG of the refined solve
+      const int64_t nS = ne * (int64_t)c->m * c->m;
+      c->n_launch += 2;
+      to32_copy_kernel<<<grid_for(c, nS), 256, 0, c->stream>>>(nS, c->d_S, c->d_S32);
+      to32_kernel<<<grid_for(c, nfe), 256, 0, c->stream>>>(nfe, c->d_dinv, c->d_dinv32);
+    }
     CUDA_TRY(c, cudaMemsetAsync(v->d_dl, 0, nfe * 8, c->stream));
     hdg_status s = check_launch(c, "svk_condense");
     if (s) return s;

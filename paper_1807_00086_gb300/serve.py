@@ -268,8 +268,14 @@ class Server:
             w.join()
         wall = clock() - t_start
         lat = np.array([r.finished - r.arrival for r in self.done]) if self.done else np.zeros(1)
+        # latency = waiting for a slot (and a context) + being stepped in the slot
+        wait = np.array([r.admitted - r.arrival for r in self.done]) if self.done else np.zeros(1)
+        serv = lat - wait
         return {"requests": len(self.done), "wall_s": wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+                "wait_p50_ms": float(np.percentile(wait, 50) * 1e3), "wait_p99_ms": float(np.percentile(wait, 99) * 1e3),
+                "service_p50_ms": float(np.percentile(serv, 50) * 1e3),
+                "service_p99_ms": float(np.percentile(serv, 99) * 1e3),
                 "dof_steps": self.dof_steps, "dof_steps_per_s": self.dof_steps / wall if wall > 0 else 0.0,
                 "contexts_created": len(self.engines)}
 
