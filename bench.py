@@ -368,8 +368,7 @@ def run_ours(args):
     field_bytes = int(np.prod(s._fshape)) * 8
     trace_bytes = int(np.prod(s._tshape)) * 8
     nschur, nslot = s.sizes.schur_entries, s.sizes.slot_entries
-    # the rest of the configured run (Krylov counts over every step of it); the e2e steps above
-    # restarted the guess history (hdg_set_state), as a resumed run would
+    # the rest of the configured run (Krylov counts over every step of it)
     advance(s, total - run["steps"], run)
     full_run = {"steps": run["steps"], "krylov_iters_per_step": run["iters"] / max(1, run["steps"]),
                 "refinement_sweeps_per_step": run["sweeps"] / max(1, run["steps"]) if args.prec != "fp64" else None,

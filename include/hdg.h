@@ -329,7 +329,10 @@ hdg_status hdg_set_dirichlet(hdg_ctx* ctx, const double* vals_host, double omega
 /* Time state (checkpoint/resume). hdg_set_state sets the fields u at time t (u_dev
  * [n_elem][n]), the previous level used by BDF2 (uprev_dev, same layout; NULL: equal
  * to u, i.e. a start from rest or a steady state) and the traces (lam_dev
- * [n_faces][Nf]; NULL: zero), which the next trace solve takes as its initial guess.
+ * [n_faces][Nf]; NULL: zero), which the next trace solve takes as its initial guess unless
+ * the least-squares guess replaces it: its stored (right-hand side, solution) pairs satisfy
+ * K lam_i = b_i for the current operator whatever the state, so they are kept (hdg_condense
+ * and a new mass shift drop them).
  * hdg_get_state copies the current
  * fields, the previous level and the traces (lam_dev [n_faces][Nf], boundary entries =
  * Dirichlet values); any output pointer may be NULL. Both complete before returning. */

@@ -2287,7 +2287,7 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
   c->have_state = true;
   c->n_lam_hist = 0;
   if (c->d_mu) CUDA_TRY(c, cudaMemsetAsync(c->d_mu, 0, (size_t)c->n_mu * 8, c->stream));
-  guess_clear(c);
+  // the least-squares guess keeps its pairs: K lam_i = b_i holds for any state
   return check_launch(c, "set_state");
 }
 
