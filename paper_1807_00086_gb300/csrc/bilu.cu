@@ -214,10 +214,6 @@ hdg_status bilu_apply(hdg_ctx* c, const double* in, double* out) {
   return HDG_OK;
 }
 
-int bilu_levels(const hdg_ctx* c, int backward) {
-  return c->bilu ? (int)(backward ? c->bilu->blev.size() : c->bilu->flev.size()) - 1 : 0;
-}
-
 void bilu_destroy(hdg_ctx* c) {
   Bilu* b = c->bilu;
   if (!b) return;

@@ -373,7 +373,6 @@ void svk_destroy(hdg_ctx* c);
 hdg_status bilu_setup(hdg_ctx* c);
 hdg_status bilu_factor(hdg_ctx* c);
 hdg_status bilu_apply(hdg_ctx* c, const double* in, double* out);
-int bilu_levels(const hdg_ctx* c, int backward);
 void bilu_destroy(hdg_ctx* c);
 // api.cu: the context's trace solve (CG on the assembled S_K, device- or host-driven) and the
 // DIRK(3,3) tableau
