@@ -333,35 +333,23 @@ def run_ours(args):
     s.hdg_enable_stats(False)
     instrumented_ms_per_step = a_i.elapsed_time(b_i) / args.steps
 
-    # end to end through the public API with host buffers: the state (u^n, u^{n-1}) goes
-    # host -> device, one step, and u^{n+1}, u^n come back device -> host, every step.
+    # end to end through the public API with host buffers: the state (u^n, u^{n-1}, lambda) goes
+    # host -> device, one step, and u^{n+1}, u^n, lambda come back device -> host, every step
+    # (the state calls copy straight between the page-locked host buffers and the context)
     u_h = torch.empty(s._fshape, dtype=torch.float64).pin_memory()
     up_h = torch.empty(s._fshape, dtype=torch.float64).pin_memory()
     l_h = torch.empty(s._tshape, dtype=torch.float64).pin_memory()
-    u_d, up_d, l_d = s.empty_fields(), s.empty_fields(), s.empty_traces()
-    _, _, _, t_now = s.hdg_get_state(u=u_d, uprev=up_d, lam=l_d, want_prev=True)
-    u_h.copy_(u_d)
-    up_h.copy_(up_d)
-    l_h.copy_(l_d)
+    _, _, _, t_now = s.hdg_get_state(u=u_h, uprev=up_h, lam=l_h, want_prev=True)
     torch.cuda.synchronize()
     barrier()
     e2e_steps = max(1, min(args.steps, 10 if R == 1 else 3))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with torch.cuda.stream(stream):
-            u_d.copy_(u_h, non_blocking=True)
-            up_d.copy_(up_h, non_blocking=True)
-            l_d.copy_(l_h, non_blocking=True)
-        s.hdg_set_state(u_d, t_now, uprev=up_d, lam=l_d)
+        s.hdg_set_state(u_h, t_now, uprev=up_h, lam=l_h)
         info = s.hdg_step(dt, scheme, 1)
         run["iters"] += info["iterations"]
         run["sweeps"] += info["sweeps"]
-        _, _, _, t_now = s.hdg_get_state(u=u_d, uprev=up_d, lam=l_d, want_prev=True)
-        with torch.cuda.stream(stream):
-            u_h.copy_(u_d, non_blocking=True)
-            up_h.copy_(up_d, non_blocking=True)
-            l_h.copy_(l_d, non_blocking=True)
-        stream.synchronize()
+        _, _, _, t_now = s.hdg_get_state(u=u_h, uprev=up_h, lam=l_h, want_prev=True)
     e2e_s = time.perf_counter() - t0
     run["steps"] += e2e_steps
     e2e_value = world * dofs * e2e_steps / max_over_ranks(dist, e2e_s, "cuda")
@@ -742,24 +730,14 @@ def run_svk(args):
     # end to end through the public API with host buffers: fields and traces in, one step, out
     u_h = torch.empty(s._fshape, dtype=torch.float64).pin_memory()
     l_h = torch.empty(s._tshape, dtype=torch.float64).pin_memory()
-    u_d, l_d = s.empty_fields(), s.empty_traces()
-    _, _, t_now = s.hdg_get_state(u=u_d, lam=l_d)
-    u_h.copy_(u_d)
-    l_h.copy_(l_d)
+    _, _, t_now = s.hdg_get_state(u=u_h, lam=l_h)
     torch.cuda.synchronize()
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        with torch.cuda.stream(stream):
-            u_d.copy_(u_h, non_blocking=True)
-            l_d.copy_(l_h, non_blocking=True)
-        s.hdg_set_state(u_d, t_now, lam=l_d)
+        s.hdg_set_state(u_h, t_now, lam=l_h)
         s.hdg_step(dt, "dirk3", 1)
-        _, _, t_now = s.hdg_get_state(u=u_d, lam=l_d)
-        with torch.cuda.stream(stream):
-            u_h.copy_(u_d, non_blocking=True)
-            l_h.copy_(l_d, non_blocking=True)
-        stream.synchronize()
+        _, _, t_now = s.hdg_get_state(u=u_h, lam=l_h)
     e2e_s = time.perf_counter() - t0
     e2e_value = world * dofs * e2e_steps / max_over_ranks(dist, e2e_s, "cuda")
     fb, tb = int(np.prod(s._fshape)) * 8, int(np.prod(s._tshape)) * 8

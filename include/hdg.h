@@ -335,7 +335,9 @@ hdg_status hdg_set_dirichlet(hdg_ctx* ctx, const double* vals_host, double omega
  * and a new mass shift drop them).
  * hdg_get_state copies the current
  * fields, the previous level and the traces (lam_dev [n_faces][Nf], boundary entries =
- * Dirichlet values); any output pointer may be NULL. Both complete before returning. */
+ * Dirichlet values); any output pointer may be NULL. Both complete before returning. The
+ * buffers of both calls may also be page-locked host memory (cudaHostAlloc /
+ * cudaHostRegister): the copies then run host <-> device on the context stream. */
 hdg_status hdg_set_state(hdg_ctx* ctx, const double* u_dev, const double* uprev_dev, const double* lam_dev,
                          double t);
 hdg_status hdg_get_state(hdg_ctx* ctx, double* u_dev, double* uprev_dev, double* lam_dev, double* t);

@@ -2276,10 +2276,11 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
   if (!c || !u) return fail(c, HDG_EINVAL, "null argument");
   const size_t bytes = (size_t)c->nfld * c->R * 8;
   const size_t tbytes = (size_t)c->ntr * c->R * 8;
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_u, u, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_uprev, uprev ? uprev : u, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  // device or page-locked host buffers (unified addressing decides the direction)
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_u, u, bytes, cudaMemcpyDefault, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_uprev, uprev ? uprev : c->d_u, bytes, cudaMemcpyDefault, c->stream));
   if (lam)
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_lam, lam, tbytes, cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_lam, lam, tbytes, cudaMemcpyDefault, c->stream));
   else
     CUDA_TRY(c, cudaMemsetAsync(c->d_lam, 0, tbytes, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -2294,9 +2295,9 @@ hdg_status hdg_set_state(hdg_ctx* c, const double* u, const double* uprev, const
 hdg_status hdg_get_state(hdg_ctx* c, double* u, double* uprev, double* lam, double* t) {
   if (!c) return HDG_EINVAL;
   const size_t bytes = (size_t)c->nfld * c->R * 8;
-  if (u) CUDA_TRY(c, cudaMemcpyAsync(u, c->d_u, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  if (uprev) CUDA_TRY(c, cudaMemcpyAsync(uprev, c->d_uprev, bytes, cudaMemcpyDeviceToDevice, c->stream));
-  if (lam) CUDA_TRY(c, cudaMemcpyAsync(lam, c->d_lam, (size_t)c->ntr * c->R * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (u) CUDA_TRY(c, cudaMemcpyAsync(u, c->d_u, bytes, cudaMemcpyDefault, c->stream));
+  if (uprev) CUDA_TRY(c, cudaMemcpyAsync(uprev, c->d_uprev, bytes, cudaMemcpyDefault, c->stream));
+  if (lam) CUDA_TRY(c, cudaMemcpyAsync(lam, c->d_lam, (size_t)c->ntr * c->R * 8, cudaMemcpyDefault, c->stream));
   if (t) *t = c->t;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return HDG_OK;

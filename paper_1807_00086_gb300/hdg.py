@@ -426,10 +426,20 @@ class Solver:
         assert vals.shape == (self.n_bnd, self.sizes.nq_face)
         self._check(self.lib.hdg_set_dirichlet(self.ctx, _np_ptr(vals, c_double), omega, phase))
 
+    def _state(self, t, shape):
+        """a CUDA tensor or a page-locked CPU tensor (the state calls copy either way)"""
+        if not t.is_cuda:
+            assert t.dtype == self.torch.float64 and t.is_contiguous() and t.is_pinned(), "pinned float64 CPU tensor"
+            assert t.numel() == int(np.prod(shape)), (tuple(t.shape), shape)
+            return _ptr(t)
+        return self._dev(t, shape)
+
     def hdg_set_state(self, u, t=0.0, uprev=None, lam=None):
+        """u, uprev, lam: CUDA tensors or page-locked CPU tensors."""
         shp = self._fshape
-        self._check(self.lib.hdg_set_state(self.ctx, self._dev(u, shp), None if uprev is None else self._dev(uprev, shp),
-                                           None if lam is None else self._dev(lam, self._tshape), t))
+        self._check(self.lib.hdg_set_state(self.ctx, self._state(u, shp),
+                                           None if uprev is None else self._state(uprev, shp),
+                                           None if lam is None else self._state(lam, self._tshape), t))
 
     def hdg_get_state(self, u=None, uprev=None, lam=None, want_prev=False):
         """Returns (u, lam, t) or, with want_prev, (u, uprev, lam, t); buffers may be passed in."""
@@ -438,8 +448,9 @@ class Solver:
         if want_prev and uprev is None:
             uprev = self.empty_fields()
         t = ctypes.c_double()
-        self._check(self.lib.hdg_get_state(self.ctx, _ptr(u), _ptr(uprev) if uprev is not None else None, _ptr(lam),
-                                           ctypes.byref(t)))
+        self._check(self.lib.hdg_get_state(self.ctx, self._state(u, self._fshape),
+                                           self._state(uprev, self._fshape) if uprev is not None else None,
+                                           self._state(lam, self._tshape), ctypes.byref(t)))
         return (u, uprev, lam, t.value) if want_prev else (u, lam, t.value)
 
     def hdg_enable_stats(self, enable=True):
