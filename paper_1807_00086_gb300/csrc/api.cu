@@ -163,6 +163,18 @@ void launch_pack16(hdg_ctx* c) {
   scale16_kernel<DIM, K><<<grid_for(c, ne * 32), 256, 0, c->stream>>>(ne, c->d_S, c->d_sc16);
   pack16_kernel<DIM, K><<<grid_for(c, ((ne + 31) / 32) * PK::P8 * 256), 256, 0, c->stream>>>(ne, c->d_S, c->d_sc16,
                                                                                                c->d_S16);
+  using C = Apply16Cfg<DIM, K>;
+  const int64_t ng = ((ne + 31) / 32) * 32 * Dims<DIM, K>::NFC;
+  c->n_launch += 1;
+  gface_kernel<<<grid_for(c, ng), 256, 0, c->stream>>>(ng, ne * Dims<DIM, K>::NFC, c->d_elem_face, c->d_face_bnd,
+                                                       c->d_gface16);
+  cudaFuncSetAttribute(apply16_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply16_kernel<DIM, K>, 32 * C::WARPS, C::SMEM) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  c->a16_per_sm = per_sm;
 }
 
 template <int DIM, int K>
@@ -170,8 +182,11 @@ void launch_apply16(hdg_ctx* c, const float* x, float* slot, const int* done, in
   const int64_t ngroups = (c->sk.ne + 31) / 32;
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 3, iter);
-  apply16_kernel<DIM, K><<<(unsigned)((ngroups + 3) / 4), 128, 0, c->stream>>>(
-      c->sk.ne, c->d_elem_face, c->d_face_bnd, c->d_S16, c->d_sc16, x, slot, done, pq_out(c, c->d_dtime + 1));
+  using C = Apply16Cfg<DIM, K>;
+  const unsigned grid = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((ngroups + C::WARPS - 1) / C::WARPS, (int64_t)c->sms * std::max(1, c->a16_per_sm)));
+  apply16_kernel<DIM, K><<<grid, 32 * C::WARPS, C::SMEM, c->stream>>>(c->sk.ne, c->d_gface16, c->d_S16, c->d_sc16, x,
+                                                                      slot, done, pq_out(c, c->d_dtime + 1));
   apply_end(c, stop);
 }
 
@@ -1894,6 +1909,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int32_t k, double tau, const hdg_mate
         const size_t n16 = (size_t)ngroups * P8 * 256;
         if ((s = dalloc(c, &c->d_S16, n16))) return s;
         if ((s = dalloc(c, &c->d_sc16, (size_t)ngroups * 32))) return s;
+        if ((s = dalloc(c, &c->d_gface16, (size_t)ngroups * 32 * c->nfc))) return s;
         CUDA_TRY(c, cudaMemsetAsync(c->d_sc16, 0, (size_t)ngroups * 32 * 4, c->stream));
       }
       CUDA_TRY(c, cudaMemsetAsync(c->d_Sdf, 0, nSdf * 4, c->stream));

@@ -65,6 +65,8 @@ struct hdg_ctx {
   TabsDf tabsdf{};
   __half* d_S16 = nullptr;      // FP16 packed S_K (inner Krylov operator of HDG_MIXED16)
   float* d_sc16 = nullptr;      // its per-element scales
+  int32_t* d_gface16 = nullptr; // its trace gather table [whole groups][nfc] (face id, -1: none)
+  int a16_per_sm = 1;           // resident CTAs per SM of the persistent FP16 apply
   double *d_pqpart = nullptr, *d_pq = nullptr;   // p.q block partials and result of the FP32/FP16 apply
   unsigned* d_ticket = nullptr;                   // last-block counter of that reduction
   DevTiming* d_dtime = nullptr;   // device-side launch timing: [0] FP32 apply, [1] FP16 apply

@@ -949,78 +949,128 @@ __global__ void pack16_kernel(int64_t ne, const double* __restrict__ S, const fl
   }
 }
 
-// slot = S_K x_K with the FP16 copy; the same thread-per-element structure as apply32_kernel
-// (FP32 accumulation, the element scale applied once at the end).
+// Trace gather table of the FP16 apply: gface[e][f] = the id of face f of element e where it
+// carries trace unknowns (an interior face), else -1; rows past the last element are -1
+// (n = whole 32-element groups x NFC).
+static __global__ void gface_kernel(int64_t n, int64_t nval, const int32_t* __restrict__ elem_face,
+                                    const int32_t* __restrict__ face_bnd, int32_t* __restrict__ gface) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    int v = -1;
+    if (t < nval) {
+      const int f = elem_face[t];
+      if (f >= 0 && face_bnd[f] < 0) v = f;
+    }
+    gface[t] = v;
+  }
+}
+
+// Shared memory of the FP16 apply, per warp: the staged traces of the next group (row stride
+// XS floats; each face run is copied by 8-byte asynchronous copies when NF is even, else
+// 4-byte ones) and the transpose buffer of the slot write (row stride MP).
 template <int DIM, int K>
-__global__ void __launch_bounds__(128, 4) apply16_kernel(int64_t ne, const int32_t* __restrict__ elem_face,
-                                                      const int32_t* __restrict__ face_bnd,
+struct Apply16Cfg {
+  static constexpr int NF = Dims<DIM, K>::NF, M = Dims<DIM, K>::M;
+  static constexpr int CPB = NF % 2 == 0 ? 8 : 4;
+  static constexpr int XS = CPB == 8 ? M + 2 : M + 1;
+  static constexpr int MP = M + 1;
+  static constexpr int WARPS = 4;
+  static constexpr size_t SMEM = sizeof(float) * WARPS * 32 * (XS + MP);
+};
+
+// slot = S_K x_K with the FP16 copy (FP32 accumulation, the element scale applied once at the
+// end), one thread per element, one warp per group of 32 elements. Persistent: warps stride
+// over the groups, and the traces of a warp's next group are gathered into shared memory by
+// asynchronous copies (from gface, read one more group ahead) while the current group's S16
+// streams in, so the gather latency is off the streaming path.
+template <int DIM, int K>
+__global__ void __launch_bounds__(128, 4) apply16_kernel(int64_t ne, const int32_t* __restrict__ gface,
                                                       const __half* __restrict__ S16, const float* __restrict__ sc16,
                                                       const float* __restrict__ x, float* __restrict__ slot,
                                                       const int* __restrict__ done, PqOut pqo) {
   using D = Dims<DIM, K>;
   using PK = Packed16<DIM, K>;
-  constexpr int NF = D::NF, M = D::M, NFC = D::NFC, P8 = PK::P8;
-  constexpr int MP = M + 1;
-  __shared__ float tr[4][32 * MP];
+  using C = Apply16Cfg<DIM, K>;
+  constexpr int NF = D::NF, M = D::M, NFC = D::NFC, P8 = PK::P8, XS = C::XS, MP = C::MP, CPB = C::CPB;
+  extern __shared__ __align__(16) float a16sm[];
   if (done && *done) return;
   timing_start(pqo);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t g0 = (int64_t)blockIdx.x * 4 + wid;
-  const bool wact = g0 * 32 < ne;
-  const int64_t g = wact ? g0 : 0;
-  const int64_t e = g0 * 32 + lane;
-  float xl[M], y[M];
+  float* t = a16sm + wid * 32 * (XS + MP) + 32 * XS;
+  const unsigned xrow = (unsigned)__cvta_generic_to_shared(a16sm + wid * 32 * (XS + MP) + lane * XS);
+  const float* xrow_g = a16sm + wid * 32 * (XS + MP) + lane * XS;
+  const int64_t ngroups = (ne + 31) / 32;
+  const int64_t nw = (int64_t)gridDim.x * C::WARPS;
+  int gf[NFC];
+  auto load_gf = [&](int64_t gg) {
 #pragma unroll
-  for (int f = 0; f < NFC; ++f) {
-    int fid = -1;
-    if (e < ne) fid = elem_face[e * NFC + f];
-    const bool use = fid >= 0 && face_bnd[fid] < 0;
+    for (int f = 0; f < NFC; ++f) gf[f] = gg < ngroups ? gface[(gg * 32 + lane) * NFC + f] : -1;
+  };
+  // this lane's traces into its own row (zeros where gf < 0); only this lane reads the row
+  auto issue = [&]() {
 #pragma unroll
-    for (int mm = 0; mm < NF; ++mm) xl[f * NF + mm] = use ? x[(int64_t)fid * NF + mm] : 0.f;
-  }
+    for (int f = 0; f < NFC; ++f) {
+      const float* src = gf[f] >= 0 ? x + (int64_t)gf[f] * NF : x;
+      const unsigned nb = gf[f] >= 0 ? CPB : 0;
 #pragma unroll
-  for (int r = 0; r < M; ++r) y[r] = 0.f;
-  const uint4* Sg = reinterpret_cast<const uint4*>(S16) + g * (int64_t)P8 * 32 + lane;
-  float sv[8];
-#pragma unroll
-  for (int r = 0; r < M; ++r) {
-#pragma unroll
-    for (int c = r; c < M; ++c) {
-      const int p = packed_index(M, r, c);
-      if ((p & 7) == 0) {
-        const uint4 u = __ldcs(Sg + (p >> 3) * 32);
-        const unsigned w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&w4[h]));
-          sv[2 * h] = f2.x;
-          sv[2 * h + 1] = f2.y;
-        }
-      }
-      const float s = sv[p & 7];
-      y[r] = fmaf(s, xl[c], y[r]);
-      if (c != r) y[c] = fmaf(s, xl[r], y[c]);
+      for (int j = 0; j < NF * 4 / CPB; ++j)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(xrow + 4 * f * NF + CPB * j),
+                     "l"(src + (CPB / 4) * j), "n"(CPB), "r"(nb)
+                     : "memory");
     }
-  }
-  const float scl = e < ne ? sc16[e] : 0.f;
-  float* t = tr[wid];
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int64_t g = (int64_t)blockIdx.x * C::WARPS + wid;
+  load_gf(g);
+  issue();
+  load_gf(g + nw);
+  Acc2 a;
+  for (; g < ngroups; g += nw) {
+    const int64_t e = g * 32 + lane;
+    const float scl = e < ne ? sc16[e] : 0.f;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    float xl[M], y[M];
 #pragma unroll
-  for (int r = 0; r < M; ++r) {
-    y[r] *= scl;
-    t[lane * MP + r] = y[r];
-  }
-  __syncwarp();
-  if (wact) {
+    for (int r = 0; r < M; ++r) xl[r] = xrow_g[r];
+    issue();              // the next group's traces
+    load_gf(g + 2 * nw);  // and the group after it's gather table
+#pragma unroll
+    for (int r = 0; r < M; ++r) y[r] = 0.f;
+    const uint4* Sg = reinterpret_cast<const uint4*>(S16) + g * (int64_t)P8 * 32 + lane;
+    float sv[8];
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+#pragma unroll
+      for (int c = r; c < M; ++c) {
+        const int p = packed_index(M, r, c);
+        if ((p & 7) == 0) {
+          const uint4 u = __ldcs(Sg + (p >> 3) * 32);
+          const unsigned w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&w4[h]));
+            sv[2 * h] = f2.x;
+            sv[2 * h + 1] = f2.y;
+          }
+        }
+        const float s = sv[p & 7];
+        y[r] = fmaf(s, xl[c], y[r]);
+        if (c != r) y[c] = fmaf(s, xl[r], y[c]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      y[r] *= scl;
+      t[lane * MP + r] = y[r];
+      a.dot(xl[r], y[r]);
+    }
+    __syncwarp();
     const int64_t nvalid = (ne - g * 32) < 32 ? (ne - g * 32) : 32;
     float* dst = slot + g * 32 * (int64_t)M;
     for (int idx = lane; idx < nvalid * M; idx += 32) dst[idx] = t[(idx / M) * MP + idx % M];
+    __syncwarp();   // the transpose buffer is rewritten by the next group
   }
-  if (pqo.part) {
-    Acc2 a;
-#pragma unroll
-    for (int r = 0; r < M; ++r) a.dot(xl[r], y[r]);
-    pq_epilogue(pqo, a.value());
-  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  if (pqo.part) pq_epilogue(pqo, a.value());
 }
 
 // q = sgn K32 p on faces; partial p.q in FP64. NF is compile-time (no integer division).
