@@ -191,13 +191,13 @@ void launch_apply16(hdg_ctx* c, const float* x, float* slot, const int* done, in
 }
 
 template <int DIM, int K>
-void launch_apply_df(hdg_ctx* c, const double* x, double* zslot) {
+void launch_apply_df(hdg_ctx* c, const double* x, double* zslot, const int* skip = nullptr) {
   using C = ApplyDfCfg<DIM, K>;
   const int64_t ngroups = (c->sk.ne + C::EPB - 1) / C::EPB;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ngroups, (int64_t)c->sms * std::max(1, c->df_per_sm)));
   c->n_launch += 1;
   cudaEvent_t stop = apply_begin(c, 2, -1);
-  apply_df_kernel<DIM, K><<<grid, C::NT, C::SMEM, c->stream>>>(devmesh(c), c->d_Sdf, x, zslot, ngroups);
+  apply_df_kernel<DIM, K><<<grid, C::NT, C::SMEM, c->stream>>>(devmesh(c), c->d_Sdf, x, zslot, ngroups, skip);
   apply_end(c, stop);
 }
 
@@ -429,7 +429,7 @@ hdg_status solve_mixed(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
     }
     c->n_launch += 2;
     refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec,
-                                                      c->d_res, c->d_part);
+                                                      c->d_res, c->d_part, nullptr);
     refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
     if ((s = check_launch(c, "refine_residual"))) return s;
     CUDA_TRY(c, cudaMemcpyAsync(c->h_rs, c->d_rs, sizeof(RefScal), cudaMemcpyDeviceToHost, c->stream));
@@ -518,6 +518,10 @@ hdg_status solve_mixed_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solv
   const int nb = c->nb_red, maxit = c->opt.maxit;
   const int64_t n4 = c->nfe4 / 4;
   const bool has16 = c->d_S16 != nullptr;
+  // x = sum c_i lam_i from the least-squares guess just before this solve: the first residual
+  // comes from the stored pairs instead of an apply (acoustic double-float path)
+  const bool from_guess = c->guess_x && c->g_q && c->d_Sdf && c->phys == HDG_ACOUSTIC && c->R == 1;
+  const int* skip = from_guess ? &c->d_lc->skip_res : nullptr;
   auto inner = [&](bool use16, cudaGraphConditionalHandle h) {
     for (int par = 0; par < 2; ++par) {
       if (use16) {
@@ -546,6 +550,11 @@ hdg_status solve_mixed_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solv
     gb.seq(G, deps, [&] {
       c->n_launch += 1;
       loopctl_init_kernel<<<1, 32, 0, c->stream>>>(c->d_lc, has16 ? 1 : 0);
+      if (from_guess) {
+        c->n_launch += 1;
+        gresidual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->d_face_bnd, c->d_gd, c->d_gb, bvec, c->d_res,
+                                                    c->d_part, c->d_lc);
+      }
     });
     const cudaGraphConditionalHandle h_sweep = gb.handle(G, 1, true);
     cudaGraph_t B = gb.loop(G, deps, h_sweep);
@@ -554,13 +563,13 @@ hdg_status solve_mixed_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solv
     const int64_t n1 = c->n_launch;
     gb.seq(B, bd, [&] {
       if (c->d_Sdf) {
-        HDG_DISPATCH(c, launch_apply_df, c, x, c->d_slot);
+        HDG_DISPATCH(c, launch_apply_df, c, x, c->d_slot, skip);
       } else {
         HDG_DISPATCH(c, launch_apply, c, x, c->d_slot, (const int*)nullptr, -1);
       }
       c->n_launch += 6;
       refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot,
-                                                        bvec, c->d_res, c->d_part);
+                                                        bvec, c->d_res, c->d_part, skip);
       refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
       sweep_ctl_kernel<<<1, 32, 0, c->stream>>>(c->d_rs, c->d_sc, c->d_lc, c->opt.rtol, c->opt.inner_rtol,
                                                 c->opt.max_sweeps, h_sweep, has16 ? 1 : 0, h16, h32);
@@ -592,7 +601,7 @@ hdg_status solve_mixed_graph(hdg_ctx* c, const double* bvec, double* x, hdg_solv
     dg.n_body = (n2 - n1) + (n5 - n4_);
     dg.n_trip = n4_ - n3;
   };
-  return devgraph_solve(c, 1, bvec, x, build, info);
+  return devgraph_solve(c, from_guess ? 8 : 1, bvec, x, build, info);
 }
 
 // ---- continuous traces: device-driven solves of (sgn R^T K R) mu = b_mu on the free nodes
@@ -799,7 +808,7 @@ hdg_status gmres_solve(hdg_ctx* c, const double* bvec, double* x, hdg_solve_info
     HDG_DISPATCH(c, launch_apply, c, (const double*)x, c->d_slot, (const int*)nullptr, -1);
     c->n_launch += 2;
     refine_residual_kernel<<<nb, 256, 0, c->stream>>>(c->sk.nf, c->Nf, c->sgn, c->d_face_slot, c->d_face_bnd, c->d_slot, bvec,
-                                                      c->d_res, c->d_part);
+                                                      c->d_res, c->d_part, nullptr);
     refine_scalars<<<1, 256, 0, c->stream>>>(nb, c->d_part, c->d_rs);
     CUDA_TRY(c, cudaMemcpyAsync(c->h_rs, c->d_rs, sizeof(RefScal), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1371,7 +1380,10 @@ hdg_status stage_solve(hdg_ctx* c, const double* hist, double tt, double* uout, 
     return check_launch(c, "recover");
   }
   if ((s = guess_before(c))) return s;
-  if ((s = cg_solve(c, c->d_b, c->d_lam, info))) return s;
+  c->guess_x = true;
+  s = cg_solve(c, c->d_b, c->d_lam, info);
+  c->guess_x = false;
+  if (s) return s;
   if ((s = guess_after(c))) return s;
   HDG_DISPATCH(c, launch_local, c, 1, (const double*)nullptr, hist, tt, c->d_lam, uout);
   return check_launch(c, "recover");

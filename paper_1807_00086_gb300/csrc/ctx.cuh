@@ -145,6 +145,7 @@ struct hdg_ctx {
     double alpha;                       // mass shift baked into a whole-step graph (0 for a solve)
   };
   std::vector<DevGraph> dgraphs;
+  bool guess_x = false;   // the solve being issued starts from the least-squares guess of its b
   StepAcc* d_sacc = nullptr;   // totals of a graph-launched step, and their pinned host copy
   StepAcc* h_sacc = nullptr;
   // continuous traces (IEDG / EDG): free face nodes, the node map and its incidence lists, the

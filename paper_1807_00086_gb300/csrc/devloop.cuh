@@ -24,6 +24,7 @@ struct LoopCtl {
   int use16;              // inner operator of the next sweep: 1 FP16 copy, 0 FP32 copy
   int stop;               // 0 running, 1 converged, 2 zero right-hand side, 3 max_sweeps, 4 maxit
   int total_it;           // inner iterations summed over the finished sweeps
+  int skip_res;           // the next residual is already in place (taken from the guess's pairs)
 };
 
 // Refinement sweep control, one thread, after the FP64 residual of a sweep (rs): records the
@@ -44,9 +45,12 @@ static __global__ void sweep_ctl_kernel(const RefScal* __restrict__ rs, const Cg
     L->rel_prev = L->rel;
     L->rel = sqrt(rs->rr / rs->bb);
     if (L->use16 && L->sweep > 0 && L->rel > 0.1 * L->rel_prev) L->use16 = 0;
-    if (L->rel <= rtol) stop = 1;
+    // a residual taken from the guess's pairs is accurate only to the tolerance the pairs
+    // were solved to, so it never ends the solve: the stop test waits for a computed one
+    if (L->rel <= rtol && !L->skip_res) stop = 1;
     else if (L->sweep >= max_sweeps) stop = 3;
   }
+  L->skip_res = 0;
   if (!stop) {
     L->tol = fmin(0.5, fmax(inner_rtol, 0.25 * rtol / L->rel));
     L->sweep += 1;
@@ -78,7 +82,7 @@ static __global__ void zero_masked_if_kernel(int64_t n, const uint8_t* __restric
 static __global__ void loopctl_init_kernel(LoopCtl* L, int use16) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   L->rel = 0.0; L->rel_prev = 0.0; L->tol = 0.5;
-  L->sweep = 0; L->use16 = use16; L->stop = 0; L->total_it = 0;
+  L->sweep = 0; L->use16 = use16; L->stop = 0; L->total_it = 0; L->skip_res = 0;
 }
 
 // Totals of the trace solves inside one graph-launched time step.
@@ -197,6 +201,43 @@ static __global__ void glincomb_kernel(int64_t n, const GuessDev* __restrict__ g
       if (i < m) v += c[i] * ring[i * n + t];
     lam[t] = v;
   }
+}
+
+// The refinement's first residual without an apply, when lam0 = sum c_i lam_i came from the
+// guess: K lam_i = b_i up to the pairs' solve tolerance, so b - K lam0 = b - sum c_i b_i on
+// interior entries (0 on the others). Same output and block partials (|rho|^2, |b|^2) as
+// refine_residual_kernel; sets L->skip_res so that the sweep's own residual kernels stand
+// aside. Does nothing when the coefficients are not valid.
+static __global__ void gresidual_kernel(int64_t nf, int NF, const int32_t* __restrict__ face_bnd,
+                                        const GuessDev* __restrict__ g, const double* __restrict__ ring,
+                                        const double* __restrict__ b, double* __restrict__ rho,
+                                        double* __restrict__ part, LoopCtl* L) {
+  if (!g->ok) return;
+  __shared__ double red[8];
+  const int m = g->n;
+  const int64_t n = nf * NF;
+  double c[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) c[i] = i < m ? g->coef[i] : 0.0;
+  double rr = 0, bb = 0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (face_bnd[t / NF] < 0) {
+      const double bv = b[t];
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (i < m) s += c[i] * ring[i * n + t];
+      v = bv - s;
+      bb += bv * bv;
+    }
+    rho[t] = v;
+    rr += v * v;
+  }
+  double s;
+  s = block_sum256(rr, red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 0] = s;
+  s = block_sum256(bb, red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 1] = s;
+  if (blockIdx.x == 0 && threadIdx.x == 0) L->skip_res = 1;
 }
 
 // stores (b, lam) of the solve just finished in ring slot g->next

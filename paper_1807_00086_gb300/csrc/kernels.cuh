@@ -1275,7 +1275,8 @@ static __global__ void cg32_direction_kernel(int64_t n4, int nb, int parity, int
 static __global__ void refine_residual_kernel(int64_t nf, int NF, double sgn, const int32_t* __restrict__ face_slot,
                                        const int32_t* __restrict__ face_bnd, const double* __restrict__ zslot,
                                        const double* __restrict__ b, double* __restrict__ rho,
-                                       double* __restrict__ part) {
+                                       double* __restrict__ part, const int* __restrict__ skip) {
+  if (skip && *skip) return;   // rho and the partials are already in place
   __shared__ double red[8];
   const int64_t n = nf * NF;
   double rr = 0, bb = 0;
@@ -1415,9 +1416,11 @@ struct ApplyDfCfg {
 template <int DIM, int K>
 __global__ void __launch_bounds__(ApplyDfCfg<DIM, K>::NT) apply_df_kernel(DevMesh mesh, const float* __restrict__ Sdf,
                                                                          const double* __restrict__ x,
-                                                                         double* __restrict__ zslot, int64_t ngroups) {
+                                                                         double* __restrict__ zslot, int64_t ngroups,
+                                                                         const int* __restrict__ skip) {
   using D = Dims<DIM, K>;
   using C = ApplyDfCfg<DIM, K>;
+  if (skip && *skip) return;   // the residual this apply serves is already in place
   constexpr int NF = D::NF, M = D::M, NFC = D::NFC, EPB = C::EPB, PD = C::PD;
   extern __shared__ __align__(16) float dsm[];
   df2* lx = reinterpret_cast<df2*>(dsm + 2 * C::STAGE);   // [EPB][M]
