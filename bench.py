@@ -406,7 +406,14 @@ def run_ours(args):
     if R > 1:
         if args.prec != "fp64":
             a32 = st["apply32_ms"] / max(1, st["apply32_launches"])
-            roof_multi = hbm_line("apply32m_kernel<3,3> (FP32 packed S_K, %d columns)" % R, alg_bytes(4, 0, 4, R), a32,
+            if R in (32, 64):
+                kname = ("apply_tc_pq_kernel<3,3,%d> (S_K x the %d-column trace block on the tensor cores, TF32 "
+                         "mma.sync with split X; p.q and alpha in its epilogue)" % (R, R))
+            elif R > 64:
+                kname = "apply_tc_kernel<3,3,64> (S_K x the %d-column trace block on the tensor cores)" % R
+            else:
+                kname = "apply_multi_kernel<3,3,float> (FP32 packed S_K, %d columns)" % R
+            roof_multi = hbm_line(kname, alg_bytes(4, 0, 4, R), a32,
                                   st["apply32_launches"],
                                   {"implementation_bytes_per_elem": ((P + 3) // 4) * 16 + 2 * m * R * 4,
                                    "flops_per_elem": 2 * m * m * R})

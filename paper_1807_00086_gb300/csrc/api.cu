@@ -217,9 +217,17 @@ void attr_apply_df(hdg_ctx* c) {
 // dynamic shared memory of the tensor-core column-block apply (set outside any stream capture)
 template <int DIM, int K>
 void attr_apply_tc(hdg_ctx* c) {
-  (void)c;
+  using CP = ApplyTcPCfg<DIM, K>;
   cudaFuncSetAttribute(apply_tc_kernel<DIM, K, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ApplyTcCfg<DIM, K>::SMEM);
   cudaFuncSetAttribute(apply_tc_kernel<DIM, K, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ApplyTcCfg<DIM, K>::SMEM);
+  cudaFuncSetAttribute(apply_tc_pq_kernel<DIM, K, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP::SMEM);
+  cudaFuncSetAttribute(apply_tc_pq_kernel<DIM, K, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CP::SMEM);
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_tc_pq_kernel<DIM, K, 64>, 32 * CP::WPB, CP::SMEM) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  c->tcp_per_sm = per_sm;
 }
 
 template <int DIM, int K>
@@ -981,10 +989,11 @@ void mlaunch_local(hdg_ctx* c, int mode, const double* F, const double* hist, do
   const SrcArgs sa = srcargs(c, t);
   c->n_launch += 1;
   // as many columns per CTA as the batch has (up to the kernel's width)
+  // (the double-float kernels of the mixed path take at most 16, for three CTAs per SM)
   if (c->R <= 2) mlaunch_local_cw<DIM, K, 2>(c, mode, F, hist, sa, lam, out);
   else if (c->R <= 4) mlaunch_local_cw<DIM, K, 4>(c, mode, F, hist, sa, lam, out);
   else if (c->R <= 8) mlaunch_local_cw<DIM, K, 8>(c, mode, F, hist, sa, lam, out);
-  else if (c->R <= 16) mlaunch_local_cw<DIM, K, 16>(c, mode, F, hist, sa, lam, out);
+  else if (c->R <= 16 || c->d_Hinvdf) mlaunch_local_cw<DIM, K, 16>(c, mode, F, hist, sa, lam, out);
   else mlaunch_local_cw<DIM, K, 32>(c, mode, F, hist, sa, lam, out);
 }
 
@@ -1062,7 +1071,14 @@ void mlaunch_face_q(hdg_ctx* c, const TV* slot, const TV* p, TV* q) {
 template <int DIM, int K>
 void mlaunch_face_q64(hdg_ctx* c, const double* slot, const double* p, double* q) { mlaunch_face_q<DIM, K, double>(c, slot, p, q); }
 template <int DIM, int K>
-void mlaunch_face_q32(hdg_ctx* c, const float* slot, const float* p, float* q) { mlaunch_face_q<DIM, K, float>(c, slot, p, q); }
+void mlaunch_face_q32(hdg_ctx* c, const float* slot, const float* p, float* q) {
+  if (c->R % 4 == 0)
+    mface_q4_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->R, (const int2*)c->d_face_slot,
+                                                               c->d_face_bnd, (const float4*)slot, (const float4*)p,
+                                                               (float4*)q, c->d_part, c->d_mdone);
+  else
+    mlaunch_face_q<DIM, K, float>(c, slot, p, q);
+}
 
 template <int DIM, int K, typename TV>
 void mlaunch_init(hdg_ctx* c, const TV* slot, const TV* b, const TV* dinv, TV* r, TV* z, TV* p) {
@@ -1089,10 +1105,99 @@ void mlaunch_gather(hdg_ctx* c, const double* slot, double scale, double* out) {
 template <int DIM, int K>
 void mlaunch_refres(hdg_ctx* c, const double* b) {
   c->n_launch += 2;
-  mrefine_residual_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->R, c->d_face_slot, c->d_face_bnd,
-                                                                     c->d_mslot, b, c->d_res, c->d_part);
+  if (c->R % 2 == 0 && aligned16(b))
+    mrefine_residual2_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->R, (const int2*)c->d_face_slot,
+                                                                        c->d_face_bnd, (const double2*)c->d_mslot,
+                                                                        (const double2*)b, (double2*)c->d_res, c->d_part);
+  else
+    mrefine_residual_kernel<DIM, K><<<c->nb_red, 256, 0, c->stream>>>((int)c->sk.nf, c->R, c->d_face_slot, c->d_face_bnd,
+                                                                       c->d_mslot, b, c->d_res, c->d_part);
   mrefine_scalars<<<1, 256, 0, c->stream>>>(c->nb_red, c->R, c->opt.rtol, c->d_part, c->d_mrr2, c->d_mbb2, c->d_mscale,
                                             c->d_mnconv);
+}
+
+// Column-block update and direction of the per-column PCG. FP32 with R a multiple of 4: four
+// columns per thread (z is not stored, the direction forms it again); otherwise one column per
+// thread. The overloads keep mcg generic in the vector type.
+void mupdate_cols(hdg_ctx* c, int64_t n, const float* p, const float* q, const float* dinv, float* x, float* r, float* z) {
+  if (c->R % 4 == 0)
+    mupdate4_kernel<<<c->nb_red, 256, 0, c->stream>>>(n / 4, c->R, (const float4*)p, (const float4*)q, dinv, (float4*)x,
+                                                      (float4*)r, c->d_part, mscal(c));
+  else
+    mupdate_kernel<float><<<c->nb_red, 256, 0, c->stream>>>(n, c->R, p, q, dinv, x, r, z, c->d_part, mscal(c));
+}
+void mupdate_cols(hdg_ctx* c, int64_t n, const double* p, const double* q, const double* dinv, double* x, double* r,
+                  double* z) {
+  mupdate_kernel<double><<<c->nb_red, 256, 0, c->stream>>>(n, c->R, p, q, dinv, x, r, z, c->d_part, mscal(c));
+}
+void mdirection_cols(hdg_ctx* c, int64_t n, const float* r, const float* z, const float* dinv, float* p) {
+  if (c->R % 4 == 0)
+    mdirection4_kernel<<<c->nb_red, 256, 0, c->stream>>>(n / 4, c->R, (const float4*)r, dinv, (float4*)p, c->d_mbeta,
+                                                         c->d_mdone);
+  else
+    mdirection_kernel<float><<<c->nb_red, 256, 0, c->stream>>>(n, c->R, z, p, c->d_mbeta, c->d_mdone);
+}
+void mdirection_cols(hdg_ctx* c, int64_t n, const double* r, const double* z, const double* dinv, double* p) {
+  mdirection_kernel<double><<<c->nb_red, 256, 0, c->stream>>>(n, c->R, z, p, c->d_mbeta, c->d_mdone);
+}
+
+// Ends of a refinement sweep: the inner right-hand side b32 = fl32(rho / |rho|_j), and
+// lam += x32 |rho|_j; four columns per thread when R is a multiple of 4 (and lam 16-byte aligned)
+void mto32_cols(hdg_ctx* c, int64_t n) {
+  if (c->R % 4 == 0)
+    mto32_scaled4_kernel<<<grid_for(c, n / 4), 256, 0, c->stream>>>(n / 4, c->R, (const double2*)c->d_res, c->d_mscale,
+                                                                    (float4*)c->d_b32);
+  else
+    mto32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->R, c->d_res, c->d_mscale, c->d_b32);
+}
+void mrefine_update_cols(hdg_ctx* c, int64_t n, double* lam) {
+  if (c->R % 4 == 0 && aligned16(lam))
+    mrefine_update4_kernel<<<grid_for(c, n / 4), 256, 0, c->stream>>>(n / 4, c->R, c->Nf, c->d_face_bnd,
+                                                                      (const float4*)c->d_x32, c->d_mscale, (double2*)lam);
+  else
+    mrefine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->R, c->Nf, c->d_face_bnd, c->d_x32, c->d_mscale, lam);
+}
+
+// One FP32 iteration of the inner column-block PCG on the context's FP32 vectors (p32, x32,
+// r32, slots32), iteration parity par. R = 32 or 64: the persistent tensor-core apply forms
+// (p, q) and alpha in its epilogue and the update reads q from the slots (4 launches). Other R:
+// apply, face pass with (p, q), alpha, update (6 launches). dev != 0: the beta kernel also sets
+// the device-driven loop's condition h.
+template <int DIM, int K>
+void m_iter32(hdg_ctx* c, int par, int maxit, int dev, cudaGraphConditionalHandle h, int iter) {
+  const int64_t n = c->sk.nf * c->Nf * (int64_t)c->R;
+  const int nb = c->nb_red, R = c->R;
+  if (R == 32 || R == 64) {
+    using CP = ApplyTcPCfg<DIM, K>;
+    const int64_t nq = (c->sk.ne + CP::WPB - 1) / CP::WPB;
+    // CTA partials [grid][R] fit the partials buffer ([3 nb_red][R])
+    const int64_t g = std::min<int64_t>(std::min<int64_t>(nq, (int64_t)c->tcp_per_sm * c->sms), 3 * (int64_t)nb);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, g);
+    const MPqOut o{c->d_part, c->d_ticket, mscal(c), par};
+    c->n_launch += 4;
+    cudaEvent_t stop = apply_begin(c, 1, iter);
+    if (R == 32)
+      apply_tc_pq_kernel<DIM, K, 32><<<grid, 32 * CP::WPB, CP::SMEM, c->stream>>>(
+          c->sk.ne, c->d_elem_face, c->d_face_bnd, (const float4*)c->d_S32, c->d_p32, c->d_mslot32, o);
+    else
+      apply_tc_pq_kernel<DIM, K, 64><<<grid, 32 * CP::WPB, CP::SMEM, c->stream>>>(
+          c->sk.ne, c->d_elem_face, c->d_face_bnd, (const float4*)c->d_S32, c->d_p32, c->d_mslot32, o);
+    apply_end(c, stop);
+    mupdate4s_kernel<DIM, K><<<nb, 256, 0, c->stream>>>((int)c->sk.nf, R, (const int2*)c->d_face_slot, c->d_face_bnd,
+                                                         (const float4*)c->d_mslot32, (const float4*)c->d_p32,
+                                                         c->d_dinv32, (float4*)c->d_x32, (float4*)c->d_r32, c->d_part,
+                                                         mscal(c));
+    mcols_beta<<<1, 256, 0, c->stream>>>(nb, R, par, maxit, c->d_part, mscal(c), c->d_mbeta, dev, h);
+    mdirection_cols(c, n, c->d_r32, c->d_z32, c->d_dinv32, c->d_p32);
+    return;
+  }
+  c->n_launch += 5;
+  mlaunch_apply32<DIM, K>(c, (const float*)c->d_p32, c->d_mslot32, c->d_mdone, iter);
+  mlaunch_face_q32<DIM, K>(c, (const float*)c->d_mslot32, (const float*)c->d_p32, c->d_q32);
+  mcols_alpha<<<1, 256, 0, c->stream>>>(nb, R, par, c->d_part, mscal(c));
+  mupdate_cols(c, n, c->d_p32, c->d_q32, c->d_dinv32, c->d_x32, c->d_r32, c->d_z32);
+  mcols_beta<<<1, 256, 0, c->stream>>>(nb, R, par, maxit, c->d_part, mscal(c), c->d_mbeta, dev, h);
+  mdirection_cols(c, n, c->d_r32, c->d_z32, c->d_dinv32, c->d_p32);
 }
 
 // Per-column PCG on (-K) x = b. FP64 (outer, x holds the initial guess) or FP32 (inner, x0 = 0).
@@ -1133,18 +1238,17 @@ hdg_status mcg(hdg_ctx* c, const TV* b, TV* x, TV* r, TV* z, TV* p, TV* q, TV* s
   auto issue = [&](int it0, int count) {
     for (int i = it0; i < it0 + count; ++i) {
       const int par = i & 1;
-      c->n_launch += 5;
-      if (sizeof(TV) == 8) {
-        HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)p, (double*)slot, c->d_mdone, i);
-        HDG_DISPATCH(c, mlaunch_face_q64, c, (const double*)slot, (const double*)p, (double*)q);
-      } else {
-        HDG_DISPATCH(c, mlaunch_apply32, c, (const float*)p, (float*)slot, c->d_mdone, i);
-        HDG_DISPATCH(c, mlaunch_face_q32, c, (const float*)slot, (const float*)p, (float*)q);
+      if (sizeof(TV) == 4) {   // the inner solve runs on the context's FP32 vectors
+        HDG_DISPATCH(c, m_iter32, c, par, maxit, 0, cudaGraphConditionalHandle{}, i);
+        continue;
       }
+      c->n_launch += 5;
+      HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)p, (double*)slot, c->d_mdone, i);
+      HDG_DISPATCH(c, mlaunch_face_q64, c, (const double*)slot, (const double*)p, (double*)q);
       mcols_alpha<<<1, 256, 0, c->stream>>>(nb, c->R, par, c->d_part, mscal(c));
-      mupdate_kernel<TV><<<nb, 256, 0, c->stream>>>(n, c->R, p, q, dinv, x, r, z, c->d_part, mscal(c));
+      mupdate_cols(c, n, p, q, dinv, x, r, z);
       mcols_beta<<<1, 256, 0, c->stream>>>(nb, c->R, par, maxit, c->d_part, mscal(c), c->d_mbeta, 0, 0);
-      mdirection_kernel<TV><<<nb, 256, 0, c->stream>>>(n, c->R, z, p, c->d_mbeta, c->d_mdone);
+      mdirection_cols(c, n, r, z, dinv, p);
     }
   };
   // graph mode: chunks of GCH iterations (even, so the parity pattern repeats) captured once
@@ -1203,16 +1307,10 @@ hdg_status msolve_graph(hdg_ctx* c, const double* b, double* x, hdg_solve_info* 
   const bool mixed = c->opt.prec != HDG_FP64;
   auto iters = [&](bool f32, cudaGraphConditionalHandle h) {
     for (int par = 0; par < 2; ++par) {
-      c->n_launch += 5;
       if (f32) {
-        HDG_DISPATCH(c, mlaunch_apply32, c, (const float*)c->d_p32, c->d_mslot32, c->d_mdone, -1);
-        HDG_DISPATCH(c, mlaunch_face_q32, c, (const float*)c->d_mslot32, (const float*)c->d_p32, c->d_q32);
-        mcols_alpha<<<1, 256, 0, c->stream>>>(nb, R, par, c->d_part, mscal(c));
-        mupdate_kernel<float><<<nb, 256, 0, c->stream>>>(n, R, c->d_p32, c->d_q32, c->d_dinv32, c->d_x32, c->d_r32,
-                                                         c->d_z32, c->d_part, mscal(c));
-        mcols_beta<<<1, 256, 0, c->stream>>>(nb, R, par, maxit, c->d_part, mscal(c), c->d_mbeta, 1, h);
-        mdirection_kernel<float><<<nb, 256, 0, c->stream>>>(n, R, c->d_z32, c->d_p32, c->d_mbeta, c->d_mdone);
+        HDG_DISPATCH(c, m_iter32, c, par, maxit, 1, h, -1);
       } else {
+        c->n_launch += 5;
         HDG_DISPATCH(c, mlaunch_apply64, c, (const double*)c->d_p, c->d_mslot, c->d_mdone, -1);
         HDG_DISPATCH(c, mlaunch_face_q64, c, (const double*)c->d_mslot, (const double*)c->d_p, c->d_q);
         mcols_alpha<<<1, 256, 0, c->stream>>>(nb, R, par, c->d_part, mscal(c));
@@ -1260,7 +1358,7 @@ hdg_status msolve_graph(hdg_ctx* c, const double* b, double* x, hdg_solve_info* 
       HDG_DISPATCH(c, mlaunch_refres, c, b);
       c->n_launch += 4;
       msweep_ctl_kernel<<<1, 32, 0, c->stream>>>(c->d_mnconv, c->d_miters, c->d_lc, c->opt.max_sweeps, h_sweep, h_in);
-      mto32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, R, c->d_res, c->d_mscale, c->d_b32);
+      mto32_cols(c, n);
       cudaMemsetAsync(c->d_x32, 0, (size_t)n * sizeof(float), c->stream);
       HDG_DISPATCH(c, mlaunch_init32, c, (const float*)nullptr, (const float*)c->d_b32, (const float*)c->d_dinv32,
                    c->d_r32, c->d_z32, c->d_p32);
@@ -1273,7 +1371,7 @@ hdg_status msolve_graph(hdg_ctx* c, const double* b, double* x, hdg_solve_info* 
     const int64_t n3 = c->n_launch;
     gb.seq(B, bd, [&] {
       c->n_launch += 1;
-      mrefine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, R, c->Nf, c->d_face_bnd, c->d_x32, c->d_mscale, x);
+      mrefine_update_cols(c, n, x);
     });
     const int64_t n4 = c->n_launch;
     dg.n_static = n1 - n0;
@@ -1329,14 +1427,14 @@ hdg_status msolve(hdg_ctx* c, const double* b, double* x, hdg_solve_info* info) 
       return HDG_OK;
     }
     c->n_launch += 1;
-    mto32_scaled_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->R, c->d_res, c->d_mscale, c->d_b32);
+    mto32_cols(c, n);
     int it = 0;
     if ((s = mcg<float>(c, c->d_b32, c->d_x32, c->d_r32, c->d_z32, c->d_p32, c->d_q32, c->d_mslot32, c->d_dinv32,
                         c->opt.inner_rtol, true, &it)))
       if (s != HDG_ENOCONV) return s;
     total += it;
     c->n_launch += 1;
-    mrefine_update_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, c->R, c->Nf, c->d_face_bnd, c->d_x32, c->d_mscale, x);
+    mrefine_update_cols(c, n, x);
     if ((s = check_launch(c, "mrefine_update"))) return s;
   }
 }

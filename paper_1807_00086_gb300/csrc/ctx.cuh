@@ -56,6 +56,7 @@ struct hdg_ctx {
   CgScal* h_sc = nullptr;   // pinned
   int nb_red = 0;
   int df_per_sm = 1;            // resident CTAs per SM of the persistent double-float apply
+  int tcp_per_sm = 1;           // resident CTAs per SM of the persistent tensor-core column-block apply
   // mixed precision
   float *d_S32 = nullptr, *d_dinv32 = nullptr, *d_slot32 = nullptr;
   float* d_Sdf = nullptr;       // double-float diagonal-major copy of S_K (refinement apply)
@@ -203,6 +204,9 @@ hdg_status check_launch(hdg_ctx* c, const char* what) {
   if (e != cudaSuccess) return fail(c, HDG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
   return HDG_OK;
 }
+
+// a caller's device pointer may be read as 16-byte vectors only when it is 16-byte aligned
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int grid_for(const hdg_ctx* c, int64_t n, int block = 256) {
   int64_t g = (n + block - 1) / block;

@@ -254,8 +254,10 @@ __global__ void __launch_bounds__(LocalDfCfg<DIM, K>::NT)
 // R-column version (the multi-source and serving batches): CTA = one element x CW columns x
 // NP rows, the layouts and work split of local_multi_kernel, every operation as in
 // local_df_kernel (double-float products and sums on the FP32 pipe).
+// Up to 320 threads per CTA the kernel is bounded to three resident CTAs per SM (64 registers):
+// at its natural 96 registers a 640-thread CTA (32 columns of a 20-row element) held an SM alone.
 template <int DIM, int K, int MODE, int CWW>
-__global__ void __launch_bounds__(LocalMultiCfg<DIM, K, CWW>::NT)
+__global__ void __launch_bounds__(LocalMultiCfg<DIM, K, CWW>::NT, LocalMultiCfg<DIM, K, CWW>::NT <= 320 ? 3 : 1)
     local_df_multi_kernel(DevMesh mesh, TabsDf T, const df2* __restrict__ geo, const df2* __restrict__ Hinv,
                           double alpha, df2 tau, int R, const double* __restrict__ F, const double* __restrict__ hist,
                           SrcArgs src, const double* __restrict__ lam, double* __restrict__ out) {

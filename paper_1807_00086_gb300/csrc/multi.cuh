@@ -521,14 +521,23 @@ __device__ __forceinline__ void block_cols(double v, int R, double* red /*[256]*
 }
 
 // Per-column sums of block partials part[(b0 + b) * R + j] (b < nb) by the whole block (256
-// threads, R a power of two <= 256): 256 / R threads per column, fixed partition and tree,
-// so the sums are deterministic; column j's sum is left in red[j].
+// threads, R a power of two <= 256): 256 / R threads per column, each with four accumulators
+// (so four independent loads are in flight: one dependent chain of nb / G loads made the
+// single-block scalar kernels latency-bound), fixed partition, order and tree, so the sums are
+// deterministic; column j's sum is left in red[j].
 __device__ __forceinline__ void col_partials(const double* __restrict__ part, int nb, int R, int64_t b0,
                                              double* red /*[256]*/) {
   const int G = 256 / R, j = threadIdx.x & (R - 1), g = threadIdx.x / R;
-  double s = 0.0;
-  for (int b = g; b < nb; b += G) s += part[(b0 + b) * R + j];
-  block_cols(s, R, red);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int b = g;
+  for (; b + 3 * G < nb; b += 4 * G) {
+    s0 += part[(b0 + b) * R + j];
+    s1 += part[(b0 + b + G) * R + j];
+    s2 += part[(b0 + b + 2 * G) * R + j];
+    s3 += part[(b0 + b + 3 * G) * R + j];
+  }
+  for (; b < nb; b += G) s0 += part[(b0 + b) * R + j];
+  block_cols((s0 + s1) + (s2 + s3), R, red);
 }
 
 // Per-column least-squares initial guess over stored pairs (b_i, lam_i), i < q, ring
@@ -718,6 +727,498 @@ __global__ void __launch_bounds__(256) mdirection_kernel(int64_t n, int R, const
   for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n; t += (int64_t)gridDim.x * 256) p[t] = z[t] + be * p[t];
 }
 
+// ---- column-block Krylov kernels with NV columns per thread (R a multiple of NV)
+// Vectors are read NV columns at a time (float4 for the FP32 inner solve, double2 for the FP64
+// refinement residual): thread t holds entry t >> lg and columns NV (t & (R/NV - 1)) + 0..NV-1.
+// The grid stride (gridDim.x * 256 vector elements) is a multiple of R/NV (R/NV <= 64 divides
+// 256), so a thread keeps its columns, and several independent vector loads per trip keep
+// enough bytes in flight per SM to stream at HBM rate (one 4-byte load per thread and trip
+// does not). In the FP32 inner solve z = D^{-1} r is not stored: the direction kernel forms it
+// again from r, with the same rounding as the one-column-per-thread kernels that store it.
+
+// per-column block sums of NV values per thread (thread t: columns NV (t mod R/NV) + c), written
+// to part[row][R]; fixed partition and tree, so the sums are deterministic
+template <int NV>
+__device__ __forceinline__ void block_cols_v(const double (&v)[NV], int R, double* red /*[256]*/,
+                                             double* __restrict__ part, int64_t row) {
+  const int RV = R / NV;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    block_cols(v[c], RV, red);
+    if (threadIdx.x < RV) part[row * R + NV * threadIdx.x + c] = red[threadIdx.x];
+  }
+}
+
+// q = (-K) p from the two slots of each interior entry; partial p.q per column. The reducing
+// kernels of this family are bounded to 64 registers, so four 256-thread CTAs are resident per
+// SM and the reduction grid (a multiple of the SM count) runs in whole waves.
+template <int DIM, int K>
+__global__ void __launch_bounds__(256, 4) mface_q4_kernel(int nf, int R, const int2* __restrict__ face_slot2,
+                                                       const int32_t* __restrict__ face_bnd,
+                                                       const float4* __restrict__ slot, const float4* __restrict__ p,
+                                                       float4* __restrict__ q, double* __restrict__ part,
+                                                       const int* __restrict__ done) {
+  constexpr int NF = Dims<DIM, K>::NF, U = 4;
+  if (*done) return;
+  __shared__ double red[256];
+  const int R4 = R >> 2, lg = __ffs(R4) - 1, jq = threadIdx.x & (R4 - 1);
+  const int64_t n4 = (int64_t)nf * NF * R4, S = (int64_t)gridDim.x * 256;
+  Acc2 acc[4];
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n4; t += U * S) {
+    float4 s0[U], s1[U], pv[U];
+    bool in[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      in[u] = false;
+      s0[u] = s1[u] = pv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (tu < n4) {
+        const uint32_t fe = (uint32_t)(tu >> lg);
+        const uint32_t f = fe / NF;
+        const int mm = (int)(fe - f * NF);
+        const int fb = face_bnd[f];
+        const int2 fs = face_slot2[f];
+        pv[u] = p[tu];
+        if (fb < 0) {
+          in[u] = true;
+          s0[u] = slot[((int64_t)fs.x * NF + mm) * R4 + jq];
+          s1[u] = slot[((int64_t)fs.y * NF + mm) * R4 + jq];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      if (tu >= n4) break;
+      float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (in[u]) qv = make_float4(-(s0[u].x + s1[u].x), -(s0[u].y + s1[u].y), -(s0[u].z + s1[u].z), -(s0[u].w + s1[u].w));
+      q[tu] = qv;
+      acc[0].dot(pv[u].x, qv.x); acc[1].dot(pv[u].y, qv.y); acc[2].dot(pv[u].z, qv.z); acc[3].dot(pv[u].w, qv.w);
+    }
+  }
+  const double v[4] = {acc[0].value(), acc[1].value(), acc[2].value(), acc[3].value()};
+  block_cols_v<4>(v, R, red, part, blockIdx.x);
+}
+
+// x += alpha p, r -= alpha q; partials (r, D^{-1} r) and (r, r) per column (z is not stored)
+static __global__ void __launch_bounds__(256, 4) mupdate4_kernel(int64_t n4, int R, const float4* __restrict__ p,
+                                                              const float4* __restrict__ q, const float* __restrict__ dinv,
+                                                              float4* __restrict__ x, float4* __restrict__ r,
+                                                              double* __restrict__ part, MScal sc) {
+  constexpr int U = 2;
+  if (*sc.done) return;
+  __shared__ double red[256];
+  const int R4 = R >> 2, lg = __ffs(R4) - 1, jq = threadIdx.x & (R4 - 1);
+  const int64_t S = (int64_t)gridDim.x * 256;
+  float al[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) al[c] = (float)sc.alpha[4 * jq + c];
+  Acc2 rz[4], rr[4];
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n4; t += U * S) {
+    float4 pv[U], qv[U], xv[U], rv[U];
+    float d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      if (tu < n4) { pv[u] = p[tu]; qv[u] = q[tu]; xv[u] = x[tu]; rv[u] = r[tu]; d[u] = dinv[tu >> lg]; }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      if (tu >= n4) break;
+      x[tu] = make_float4(fmaf(al[0], pv[u].x, xv[u].x), fmaf(al[1], pv[u].y, xv[u].y), fmaf(al[2], pv[u].z, xv[u].z),
+                          fmaf(al[3], pv[u].w, xv[u].w));
+      const float4 rn = make_float4(fmaf(-al[0], qv[u].x, rv[u].x), fmaf(-al[1], qv[u].y, rv[u].y),
+                                    fmaf(-al[2], qv[u].z, rv[u].z), fmaf(-al[3], qv[u].w, rv[u].w));
+      r[tu] = rn;
+      rz[0].dot(rn.x, __fmul_rn(d[u], rn.x)); rr[0].dot(rn.x, rn.x);
+      rz[1].dot(rn.y, __fmul_rn(d[u], rn.y)); rr[1].dot(rn.y, rn.y);
+      rz[2].dot(rn.z, __fmul_rn(d[u], rn.z)); rr[2].dot(rn.z, rn.z);
+      rz[3].dot(rn.w, __fmul_rn(d[u], rn.w)); rr[3].dot(rn.w, rn.w);
+    }
+  }
+  const double vz[4] = {rz[0].value(), rz[1].value(), rz[2].value(), rz[3].value()};
+  block_cols_v<4>(vz, R, red, part, blockIdx.x);
+  const double vr[4] = {rr[0].value(), rr[1].value(), rr[2].value(), rr[3].value()};
+  block_cols_v<4>(vr, R, red, part, (int64_t)gridDim.x + blockIdx.x);
+}
+
+// Persistent form of apply_tc_kernel for exactly NC = R columns (32 or 64) inside the FP32
+// Krylov iteration, with the iteration's p.q and step length in its epilogue. With
+// K = sum_K P_K^T S_K P_K and q = -K p, (p, q)_j = -sum_K sum_r X_K[r][j] (S_K X_K)[r][j] (the
+// gathered block is zero on boundary faces), so the face pass that formed q before alpha is not
+// needed: the update kernel forms q from the two slots of each entry itself.
+// Each CTA loops over groups of WPB elements (one per warp) with two stages per warp: after
+// the A fragments of the current group are in registers, the packed S_K of the next group
+// (all threads) and each warp's next trace block are copied by cp.async while the current
+// block is multiplied. Per-lane p.q partials (columns 8 g + 2 tq, + 1 of n-tile g) are summed
+// over the warp's rows by shuffles, over the CTA's warps in warp order, and the last CTA to
+// finish (ticket counter, no waiting) sums the CTA partials in index order and writes
+// alpha_j = rho_j / (p, q)_j (0 for converged columns).
+template <int DIM, int K>
+struct ApplyTcPCfg {
+  using C = ApplyTcCfg<DIM, K>;
+  static constexpr int WPB = 4;
+  static constexpr int XB = C::KS * 8 * C::XS;   // floats of one staged trace block
+  static constexpr size_t SMEM = (size_t)WPB * C::P4 * 16 + (size_t)2 * WPB * XB * 4 + (size_t)WPB * 64 * 8;
+};
+
+struct MPqOut {
+  double* part;       // [gridDim.x][R] CTA partials of (p, q) per column
+  unsigned* ticket;   // zero between launches
+  MScal sc;           // alpha is written by the last CTA
+  int parity;         // selects rho0 / rho1 as mcols_alpha does
+};
+
+template <int DIM, int K, int NC>
+__global__ void __launch_bounds__(32 * ApplyTcPCfg<DIM, K>::WPB) apply_tc_pq_kernel(
+    int64_t ne, const int32_t* __restrict__ elem_face, const int32_t* __restrict__ face_bnd,
+    const float4* __restrict__ S32m, const float* __restrict__ x, float* __restrict__ slot, MPqOut o) {
+  using C = ApplyTcCfg<DIM, K>;
+  using CP = ApplyTcPCfg<DIM, K>;
+  using Dm = Dims<DIM, K>;
+  constexpr int M = C::M, NF = Dm::NF, NFC = Dm::NFC, P4 = C::P4, MT = C::MT, KS = C::KS, WPB = CP::WPB,
+                XS = C::XS, XB = CP::XB, R = NC;
+  constexpr int Q = NC / 4, NLD = KS * 8 * Q, LPL = (NLD + 31) / 32;   // float4 copies of X: total, per lane
+  static_assert(NC == 32 || NC == 64, "one n-tile of 8 columns per lane group g");
+  if (*o.sc.done) return;
+  extern __shared__ float4 smem4[];
+  float* sS = reinterpret_cast<float*>(smem4);                       // [WPB][P4 * 4] packed S_K
+  float* sX = sS + WPB * P4 * 4;                                     // [2][WPB][XB] trace blocks
+  double* sPq = reinterpret_cast<double*>(sX + 2 * WPB * XB);         // [WPB][NC]
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int64_t nq = (ne + WPB - 1) / WPB;
+  const unsigned ss = (unsigned)__cvta_generic_to_shared(sS);
+  // copies of group qd: the packed S_K of its elements (all threads) and warp w's trace block
+  // (rows of boundary faces and rows M..KS*8 zero-filled: source size 0 reads no memory)
+  auto stage = [&](int64_t qd, int b) {
+    const int64_t e0 = qd * WPB;
+    const int nel = (int)((ne - e0) < WPB ? (ne - e0) : WPB);
+    for (int t = threadIdx.x; t < nel * P4; t += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(ss + 16u * (unsigned)t), "l"(S32m + e0 * P4 + t)
+                   : "memory");
+    const bool act = w < nel;
+    int64_t fo = -1;
+    if (act && lane < NFC) {
+      const int f = elem_face[(e0 + w) * NFC + lane];
+      fo = face_bnd[f] < 0 ? (int64_t)f * NF * R : -1;
+    }
+    const unsigned xs = (unsigned)__cvta_generic_to_shared(sX + ((size_t)b * WPB + w) * XB);
+#pragma unroll 4
+    for (int i = 0; i < LPL; ++i) {
+      const int t = lane + 32 * i;
+      const int r = (t < NLD ? t : 0) / Q, q = t % Q;
+      const int64_t off = __shfl_sync(0xffffffffu, fo, (r < M ? r : 0) / NF);
+      if (t < NLD) {
+        const bool rd = act && r < M && off >= 0;
+        const float* src = rd ? x + off + (int64_t)(r % NF) * R + 4 * q : x;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(xs + 4u * (unsigned)(r * XS + 4 * q)),
+                     "l"(src), "r"(rd ? 16 : 0)
+                     : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  double pq0 = 0.0, pq1 = 0.0;   // lanes of n-tile g: columns 8 g + 2 tq and 8 g + 2 tq + 1
+  int b = 0;
+  if ((int64_t)blockIdx.x < nq) stage(blockIdx.x, 0);
+  for (int64_t qd = blockIdx.x; qd < nq; qd += gridDim.x, b ^= 1) {
+    const int64_t e0 = qd * WPB;
+    const int nel = (int)((ne - e0) < WPB ? (ne - e0) : WPB);
+    const bool act = w < nel;
+    const int64_t e = e0 + (act ? w : 0);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");   // this group's copies (the only ones in flight)
+    __syncthreads();                                          // S_K copied by all threads is visible
+    uint32_t a[MT][KS][4];
+    if (act) {
+      const float* Se = sS + w * P4 * 4;
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const int r = mt * 16 + g + (h & 1) * 8, cc = ks * 8 + tq + (h >> 1) * 4;
+            float sv = 0.f;
+            if (r < M && cc < M) sv = Se[r <= cc ? packed_index(M, r, cc) : packed_index(M, cc, r)];
+            a[mt][ks][h] = to_tf32(sv);
+          }
+    }
+    __syncthreads();   // every warp holds its A fragments: the S_K stage may be refilled
+    if (qd + gridDim.x < nq) stage(qd + gridDim.x, b ^ 1);
+    if (!act) continue;
+    const float* Xe = sX + ((size_t)b * WPB + w) * XB;
+#pragma unroll 2
+    for (int nt = 0; nt < NC / 8; ++nt) {
+      float acc[MT][4];
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) acc[mt][0] = acc[mt][1] = acc[mt][2] = acc[mt][3] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const float x0 = Xe[(ks * 8 + tq) * XS + nt * 8 + g];
+        const float x1 = Xe[(ks * 8 + tq + 4) * XS + nt * 8 + g];
+        const uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1);
+        const uint32_t l0 = to_tf32(x0 - __uint_as_float(h0)), l1 = to_tf32(x1 - __uint_as_float(h1));
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+          mma_tf32(acc[mt], a[mt][ks], h0, h1);
+          mma_tf32(acc[mt], a[mt][ks], l0, l1);
+        }
+      }
+      const int col = nt * 8 + 2 * tq;
+      float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt) {
+        const int r0 = mt * 16 + g, r1 = r0 + 8;
+        if (r0 < M) {
+          *reinterpret_cast<float2*>(slot + (e * M + r0) * R + col) = make_float2(acc[mt][0], acc[mt][1]);
+          v0 = fmaf(Xe[r0 * XS + col], acc[mt][0], v0);
+          v1 = fmaf(Xe[r0 * XS + col + 1], acc[mt][1], v1);
+        }
+        if (r1 < M) {
+          *reinterpret_cast<float2*>(slot + (e * M + r1) * R + col) = make_float2(acc[mt][2], acc[mt][3]);
+          v0 = fmaf(Xe[r1 * XS + col], acc[mt][2], v0);
+          v1 = fmaf(Xe[r1 * XS + col + 1], acc[mt][3], v1);
+        }
+      }
+      // rows of the 8 lanes with this tq (g = 0..7)
+      v0 += __shfl_xor_sync(0xffffffffu, v0, 4);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 4);
+      v0 += __shfl_xor_sync(0xffffffffu, v0, 8);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 8);
+      v0 += __shfl_xor_sync(0xffffffffu, v0, 16);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, 16);
+      if (g == nt) { pq0 += (double)v0; pq1 += (double)v1; }
+    }
+  }
+  // CTA partial per column (warps in order), then the last CTA's column sums in CTA order
+  if (g < NC / 8) {
+    sPq[w * NC + 8 * g + 2 * tq] = pq0;
+    sPq[w * NC + 8 * g + 2 * tq + 1] = pq1;
+  }
+  __syncthreads();
+  if (threadIdx.x < NC) {
+    double v = 0.0;
+#pragma unroll
+    for (int w2 = 0; w2 < WPB; ++w2) v += sPq[w2 * NC + threadIdx.x];
+    o.part[(int64_t)blockIdx.x * NC + threadIdx.x] = v;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(o.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  {
+    // column j = t mod NC; the blockDim / NC threads of a column take every (blockDim / NC)-th CTA
+    constexpr int G = 32 * WPB / NC;
+    const int j = threadIdx.x % NC, h = threadIdx.x / NC;
+    double v = 0.0;
+    for (unsigned bk = h; bk < gridDim.x; bk += G) v += __ldcg(o.part + (int64_t)bk * NC + j);
+    __syncthreads();
+    sPq[h * NC + j] = v;
+    __syncthreads();
+    if (threadIdx.x < NC) {
+      double sum = 0.0;
+#pragma unroll
+      for (int h2 = 0; h2 < G; ++h2) sum += sPq[h2 * NC + j];
+      const double pq = -sum;
+      const double rho = o.parity ? o.sc.rho1[j] : o.sc.rho0[j];
+      o.sc.alpha[j] = (o.sc.conv[j] || pq == 0.0) ? 0.0 : rho / pq;
+    }
+    if (threadIdx.x == 0) *o.ticket = 0u;
+  }
+}
+
+// mupdate4_kernel with q = -K p formed from the two slots of each interior entry (after
+// apply_tc_pq_kernel, which leaves no q vector)
+template <int DIM, int K>
+__global__ void __launch_bounds__(256, 4) mupdate4s_kernel(int nf, int R, const int2* __restrict__ face_slot2,
+                                                        const int32_t* __restrict__ face_bnd,
+                                                        const float4* __restrict__ slot, const float4* __restrict__ p,
+                                                        const float* __restrict__ dinv, float4* __restrict__ x,
+                                                        float4* __restrict__ r, double* __restrict__ part, MScal sc) {
+  constexpr int NF = Dims<DIM, K>::NF, U = 2;
+  if (*sc.done) return;
+  __shared__ double red[256];
+  const int R4 = R >> 2, lg = __ffs(R4) - 1, jq = threadIdx.x & (R4 - 1);
+  const int64_t n4 = (int64_t)nf * NF * R4, S = (int64_t)gridDim.x * 256;
+  float al[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) al[c] = (float)sc.alpha[4 * jq + c];
+  Acc2 rz[4], rr[4];
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n4; t += U * S) {
+    float4 pv[U], s0[U], s1[U], xv[U], rv[U];
+    float d[U];
+    bool in[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      in[u] = false;
+      s0[u] = s1[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (tu < n4) {
+        const uint32_t fe = (uint32_t)(tu >> lg);
+        const uint32_t f = fe / NF;
+        const int mm = (int)(fe - f * NF);
+        const int fb = face_bnd[f];
+        const int2 fs = face_slot2[f];
+        pv[u] = p[tu]; xv[u] = x[tu]; rv[u] = r[tu]; d[u] = dinv[fe];
+        if (fb < 0) {
+          in[u] = true;
+          s0[u] = slot[((int64_t)fs.x * NF + mm) * R4 + jq];
+          s1[u] = slot[((int64_t)fs.y * NF + mm) * R4 + jq];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      if (tu >= n4) break;
+      float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (in[u]) qv = make_float4(-(s0[u].x + s1[u].x), -(s0[u].y + s1[u].y), -(s0[u].z + s1[u].z), -(s0[u].w + s1[u].w));
+      x[tu] = make_float4(fmaf(al[0], pv[u].x, xv[u].x), fmaf(al[1], pv[u].y, xv[u].y), fmaf(al[2], pv[u].z, xv[u].z),
+                          fmaf(al[3], pv[u].w, xv[u].w));
+      const float4 rn = make_float4(fmaf(-al[0], qv.x, rv[u].x), fmaf(-al[1], qv.y, rv[u].y), fmaf(-al[2], qv.z, rv[u].z),
+                                    fmaf(-al[3], qv.w, rv[u].w));
+      r[tu] = rn;
+      rz[0].dot(rn.x, __fmul_rn(d[u], rn.x)); rr[0].dot(rn.x, rn.x);
+      rz[1].dot(rn.y, __fmul_rn(d[u], rn.y)); rr[1].dot(rn.y, rn.y);
+      rz[2].dot(rn.z, __fmul_rn(d[u], rn.z)); rr[2].dot(rn.z, rn.z);
+      rz[3].dot(rn.w, __fmul_rn(d[u], rn.w)); rr[3].dot(rn.w, rn.w);
+    }
+  }
+  const double vz[4] = {rz[0].value(), rz[1].value(), rz[2].value(), rz[3].value()};
+  block_cols_v<4>(vz, R, red, part, blockIdx.x);
+  const double vr[4] = {rr[0].value(), rr[1].value(), rr[2].value(), rr[3].value()};
+  block_cols_v<4>(vr, R, red, part, (int64_t)gridDim.x + blockIdx.x);
+}
+
+// p = D^{-1} r + beta p
+static __global__ void __launch_bounds__(256) mdirection4_kernel(int64_t n4, int R, const float4* __restrict__ r,
+                                                                 const float* __restrict__ dinv, float4* __restrict__ p,
+                                                                 const double* __restrict__ beta,
+                                                                 const int* __restrict__ done) {
+  constexpr int U = 4;
+  if (*done) return;
+  const int R4 = R >> 2, lg = __ffs(R4) - 1, jq = threadIdx.x & (R4 - 1);
+  const int64_t S = (int64_t)gridDim.x * 256;
+  float be[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) be[c] = (float)beta[4 * jq + c];
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n4; t += U * S) {
+    float4 rv[U], pv[U];
+    float d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      if (tu < n4) { rv[u] = r[tu]; pv[u] = p[tu]; d[u] = dinv[tu >> lg]; }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      if (tu >= n4) break;
+      p[tu] = make_float4(fmaf(be[0], pv[u].x, __fmul_rn(d[u], rv[u].x)), fmaf(be[1], pv[u].y, __fmul_rn(d[u], rv[u].y)),
+                          fmaf(be[2], pv[u].z, __fmul_rn(d[u], rv[u].z)), fmaf(be[3], pv[u].w, __fmul_rn(d[u], rv[u].w)));
+    }
+  }
+}
+
+// FP64 refinement residual, two columns per thread: rho = b + sum of the two slots (interior
+// entries), partials |rho|^2 and |b|^2 per column
+template <int DIM, int K>
+__global__ void __launch_bounds__(256) mrefine_residual2_kernel(int nf, int R, const int2* __restrict__ face_slot2,
+                                                                const int32_t* __restrict__ face_bnd,
+                                                                const double2* __restrict__ slot,
+                                                                const double2* __restrict__ b, double2* __restrict__ res,
+                                                                double* __restrict__ part) {
+  constexpr int NF = Dims<DIM, K>::NF, U = 4;
+  __shared__ double red[256];
+  const int R2 = R >> 1, lg = __ffs(R2) - 1, jh = threadIdx.x & (R2 - 1);
+  const int64_t n2 = (int64_t)nf * NF * R2, S = (int64_t)gridDim.x * 256;
+  double rr[2] = {0.0, 0.0}, bb[2] = {0.0, 0.0};
+  for (int64_t t = blockIdx.x * 256 + threadIdx.x; t < n2; t += U * S) {
+    double2 bv[U], s0[U], s1[U];
+    bool in[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      in[u] = false;
+      bv[u] = s0[u] = s1[u] = make_double2(0.0, 0.0);
+      if (tu < n2) {
+        const uint32_t fe = (uint32_t)(tu >> lg);
+        const uint32_t f = fe / NF;
+        const int mm = (int)(fe - f * NF);
+        const int fb = face_bnd[f];
+        const int2 fs = face_slot2[f];
+        if (fb < 0) {
+          in[u] = true;
+          bv[u] = b[tu];
+          s0[u] = slot[((int64_t)fs.x * NF + mm) * R2 + jh];
+          s1[u] = slot[((int64_t)fs.y * NF + mm) * R2 + jh];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * S;
+      if (tu >= n2) break;
+      double2 v = make_double2(0.0, 0.0);
+      if (in[u]) {
+        v = make_double2(bv[u].x + s0[u].x + s1[u].x, bv[u].y + s0[u].y + s1[u].y);
+        bb[0] += bv[u].x * bv[u].x;
+        bb[1] += bv[u].y * bv[u].y;
+      }
+      res[tu] = v;
+      rr[0] += v.x * v.x;
+      rr[1] += v.y * v.y;
+    }
+  }
+  block_cols_v<2>(rr, R, red, part, blockIdx.x);
+  block_cols_v<2>(bb, R, red, part, (int64_t)gridDim.x + blockIdx.x);
+}
+
+// inner right-hand side of a sweep, four columns per thread: b32 = fl32(rho * scale_j)
+static __global__ void mto32_scaled4_kernel(int64_t n4, int R, const double2* __restrict__ res,
+                                            const double* __restrict__ scale, float4* __restrict__ b32) {
+  const int R4 = R >> 2, jq = threadIdx.x & (R4 - 1);
+  double s[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) s[c] = scale[4 * jq + c];
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = res[2 * t], b = res[2 * t + 1];
+    b32[t] = make_float4((float)(a.x * s[0]), (float)(a.y * s[1]), (float)(b.x * s[2]), (float)(b.y * s[3]));
+  }
+}
+
+// lam += delta |rho|_j (|rho|_j = 1 / scale_j) on interior entries of the columns still refined
+// (scale_j != 0), four columns per thread. The reciprocal is taken once per thread: an FP64
+// division per entry made this kernel FP64-ALU-bound (8x its streaming time).
+static __global__ void mrefine_update4_kernel(int64_t n4, int R, int NF, const int32_t* __restrict__ face_bnd,
+                                              const float4* __restrict__ delta, const double* __restrict__ scale,
+                                              double2* __restrict__ lam) {
+  const int R4 = R >> 2, lg = __ffs(R4) - 1, jq = threadIdx.x & (R4 - 1);
+  double s[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double sc = scale[4 * jq + c];
+    s[c] = sc != 0.0 ? 1.0 / sc : 0.0;
+  }
+  if (s[0] == 0.0 && s[1] == 0.0 && s[2] == 0.0 && s[3] == 0.0) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += (int64_t)gridDim.x * blockDim.x) {
+    if (face_bnd[(uint32_t)(t >> lg) / (uint32_t)NF] >= 0) continue;
+    const float4 d = delta[t];
+    double2 a = lam[2 * t], b = lam[2 * t + 1];
+    if (s[0] != 0.0) a.x += (double)d.x * s[0];
+    if (s[1] != 0.0) a.y += (double)d.y * s[1];
+    if (s[2] != 0.0) b.x += (double)d.z * s[2];
+    if (s[3] != 0.0) b.y += (double)d.w * s[3];
+    lam[2 * t] = a;
+    lam[2 * t + 1] = b;
+  }
+}
+
 // PCG start: r = b - (-K) x0 (x0 given; slot holds S x0 or zero), z = Dinv r, p = z; partials rz, rr, bb
 template <int DIM, int K, typename TV>
 __global__ void __launch_bounds__(256) minit_kernel(int nf, int R, const int32_t* __restrict__ face_slot,
@@ -851,11 +1352,13 @@ static __global__ void mto32_scaled_kernel(int64_t n, int R, const double* __res
 static __global__ void mrefine_update_kernel(int64_t n, int R, int NF, const int32_t* __restrict__ face_bnd,
                                       const float* __restrict__ delta, const double* __restrict__ scale,
                                       double* __restrict__ lam) {
+  // the grid stride (a multiple of 256) is a multiple of R: a thread keeps its column j
   const int lg = __ffs(R) - 1;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-    const double s = scale[t & (R - 1)];
-    if (s != 0.0 && face_bnd[(uint32_t)(t >> lg) / (uint32_t)NF] < 0) lam[t] += (double)delta[t] / s;
-  }
+  const double sc = scale[(blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & (R - 1)];
+  if (sc == 0.0) return;
+  const double inv = 1.0 / sc;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    if (face_bnd[(uint32_t)(t >> lg) / (uint32_t)NF] < 0) lam[t] += (double)delta[t] * inv;
 }
 
 // boundary entries of lam (all columns) <- coef[b] * fac

@@ -33,11 +33,13 @@ def _setup(prec, R, dim=3, N=2, k=2, seed=3):
     return s, prob, pos, u0
 
 
-@pytest.mark.parametrize("R", [2, 4, 32, 64])
+@pytest.mark.parametrize("R", [2, 4, 8, 32, 64])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 1e-9)])
 def test_multi_source_batch_matches_single_column_oracle(prec, tol, R):
     """R < 32 runs the narrow kernels (several elements per warp), R = 32 the wide ones with
-    one column group, R = 64 (the multi-source workload's width) two column groups."""
+    one column group, R = 64 (the multi-source workload's width) two column groups. In the
+    mixed path R = 2 keeps the one-column-per-thread Krylov vector kernels and R = 4, 8, 32, 64
+    take the four-columns-per-thread ones (R = 4: one column group per thread)."""
     dt, nsteps = 2e-3, 3
     s, prob, pos, u0 = _setup(prec, R)
     amps = np.linspace(1.0, 2.0, R)
