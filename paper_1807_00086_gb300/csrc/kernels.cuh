@@ -1188,16 +1188,40 @@ static __global__ void cg32_update_kernel(int64_t n4, int nb, int parity, const 
 // is folded in): q = sgn (slot0 + slot1) on interior faces (0 on the boundary),
 // x += alpha p, r -= alpha q, z = Dinv r; partials (r.z, r.r). alpha = rho / pq with pq
 // from the apply's reduction. Vectors are processed as float4 (coalesced); the two slot
-// values of each entry are gathered per entry (runs of NF consecutive floats).
+// values of each entry are gathered per entry (runs of NF consecutive floats). Two float4
+// per trip, and the face flags and slot pairs loaded before the branch on them, keep two
+// independent load chains in flight per thread; a thread visits its entries in the same order
+// as with one float4 per trip, so the sums are the same.
 template <class LD>
-__device__ __forceinline__ float q_entry(int64_t d, int64_t nfe, float sgn, const int32_t* __restrict__ face_slot,
-                                         const int32_t* __restrict__ face_bnd, const float* __restrict__ slot) {
+__device__ __forceinline__ float4 q_entries4(int64_t t, int64_t nfe, float sgn, const int2* __restrict__ face_slot2,
+                                             const int32_t* __restrict__ face_bnd, const float* __restrict__ slot) {
   constexpr int NF = LD::NF;
-  if (d >= nfe) return 0.f;
-  const int f = (int)(d / NF);
-  const int mm = (int)(d - (int64_t)f * NF);
-  if (face_bnd[f] >= 0) return 0.f;
-  return sgn * (slot[(int64_t)face_slot[2 * f] * NF + mm] + slot[(int64_t)face_slot[2 * f + 1] * NF + mm]);
+  const int64_t d0 = 4 * t;
+  uint32_t f = (uint32_t)(d0 / NF);   // n_faces * NF < 2^32
+  int mm = (int)(d0 - (int64_t)f * NF);
+  uint32_t fi[4];
+  int mi[4], fb[4];
+  int2 fs[4];
+  bool ok[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    fi[i] = f;
+    mi[i] = mm;
+    if (++mm == NF) { mm = 0; ++f; }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    ok[i] = d0 + i < nfe;
+    fb[i] = ok[i] ? face_bnd[fi[i]] : 0;
+    fs[i] = ok[i] ? face_slot2[fi[i]] : make_int2(0, 0);
+  }
+  float q[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    q[i] = (ok[i] && fb[i] < 0)
+               ? sgn * (slot[(int64_t)fs[i].x * NF + mi[i]] + slot[(int64_t)fs[i].y * NF + mi[i]])
+               : 0.f;
+  return make_float4(q[0], q[1], q[2], q[3]);
 }
 
 template <class LD>
@@ -1210,25 +1234,35 @@ __global__ void __launch_bounds__(256) cg32_update_f_kernel(int64_t n4, int64_t 
                                                             float4* __restrict__ r, float4* __restrict__ z,
                                                             const double* __restrict__ pq_in,
                                                             double* __restrict__ part, const CgScal* __restrict__ sc) {
+  constexpr int U = 2;
   if (sc->done) return;
   __shared__ double red[8];
   const float al = (float)(sc->rho[parity] / *pq_in);
+  const int2* face_slot2 = reinterpret_cast<const int2*>(face_slot);
   Acc2 rz, rr;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += stride) {
-    const float4 pv = p[t], xv = x[t], rv = r[t], dv = dinv[t];
-    float4 qv;
-    qv.x = q_entry<LD>(4 * t + 0, nfe, sgn, face_slot, face_bnd, slot);
-    qv.y = q_entry<LD>(4 * t + 1, nfe, sgn, face_slot, face_bnd, slot);
-    qv.z = q_entry<LD>(4 * t + 2, nfe, sgn, face_slot, face_bnd, slot);
-    qv.w = q_entry<LD>(4 * t + 3, nfe, sgn, face_slot, face_bnd, slot);
-    x[t] = f4fma(al, pv, xv);
-    const float4 rn = f4fma(-al, qv, rv);
-    const float4 zn = f4mul(dv, rn);
-    r[t] = rn;
-    z[t] = zn;
-    rz.dot4(rn, zn);
-    rr.dot4(rn, rn);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n4; t += U * stride) {
+    float4 pv[U], xv[U], rv[U], dv[U], qv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * stride;
+      if (tu < n4) {
+        pv[u] = p[tu]; xv[u] = x[tu]; rv[u] = r[tu]; dv[u] = dinv[tu];
+        qv[u] = q_entries4<LD>(tu, nfe, sgn, face_slot2, face_bnd, slot);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t tu = t + u * stride;
+      if (tu >= n4) break;
+      x[tu] = f4fma(al, pv[u], xv[u]);
+      const float4 rn = f4fma(-al, qv[u], rv[u]);
+      const float4 zn = f4mul(dv[u], rn);
+      r[tu] = rn;
+      z[tu] = zn;
+      rz.dot4(rn, zn);
+      rr.dot4(rn, rn);
+    }
   }
   double s;
   s = block_sum256(rz.value(), red); if (threadIdx.x == 0) part[blockIdx.x * 2 + 0] = s;
