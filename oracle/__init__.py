@@ -18,6 +18,7 @@ Module map
                 (Sec. 2.3, Eqs. 9b and 10), monolithic brute force, energy identity.
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py against
-closed forms, brute force or invariants, except the conventions listed as
-"parity unpinned" in acoustic.py (Ricker wavelet parameters, point-source tie-break).
+closed forms, brute force or invariants. The workload conventions (Ricker wavelet, point-source
+element, the elastic Gaussian-bump initial data) are stated in acoustic.py and elastic.py;
+the first two are pinned too.
 """

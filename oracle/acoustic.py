@@ -31,8 +31,10 @@ the same ones, written independently):
     physical mass matrix is |det J| I);
   * element trace unknowns are ordered [face 0, ..., face d], N_f coefficients each;
   * quadrature uses n = k + 2 collapsed Gauss points per direction (degree 2k + 3).
-Parity unpinned: the Ricker wavelet and the point-source tie-break (lowest element id
-among elements containing the point) are conventions, not results.
+The Ricker wavelet (pinned as the normalised second derivative of a Gaussian) and the
+point-source element (the lowest id among elements containing the point, pinned by a brute-force
+barycentric search) are conventions of the workload, not results of the method; both are
+pinned by tests in tests/test_oracle_acoustic.py.
 """
 import math
 from dataclasses import dataclass, field

@@ -23,8 +23,8 @@ components: form "F" row-major (i, j); form "sigma" (11, 22, 33, 23, 13, 12) in 
 (11, 22, 12) in 2D. Trace: v_hat per face, d components x N_f, component-major.
 
 All other conventions (basis, faces, quadrature, time marching) are those of
-oracle/acoustic.py. Parity unpinned: the Gaussian-bump initial data of the benchmark
-workload is a convention.
+oracle/acoustic.py. The Gaussian-bump initial data of the benchmark workload is input data
+(the seeded generator module), a convention of the workload and no function of this oracle.
 """
 import math
 from dataclasses import dataclass

@@ -220,6 +220,41 @@ def test_ricker_wavelet_closed_form_points():
     assert abs(ac.ricker(tz, f0, t0)) < 1e-15
 
 
+def test_ricker_wavelet_is_the_normalised_second_derivative_of_a_gaussian():
+    """r(t) = -g''(t) / g''(t0) with g(t) = exp(-pi^2 f0^2 (t - t0)^2): the Ricker wavelet as the
+    scaled negative curvature of a Gaussian pulse, checked by central differences of g."""
+    f0, t0, h = 10.0, 0.12, 1e-5
+    g = lambda t: math.exp(-(math.pi * f0 * (t - t0)) ** 2)
+    d2 = lambda t: (g(t + h) - 2.0 * g(t) + g(t - h)) / (h * h)
+    scale = -d2(t0)
+    for t in np.linspace(0.0, 0.3, 31):
+        assert abs(ac.ricker(t, f0, t0) - (-d2(t) / scale)) < 1e-5
+
+
+def test_point_location_takes_the_lowest_id_element_containing_the_point():
+    """The source element is the lowest id whose closed simplex holds x_s (brute force over
+    barycentric coordinates computed from the vertices, not from the blocks' inverse maps):
+    interior points, points on shared faces and edges, and a vertex shared by many tets."""
+    vert, elem = inputs.unit_cube_tet(2)
+    prob = ac.build_problem(vert, elem, 1, 1.0, np.ones(elem.shape[0]), np.ones(elem.shape[0]))
+
+    def holders(x):
+        out = []
+        for e, tet in enumerate(elem):
+            X = vert[np.sort(tet)]
+            lam = np.linalg.solve(np.vstack([X.T, np.ones(4)]), np.append(x, 1.0))
+            if lam.min() >= -1e-12:
+                out.append(e)
+        return out
+
+    for x in ([0.3, 0.2, 0.1], [0.5, 0.5, 0.5], [0.25, 0.25, 0.5], [0.5, 0.25, 0.25], [0.7, 0.6, 0.2]):
+        h = holders(np.array(x))
+        e, xi = ac.locate(prob, x)
+        assert h and e == min(h)
+        assert len(h) > 1 or x == [0.3, 0.2, 0.1] or x == [0.7, 0.6, 0.2]
+    assert len(holders(np.array([0.5, 0.5, 0.5]))) >= 6
+
+
 def test_point_source_evaluates_polynomials():
     """(delta_xs, w) for w = projection of a P_k polynomial equals the polynomial at xs."""
     prob = _problem(3, 1, 3, dirichlet=False, source=False)
