@@ -117,7 +117,7 @@ typedef struct {
                             /* columns each column has its own fit; hdg_reset_column  */
                             /* drops a column's pairs. 0: the polynomial extrapolation */
                             /* of the last traces (BDF only)                           */
-  int32_t device_loops;     /* nrhs = 1: each trace solve is one CUDA-graph launch whose */
+  int32_t device_loops;     /* each trace solve (any nrhs) is one CUDA-graph launch whose */
                             /* Krylov iterations and refinement sweeps are WHILE loops   */
                             /* with conditions set on the device (no host polling; the   */
                             /* graphs are built at the first solve per buffer pair and   */
