@@ -107,7 +107,9 @@ def plate_tet(n, thickness=0.01):
 
 def acoustic_3d_workload(N=32, k=3, seed=DEFAULT_SEED):
     """3D acoustic wave workload: unit cube, 6 N^3 tets, c ~ logU[1, 3] per element, rho = 1,
-    one Ricker point source at the cube centre shifted by 0.3 h (1, 1, 1) (no vertex/face tie)."""
+    one Ricker point source at the cube centre shifted by 0.3 h (1, 1, 1). The point lies on the
+    main diagonal of its cell, the edge shared by the cell's 6 tets (no mesh vertex); the source
+    goes to the lowest-id tet containing it."""
     vert, elem = unit_cube_tet(N)
     ne = elem.shape[0]
     c = loguniform(ne, 1.0, 3.0, seed)
